@@ -1,0 +1,287 @@
+"""CPU oracle for the extraction path -- TEST INFRASTRUCTURE ONLY.
+
+Plain FP64 statement of what the per-frame extraction computes (paper
+Sections 3.1, 3.2 and 3.4, with the readings [R#] listed in oracle.c).  Only
+tests/, the smoke check and bench.py's CPU-baseline leg import this package;
+the CUDA library never does, and the two share no code.  The loops live in
+oracle.c (compiled with gcc, no fast-math, no FMA contraction); the
+element-wise glue between steps is plain numpy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FLAG_SAT = 1
+FLAG_CENTROID_FALLBACK = 2
+FLAG_TRUNCATED = 4
+FLAG_BAD = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_lib/liboracle.so (single-threaded, -O2,
+    strict IEEE: no fast-math and no FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            d, i, l, u8, u32, vp = C.c_double, C.c_int, C.c_long, C.c_uint8, C.c_uint32, C.c_void_p
+            L.orc_sigma_clip.argtypes = [vp, l, d, i, vp, vp, vp, vp]
+            L.orc_sigma_clip.restype = i
+            L.orc_mode_estimate.argtypes = [d, d, d]
+            L.orc_mode_estimate.restype = d
+            L.orc_box_stats.argtypes = [vp, vp, i, i, i, d, i, vp, vp, vp, vp, vp, vp]
+            L.orc_fill_invalid.argtypes = [vp, vp, vp, i, i]
+            L.orc_median_filter.argtypes = [vp, vp, i, i, i]
+            L.orc_median_filter.restype = i
+            L.orc_spline_at.argtypes = [vp, i, i, i, i, i, vp, vp, l, vp]
+            L.orc_spline_map.argtypes = [vp, i, i, i, i, i, vp]
+            L.orc_filter.argtypes = [vp, i, i, vp, i, i, vp]
+            L.orc_filter.restype = i
+            L.orc_filter_at.argtypes = [vp, i, i, vp, i, i, vp, vp, l, vp]
+            L.orc_filter_at.restype = i
+            L.orc_label.argtypes = [vp, i, i, i, vp]
+            L.orc_label.restype = l
+            L.orc_moments.argtypes = [vp, vp, vp, i, i, l] + [vp] * 16
+            L.orc_moments.restype = l
+            L.orc_overlap_area.argtypes = [d, d, d, d, d]
+            L.orc_overlap_area.restype = d
+            L.orc_apertures.argtypes = [vp, vp, vp, vp, i, i, vp, vp, l, vp, i, d, vp, vp, vp]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+# ---------------------------------------------------------------- pixels ---
+def pixel_values(image, mask=None):
+    """[R1] pixel values as exact doubles and the bad-pixel map (masked or
+    NaN pixels are bad)."""
+    img = np.asarray(image).astype(np.float64)
+    bad = ~np.isfinite(img)
+    if mask is not None:
+        bad |= np.asarray(mask) != 0
+    return np.where(bad, 0.0, img), bad.astype(np.uint8)
+
+
+def saturated(image, saturation):
+    if saturation is None or saturation <= 0:
+        return np.zeros(np.shape(image), np.uint8)
+    a = np.asarray(image).astype(np.float64)
+    return (np.isfinite(a) & (a >= saturation)).astype(np.uint8)
+
+
+# ------------------------------------------------------------ background ---
+def sigma_clip(values, k=3.0, maxiter=10):
+    """[R3] clipped (median, mean, std, nkept, passes) of a 1-D set."""
+    v = _f64(values).copy()
+    med, mean, sd = C.c_double(), C.c_double(), C.c_double()
+    nk = C.c_long()
+    passes = lib().orc_sigma_clip(_p(v), v.size, k, maxiter, C.byref(med), C.byref(mean),
+                                  C.byref(sd), C.byref(nk))
+    return med.value, mean.value, sd.value, nk.value, passes
+
+
+def mode_estimate(med, mean, sd):
+    return lib().orc_mode_estimate(med, mean, sd)
+
+
+def box_stats(img, bad, mesh, k=3.0, maxiter=10):
+    """[R2]-[R4] raw per-box statistics; dict of My x Mx arrays."""
+    img, bad = _f64(img), _u8(bad)
+    H, W = img.shape
+    Mx, My = -(-W // mesh), -(-H // mesh)
+    out = {n: np.zeros((My, Mx)) for n in ("bkg", "rms", "med", "mean")}
+    valid = np.zeros((My, Mx), np.uint8)
+    nk = np.zeros((My, Mx), np.int64)
+    lib().orc_box_stats(_p(img), _p(bad), W, H, mesh, k, maxiter, _p(out["bkg"]), _p(out["rms"]),
+                        _p(valid), _p(out["med"]), _p(out["mean"]), _p(nk))
+    out["valid"] = valid
+    out["nkept"] = nk
+    return out
+
+
+def fill_invalid(bkg, rms, valid):
+    """[R5]"""
+    bkg, rms, valid = _f64(bkg).copy(), _f64(rms).copy(), _u8(valid).copy()
+    My, Mx = bkg.shape
+    lib().orc_fill_invalid(_p(bkg), _p(rms), _p(valid), Mx, My)
+    return bkg, rms
+
+
+def median_filter(mesh, fsize=3):
+    """[R6]"""
+    a = _f64(mesh)
+    out = np.zeros_like(a)
+    My, Mx = a.shape
+    if lib().orc_median_filter(_p(a), _p(out), Mx, My, fsize) != 0:
+        raise ValueError("filter size too large")
+    return out
+
+
+def background_meshes(img, bad, mesh, fsize=3, k=3.0, maxiter=10):
+    """Filtered background and rms meshes ([R2]-[R6])."""
+    st = box_stats(img, bad, mesh, k, maxiter)
+    b, r = fill_invalid(st["bkg"], st["rms"], st["valid"])
+    if fsize > 1:
+        b, r = median_filter(b, fsize), median_filter(r, fsize)
+    return b, r, st
+
+
+def spline_map(mesh_vals, W, H, B):
+    """[R7] full-resolution map from a mesh."""
+    a = _f64(mesh_vals)
+    My, Mx = a.shape
+    out = np.zeros((H, W))
+    lib().orc_spline_map(_p(a), Mx, My, W, H, B, _p(out))
+    return out
+
+
+def spline_at(mesh_vals, W, H, B, xs, ys):
+    """[R7] the map at selected pixel positions."""
+    a = _f64(mesh_vals)
+    My, Mx = a.shape
+    xs, ys = _f64(xs), _f64(ys)
+    out = np.zeros(xs.size)
+    lib().orc_spline_at(_p(a), Mx, My, W, H, B, _p(xs), _p(ys), xs.size, _p(out))
+    return out
+
+
+# ------------------------------------------------------------- detection ---
+def matched_filter(m, kernel):
+    """[R8] F = normalised kernel correlated with m, mirror border."""
+    m, K = _f64(m), _f64(kernel)
+    H, W = m.shape
+    kh, kw = K.shape
+    F = np.zeros_like(m)
+    if lib().orc_filter(_p(m), W, H, _p(K), kw, kh, _p(F)) != 0:
+        raise ValueError("kernel sums to zero")
+    return F
+
+
+def matched_filter_at(m, kernel, xs, ys):
+    m, K = _f64(m), _f64(kernel)
+    H, W = m.shape
+    kh, kw = K.shape
+    xs = np.ascontiguousarray(xs, dtype=np.int64)
+    ys = np.ascontiguousarray(ys, dtype=np.int64)
+    out = np.zeros(xs.size)
+    if lib().orc_filter_at(_p(m), W, H, _p(K), kw, kh, _p(xs), _p(ys), xs.size, _p(out)) != 0:
+        raise ValueError("kernel sums to zero")
+    return out
+
+
+def threshold(F, rms_map, bad, k):
+    """[R10] foreground mask, strict, never on bad pixels."""
+    return ((F > k * rms_map) & (np.asarray(bad) == 0)).astype(np.uint8)
+
+
+def near_threshold(F, rms_map, k, rel=1e-5):
+    """Pixels whose decision is within rel of the threshold (set N)."""
+    t = k * rms_map
+    return np.abs(F - t) <= rel * np.abs(t)
+
+
+def label(fg, minarea=1):
+    """[R11][R12] uint32 segmentation map and number of kept components."""
+    fg = _u8(fg)
+    H, W = fg.shape
+    seg = np.zeros((H, W), np.uint32)
+    n = lib().orc_label(_p(fg), W, H, minarea, _p(seg))
+    return seg, int(n)
+
+
+def moments(seg, m, sat=None):
+    """[R13] catalog dict in ascending label order."""
+    seg = np.ascontiguousarray(seg, dtype=np.uint32)
+    m = _f64(m)
+    H, W = seg.shape
+    sat = _u8(sat) if sat is not None else None
+    ncap = int(np.count_nonzero(seg)) + 1
+    f64 = lambda: np.zeros(ncap)
+    i32 = lambda: np.zeros(ncap, np.int32)
+    cat = dict(label=np.zeros(ncap, np.uint32), npix=np.zeros(ncap, np.int64), flux=f64(),
+               x=f64(), y=f64(), x2=f64(), y2=f64(), xy=f64(), xmin=i32(), xmax=i32(),
+               ymin=i32(), ymax=i32(), peak=f64(), xpeak=i32(), ypeak=i32(),
+               flags=np.zeros(ncap, np.uint32))
+    order = ["label", "npix", "flux", "x", "y", "x2", "y2", "xy", "xmin", "xmax", "ymin", "ymax",
+             "peak", "xpeak", "ypeak", "flags"]
+    n = lib().orc_moments(_p(seg), _p(m), _p(sat), W, H, ncap, *[_p(cat[k]) for k in order])
+    return {k: v[:n] for k, v in cat.items()}
+
+
+# ------------------------------------------------------------- apertures ---
+def overlap_area(x0, x1, y0, y1, r):
+    """[R14] exact area of disc(0, r) n [x0,x1] x [y0,y1]."""
+    return lib().orc_overlap_area(x0, x1, y0, y1, r)
+
+
+def apertures(m, var, bad, sat, xs, ys, radii, gain):
+    """[R14] (flux, fluxerr, flags), each n x nr."""
+    m, var, bad = _f64(m), _f64(var), _u8(bad)
+    sat = _u8(sat) if sat is not None else None
+    H, W = m.shape
+    xs, ys = _f64(xs), _f64(ys)
+    radii = _f64(radii)
+    n, nr = xs.size, radii.size
+    flux = np.zeros((n, nr))
+    err = np.zeros((n, nr))
+    flags = np.zeros((n, nr), np.uint32)
+    lib().orc_apertures(_p(m), _p(var), _p(bad), _p(sat), W, H, _p(xs), _p(ys), n, _p(radii), nr,
+                        float(gain), _p(flux), _p(err), _p(flags))
+    return flux, err, flags
+
+
+# ------------------------------------------------------------ whole path ---
+def extract(image, mesh, kernel, thresh, minarea, radii, gain, mask=None, saturation=0.0,
+            fsize=3, clip_k=3.0, clip_maxiter=10):
+    """The whole per-frame path in the paper's stage order: background and
+    noise map, matched filter, threshold, labelling, moments, apertures at
+    the centroids.  Returns a dict with every intermediate."""
+    img, bad = pixel_values(image, mask)
+    H, W = img.shape
+    bkg_mesh, rms_mesh, st = background_meshes(img, bad, mesh, fsize, clip_k, clip_maxiter)
+    bkg_map = spline_map(bkg_mesh, W, H, mesh)
+    rms_map = spline_map(rms_mesh, W, H, mesh)
+    m = np.where(bad != 0, 0.0, img - bkg_map)
+    F = matched_filter(m, kernel)
+    fg = threshold(F, rms_map, bad, thresh)
+    seg, n = label(fg, minarea)
+    sat = saturated(image, saturation)
+    cat = moments(seg, m, sat)
+    flux, err, apflags = apertures(m, rms_map ** 2, bad, sat, cat["x"], cat["y"], radii, gain)
+    return dict(bkg_mesh=bkg_mesh, rms_mesh=rms_mesh, box=st, bkg_map=bkg_map, rms_map=rms_map,
+                m=m, bad=bad, sat=sat, F=F, fg=fg, seg=seg, cat=cat, flux=flux, fluxerr=err,
+                apflags=apflags, near=near_threshold(F, rms_map, thresh))

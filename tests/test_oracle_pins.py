@@ -1,0 +1,474 @@
+"""Pins of the CPU oracle to things other than itself.
+
+Each test ties one oracle step to a closed form, an invariant, a library
+routine that computes a special case of the same definition, or brute force
+on tiny inputs, so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails here.  No GPU involved.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage
+from scipy.interpolate import CubicSpline
+from scipy.stats import norm
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.txt")
+
+
+def golden():
+    vals = {}
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            name, v = line.split()[:2]
+            vals[name] = float(v)
+    return vals
+
+
+# ------------------------------------------------------------------ CCL ---
+def brute_label(fg, minarea=1):
+    """Independent brute force: relax every pixel to the minimum linear index
+    over its 8-neighbourhood until nothing changes."""
+    H, W = fg.shape
+    lab = np.where(fg, np.arange(H * W).reshape(H, W) + 1, 0).astype(np.int64)
+    big = np.iinfo(np.int64).max
+    while True:
+        p = np.pad(np.where(lab > 0, lab, big), 1, constant_values=big)
+        nb = np.min([p[1 + dy:1 + dy + H, 1 + dx:1 + dx + W] for dy in (-1, 0, 1) for dx in (-1, 0, 1)], axis=0)
+        new = np.where(fg, np.minimum(lab, nb), 0)
+        if np.array_equal(new, lab):
+            break
+        lab = new
+    if minarea > 1:
+        ids, cnt = np.unique(lab[lab > 0], return_counts=True)
+        small = ids[cnt < minarea]
+        lab[np.isin(lab, small)] = 0
+    return lab.astype(np.uint32)
+
+
+def scipy_label_minindex(fg, minarea=1):
+    """scipy.ndimage.label with the 3x3 structure, relabelled by min index."""
+    lab, n = ndimage.label(fg, structure=np.ones((3, 3), int))
+    out = np.zeros(fg.shape, np.uint32)
+    flat = lab.ravel()
+    for k in range(1, n + 1):
+        idx = np.flatnonzero(flat == k)
+        if idx.size >= minarea:
+            out.ravel()[idx] = idx.min() + 1
+    return out
+
+
+def test_label_exhaustive_4x4():
+    """Every one of the 65,536 4x4 masks against brute-force relaxation."""
+    bits = np.arange(65536, dtype=np.uint32)
+    masks = ((bits[:, None] >> np.arange(16, dtype=np.uint32)) & 1).astype(np.uint8).reshape(-1, 4, 4)
+    # brute force vectorised over all masks at once
+    H = W = 4
+    fg = masks.astype(bool)
+    lab = np.where(fg, np.arange(16).reshape(4, 4)[None] + 1, 0).astype(np.int64)
+    big = 1 << 40
+    while True:
+        p = np.pad(np.where(lab > 0, lab, big), ((0, 0), (1, 1), (1, 1)), constant_values=big)
+        nb = np.min([p[:, 1 + dy:1 + dy + H, 1 + dx:1 + dx + W] for dy in (-1, 0, 1) for dx in (-1, 0, 1)], axis=0)
+        new = np.where(fg, np.minimum(lab, nb), 0)
+        if np.array_equal(new, lab):
+            break
+        lab = new
+    for i in range(65536):
+        seg, _ = oracle.label(masks[i], 1)
+        assert np.array_equal(seg, lab[i]), i
+
+
+@pytest.mark.parametrize("density", [0.2, 0.35, 0.41, 0.5, 0.7])
+def test_label_random_vs_scipy(density):
+    rng = np.random.default_rng(int(density * 100))
+    for trial in range(40):
+        h, w = rng.integers(1, 65, 2)
+        fg = (rng.random((h, w)) < density).astype(np.uint8)
+        minarea = int(rng.integers(1, 6))
+        seg, n = oracle.label(fg, minarea)
+        ref = scipy_label_minindex(fg, minarea)
+        assert np.array_equal(seg, ref)
+        assert n == len(np.unique(ref[ref > 0]))
+
+
+def test_label_adversarial_shapes():
+    shapes = []
+    # spiral
+    s = np.zeros((41, 41), np.uint8)
+    x0, y0, x1, y1 = 0, 0, 40, 40
+    while x0 <= x1 and y0 <= y1:
+        s[y0, x0:x1 + 1] = 1; s[y0:y1 + 1, x1] = 1; s[y1, x0:x1 + 1] = 1
+        if y0 + 2 <= y1: s[y0 + 2:y1 + 1, x0] = 1
+        x0 += 2; y0 += 2; x1 -= 2; y1 -= 2
+        if x0 <= x1: s[y0 - 1, x0 - 1] = 1 if x0 - 1 >= 0 else 0
+    shapes.append(s)
+    # comb hanging from the bottom row (min index far from the start)
+    c = np.zeros((30, 33), np.uint8); c[29, :] = 1; c[:, ::2] = 1; shapes.append(c)
+    # diagonal chain: only 8-connected
+    shapes.append(np.eye(37, dtype=np.uint8)[::-1].copy())
+    shapes.append(np.ones((17, 23), np.uint8))
+    shapes.append(np.ones((1, 1), np.uint8))
+    chk = (np.indices((16, 16)).sum(0) % 2).astype(np.uint8); shapes.append(chk)
+    for fg in shapes:
+        for minarea in (1, 5, 50):
+            seg, _ = oracle.label(fg, minarea)
+            assert np.array_equal(seg, brute_label(fg.astype(bool), minarea))
+    # the anti-diagonal is one 8-connected component labelled at its top-right pixel
+    seg, n = oracle.label(np.eye(37, dtype=np.uint8)[::-1].copy(), 1)
+    assert n == 1 and set(np.unique(seg)) == {0, 36 + 1}
+
+
+# -------------------------------------------------------- overlap areas ---
+@pytest.mark.parametrize("r", [0.3, 0.5, 1.0, 1.7, 3.0, 5.0, 8.0, 10.0])
+def test_overlap_sums_to_disc_area(r):
+    rng = np.random.default_rng(int(r * 10))
+    for _ in range(5):
+        cx, cy = rng.uniform(-0.5, 0.5, 2)
+        R = int(math.ceil(r)) + 2
+        tot = 0.0
+        for y in range(-R, R + 1):
+            for x in range(-R, R + 1):
+                tot += oracle.overlap_area(x - 0.5 - cx, x + 0.5 - cx, y - 0.5 - cy, y + 0.5 - cy, r)
+        assert abs(tot - math.pi * r * r) < 1e-12 * max(1.0, r * r)
+
+
+def test_overlap_interior_exterior_and_small_disc():
+    r = 5.0
+    for y in range(-7, 8):
+        for x in range(-7, 8):
+            a = oracle.overlap_area(x - 0.5, x + 0.5, y - 0.5, y + 0.5, r)
+            far = math.hypot(abs(x) + 0.5, abs(y) + 0.5)
+            near = math.hypot(max(abs(x) - 0.5, 0), max(abs(y) - 0.5, 0))
+            if far <= r:
+                assert a == pytest.approx(1.0, abs=1e-14)
+            if near >= r:
+                assert a == 0.0
+            assert 0.0 <= a <= 1.0 + 1e-15
+    for r in (0.1, 0.25, 0.49):
+        assert oracle.overlap_area(-0.5, 0.5, -0.5, 0.5, r) == pytest.approx(math.pi * r * r, rel=1e-13)
+
+
+def test_overlap_symmetries_and_monte_carlo():
+    rng = np.random.default_rng(7)
+    for _ in range(30):
+        x0, y0 = rng.uniform(-4, 3, 2)
+        x1, y1 = x0 + rng.uniform(0.2, 1.5), y0 + rng.uniform(0.2, 1.5)
+        r = rng.uniform(0.5, 4)
+        a = oracle.overlap_area(x0, x1, y0, y1, r)
+        assert a == pytest.approx(oracle.overlap_area(y0, y1, x0, x1, r), abs=1e-13)       # x <-> y
+        assert a == pytest.approx(oracle.overlap_area(-x1, -x0, y0, y1, r), abs=1e-13)     # x -> -x
+        assert a == pytest.approx(oracle.overlap_area(x0, x1, -y1, -y0, r), abs=1e-13)     # y -> -y
+    # Monte Carlo on boundary pixels
+    for (x0, y0, r) in [(2.5, 0.5, 3.0), (1.5, 1.5, 2.3), (-0.5, 2.5, 3.1), (3.5, -4.5, 5.2)]:
+        pts = rng.uniform(0, 1, (1_000_000, 2))
+        inside = ((x0 + pts[:, 0]) ** 2 + (y0 + pts[:, 1]) ** 2 <= r * r).mean()
+        a = oracle.overlap_area(x0, x0 + 1, y0, y0 + 1, r)
+        assert abs(a - inside) < 5 * math.sqrt(max(inside * (1 - inside), 1e-6) / 1e6) + 1e-6
+
+
+# ---------------------------------------------------------- sigma clip ---
+def test_sigma_clip_gaussian_fixed_point():
+    g = golden()
+    # the fixed point itself, from the truncated-normal variance
+    var_trunc = lambda a: 1 - 2 * a * norm.pdf(a) / (2 * norm.cdf(a) - 1)
+    s = g["clip3_fixed_point"]
+    assert s == pytest.approx(math.sqrt(var_trunc(3 * s)), abs=1e-12)
+    rng = np.random.default_rng(1)
+    v = rng.normal(100.0, 7.0, 2_000_000)
+    med, mean, sd, nk, passes = oracle.sigma_clip(v, 3.0, 50)
+    assert sd / 7.0 == pytest.approx(s, abs=2.5e-3)
+    assert mean == pytest.approx(100.0, abs=0.03)
+    assert med == pytest.approx(100.0, abs=0.03)
+    # a single pass clips at 3 sigma of the raw sample
+    med1, _, sd1, _, p1 = oracle.sigma_clip(v, 3.0, 1)
+    assert p1 == 1 and sd1 / 7.0 == pytest.approx(g["clip3_single_pass"], abs=2.5e-3)
+
+
+def test_sigma_clip_special_cases():
+    v = np.full(1000, 42.0)
+    med, mean, sd, nk, passes = oracle.sigma_clip(v, 3.0, 10)
+    assert (med, mean, sd, nk, passes) == (42.0, 42.0, 0.0, 1000, 0)
+    rng = np.random.default_rng(3)
+    w = rng.normal(0, 1, 4001)
+    # no clipping pass: plain median / mean / population std (numpy routines)
+    med, mean, sd, nk, passes = oracle.sigma_clip(w, 3.0, 0)
+    assert med == np.median(w) and nk == w.size and passes == 0
+    assert mean == pytest.approx(np.mean(w), abs=1e-13) and sd == pytest.approx(np.std(w), rel=1e-13)
+    # even count: median is the mean of the two middle order statistics
+    med, *_ = oracle.sigma_clip(np.array([4.0, 1.0, 3.0, 10.0]), 3.0, 0)
+    assert med == 3.5
+
+
+def test_sigma_clip_equivariance_and_outliers():
+    rng = np.random.default_rng(5)
+    v = np.round(rng.normal(1000, 30, 20000))
+    a = oracle.sigma_clip(v, 3.0, 10)
+    b = oracle.sigma_clip(4.0 * v + 1024.0, 3.0, 10)          # exact in binary
+    assert b[3] == a[3] and b[4] == a[4]
+    assert b[0] == 4 * a[0] + 1024 and b[1] == pytest.approx(4 * a[1] + 1024, rel=1e-15)
+    assert b[2] == pytest.approx(4 * a[2], rel=1e-12)
+    c = oracle.sigma_clip(-v, 3.0, 10)                         # reflection
+    assert c[3] == a[3] and c[0] == -a[0] and c[2] == pytest.approx(a[2], rel=1e-12)
+    # 5 % of far outliers are removed and the clean result comes back
+    out = np.concatenate([v, np.full(1000, 60000.0)])
+    d = oracle.sigma_clip(out, 3.0, 20)
+    e = oracle.sigma_clip(v, 3.0, 20)
+    assert d[3] == e[3] and d[0] == e[0] and d[2] == pytest.approx(e[2], rel=1e-12)
+    # the final kept set is contiguous in value order and inside its bounds
+    med, mean, sd, nk, _ = e
+    kept = np.sort(v)[(np.sort(v) >= med - 3 * sd - 1e-9) & (np.sort(v) <= med + 3 * sd + 1e-9)]
+    assert kept.size == nk
+
+
+def test_mode_estimate_symmetric():
+    assert oracle.mode_estimate(10.0, 10.0, 2.0) == 10.0      # symmetric: mode = median
+    assert oracle.mode_estimate(10.0, 12.0, 2.0) == 10.0      # skewed > 0.3 sigma: median
+    assert oracle.mode_estimate(10.0, 10.4, 2.0) == pytest.approx(9.4)
+    assert oracle.mode_estimate(5.0, 7.0, 0.0) == 5.0
+
+
+# ------------------------------------------------------- mesh and spline ---
+def test_median_filter_interior_matches_scipy_and_edges():
+    rng = np.random.default_rng(11)
+    a = rng.normal(0, 1, (9, 12))
+    out = oracle.median_filter(a, 3)
+    ref = ndimage.median_filter(a, size=3, mode="nearest")
+    assert np.array_equal(out[1:-1, 1:-1], ref[1:-1, 1:-1])
+    # corner window is the 2x2 block: mean of its two middle values
+    c = np.sort(a[:2, :2].ravel())
+    assert out[0, 0] == pytest.approx(0.5 * (c[1] + c[2]), abs=1e-15)
+    spike = np.ones((5, 5)); spike[2, 2] = 1e6
+    assert np.all(oracle.median_filter(spike, 3) == 1.0)
+
+
+def test_spline_reproduces_linear_and_constant():
+    W, H, B = 300, 250, 64             # partial last boxes on both axes
+    Mx, My = -(-W // B), -(-H // B)
+    cx = np.array([i * B + (min((i + 1) * B, W) - i * B - 1) / 2 for i in range(Mx)])
+    cy = np.array([j * B + (min((j + 1) * B, H) - j * B - 1) / 2 for j in range(My)])
+    mesh = 3.0 + 0.25 * cx[None, :] - 0.5 * cy[:, None]
+    m = oracle.spline_map(mesh, W, H, B)
+    yy, xx = np.mgrid[0:H, 0:W]
+    assert np.allclose(m, 3.0 + 0.25 * xx - 0.5 * yy, atol=1e-9, rtol=0)
+    c = oracle.spline_map(np.full((My, Mx), 1234.5), W, H, B)
+    assert np.all(c == 1234.5)            # exact, so m = I - B is exactly 0 on a flat sky
+
+
+def test_spline_is_natural_cubic_tensor_product():
+    W, H, B = 700, 520, 64
+    Mx, My = -(-W // B), -(-H // B)
+    cx = np.array([i * B + (min((i + 1) * B, W) - i * B - 1) / 2 for i in range(Mx)])
+    cy = np.array([j * B + (min((j + 1) * B, H) - j * B - 1) / 2 for j in range(My)])
+    rng = np.random.default_rng(2)
+    mesh = rng.normal(0, 10, (My, Mx))
+    m = oracle.spline_map(mesh, W, H, B)
+    # interpolates the mesh at the box centres
+    for j in range(My):
+        for i in range(Mx):
+            if float(cx[i]).is_integer() and float(cy[j]).is_integer():
+                assert m[int(cy[j]), int(cx[i])] == pytest.approx(mesh[j, i], abs=1e-9)
+    # inside the node range: scipy's natural CubicSpline along x, then y
+    xs = np.arange(int(math.ceil(cx[0])), int(cx[-1]) + 1)
+    ys = np.arange(int(math.ceil(cy[0])), int(cy[-1]) + 1)
+    rows = CubicSpline(cx, mesh, axis=1, bc_type="natural")(xs)
+    ref = CubicSpline(cy, rows, axis=0, bc_type="natural")(ys)
+    assert np.allclose(m[np.ix_(ys, xs)], ref, atol=1e-9, rtol=0)
+    # the other order gives the same surface (tensor product)
+    cols = CubicSpline(cy, mesh, axis=0, bc_type="natural")(ys)
+    ref2 = CubicSpline(cx, cols, axis=1, bc_type="natural")(xs)
+    assert np.allclose(ref, ref2, atol=1e-9)
+    # beyond the outer centres the map is linear in x (zero second difference)
+    d2 = m[:, 2:int(cx[0])] - 2 * m[:, 1:int(cx[0]) - 1] + m[:, 0:int(cx[0]) - 2]
+    assert np.abs(d2).max() < 1e-9
+    # samples agree with the full map
+    qx = rng.integers(0, W, 50); qy = rng.integers(0, H, 50)
+    assert np.allclose(oracle.spline_at(mesh, W, H, B, qx, qy), m[qy, qx], atol=1e-12, rtol=0)
+
+
+def test_spline_one_and_two_nodes():
+    m = oracle.spline_map(np.array([[7.0]]), 40, 30, 64)
+    assert np.all(m == 7.0)
+    m = oracle.spline_map(np.array([[1.0, 3.0]]), 100, 20, 64)   # centres 31.5 and 81.5
+    assert m[0, 31] == pytest.approx(1.0 - 0.5 * 2 / 50) and m[5, 99] == pytest.approx(1 + 2 * (99 - 31.5) / 50)
+
+
+# ---------------------------------------------------------------- filter ---
+def test_filter_matches_scipy_mirror_correlation():
+    rng = np.random.default_rng(4)
+    m = rng.normal(0, 1, (37, 53))
+    K = rng.uniform(0.1, 1, (5, 3))                    # asymmetric, non-square
+    F = oracle.matched_filter(m, K)
+    ref = ndimage.correlate(m, K / K.sum(), mode="mirror")
+    assert np.allclose(F, ref, atol=1e-12, rtol=0)
+    # a delta reproduces the flipped, normalised kernel (correlation, not convolution)
+    d = np.zeros((11, 11)); d[5, 5] = 1.0
+    F = oracle.matched_filter(d, K)
+    assert np.allclose(F[3:8, 4:7], (K / K.sum())[::-1, ::-1], atol=1e-15)
+    with pytest.raises(ValueError):
+        oracle.matched_filter(m, np.array([[1.0, -1.0, 0.0]]))
+
+
+def test_filter_golden_kernel_taps():
+    g = golden()
+    K = synth.gaussian_kernel(5, 3.0).astype(np.float64)
+    d = np.zeros((9, 9)); d[4, 4] = 1.0
+    F = oracle.matched_filter(d, K)
+    assert F[4, 4] == pytest.approx(g["gauss5_fwhm3_centre"], abs=1e-6)
+    assert F[2, 2] == pytest.approx(g["gauss5_fwhm3_corner"], abs=1e-7)
+    assert math.sqrt((F ** 2).sum()) == pytest.approx(g["gauss5_fwhm3_l2"], abs=1e-6)
+
+
+# --------------------------------------------------------------- moments ---
+def test_moments_closed_forms():
+    seg = np.zeros((20, 30), np.uint32)
+    m = np.zeros((20, 30))
+    # uniform w x h rectangle: centroid at its centre, x2 = (w^2-1)/12
+    seg[2:7, 3:12] = 2 * 30 + 3 + 1
+    m[2:7, 3:12] = 5.0
+    # single pixel
+    seg[15, 25] = 15 * 30 + 25 + 1
+    m[15, 25] = 3.0
+    # diagonal pair with weights 1 and 3
+    seg[10, 1] = seg[11, 2] = 10 * 30 + 1 + 1
+    m[10, 1], m[11, 2] = 1.0, 3.0
+    cat = oracle.moments(seg, m)
+    assert list(cat["label"]) == sorted(cat["label"])
+    r = 0
+    assert cat["x"][r] == pytest.approx(7.0) and cat["y"][r] == pytest.approx(4.0)
+    assert cat["x2"][r] == pytest.approx((81 - 1) / 12) and cat["y2"][r] == pytest.approx((25 - 1) / 12)
+    assert cat["xy"][r] == pytest.approx(0.0, abs=1e-12) and cat["npix"][r] == 45
+    assert cat["flux"][r] == pytest.approx(225.0)
+    assert (cat["xmin"][r], cat["xmax"][r], cat["ymin"][r], cat["ymax"][r]) == (3, 11, 2, 6)
+    r = 1
+    assert cat["x"][r] == pytest.approx(1.75) and cat["y"][r] == pytest.approx(10.75)
+    assert cat["x2"][r] == pytest.approx(0.1875) and cat["xy"][r] == pytest.approx(0.1875)
+    assert (cat["xpeak"][r], cat["ypeak"][r], cat["peak"][r]) == (2, 11, 3.0)
+    r = 2
+    assert (cat["x"][r], cat["y"][r], cat["x2"][r]) == (25.0, 15.0, 0.0)
+    # non-positive sum: unweighted centroid and the fallback flag
+    m2 = m.copy(); m2[10, 1], m2[11, 2] = -1.0, -3.0
+    cat = oracle.moments(seg, m2)
+    assert cat["x"][1] == 1.5 and cat["flags"][1] & oracle.FLAG_CENTROID_FALLBACK
+    assert cat["x2"][1] == pytest.approx(0.25)
+
+
+# ------------------------------------------------------------- apertures ---
+def test_aperture_moffat_encircled_energy():
+    """Aperture sums of a rendered Moffat star against the closed-form
+    encircled energy.  A pixelised aperture differs from the continuous
+    integral by a pixel-integration error that falls as the square of the
+    sampling, while EE(r; alpha) = EE(s r; s alpha); so the star is drawn s
+    times finer (FWHM 3 s, radii r s) and compared with the golden FWHM-3
+    values."""
+    g = golden()
+    beta, F, s = 2.5, 1e5, 6
+    R = 10 * s + 4
+    W = H = 2 * R + 1
+    cx, cy = R + 0.3, R - 0.2
+    img, _ = synth.render_moffat((H, W), np.array([cx]), np.array([cy]), np.array([F]),
+                                 np.array([3.0 * s]), np.array([0.0]), np.array([0.0]), beta, R, 8)
+    radii = np.array([3.0, 5.0, 8.0, 10.0]) * s
+    flux, err, flags = oracle.apertures(img, np.zeros_like(img), np.zeros((H, W), np.uint8), None,
+                                        [cx], [cy], radii, 0.0)
+    for k, r in enumerate((3, 5, 8, 10)):
+        assert flux[0, k] / F == pytest.approx(g[f"moffat_ee_r{r}"], rel=1e-3)
+    assert np.all(flags == 0) and np.all(err == 0)
+
+
+def test_aperture_constant_image_and_flags():
+    W, H = 40, 30
+    img = np.full((H, W), 2.0)
+    var = np.full((H, W), 9.0)
+    bad = np.zeros((H, W), np.uint8)
+    flux, err, flags = oracle.apertures(img, var, bad, None, [20.2], [14.9], [3.0, 6.5], 2.0)
+    area = math.pi * np.array([9.0, 42.25])
+    assert np.allclose(flux[0], 2.0 * area, rtol=1e-12)
+    assert np.allclose(err[0] ** 2, 9.0 * area + 2.0 * area / 2.0, rtol=1e-12)
+    # disc leaving the frame is flagged and sums only in-frame area
+    flux, err, flags = oracle.apertures(img, var, bad, None, [1.0], [14.0], [3.0], 0.0)
+    assert flags[0, 0] & oracle.FLAG_TRUNCATED
+    half = sum(oracle.overlap_area(x - 0.5 - 1.0, x + 0.5 - 1.0, y - 0.5, y + 0.5, 3.0)
+               for x in range(0, 5) for y in range(-4, 5))
+    assert flux[0, 0] == pytest.approx(2.0 * half, rel=1e-12)
+    bad[14, 20] = 1
+    flux, err, flags = oracle.apertures(img, var, bad, None, [20.0], [14.0], [2.0], 0.0)
+    assert flags[0, 0] & oracle.FLAG_BAD and flux[0, 0] == pytest.approx(2.0 * (math.pi * 4 - 1), rel=1e-12)
+
+
+# ----------------------------------------------------- whole-path invariants ---
+def test_constant_sky_has_no_detections():
+    img = np.full((256, 320), 1500.0, np.float32)
+    r = oracle.extract(img, 64, synth.gaussian_kernel(5, 3.0), 1.5, 5, (3.0,), 1.0)
+    assert np.all(r["bkg_map"] == 1500.0) and np.all(r["rms_map"] == 0.0)
+    assert np.all(r["F"] == 0.0) and r["fg"].sum() == 0 and len(r["cat"]["label"]) == 0
+
+
+def test_pure_noise_background_and_rms():
+    g = golden()
+    rng = np.random.default_rng(9)
+    mu, s = 1000.0, 20.0
+    img = rng.normal(mu, s, (512, 512)).astype(np.float32)
+    st = oracle.box_stats(img.astype(np.float64), np.zeros(img.shape, np.uint8), 128)
+    n = 128 * 128
+    assert np.all(np.abs(st["bkg"] - mu) < 6 * s / math.sqrt(n) * 2.5)
+    assert np.all(np.abs(st["rms"] / s - g["clip3_fixed_point"]) < 0.02)
+    r = oracle.extract(img, 128, synth.gaussian_kernel(5, 3.0), 1.5, 5, (3.0,), 1.0)
+    assert len(r["cat"]["label"]) == 0        # 1.5 sigma on the filtered image is 6.2 filtered sigmas
+
+
+def test_isolated_star_recovered():
+    """Noiseless flat sky plus one Moffat star (drawn 4x finer than FWHM 3 so
+    that pixel integration is negligible): one segment, centroid at the star,
+    aperture fluxes equal to the encircled energy."""
+    g = golden()
+    W = H = 192
+    cx, cy, F = 90.4, 100.7, 2e6
+    star, _ = synth.render_moffat((H, W), np.array([cx]), np.array([cy]), np.array([F]),
+                                  np.array([12.0]), np.array([0.0]), np.array([0.0]), 2.5, 90, 6)
+    img = (500.0 + star).astype(np.float64)
+    r = oracle.extract(img, 64, synth.gaussian_kernel(5, 3.0), 1.5, 5, (12.0, 20.0), 1.0)
+    cat = r["cat"]
+    assert len(cat["label"]) == 1
+    assert cat["x"][0] == pytest.approx(cx, abs=0.05) and cat["y"][0] == pytest.approx(cy, abs=0.05)
+    # the star lifts its boxes' statistics; measure against the known sky
+    flux, _, _ = oracle.apertures(img - 500.0, np.zeros_like(img), np.zeros((H, W), np.uint8), None,
+                                  [cx], [cy], [12.0, 20.0], 0.0)
+    assert flux[0, 0] / F == pytest.approx(g["moffat_ee_r3"], rel=2e-3)
+    assert flux[0, 1] / F == pytest.approx(g["moffat_ee_r5"], rel=2e-3)
+
+
+def test_box_geometry_and_invalid_fill():
+    """[R2] box bounds including partial last boxes, [R5] filling of boxes
+    with fewer than half good pixels from their valid neighbours."""
+    W, H, B = 150, 70, 32                    # 5 x 3 boxes, last ones 22 and 6 px
+    Mx, My = 5, 3
+    vals = np.arange(Mx * My, dtype=np.float64).reshape(My, Mx) * 10 + 100
+    img = np.repeat(np.repeat(vals, B, 0), B, 1)[:H, :W]
+    bad = np.zeros((H, W), np.uint8)
+    st = oracle.box_stats(img, bad, B)
+    assert np.array_equal(st["bkg"], vals) and np.all(st["rms"] == 0) and np.all(st["valid"] == 1)
+    assert st["nkept"][2, 4] == 22 * 6 and st["nkept"][0, 0] == 32 * 32
+    # mask more than half of box (1, 2): it takes the mean of its 8 neighbours
+    bad[32:64, 64:96] = 1
+    bad[32:40, 64:70] = 0                    # 48 good of 1024: invalid
+    st = oracle.box_stats(img, bad, B)
+    assert st["valid"][1, 2] == 0
+    b, r = oracle.fill_invalid(st["bkg"], st["rms"], st["valid"])
+    nb = [vals[j, i] for j in (0, 1, 2) for i in (1, 2, 3) if (j, i) != (1, 2)]
+    assert b[1, 2] == pytest.approx(np.mean(nb)) and r[1, 2] == 0.0
+    # two invalid neighbours: the inner one is filled in the second sweep
+    valid = np.ones((1, 4), np.uint8); valid[0, 2:] = 0
+    b, _ = oracle.fill_invalid(np.array([[1.0, 3.0, 0, 0]]), np.zeros((1, 4)), valid)
+    assert b[0, 2] == 3.0 and b[0, 3] == 3.0
+
+
+def test_threshold_is_strict_and_skips_bad():
+    F = np.array([[3.0, 3.0000001, 2.9, 5.0]])
+    rms = np.array([[2.0, 2.0, 2.0, 2.0]])
+    bad = np.array([[0, 0, 0, 1]], np.uint8)
+    assert list(oracle.threshold(F, rms, bad, 1.5)[0]) == [0, 1, 0, 0]
