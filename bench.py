@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the per-frame extraction path (background + detection +
+apertures) on the dense 151.2 MP frame (12288 x 12304 uint16, 134,000
+sources, mesh 256, 5x5 Gaussian filter, 1.5 sigma, minarea 5, apertures
+r = 3, 6, 10).
+
+One step = one gp_extract call on one frame already resident in HBM.  The
+frame (302 MB) is larger than L2, so no flush is needed between steps.
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded crop of the same frame instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s extraction (bkg+detect+aperture) at 151 MP vs roofline; p50/p99 latency"
+UNIT = "Mpix/s"
+WORKLOAD = "dense_12288x12304_u16"
+CAPACITY = 400_000
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload_config(cfg):
+    return {"workload": cfg.name, "width": cfg.width, "height": cfg.height, "dtype_in": cfg.dtype,
+            "sources": cfg.nsrc, "mesh": cfg.mesh, "filter": f"{cfg.kernel_size}x{cfg.kernel_size} gaussian "
+            f"fwhm {cfg.kernel_fwhm}", "thresh": cfg.thresh, "minarea": cfg.minarea, "radii": list(cfg.radii),
+            "l2": "frame (302 MB) larger than the 129 MB L2; no flush between steps"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ oracle leg ---
+def oracle_sample(img, cfg, budget_s=12.0, max_crops=6, crop=2048):
+    """The CPU oracle (single thread) on crops of the frame until about
+    `budget_s` of CPU work; returns (Mpix/s, seconds, description)."""
+    import oracle
+    H, W = img.shape
+    offs = [(0, 0), (H // 2, W // 2), (H - crop, W - crop), (0, W - crop), (H - crop, 0), (H // 4, W // 3)]
+    tot_px, tot_t, n = 0, 0.0, 0
+    for (y0, x0) in offs[:max_crops]:
+        sub = img[y0:y0 + crop, x0:x0 + crop]
+        t0 = time.perf_counter()
+        oracle.extract(sub, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii, cfg.gain,
+                       saturation=cfg.saturation)
+        tot_t += time.perf_counter() - t0
+        tot_px += sub.size
+        n += 1
+        if tot_t >= budget_s:
+            break
+    desc = (f"{n} crop(s) of {crop}x{crop} px ({tot_px / 1e6:.1f} Mpix) of the {cfg.name} frame, full oracle "
+            f"path (background, filter, threshold, labelling, moments, apertures), 1 thread")
+    return tot_px / 1e6 / tot_t, tot_t, desc
+
+
+# ---------------------------------------------------------- clock sampler ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- traffic ---
+def kernel_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel)
+        if not e or e.get("workload") != workload:
+            return None
+        src = os.path.join(ROOT, e["source"])
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        return float(e["dram_bytes_per_launch"]) if sha == e.get("source_sha1") else None
+    except Exception:
+        return None
+
+
+STAGE_KERNEL = {"box_stats": "k_boxstats_u16", "detect_tiles": "k_detect_tile", "measure": "k_measure",
+                "tile_merge": "k_merge", "label_rank": "k_rank_place", "mesh_spline": "k_mesh_finalize"}
+
+
+def algorithmic_bytes(stage, cfg, cat):
+    """Algorithmic DRAM bytes of one launch of a stage's main kernel."""
+    import numpy as np
+    bpp = 2 if cfg.dtype == "u16" else 4
+    npix = cfg.width * cfg.height
+    if stage == "box_stats":
+        return npix * bpp
+    if stage == "detect_tiles":
+        return npix * (bpp + 4)
+    if stage == "measure" and cat is not None:
+        bw = (cat["xmax"] - cat["xmin"] + 1).astype(np.int64)
+        bh = (cat["ymax"] - cat["ymin"] + 1).astype(np.int64)
+        ap = int((2 * max(cfg.radii) + 3) ** 2)
+        return int((bw * bh).sum()) * (4 + bpp) + len(bw) * ap * bpp
+    return None
+
+
+# ------------------------------------------------------------- reference ---
+def run_reference(args):
+    import synth
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    cfg = synth.CONFIGS[args.workload]
+    img, _ = synth.make_frame(cfg, 0)
+    times = []
+    desc = ""
+    mpix = 0.0
+    for i in range(args.warmup + args.steps):
+        v, t, desc = oracle_sample(img, cfg, budget_s=0.0, max_crops=1, crop=args.ref_crop)
+        if i >= args.warmup:
+            times.append(t)
+            mpix = args.ref_crop * args.ref_crop / 1e6
+    tot = sum(times)
+    value = mpix * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / len(times), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": workload_config(cfg),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc + "; each step one crop"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU ---
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2609_32375_gb300 as gp
+    import synth
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = synth.CONFIGS[args.workload]
+    img, _ = synth.make_frame(cfg, rank)          # one independent frame per rank
+    H, W = img.shape
+    t_img = torch.from_numpy(img).to(dev)
+    L = gp.load_library()
+    ws = L.gp_workspace_bytes(W, H, cfg.mesh, CAPACITY) + (64 << 20)
+    ctx = gp.Context(local, workspace_bytes=ws)
+    ex = gp.Extractor(ctx, (H, W), t_img.dtype, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii,
+                      cfg.gain, CAPACITY, saturation=cfg.saturation, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ex.run(t_img)
+    ctx.sync()
+    nsrc, cat = ex.catalog_host()
+
+    # ---- device-resident timed region
+    ctx.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        ex.run(t_img)
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.sync()
+    stats = ctx.stats()
+    ctx.set_timing(False)
+    total_ms = t0.elapsed_time(t1)
+    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    mpix_all = W * H * world / 1e6
+    value = mpix_all / (ms_per_step / 1e3)
+
+    # ---- end to end through the C ABI from pinned host memory
+    h_img = torch.from_numpy(img).pin_memory()
+    ncopy = min(nsrc, CAPACITY)
+    nr = len(cfg.radii)
+    cat_cols = [v for k, v in ex.out["catalog"].items() if k != "n"]
+    h_out = [torch.empty((ncopy,) + tuple(v.shape[1:]), dtype=v.dtype).pin_memory() for v in cat_cols]
+    h_ap = [torch.empty((ncopy, ex.out[k].shape[1]), dtype=ex.out[k].dtype).pin_memory()
+            for k in ("flux", "fluxerr", "apflags")]
+    h_n = torch.empty(1, dtype=torch.int32).pin_memory()
+    d2h = h_n.numel() * 4 + sum(t.numel() * t.element_size() for t in h_out + h_ap)
+    h2d = h_img.numel() * h_img.element_size()
+
+    def e2e_step():
+        t_img.copy_(h_img, non_blocking=True)
+        ex.run(t_img)
+        h_n.copy_(ex.out["catalog"]["n"], non_blocking=True)
+        for src, dst in zip(cat_cols, h_out):
+            dst.copy_(src[:ncopy], non_blocking=True)
+        for k, dst in zip(("flux", "fluxerr", "apflags"), h_ap):
+            dst.copy_(ex.out[k][:ncopy], non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ne2e = args.e2e_steps or args.steps
+    e0.record(stream)
+    for _ in range(ne2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / ne2e
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    assert int(h_n.item()) == nsrc, "end-to-end run gave a different segment count"
+
+    # ---- roofline of the dominant kernel (live stage times over the timed region)
+    peak, peak_src = measured_peaks()
+    stage_ms = {k: v / max(stats["calls"], 1) for k, v in stats["ms"].items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    ab = algorithmic_bytes(dom, cfg, cat)
+    achieved = ab / (stage_ms[dom] / 1e3) / 1e9 if ab else None
+    roof = {"bound": "hbm", "kernel": STAGE_KERNEL.get(dom, dom), "achieved": round(achieved, 1) if achieved else None,
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+            "traffic": kernel_traffic(STAGE_KERNEL.get(dom, dom), cfg.name), "algorithmic_bytes": ab,
+            "avg_launch_ms": round(stage_ms[dom], 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    path_bytes = W * H * (2 * (2 if cfg.dtype == "u16" else 4) + 4) + (algorithmic_bytes("measure", cfg, cat) or 0)
+    whole = {"algorithmic_bytes": path_bytes, "achieved_GBs": round(path_bytes / (ms_per_step / 1e3) / 1e9, 1),
+             "frac": round(path_bytes / (ms_per_step / 1e3) / 1e9 / peak, 4)}
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": dict(workload_config(cfg), parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                           segments=nsrc, capacity=CAPACITY),
+            "p50_ms": round(statistics.median(step_ms), 4),
+            "p99_ms": round(step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 4),
+            "roofline": roof, "path_roofline": whole,
+            "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "e2e": {"value": round(mpix_all / (e2e_ms / 1e3), 2), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": stats["launches"] * args.steps,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, t, desc = oracle_sample(img, cfg)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": round(t, 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--ref-crop", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * gpphot.h -- C ABI of the GB300 (sm_103a) per-frame source-extraction path.
+ *
+ * The operations follow the GPU stages of the GPUPHOT paper (arXiv
+ * 2609.32375): a local background with a per-pixel noise map (Section 3.1),
+ * matched-filter detection against a significance threshold with
+ * first-moment centroids (Section 3.2) and circular-aperture sums accumulated
+ * at float64 accuracy with propagated variance (Section 3.4).  Where the
+ * paper leaves the algorithm open the library implements the SExtractor-style
+ * reading: sigma-clipped mesh statistics, natural-spline maps, labelled
+ * segments with moments and exact disc/pixel overlap apertures.
+ *
+ * Conventions (every entry point):
+ *  - All array pointers are DEVICE pointers owned by the caller unless the
+ *    comment says "host".  Images are row-major, x = column, y = row,
+ *    pixel (x, y) covers [x-1/2, x+1/2] x [y-1/2, y+1/2], linear index
+ *    L = y * width + x.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and returns without waiting.  Outputs are valid once the stream
+ *    has synchronised.  Arguments are checked on the host before any launch;
+ *    an argument error returns GP_ERR_INVALID_ARG with nothing enqueued.
+ *  - Conditions only the device can see (catalog capacity exceeded, an
+ *    internal table full, a bounded wait that gave up) are recorded in the
+ *    context's device status word; gp_ctx_sync() returns it.
+ *  - Scratch memory comes only from the context's workspace arena, which is
+ *    allocated once by gp_ctx_create(); no entry point allocates.  Calls on
+ *    one context share that arena, so calls on one context must be ordered
+ *    (same stream, or synchronised) -- use one context per concurrent stream.
+ *  - There is no CPU fallback: without a usable sm_103a device the calls
+ *    fail with GP_ERR_CUDA.
+ */
+#ifndef GPPHOT_H
+#define GPPHOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gp_stream; /* a cudaStream_t */
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_INVALID_ARG = 1,     /* rejected on the host, nothing enqueued */
+    GP_ERR_OOM = 2,             /* workspace arena too small (or allocation failed in create) */
+    GP_ERR_CAPACITY = 3,        /* more sources than catalog rows (device-side) */
+    GP_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+    GP_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    GP_ERR_NOT_IMPLEMENTED = 6,
+    GP_ERR_INTERNAL = 7         /* an internal device table overflowed */
+} gp_status;
+
+typedef enum { GP_U16 = 0, GP_F32 = 1 } gp_dtype;
+
+/* per-source / per-aperture flag bits */
+enum {
+    GP_FLAG_SAT = 1u,                 /* a pixel >= saturation in the segment / under the disc */
+    GP_FLAG_CENTROID_FALLBACK = 2u,   /* segment sum <= 0: unweighted centroid and moments */
+    GP_FLAG_TRUNCATED = 4u,           /* aperture disc extends beyond the frame */
+    GP_FLAG_BAD = 8u                  /* aperture disc covers a masked / NaN pixel */
+};
+
+typedef struct gp_ctx gp_ctx;
+
+/* Create a context on `device` with a workspace arena of `workspace_bytes`
+ * (0: 2 GiB).  gp_workspace_bytes() gives the size one frame needs.
+ * Returns GP_ERR_OOM if the arena cannot be allocated. */
+gp_status gp_ctx_create(int device, size_t workspace_bytes, gp_ctx** out);
+void gp_ctx_destroy(gp_ctx* ctx);
+
+/* Message for the last non-OK status returned on this host thread. */
+const char* gp_last_error(void);
+
+/* Synchronise `stream` and return the device-side status of the work enqueued
+ * on this context since the previous gp_ctx_sync (then reset it to GP_OK). */
+gp_status gp_ctx_sync(gp_ctx* ctx, gp_stream stream);
+
+/* Stage timing.  When enabled, every call records CUDA events on its stream
+ * at the boundaries of its stages (box statistics; mesh filter and spline
+ * tables; detection tiles; tile merge; label ranking; moments and
+ * apertures) into a ring of 256 call slots.  gp_ctx_stats() waits for the
+ * recorded events, returns the device time of each stage summed over the
+ * calls recorded since the previous gp_ctx_stats() (at most the last 256),
+ * and starts a new accumulation.  Disabled by default; the events add a few
+ * microseconds per call. */
+#define GP_NSTAGES 6
+typedef struct {
+    int32_t calls;                 /* calls summed */
+    int32_t launches;              /* kernels launched by the most recent call */
+    float ms[GP_NSTAGES];          /* summed device milliseconds per stage */
+} gp_stats;
+gp_status gp_ctx_set_timing(gp_ctx* ctx, int32_t enable);
+gp_status gp_ctx_stats(gp_ctx* ctx, gp_stats* out);
+
+/* Arena bytes needed to run gp_extract on a width x height frame with this
+ * mesh size and catalog capacity (capacity <= 0: the default internal table
+ * size of max(65536, width*height/32) segments). */
+size_t gp_workspace_bytes(int32_t width, int32_t height, int32_t mesh, int32_t capacity);
+
+/* ---------------------------------------------------------------- inputs */
+typedef struct {
+    const void* data;      /* device; uint16 or float32 pixels */
+    gp_dtype dtype;
+    int32_t width, height;
+    int64_t pitch;         /* elements between rows, >= width */
+    const uint8_t* mask;   /* device width*height (pitch = width), nonzero = bad; nullable */
+    float saturation;      /* pixels >= saturation are flagged; <= 0: none */
+} gp_image;
+
+/* Background parameters (Section 3.1): mesh box side, median filter size of
+ * the box meshes, clip factor k and the maximum number of clip passes. */
+typedef struct {
+    int32_t mesh;          /* 16 .. 256 (uint16 frames); 16 .. 128 (float32 frames) */
+    int32_t filter_size;   /* odd, 1 .. 7; 1 = no mesh filtering */
+    float clip_k;          /* >= 1, typically 3 */
+    int32_t clip_maxiter;  /* >= 0, typically 10 */
+} gp_bkg_params;
+
+/* Background result: the filtered box meshes (my rows of mx boxes), from
+ * which the per-pixel background B(p) and noise sigma(p) are the
+ * tensor-product natural cubic spline through the box centres. */
+typedef struct {
+    int32_t mesh;          /* box side used */
+    int32_t mx, my;        /* mesh size: ceil(width/mesh), ceil(height/mesh) */
+    float* bkg_mesh;       /* device my*mx, caller-owned */
+    float* rms_mesh;       /* device my*mx, caller-owned */
+    float* bkg_map;        /* device width*height full-resolution B(p); nullable (not written) */
+    float* rms_map;        /* device width*height full-resolution sigma(p); nullable */
+} gp_bkg;
+
+/* Detection parameters (Section 3.2): the matched-filter kernel (host,
+ * kh rows of kw taps, both odd <= 15; normalised to unit sum inside; a zero
+ * sum is rejected), the threshold in units of sigma(p) and the minimum
+ * segment area in pixels. */
+typedef struct {
+    const float* kernel;   /* HOST pointer, kh*kw taps */
+    int32_t kw, kh;
+    float thresh;          /* > 0 */
+    int32_t minarea;       /* >= 1 */
+    uint8_t* mask_out;     /* device width*height: the raw threshold mask (1 = foreground); nullable */
+    int32_t* nnear;        /* device scalar: pixels with |F - k sigma| <= 1e-5 |k sigma|; nullable */
+} gp_det_params;
+
+/* Segment catalog, structure of arrays, `capacity` rows, ascending label.
+ * label = 1 + minimum linear index of the segment; (x, y) is the first
+ * moment of m = I - B over the segment; x2, y2, xy its central second
+ * moments; peak is the maximum of m (position: its first pixel in raster
+ * order). */
+typedef struct {
+    int32_t capacity;
+    int32_t* n;            /* device scalar: number of segments found (may exceed capacity) */
+    uint32_t* label;
+    int32_t* npix;
+    double* flux_iso;      /* sum of m over the segment */
+    double *x, *y, *x2, *y2, *xy;
+    int32_t *xmin, *xmax, *ymin, *ymax;
+    float* peak;
+    int32_t *xpeak, *ypeak;
+    uint32_t* flags;
+} gp_catalog;
+
+/* Aperture parameters (Section 3.4): radii in pixels (host, nr <= 8) and the
+ * gain for the Poisson term of the error (<= 0: no Poisson term). */
+typedef struct {
+    const float* radii;    /* HOST pointer */
+    int32_t nr;
+    float gain;
+} gp_ap_params;
+
+/* ------------------------------------------------------------ operations */
+
+/* Section 3.1: per-box sigma-clipped statistics, invalid-box filling, mesh
+ * median filter.  Fills bkg->bkg_mesh / rms_mesh (and the full maps when
+ * their pointers are non-null).  bkg->mesh/mx/my are set by the call. */
+gp_status gp_background(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p,
+                        gp_bkg* bkg, gp_stream stream);
+
+/* Section 3.2: m = I - B, F = K (x) m (correlation, mirror border),
+ * foreground F > thresh * sigma(p), 8-connected segments of at least
+ * minarea pixels labelled 1 + min linear index (others 0) into `segmap`
+ * (device width*height, caller-owned), and the segment catalog. */
+gp_status gp_detect(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* p,
+                    uint32_t* segmap, gp_catalog* cat, gp_stream stream);
+
+/* Section 3.4: circular apertures of each radius around (x[i], y[i])
+ * (device, n sources): flux = sum over in-frame good pixels of the exact
+ * disc/pixel overlap area times m; fluxerr^2 = sum area * sigma(p)^2 +
+ * max(flux, 0) / gain.  Outputs n*nr (source-major), device, caller-owned. */
+gp_status gp_aperture(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
+                      const double* x, const double* y, int32_t n, const gp_ap_params* p,
+                      double* flux, double* fluxerr, uint32_t* flags, gp_stream stream);
+
+/* The three stages in one call; apertures at each segment's centroid, rows
+ * aligned with the catalog (capacity*nr). */
+gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp,
+                     const gp_det_params* dp, const gp_ap_params* ap, gp_bkg* bkg,
+                     uint32_t* segmap, gp_catalog* cat, double* flux, double* fluxerr,
+                     uint32_t* apflags, gp_stream stream);
+
+/* The labelling step of gp_detect alone on a caller-supplied mask (device
+ * width*height, nonzero = foreground): same 8-connectivity, canonical labels
+ * and minarea rule, so labels can be compared from an identical mask.
+ * n_out (device scalar, nullable) receives the number of segments kept. */
+gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t height,
+                        int32_t minarea, uint32_t* segmap, int32_t* n_out, gp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPPHOT_H */

@@ -1,0 +1,380 @@
+"""GB300-native per-frame source extraction: Python binding of libgpphot.
+
+A thin ctypes layer over the C ABI declared in include/gpphot.h.  It only
+marshals arguments: torch supplies device memory and streams, every step of
+the extraction runs in the library's CUDA kernels.  There is no fallback --
+importing works without a GPU, but any call needs the compiled library and a
+CUDA device and raises otherwise.
+
+Entry points keep the C names (gp_background, gp_detect, gp_aperture,
+gp_extract, gp_label_mask); `Context` and `Extractor` wrap them with tensor
+allocation for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgpphot.so")
+
+GP_OK, GP_ERR_INVALID_ARG, GP_ERR_OOM, GP_ERR_CAPACITY, GP_ERR_CUDA, GP_ERR_TIMEOUT, \
+    GP_ERR_NOT_IMPLEMENTED, GP_ERR_INTERNAL = range(8)
+GP_U16, GP_F32 = 0, 1
+GP_FLAG_SAT, GP_FLAG_CENTROID_FALLBACK, GP_FLAG_TRUNCATED, GP_FLAG_BAD = 1, 2, 4, 8
+
+STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CAPACITY", 4: "GP_ERR_CUDA",
+                5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NOT_IMPLEMENTED", 7: "GP_ERR_INTERNAL"}
+
+EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
+           "gp_workspace_bytes",
+           "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask")
+
+
+class GpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ------------------------------------------------------------ C structs ---
+class GpImage(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dtype", C.c_int), ("width", C.c_int32), ("height", C.c_int32),
+                ("pitch", C.c_int64), ("mask", C.c_void_p), ("saturation", C.c_float)]
+
+
+class GpBkgParams(C.Structure):
+    _fields_ = [("mesh", C.c_int32), ("filter_size", C.c_int32), ("clip_k", C.c_float),
+                ("clip_maxiter", C.c_int32)]
+
+
+class GpBkg(C.Structure):
+    _fields_ = [("mesh", C.c_int32), ("mx", C.c_int32), ("my", C.c_int32), ("bkg_mesh", C.c_void_p),
+                ("rms_mesh", C.c_void_p), ("bkg_map", C.c_void_p), ("rms_map", C.c_void_p)]
+
+
+class GpDetParams(C.Structure):
+    _fields_ = [("kernel", C.POINTER(C.c_float)), ("kw", C.c_int32), ("kh", C.c_int32), ("thresh", C.c_float),
+                ("minarea", C.c_int32), ("mask_out", C.c_void_p), ("nnear", C.c_void_p)]
+
+
+class GpCatalog(C.Structure):
+    _fields_ = [("capacity", C.c_int32), ("n", C.c_void_p), ("label", C.c_void_p), ("npix", C.c_void_p),
+                ("flux_iso", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("x2", C.c_void_p),
+                ("y2", C.c_void_p), ("xy", C.c_void_p), ("xmin", C.c_void_p), ("xmax", C.c_void_p),
+                ("ymin", C.c_void_p), ("ymax", C.c_void_p), ("peak", C.c_void_p), ("xpeak", C.c_void_p),
+                ("ypeak", C.c_void_p), ("flags", C.c_void_p)]
+
+
+GP_NSTAGES = 6
+STAGE_NAMES = ("box_stats", "mesh_spline", "detect_tiles", "tile_merge", "label_rank", "measure")
+
+
+class GpStats(C.Structure):
+    _fields_ = [("calls", C.c_int32), ("launches", C.c_int32), ("ms", C.c_float * GP_NSTAGES)]
+
+
+class GpApParams(C.Structure):
+    _fields_ = [("radii", C.POINTER(C.c_float)), ("nr", C.c_int32), ("gain", C.c_float)]
+
+
+CATALOG_COLUMNS = (("label", "uint32"), ("npix", "int32"), ("flux_iso", "float64"), ("x", "float64"),
+                   ("y", "float64"), ("x2", "float64"), ("y2", "float64"), ("xy", "float64"), ("xmin", "int32"),
+                   ("xmax", "int32"), ("ymin", "int32"), ("ymax", "int32"), ("peak", "float32"),
+                   ("xpeak", "int32"), ("ypeak", "int32"), ("flags", "uint32"))
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load_library():
+    """Load libgpphot.so (building it first if it is missing and nvcc is
+    present).  Raises if it cannot be loaded: there is no fallback."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            from . import _build
+            _build.build()
+        L = C.CDLL(LIB_PATH)
+        vp, i32, st = C.c_void_p, C.c_int32, C.c_int
+        L.gp_ctx_create.argtypes = [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]
+        L.gp_ctx_create.restype = st
+        L.gp_ctx_destroy.argtypes = [vp]
+        L.gp_ctx_destroy.restype = None
+        L.gp_last_error.argtypes = []
+        L.gp_last_error.restype = C.c_char_p
+        L.gp_ctx_sync.argtypes = [vp, vp]
+        L.gp_ctx_sync.restype = st
+        L.gp_ctx_set_timing.argtypes = [vp, i32]
+        L.gp_ctx_set_timing.restype = st
+        L.gp_ctx_stats.argtypes = [vp, C.POINTER(GpStats)]
+        L.gp_ctx_stats.restype = st
+        L.gp_workspace_bytes.argtypes = [i32, i32, i32, i32]
+        L.gp_workspace_bytes.restype = C.c_size_t
+        L.gp_background.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpBkg), vp]
+        L.gp_background.restype = st
+        L.gp_detect.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), C.POINTER(GpDetParams), vp,
+                                C.POINTER(GpCatalog), vp]
+        L.gp_detect.restype = st
+        L.gp_aperture.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), vp, vp, i32, C.POINTER(GpApParams),
+                                  vp, vp, vp, vp]
+        L.gp_aperture.restype = st
+        L.gp_extract.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
+                                 C.POINTER(GpApParams), C.POINTER(GpBkg), vp, C.POINTER(GpCatalog), vp, vp, vp, vp]
+        L.gp_extract.restype = st
+        L.gp_label_mask.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
+        L.gp_label_mask.restype = st
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != GP_OK:
+        raise GpError(status, load_library().gp_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+def make_image(img, mask=None, saturation: float = 0.0) -> GpImage:
+    """GpImage for a 2-D CUDA tensor of uint16 or float32 (rows may be
+    strided; columns must be contiguous)."""
+    import torch
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("image must be 2-D with contiguous rows")
+    if img.dtype == torch.uint16:
+        dt = GP_U16
+    elif img.dtype == torch.float32:
+        dt = GP_F32
+    else:
+        raise ValueError(f"unsupported dtype {img.dtype}")
+    if mask is not None:
+        if mask.dtype != torch.uint8 or not mask.is_contiguous() or tuple(mask.shape) != tuple(img.shape):
+            raise ValueError("mask must be a contiguous uint8 tensor of the image's shape")
+    H, W = img.shape
+    return GpImage(img.data_ptr(), dt, W, H, img.stride(0), _ptr(mask), float(saturation))
+
+
+def _taps(kernel):
+    k = np.ascontiguousarray(np.asarray(kernel, dtype=np.float32))
+    if k.ndim != 2:
+        raise ValueError("kernel must be 2-D")
+    return k, k.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _radii(radii):
+    r = np.ascontiguousarray(np.asarray(radii, dtype=np.float32).reshape(-1))
+    return r, r.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def allocate_catalog(capacity: int, device):
+    """Device tensors for a catalog of `capacity` rows and its GpCatalog."""
+    import torch
+    cols = {"n": torch.zeros(1, dtype=torch.int32, device=device)}
+    for name, dt in CATALOG_COLUMNS:
+        cols[name] = torch.zeros(max(capacity, 1), dtype=getattr(torch, dt), device=device)
+    cat = GpCatalog(capacity, cols["n"].data_ptr(), *[cols[n].data_ptr() for n, _ in CATALOG_COLUMNS])
+    return cols, cat
+
+
+# ---------------------------------------------------------- the context ---
+class Context:
+    """One gp_ctx: a device and a workspace arena.  Calls on one context must
+    be ordered (one stream); use one context per concurrent stream."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        L = load_library()
+        h = C.c_void_p()
+        _check(L.gp_ctx_create(int(device), int(workspace_bytes), C.byref(h)))
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().gp_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        """Synchronise the stream and raise if the device reported an error."""
+        _check(load_library().gp_ctx_sync(self._h, _stream_handle(stream)))
+
+    def set_timing(self, enable: bool = True):
+        _check(load_library().gp_ctx_set_timing(self._h, 1 if enable else 0))
+
+    def stats(self):
+        """Per-stage device milliseconds summed over the calls since the
+        previous stats() (see gp_ctx_stats), the call count and the number of
+        kernels the most recent call launched."""
+        st = GpStats()
+        _check(load_library().gp_ctx_stats(self._h, C.byref(st)))
+        return {"calls": st.calls, "launches": st.launches,
+                "ms": {n: float(st.ms[i]) for i, n in enumerate(STAGE_NAMES)}}
+
+    # ------------------------------------------------------- operations ---
+    def gp_background(self, img, mesh, filter_size=3, clip_k=3.0, clip_maxiter=10, mask=None, saturation=0.0,
+                      maps=False, stream=None):
+        import torch
+        gi = make_image(img, mask, saturation)
+        H, W = img.shape
+        mx, my = -(-W // mesh), -(-H // mesh)
+        out = {"bkg_mesh": torch.empty((my, mx), dtype=torch.float32, device=img.device),
+               "rms_mesh": torch.empty((my, mx), dtype=torch.float32, device=img.device), "mesh": mesh}
+        if maps:
+            out["bkg_map"] = torch.empty((H, W), dtype=torch.float32, device=img.device)
+            out["rms_map"] = torch.empty((H, W), dtype=torch.float32, device=img.device)
+        b = GpBkg(mesh, mx, my, out["bkg_mesh"].data_ptr(), out["rms_mesh"].data_ptr(),
+                  _ptr(out.get("bkg_map")), _ptr(out.get("rms_map")))
+        p = GpBkgParams(mesh, filter_size, clip_k, clip_maxiter)
+        _check(load_library().gp_background(self._h, C.byref(gi), C.byref(p), C.byref(b), _stream_handle(stream)))
+        return out
+
+    @staticmethod
+    def _bkg_struct(bkg):
+        my, mx = bkg["bkg_mesh"].shape
+        return GpBkg(bkg["mesh"], mx, my, bkg["bkg_mesh"].data_ptr(), bkg["rms_mesh"].data_ptr(), None, None)
+
+    def gp_detect(self, img, bkg, kernel, thresh, minarea, capacity, mask=None, saturation=0.0, mask_out=False,
+                  count_near=False, stream=None):
+        import torch
+        gi = make_image(img, mask, saturation)
+        H, W = img.shape
+        k, kp = _taps(kernel)
+        out = {"segmap": torch.empty((H, W), dtype=torch.int32, device=img.device)}
+        if mask_out:
+            out["mask"] = torch.empty((H, W), dtype=torch.uint8, device=img.device)
+        if count_near:
+            out["nnear"] = torch.zeros(1, dtype=torch.int32, device=img.device)
+        dp = GpDetParams(kp, k.shape[1], k.shape[0], float(thresh), int(minarea), _ptr(out.get("mask")),
+                         _ptr(out.get("nnear")))
+        cols, cat = allocate_catalog(capacity, img.device)
+        b = self._bkg_struct(bkg)
+        _check(load_library().gp_detect(self._h, C.byref(gi), C.byref(b), C.byref(dp), out["segmap"].data_ptr(),
+                                        C.byref(cat), _stream_handle(stream)))
+        out["catalog"] = cols
+        return out
+
+    def gp_aperture(self, img, bkg, x, y, radii, gain=0.0, mask=None, saturation=0.0, stream=None):
+        import torch
+        gi = make_image(img, mask, saturation)
+        r, rp = _radii(radii)
+        n = int(x.numel())
+        x = x.to(device=img.device, dtype=torch.float64).contiguous()
+        y = y.to(device=img.device, dtype=torch.float64).contiguous()
+        flux = torch.empty((max(n, 1), r.size), dtype=torch.float64, device=img.device)
+        ferr = torch.empty_like(flux)
+        fl = torch.empty((max(n, 1), r.size), dtype=torch.int32, device=img.device)
+        ap = GpApParams(rp, r.size, float(gain))
+        b = self._bkg_struct(bkg)
+        _check(load_library().gp_aperture(self._h, C.byref(gi), C.byref(b), x.data_ptr(), y.data_ptr(), n,
+                                          C.byref(ap), flux.data_ptr(), ferr.data_ptr(), fl.data_ptr(),
+                                          _stream_handle(stream)))
+        return flux[:n], ferr[:n], fl[:n]
+
+    def gp_extract(self, img, mesh, kernel, thresh, minarea, radii, gain, capacity, mask=None, saturation=0.0,
+                   filter_size=3, clip_k=3.0, clip_maxiter=10, maps=False, mask_out=False, count_near=False,
+                   stream=None):
+        ex = Extractor(self, tuple(img.shape), img.dtype, mesh, kernel, thresh, minarea, radii, gain, capacity,
+                       saturation=saturation, filter_size=filter_size, clip_k=clip_k, clip_maxiter=clip_maxiter,
+                       maps=maps, mask_out=mask_out, count_near=count_near, device=img.device)
+        ex.run(img, mask=mask, stream=stream)
+        return ex.out
+
+    def gp_label_mask(self, mask, minarea=1, stream=None):
+        import torch
+        if not mask.is_cuda or mask.dtype != torch.uint8 or not mask.is_contiguous():
+            raise ValueError("mask must be a contiguous uint8 CUDA tensor")
+        H, W = mask.shape
+        seg = torch.empty((H, W), dtype=torch.int32, device=mask.device)
+        n = torch.zeros(1, dtype=torch.int32, device=mask.device)
+        _check(load_library().gp_label_mask(self._h, mask.data_ptr(), W, H, int(minarea), seg.data_ptr(),
+                                            n.data_ptr(), _stream_handle(stream)))
+        return seg, n
+
+
+class Extractor:
+    """Pre-allocated outputs for repeated gp_extract calls on frames of one
+    shape: `run` allocates nothing, so it can be timed or captured."""
+
+    def __init__(self, ctx: Context, shape, dtype, mesh, kernel, thresh, minarea, radii, gain, capacity,
+                 saturation=0.0, filter_size=3, clip_k=3.0, clip_maxiter=10, maps=False, mask_out=False,
+                 count_near=False, device="cuda"):
+        import torch
+        self.ctx = ctx
+        H, W = shape
+        self.shape = (H, W)
+        mx, my = -(-W // mesh), -(-H // mesh)
+        self._k, kp = _taps(kernel)
+        self._r, rp = _radii(radii)
+        nr = self._r.size
+        self.saturation = float(saturation)
+        o = {"bkg_mesh": torch.empty((my, mx), dtype=torch.float32, device=device),
+             "rms_mesh": torch.empty((my, mx), dtype=torch.float32, device=device), "mesh": mesh,
+             "segmap": torch.empty((H, W), dtype=torch.int32, device=device)}
+        if maps:
+            o["bkg_map"] = torch.empty((H, W), dtype=torch.float32, device=device)
+            o["rms_map"] = torch.empty((H, W), dtype=torch.float32, device=device)
+        if mask_out:
+            o["mask"] = torch.empty((H, W), dtype=torch.uint8, device=device)
+        if count_near:
+            o["nnear"] = torch.zeros(1, dtype=torch.int32, device=device)
+        cols, self._cat = allocate_catalog(capacity, device)
+        o["catalog"] = cols
+        o["flux"] = torch.zeros((max(capacity, 1), max(nr, 1)), dtype=torch.float64, device=device)
+        o["fluxerr"] = torch.zeros_like(o["flux"])
+        o["apflags"] = torch.zeros((max(capacity, 1), max(nr, 1)), dtype=torch.int32, device=device)
+        self.out = o
+        self._bp = GpBkgParams(mesh, filter_size, clip_k, clip_maxiter)
+        self._dp = GpDetParams(kp, self._k.shape[1], self._k.shape[0], float(thresh), int(minarea),
+                               _ptr(o.get("mask")), _ptr(o.get("nnear")))
+        self._ap = GpApParams(rp, nr, float(gain))
+        self._bkg = GpBkg(mesh, mx, my, o["bkg_mesh"].data_ptr(), o["rms_mesh"].data_ptr(), _ptr(o.get("bkg_map")),
+                          _ptr(o.get("rms_map")))
+        self._lib = load_library()
+
+    def run(self, img, mask=None, stream=None):
+        gi = make_image(img, mask, self.saturation)
+        _check(self._lib.gp_extract(self.ctx.handle, C.byref(gi), C.byref(self._bp), C.byref(self._dp),
+                                    C.byref(self._ap), C.byref(self._bkg), self.out["segmap"].data_ptr(),
+                                    C.byref(self._cat), self.out["flux"].data_ptr(), self.out["fluxerr"].data_ptr(),
+                                    self.out["apflags"].data_ptr(), _stream_handle(stream)))
+        return self.out
+
+    def catalog_host(self):
+        """Copy the catalog rows that were filled to host numpy arrays."""
+        n = int(self.out["catalog"]["n"].item())
+        m = min(n, self._cat.capacity)
+        cat = {k: v[:m].cpu().numpy() for k, v in self.out["catalog"].items() if k != "n"}
+        nr = self._r.size
+        cat["flux"] = self.out["flux"][:m, :nr].cpu().numpy()
+        cat["fluxerr"] = self.out["fluxerr"][:m, :nr].cpu().numpy()
+        cat["apflags"] = self.out["apflags"][:m, :nr].cpu().numpy()
+        return n, cat

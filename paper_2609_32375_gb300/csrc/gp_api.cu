@@ -1,0 +1,612 @@
+// gp_api.cu -- the C ABI (include/gpphot.h): context and workspace arena,
+// host-side argument checks, and the launch sequence of each operation.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "gp_internal.cuh"
+#include "gp_launch.h"
+
+using namespace gp;
+
+constexpr int RING = 256;
+constexpr int NMARK = GP_NSTAGES + 1;
+
+struct gp_ctx {
+    int device;
+    char* arena;
+    size_t arena_bytes;
+    int* dstatus;          // device status word (first bytes of the arena)
+    char* base;            // first byte after the status block
+    // stage timing
+    int timing;
+    cudaEvent_t ev[RING][NMARK];
+    int ev_made;
+    int nrec;              // calls recorded since the last gp_ctx_stats
+    int slot;              // slot of the current call
+    int launches;          // kernels launched by the current / last call
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+gp_status fail(gp_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+gp_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(GP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GP_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// record the event of stage boundary k of the current call (timing on)
+void mark(gp_ctx* ctx, int k, cudaStream_t st)
+{
+    if (ctx->timing) cudaEventRecord(ctx->ev[ctx->slot][k], st);
+}
+
+void begin_call(gp_ctx* ctx, cudaStream_t st)
+{
+    ctx->launches = 0;
+    if (!ctx->timing) return;
+    ctx->slot = ctx->nrec % RING;
+    ctx->nrec++;
+    mark(ctx, 0, st);
+}
+
+// mark boundaries from..to (stages the call does not run take no time)
+void mark_to(gp_ctx* ctx, int from, int to, cudaStream_t st)
+{
+    for (int k = from; k <= to; ++k) mark(ctx, k, st);
+}
+
+constexpr size_t ALIGN = 256;
+constexpr size_t STATUS_BYTES = 256;
+
+// bump allocator over the arena; sizes are accumulated even past the end so
+// that the total requirement can be reported
+struct Carver {
+    char* base;
+    size_t cap;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t n)
+    {
+        off = (off + ALIGN - 1) & ~(ALIGN - 1);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+    bool ok() const { return off <= cap; }
+};
+
+struct BkgWork {
+    double *bkg_raw, *rms_raw, *tmp_b, *tmp_r;
+    int *valid, *tmp_v;
+};
+
+struct SplineWork {
+    double* scratch;
+    float4 *tab_b, *tab_r;
+};
+
+struct DetWork {
+    Tiles T;
+    Pieces P;
+    Comps C;
+    int* counters;   // [0] pieces, [1] comps
+};
+
+int piece_cap_for(int64_t npix) { return (int)std::max<int64_t>(65536, npix / 64); }
+int comp_cap_for(int64_t npix, int capacity)
+{
+    int64_t c = std::max<int64_t>(65536, npix / 32);
+    if (capacity > c) c = capacity;
+    return (int)std::min<int64_t>(c, 1ll << 30);
+}
+
+void bucket_geometry(int64_t npix, int* shift, int* nb)
+{
+    int s = 0;
+    while (((npix - 1) >> s) + 1 > 65536) ++s;
+    *shift = s;
+    *nb = (int)(((npix - 1) >> s) + 1);
+}
+
+void carve_bkg(Carver& cv, int nbox, BkgWork& w)
+{
+    w.bkg_raw = cv.take<double>(nbox);
+    w.rms_raw = cv.take<double>(nbox);
+    w.tmp_b = cv.take<double>(nbox);
+    w.tmp_r = cv.take<double>(nbox);
+    w.valid = cv.take<int>(nbox);
+    w.tmp_v = cv.take<int>(nbox);
+}
+
+void carve_spline(Carver& cv, int Mx, int My, SplineWork& w)
+{
+    w.scratch = cv.take<double>(spline_scratch_doubles(Mx, My));
+    w.tab_b = cv.take<float4>((size_t)Mx * My);
+    w.tab_r = cv.take<float4>((size_t)Mx * My);
+}
+
+void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w)
+{
+    const int64_t npix = (int64_t)W * H;
+    w.T.ntx = (W + TX - 1) / TX;
+    w.T.nty = (H + TY - 1) / TY;
+    const int64_t ntiles = (int64_t)w.T.ntx * w.T.nty;
+    w.T.edges = cv.take<int16_t>((size_t)ntiles * EDGE_PER_TILE);
+    w.T.piece_base = cv.take<int>(ntiles);
+    w.T.piece_cnt = cv.take<int>(ntiles);
+    w.counters = cv.take<int>(64);
+    w.P.count = w.counters + 0;
+    w.P.cap = piece_cap_for(npix);
+    w.P.root = cv.take<uint32_t>(w.P.cap);
+    w.P.npix = cv.take<int>(w.P.cap);
+    w.P.bbox = cv.take<int4>(w.P.cap);
+    w.P.parent = cv.take<int>(w.P.cap);
+    w.P.agg_min = cv.take<uint32_t>(w.P.cap);
+    w.P.agg_npix = cv.take<int>(w.P.cap);
+    w.P.agg_bbox = cv.take<int4>(w.P.cap);
+    w.C.count = w.counters + 32;
+    w.C.cap = comp_cap_for(npix, capacity);
+    w.C.label = cv.take<uint32_t>(w.C.cap);
+    w.C.npix = cv.take<int>(w.C.cap);
+    w.C.bbox = cv.take<int4>(w.C.cap);
+    w.C.perm = cv.take<int>(w.C.cap);
+    w.C.slots = cv.take<int>(w.C.cap);
+    bucket_geometry(npix, &w.C.shift, &w.C.nb);
+    w.C.bcnt = cv.take<int>(w.C.nb);
+    w.C.boff = cv.take<int>(w.C.nb);
+    w.C.bcur = cv.take<int>(w.C.nb);
+}
+
+gp_status check_ctx(gp_ctx* ctx)
+{
+    if (!ctx) return fail(GP_ERR_INVALID_ARG, "null context");
+    int dev = -1;
+    GP_CUDA(cudaGetDevice(&dev));
+    if (dev != ctx->device) GP_CUDA(cudaSetDevice(ctx->device));
+    return GP_OK;
+}
+
+gp_status check_image(const gp_image* img)
+{
+    if (!img || !img->data) return fail(GP_ERR_INVALID_ARG, "null image or image data");
+    if (img->dtype != GP_U16 && img->dtype != GP_F32) return fail(GP_ERR_INVALID_ARG, "dtype must be GP_U16 or GP_F32");
+    if (img->width < 1 || img->height < 1) return fail(GP_ERR_INVALID_ARG, "image size %dx%d", img->width, img->height);
+    if ((int64_t)img->width * img->height > 0x7fffffffll)
+        return fail(GP_ERR_INVALID_ARG, "image of %lld pixels exceeds 2^31-1", (long long)img->width * img->height);
+    if (img->pitch < img->width) return fail(GP_ERR_INVALID_ARG, "pitch %lld < width %d", (long long)img->pitch, img->width);
+    return GP_OK;
+}
+
+Image to_image(const gp_image* img)
+{
+    Image im;
+    im.data = img->data;
+    im.pitch = img->pitch;
+    im.mask = img->mask;
+    im.W = img->width;
+    im.H = img->height;
+    im.sat = img->saturation;
+    im.is_f32 = img->dtype == GP_F32;
+    return im;
+}
+
+gp_status check_bkg_params(const gp_image* img, const gp_bkg_params* p)
+{
+    if (!p) return fail(GP_ERR_INVALID_ARG, "null background parameters");
+    const int maxmesh = img->dtype == GP_U16 ? 256 : 128;
+    if (p->mesh < 16 || p->mesh > maxmesh)
+        return fail(GP_ERR_INVALID_ARG, "mesh %d outside [16, %d] for this dtype", p->mesh, maxmesh);
+    if (p->filter_size < 1 || p->filter_size > 7 || !(p->filter_size & 1))
+        return fail(GP_ERR_INVALID_ARG, "filter_size %d must be odd in [1, 7]", p->filter_size);
+    if (!(p->clip_k >= 1.f) || !isfinite(p->clip_k)) return fail(GP_ERR_INVALID_ARG, "clip_k must be >= 1");
+    if (p->clip_maxiter < 0 || p->clip_maxiter > 1000) return fail(GP_ERR_INVALID_ARG, "clip_maxiter out of range");
+    return GP_OK;
+}
+
+gp_status check_bkg(const gp_image* img, const gp_bkg* b, bool need_meshes_only)
+{
+    if (!b || !b->bkg_mesh || !b->rms_mesh) return fail(GP_ERR_INVALID_ARG, "background meshes are null");
+    if (b->mesh < 16) return fail(GP_ERR_INVALID_ARG, "background mesh %d < 16", b->mesh);
+    const int mx = (img->width + b->mesh - 1) / b->mesh, my = (img->height + b->mesh - 1) / b->mesh;
+    if (b->mx != mx || b->my != my)
+        return fail(GP_ERR_INVALID_ARG, "background mesh %dx%d does not match the image (%dx%d)", b->mx, b->my, mx, my);
+    (void)need_meshes_only;
+    return GP_OK;
+}
+
+gp_status check_det(const gp_det_params* p, float* taps)
+{
+    if (!p || !p->kernel) return fail(GP_ERR_INVALID_ARG, "null detection parameters or kernel");
+    if (p->kw < 1 || p->kh < 1 || !(p->kw & 1) || !(p->kh & 1) || p->kw > 2 * HMAX + 1 || p->kh > 2 * HMAX + 1)
+        return fail(GP_ERR_INVALID_ARG, "kernel %dx%d must have odd sides <= %d", p->kw, p->kh, 2 * HMAX + 1);
+    double s = 0;
+    for (int i = 0; i < p->kw * p->kh; ++i) {
+        if (!isfinite(p->kernel[i])) return fail(GP_ERR_INVALID_ARG, "kernel tap %d is not finite", i);
+        s += p->kernel[i];
+    }
+    if (s == 0.0) return fail(GP_ERR_INVALID_ARG, "kernel taps sum to zero");
+    for (int i = 0; i < p->kw * p->kh; ++i) taps[i] = (float)((double)p->kernel[i] / s);
+    if (!(p->thresh > 0.f) || !isfinite(p->thresh)) return fail(GP_ERR_INVALID_ARG, "thresh must be > 0");
+    if (p->minarea < 1) return fail(GP_ERR_INVALID_ARG, "minarea must be >= 1");
+    return GP_OK;
+}
+
+gp_status check_ap(const gp_ap_params* p, bool allow_empty)
+{
+    if (!p) return fail(GP_ERR_INVALID_ARG, "null aperture parameters");
+    if (p->nr < (allow_empty ? 0 : 1) || p->nr > MAX_NR) return fail(GP_ERR_INVALID_ARG, "nr %d outside [1, %d]", p->nr, MAX_NR);
+    if (p->nr && !p->radii) return fail(GP_ERR_INVALID_ARG, "null radii");
+    for (int k = 0; k < p->nr; ++k)
+        if (!(p->radii[k] > 0.f) || p->radii[k] > 1024.f) return fail(GP_ERR_INVALID_ARG, "radius %d out of (0, 1024]", k);
+    return GP_OK;
+}
+
+gp_status check_cat(const gp_catalog* c)
+{
+    if (!c || !c->n) return fail(GP_ERR_INVALID_ARG, "null catalog or count pointer");
+    if (c->capacity < 0) return fail(GP_ERR_INVALID_ARG, "negative capacity");
+    if (c->capacity > 0 && (!c->label || !c->npix || !c->flux_iso || !c->x || !c->y || !c->x2 || !c->y2 || !c->xy ||
+                            !c->xmin || !c->xmax || !c->ymin || !c->ymax || !c->peak || !c->xpeak || !c->ypeak ||
+                            !c->flags))
+        return fail(GP_ERR_INVALID_ARG, "a catalog column is null");
+    return GP_OK;
+}
+
+SplineTab make_tab(const float4* node, int W, int H, int mesh)
+{
+    SplineTab s;
+    s.node = node;
+    s.ax = make_axis(W, mesh);
+    s.ay = make_axis(H, mesh);
+    return s;
+}
+
+gp_status run_spline(Carver& cv, const gp_bkg* b, int W, int H, SplineTab* sb, SplineTab* sr, cudaStream_t st)
+{
+    SplineWork w;
+    carve_spline(cv, b->mx, b->my, w);
+    if (!cv.ok()) return GP_ERR_OOM;
+    Axis ax = make_axis(W, b->mesh), ay = make_axis(H, b->mesh);
+    GP_CUDA(launch_spline_tables(b->bkg_mesh, ax, ay, w.scratch, w.tab_b, st));
+    GP_CUDA(launch_spline_tables(b->rms_mesh, ax, ay, w.scratch, w.tab_r, st));
+    *sb = make_tab(w.tab_b, W, H, b->mesh);
+    *sr = make_tab(w.tab_r, W, H, b->mesh);
+    return GP_OK;
+}
+
+gp_status oom(const Carver& cv)
+{
+    return fail(GP_ERR_OOM, "workspace needs %zu bytes, the context arena has %zu", cv.off + STATUS_BYTES,
+                cv.cap + STATUS_BYTES);
+}
+
+gp_status run_background(gp_ctx* ctx, Carver& cv, const gp_image* img, const gp_bkg_params* p, gp_bkg* bkg,
+                         cudaStream_t st, SplineTab* sb, SplineTab* sr)
+{
+    const int W = img->width, H = img->height, B = p->mesh;
+    const int Mx = (W + B - 1) / B, My = (H + B - 1) / B;
+    bkg->mesh = B; bkg->mx = Mx; bkg->my = My;
+    BkgWork w;
+    carve_bkg(cv, Mx * My, w);
+    if (!cv.ok()) return oom(cv);
+    Image im = to_image(img);
+    GP_CUDA(launch_boxstats(im, B, (double)p->clip_k, p->clip_maxiter, w.bkg_raw, w.rms_raw, w.valid, nullptr, st));
+    mark(ctx, 1, st);
+    GP_CUDA(launch_mesh_finalize(w.bkg_raw, w.rms_raw, w.valid, w.tmp_b, w.tmp_r, w.tmp_v, Mx, My, p->filter_size,
+                                 bkg->bkg_mesh, bkg->rms_mesh, st));
+    ctx->launches += 2;
+    if (sb || bkg->bkg_map || bkg->rms_map) {
+        SplineTab tb, tr;
+        gp_status s = run_spline(cv, bkg, W, H, &tb, &tr, st);
+        if (s == GP_ERR_OOM) return oom(cv);
+        if (s != GP_OK) return s;
+        ctx->launches += 4;
+        if (bkg->bkg_map || bkg->rms_map) {
+            GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
+            ctx->launches += 1;
+        }
+        if (sb) { *sb = tb; *sr = tr; }
+    }
+    mark(ctx, 2, st);
+    return GP_OK;
+}
+
+gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineTab& sb, const SplineTab& sr,
+                     const float* taps, const gp_det_params* p, uint32_t* segmap, gp_catalog* cat,
+                     const float* radii, int nr, float gain, double* flux, double* fluxerr, uint32_t* apflags,
+                     cudaStream_t st)
+{
+    const int W = img->width, H = img->height;
+    DetWork w;
+    carve_det(cv, W, H, cat->capacity, w);
+    if (!cv.ok()) return oom(cv);
+    Image im = to_image(img);
+    GP_CUDA(cudaMemsetAsync(w.counters, 0, 64 * sizeof(int), st));
+    GP_CUDA(cudaMemsetAsync(w.C.bcnt, 0, (size_t)w.C.nb * sizeof(int), st));
+    GP_CUDA(cudaMemsetAsync(w.C.bcur, 0, (size_t)w.C.nb * sizeof(int), st));
+    if (p->nnear) GP_CUDA(cudaMemsetAsync(p->nnear, 0, sizeof(int), st));
+    GP_CUDA(launch_detect_tiles(im, sb, sr, taps, p->kw, p->kh, p->thresh, p->minarea, segmap, p->mask_out, p->nnear,
+                                nullptr, w.T, w.P, w.C, ctx->dstatus, st));
+    mark(ctx, 3, st);
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, segmap, W, H, p->minarea, ctx->dstatus, st));
+    mark(ctx, 4, st);
+    GP_CUDA(launch_rank(w.C, cat->n, cat->capacity, true, ctx->dstatus, st));
+    mark(ctx, 5, st);
+    GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
+    mark(ctx, 6, st);
+    ctx->launches += 1 + 3 + 4 + 1;
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gp_last_error(void) { return g_err.c_str(); }
+
+gp_status gp_ctx_create(int device, size_t workspace_bytes, gp_ctx** out)
+{
+    if (!out) return fail(GP_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    int n = 0;
+    GP_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(GP_ERR_INVALID_ARG, "device %d not present (%d devices)", device, n);
+    GP_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    GP_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major * 10 + prop.minor < 100)
+        return fail(GP_ERR_CUDA, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major, prop.minor);
+    if (workspace_bytes == 0) workspace_bytes = (size_t)2 << 30;
+    gp_ctx* c = new gp_ctx;
+    c->device = device;
+    c->timing = 0;
+    c->ev_made = 0;
+    c->nrec = 0;
+    c->slot = 0;
+    c->launches = 0;
+    c->arena_bytes = workspace_bytes + STATUS_BYTES;
+    cudaError_t e = cudaMalloc(&c->arena, c->arena_bytes);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(GP_ERR_OOM, "cudaMalloc of %zu workspace bytes: %s", workspace_bytes, cudaGetErrorString(e));
+    }
+    c->dstatus = reinterpret_cast<int*>(c->arena);
+    c->base = c->arena + STATUS_BYTES;
+    e = cudaMemset(c->dstatus, 0, STATUS_BYTES);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(c->arena);
+        delete c;
+        return cuda_fail(e, "context initialisation");
+    }
+    *out = c;
+    return GP_OK;
+}
+
+void gp_ctx_destroy(gp_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->ev_made)
+        for (int i = 0; i < RING; ++i)
+            for (int k = 0; k < NMARK; ++k) cudaEventDestroy(ctx->ev[i][k]);
+    cudaFree(ctx->arena);
+    delete ctx;
+}
+
+gp_status gp_ctx_set_timing(gp_ctx* ctx, int32_t enable)
+{
+    gp_status s = check_ctx(ctx);
+    if (s != GP_OK) return s;
+    if (enable && !ctx->ev_made) {
+        for (int i = 0; i < RING; ++i)
+            for (int k = 0; k < NMARK; ++k) GP_CUDA(cudaEventCreate(&ctx->ev[i][k]));
+        ctx->ev_made = 1;
+    }
+    ctx->timing = enable ? 1 : 0;
+    ctx->nrec = 0;
+    return GP_OK;
+}
+
+gp_status gp_ctx_stats(gp_ctx* ctx, gp_stats* out)
+{
+    gp_status s = check_ctx(ctx);
+    if (s != GP_OK) return s;
+    if (!out) return fail(GP_ERR_INVALID_ARG, "null stats output");
+    memset(out, 0, sizeof *out);
+    out->launches = ctx->launches;
+    if (!ctx->ev_made) return GP_OK;
+    const int n = ctx->nrec < RING ? ctx->nrec : RING;
+    for (int i = 0; i < n; ++i) {
+        GP_CUDA(cudaEventSynchronize(ctx->ev[i][NMARK - 1]));
+        for (int k = 0; k < GP_NSTAGES; ++k) {
+            float ms = 0.f;
+            GP_CUDA(cudaEventElapsedTime(&ms, ctx->ev[i][k], ctx->ev[i][k + 1]));
+            out->ms[k] += ms;
+        }
+    }
+    out->calls = n;
+    ctx->nrec = 0;
+    return GP_OK;
+}
+
+gp_status gp_ctx_sync(gp_ctx* ctx, gp_stream stream)
+{
+    gp_status s = check_ctx(ctx);
+    if (s != GP_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GP_CUDA(cudaStreamSynchronize(st));
+    int h = 0;
+    GP_CUDA(cudaMemcpy(&h, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    GP_CUDA(cudaMemset(ctx->dstatus, 0, sizeof(int)));
+    if (h == GP_ERR_CAPACITY) return fail(GP_ERR_CAPACITY, "more segments than catalog rows (see *cat.n)");
+    if (h == GP_ERR_TIMEOUT) return fail(GP_ERR_TIMEOUT, "a bounded device-side walk gave up");
+    if (h == GP_ERR_INTERNAL) return fail(GP_ERR_INTERNAL, "an internal device table overflowed; results are incomplete");
+    if (h != 0) return fail((gp_status)h, "device status %d", h);
+    return GP_OK;
+}
+
+size_t gp_workspace_bytes(int32_t width, int32_t height, int32_t mesh, int32_t capacity)
+{
+    if (width < 1 || height < 1 || mesh < 1) return 0;
+    Carver cv{nullptr, 0};
+    const int Mx = (width + mesh - 1) / mesh, My = (height + mesh - 1) / mesh;
+    BkgWork b;
+    carve_bkg(cv, Mx * My, b);
+    SplineWork s;
+    carve_spline(cv, Mx, My, s);
+    DetWork d;
+    carve_det(cv, width, height, capacity > 0 ? capacity : 0, d);
+    return cv.off + STATUS_BYTES + ALIGN;
+}
+
+gp_status gp_background(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, gp_bkg* bkg, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg_params(img, p)) != GP_OK) return s;
+    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    begin_call(ctx, st);
+    s = run_background(ctx, cv, img, p, bkg, st, nullptr, nullptr);
+    mark_to(ctx, 3, 6, st);
+    return s;
+}
+
+gp_status gp_detect(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* p, uint32_t* segmap,
+                    gp_catalog* cat, gp_stream stream)
+{
+    gp_status s;
+    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg(img, bkg, true)) != GP_OK) return s;
+    if ((s = check_det(p, taps)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if (!segmap) return fail(GP_ERR_INVALID_ARG, "null segmap");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    mark(ctx, 1, st);
+    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    ctx->launches += 4;
+    mark(ctx, 2, st);
+    return run_detect(ctx, cv, img, sb, sr, taps, p, segmap, cat, nullptr, 0, 0.f, nullptr, nullptr, nullptr, st);
+}
+
+gp_status gp_aperture(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const double* x, const double* y, int32_t n,
+                      const gp_ap_params* p, double* flux, double* fluxerr, uint32_t* flags, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg(img, bkg, true)) != GP_OK) return s;
+    if ((s = check_ap(p, false)) != GP_OK) return s;
+    if (n < 0) return fail(GP_ERR_INVALID_ARG, "negative source count");
+    if (n > 0 && (!x || !y || !flux || !fluxerr || !flags)) return fail(GP_ERR_INVALID_ARG, "null aperture array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    mark(ctx, 1, st);
+    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    ctx->launches += 4;
+    mark_to(ctx, 2, 5, st);
+    if (n > 0) {
+        GP_CUDA(launch_aperture(to_image(img), sb, sr, x, y, n, p->radii, p->nr, p->gain, flux, fluxerr, flags, st));
+        ctx->launches += 1;
+    }
+    mark(ctx, 6, st);
+    return GP_OK;
+}
+
+gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp, const gp_det_params* dp,
+                     const gp_ap_params* ap, gp_bkg* bkg, uint32_t* segmap, gp_catalog* cat, double* flux,
+                     double* fluxerr, uint32_t* apflags, gp_stream stream)
+{
+    gp_status s;
+    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg_params(img, bp)) != GP_OK) return s;
+    if ((s = check_det(dp, taps)) != GP_OK) return s;
+    if ((s = check_ap(ap, true)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
+    if (!segmap) return fail(GP_ERR_INVALID_ARG, "null segmap");
+    if (ap->nr > 0 && cat->capacity > 0 && (!flux || !fluxerr || !apflags))
+        return fail(GP_ERR_INVALID_ARG, "null aperture output array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    s = run_background(ctx, cv, img, bp, bkg, st, &sb, &sr);
+    if (s != GP_OK) return s;
+    return run_detect(ctx, cv, img, sb, sr, taps, dp, segmap, cat, ap->radii, ap->nr, ap->gain, flux, fluxerr, apflags,
+                      st);
+}
+
+gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t height, int32_t minarea,
+                        uint32_t* segmap, int32_t* n_out, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if (!mask || !segmap) return fail(GP_ERR_INVALID_ARG, "null mask or segmap");
+    if (width < 1 || height < 1 || (int64_t)width * height > 0x7fffffffll)
+        return fail(GP_ERR_INVALID_ARG, "image size %dx%d", width, height);
+    if (minarea < 1) return fail(GP_ERR_INVALID_ARG, "minarea must be >= 1");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    DetWork w;
+    carve_det(cv, width, height, 0, w);
+    if (!cv.ok()) return oom(cv);
+    Image im{};
+    im.W = width;
+    im.H = height;
+    SplineTab none{};
+    begin_call(ctx, st);
+    mark_to(ctx, 1, 2, st);
+    GP_CUDA(cudaMemsetAsync(w.counters, 0, 64 * sizeof(int), st));
+    GP_CUDA(cudaMemsetAsync(w.C.bcnt, 0, (size_t)w.C.nb * sizeof(int), st));
+    GP_CUDA(launch_detect_tiles(im, none, none, nullptr, 1, 1, 1.f, minarea, segmap, nullptr, nullptr, mask, w.T, w.P,
+                                w.C, ctx->dstatus, st));
+    mark(ctx, 3, st);
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, segmap, width, height, minarea, ctx->dstatus, st));
+    mark(ctx, 4, st);
+    GP_CUDA(launch_rank(w.C, n_out, -1, false, ctx->dstatus, st));
+    mark_to(ctx, 5, 6, st);
+    ctx->launches += 1 + 3 + 2;
+    return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// gp_internal.cuh -- device helpers and internal layouts of the extraction
+// library (sm_103a).  Not part of the public ABI (include/gpphot.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gpphot.h"
+
+namespace gp {
+
+// ------------------------------------------------------------ constants ---
+constexpr int TX = 64;           // detection tile width  (pixels)
+constexpr int TY = 32;           // detection tile height
+constexpr int TNPIX = TX * TY;
+constexpr int MAXROOT = (TX / 2) * (TY / 2);  // most 8-connected segments a tile can hold
+constexpr int HMAX = 7;          // largest filter half-size (15 x 15 taps)
+constexpr int SW = TX + 2 * HMAX;
+constexpr int SH = TY + 2 * HMAX;
+constexpr int EDGE_PER_TILE = 2 * TY + 2 * TX;   // colL, colR, rowT, rowB
+constexpr int MAX_NR = 8;        // most aperture radii per call
+constexpr int NJMAX = 8;         // most mesh node rows one detection tile touches
+
+// bounded-loop limit for union-find walks (a cycle would be a bug; the walk
+// gives up, records GP_ERR_TIMEOUT and the result is flagged invalid)
+constexpr int WALK_LIMIT = 1 << 22;
+
+__device__ __forceinline__ void set_status(int* st, int code)
+{
+    atomicCAS(st, 0, code);  // the first error wins
+}
+
+// -------------------------------------------------------------- spline ---
+// Mesh nodes along one axis: node i sits at i*B + (B-1)/2, except the last,
+// which sits at the centre of the (possibly partial) last box.
+struct Axis {
+    int n;         // nodes
+    float B;       // node spacing (box side)
+    float t0;      // first node position
+    float tl;      // last node position
+    float hl;      // width of the last interval (tl - t[n-2])
+};
+
+// Coefficients of the natural-spline value at coordinate t, written as
+//   f = v[i] + b (v[i1] - v[i]) + c0 M[i] + c1 M[i1]
+// with v the node values and M their second derivatives.  Inside the node
+// range this is the cubic spline; beyond the end nodes it is the linear
+// continuation with the end slope (the natural spline's second derivative is
+// zero there).  Written in this shifted form so that constant data give the
+// constant back exactly.
+struct AxCoef {
+    int i, i1;
+    float b, c0, c1;
+};
+
+__host__ __device__ inline Axis make_axis(int N, int B)
+{
+    Axis a;
+    a.n = (N + B - 1) / B;
+    a.B = (float)B;
+    int w0 = (B < N ? B : N);
+    a.t0 = 0.5f * (float)(w0 - 1);
+    int wl = N - (a.n - 1) * B;
+    a.tl = (float)((a.n - 1) * B) + 0.5f * (float)(wl - 1);
+    a.hl = a.n > 1 ? a.tl - ((float)((a.n - 2) * B) + 0.5f * (float)(B - 1)) : 0.f;
+    return a;
+}
+
+__device__ __forceinline__ AxCoef axis_coef(const Axis& a, float t)
+{
+    AxCoef c;
+    if (a.n == 1) {
+        c.i = c.i1 = 0;
+        c.b = c.c0 = c.c1 = 0.f;
+        return c;
+    }
+    if (t < a.t0) {
+        float h = (a.n == 2) ? a.hl : a.B;
+        float d = t - a.t0;
+        c.i = 0; c.i1 = 1;
+        c.b = d / h;
+        c.c0 = -d * h * (1.f / 3.f);
+        c.c1 = -d * h * (1.f / 6.f);
+        return c;
+    }
+    if (t > a.tl) {
+        float h = a.hl;
+        float d = t - a.tl;
+        c.i = a.n - 2; c.i1 = a.n - 1;
+        c.b = 1.f + d / h;
+        c.c0 = d * h * (1.f / 6.f);
+        c.c1 = d * h * (1.f / 3.f);
+        return c;
+    }
+    int i = (int)floorf((t - a.t0) / a.B);
+    i = i < 0 ? 0 : (i > a.n - 2 ? a.n - 2 : i);
+    float ti = a.t0 + (float)i * a.B;
+    float h = (i == a.n - 2) ? a.hl : a.B;
+    float b = (t - ti) / h;
+    float aa = 1.f - b;
+    float h26 = h * h * (1.f / 6.f);
+    c.i = i; c.i1 = i + 1;
+    c.b = b;
+    c.c0 = h26 * (aa * aa * aa - aa);
+    c.c1 = h26 * (b * b * b - b);
+    return c;
+}
+
+__device__ __forceinline__ float axis_combine(const AxCoef& c, float v0, float v1, float m0, float m1)
+{
+    return fmaf(c.c1, m1, fmaf(c.c0, m0, fmaf(c.b, v1 - v0, v0)));
+}
+
+// Per-node table of one map: (P value, X = d2P/dx2 along the row,
+// Y = d2P/dy2 along the column, XY = d2Y/dx2 along the row).  The value at
+// (x, y) is the y-spline through u_j = x-spline(P[j], X[j]) whose node second
+// derivatives are w_j = x-spline(Y[j], XY[j]) -- the tensor-product natural
+// spline evaluated with precomputed derivatives.
+struct SplineTab {
+    const float4* node;   // [ny][nx]
+    Axis ax, ay;
+};
+
+__device__ __forceinline__ float2 row_eval(const SplineTab& s, int j, const AxCoef& cx)
+{
+    const float4 n0 = s.node[j * s.ax.n + cx.i];
+    const float4 n1 = s.node[j * s.ax.n + cx.i1];
+    float2 r;
+    r.x = axis_combine(cx, n0.x, n1.x, n0.y, n1.y);   // u_j(x)
+    r.y = axis_combine(cx, n0.z, n1.z, n0.w, n1.w);   // w_j(x)
+    return r;
+}
+
+__device__ __forceinline__ float spline_eval(const SplineTab& s, float x, float y)
+{
+    AxCoef cx = axis_coef(s.ax, x);
+    AxCoef cy = axis_coef(s.ay, y);
+    float2 r0 = row_eval(s, cy.i, cx);
+    float2 r1 = row_eval(s, cy.i1, cx);
+    return axis_combine(cy, r0.x, r1.x, r0.y, r1.y);
+}
+
+// ----------------------------------------------- compensated FP32 sums ---
+// A float-float accumulator: hi carries the running sum, lo the rounding
+// errors (TwoSum), so sums of many FP32 terms keep about 48 bits.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_zero() { DF d; d.hi = 0.f; d.lo = 0.f; return d; }
+
+__device__ __forceinline__ void df_add(DF& s, float v)
+{
+    float t = s.hi + v;
+    float bp = t - s.hi;
+    float e = (s.hi - (t - bp)) + (v - bp);
+    s.hi = t;
+    s.lo += e;
+}
+
+// add the exact product a*b (TwoProduct with an FMA)
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float b)
+{
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    df_add(s, p);
+    s.lo += e;
+}
+
+__device__ __forceinline__ DF df_merge(DF a, DF b)
+{
+    float t = a.hi + b.hi;
+    float bp = t - a.hi;
+    float e = (a.hi - (t - bp)) + (b.hi - bp);
+    DF r;
+    r.hi = t;
+    r.lo = a.lo + b.lo + e;
+    return r;
+}
+
+// butterfly reduction over a full warp; every lane ends with the same value,
+// the combination order is fixed, so the result is reproducible
+__device__ __forceinline__ DF df_warp_sum(DF v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        // combine in lane order so both partners compute the same bits
+        bool lower = (threadIdx.x & o) == 0;
+        v = lower ? df_merge(v, w) : df_merge(w, v);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double df_value(DF d) { return (double)d.hi + (double)d.lo; }
+
+// ------------------------------------------------------------- borders ---
+// mirror reflection without edge repeat (-1 -> 1, N -> N-2), periodic so any
+// offset lands inside; N == 1 maps to 0
+__host__ __device__ __forceinline__ int mirror_idx(int i, int N)
+{
+    if (N == 1) return 0;
+    int p = 2 * (N - 1);
+    i %= p;
+    if (i < 0) i += p;
+    return i < N ? i : p - i;
+}
+
+// ---------------------------------------------------- workspace layout ---
+// Pieces: the parts of segments that touch a detection-tile edge shared
+// with another tile; they are merged across tiles by union-find.
+struct Pieces {
+    int* count;           // scalar
+    int cap;
+    uint32_t* root;       // min linear index of the piece
+    int* npix;
+    int4* bbox;           // xmin, xmax, ymin, ymax (frame coordinates)
+    int* parent;          // union-find over piece ids
+    uint32_t* agg_min;    // at a root piece: min linear index of the whole segment
+    int* agg_npix;
+    int4* agg_bbox;
+};
+
+// Segments that survive the minarea cut, in no particular order until ranked
+struct Comps {
+    int* count;           // scalar
+    int cap;
+    uint32_t* label;
+    int* npix;
+    int4* bbox;
+    int* perm;            // rank -> component id
+    int* slots;           // bucket scatter space
+    int* bcnt;            // per label bucket counts
+    int* boff;            // exclusive offsets
+    int* bcur;            // scatter cursors
+    int nb;               // number of buckets
+    int shift;            // bucket = (label - 1) >> shift
+};
+
+struct Tiles {
+    int ntx, nty;
+    int16_t* edges;       // [ntiles][EDGE_PER_TILE] local piece index or -1
+    int* piece_base;      // [ntiles] first piece id of the tile
+    int* piece_cnt;       // [ntiles]
+};
+
+struct Image {
+    const void* data;
+    int64_t pitch;
+    const uint8_t* mask;
+    int W, H;
+    float sat;
+    int is_f32;
+};
+
+}  // namespace gp

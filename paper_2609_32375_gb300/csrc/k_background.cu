@@ -1,0 +1,641 @@
+// k_background.cu -- local background and noise map (paper Section 3.1).
+//
+//  k_boxstats_u16  one CTA per mesh box: the box's uint16 values go into an
+//                  exact 65,536-bin shared-memory histogram (two 16-bit
+//                  counters per 32-bit word), summarised into 256 coarse bins
+//                  with exact integer count / sum / sum-of-squares prefixes.
+//                  The k-sigma clip then runs on the histogram, not on the
+//                  pixels: each pass is two range sums and one or two order
+//                  statistics, all in exact integer arithmetic.
+//  k_boxstats_f32  one CTA per box (<= 16,384 pixels): values sorted in
+//                  shared memory (bitonic), the clipped set is an index range
+//                  of the sorted array, sums in compensated FP32.
+//  k_mesh_finalize fills boxes with < 50 % good pixels from valid neighbours
+//                  and median-filters both meshes (one CTA, tiny).
+//  k_spline_*      second-derivative tables of the tensor-product natural
+//                  spline through the box centres (FP64 tridiagonal solves).
+//  k_bkg_maps      optional full-resolution B(p), sigma(p) output.
+#include <float.h>
+#include <math.h>
+
+#include "gp_internal.cuh"
+#include "gp_launch.h"
+
+namespace gp {
+
+// The box statistics of the clipped set, from which background and rms
+// follow.  bkg = median if sigma == 0 or |mean - median| / sigma > 0.3, else
+// the mode estimate 2.5 median - 1.5 mean; rms = sigma.
+__device__ __forceinline__ void box_result(double med, double mean, double sd, double* bkg, double* rms)
+{
+    double b;
+    if (sd == 0.0 || fabs(mean - med) / sd > 0.3)
+        b = med;
+    else
+        b = 2.5 * med - 1.5 * mean;
+    *bkg = b;
+    *rms = sd;
+}
+
+// ============================================================ uint16 box ===
+constexpr int U16_NT = 1024;
+constexpr int U16_WORDS = 32768;   // 65,536 16-bit counters
+
+struct HistSums {
+    unsigned long long c, s1, s2;
+};
+
+// count / sum / sum of squares of the values < v (exact integers)
+// executed by one full warp; every lane returns the result
+__device__ HistSums hist_prefix(const uint32_t* hist, const unsigned long long* pc, const unsigned long long* ps1,
+                                const unsigned long long* ps2, uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t cb = v >> 8;            // coarse bin of v (256 means "all")
+    HistSums r;
+    r.c = pc[cb]; r.s1 = ps1[cb]; r.s2 = ps2[cb];
+    if (cb >= 256) return r;
+    // fine part: values cb*256 .. v-1; lane covers 8 values (4 words)
+    unsigned long long c = 0, s1 = 0, s2 = 0;
+    uint32_t base = (cb << 8) + (uint32_t)lane * 8u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t w = hist[(base >> 1) + q];
+        uint32_t v0 = base + 2u * q, v1 = v0 + 1u;
+        uint32_t n0 = w & 0xffffu, n1 = w >> 16;
+        if (v0 < v) { c += n0; s1 += (unsigned long long)n0 * v0; s2 += (unsigned long long)n0 * v0 * v0; }
+        if (v1 < v) { c += n1; s1 += (unsigned long long)n1 * v1; s2 += (unsigned long long)n1 * v1 * v1; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    r.c += c; r.s1 += s1; r.s2 += s2;
+    return r;
+}
+
+// the value of global rank r (0-based, r < total count); one full warp
+__device__ uint32_t hist_select(const uint32_t* hist, const unsigned long long* pc, unsigned long long r)
+{
+    const int lane = threadIdx.x & 31;
+    // coarse bin: largest cb with pc[cb] <= r  (pc is non-decreasing, pc[0] = 0)
+    // lane l checks bins 8l .. 8l+7
+    int best = -1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        int cb = lane * 8 + q;
+        if (pc[cb] <= r && pc[cb + 1] > r) best = cb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    int cb = best < 0 ? 255 : best;
+    unsigned long long rem = r - pc[cb];
+    // fine: inclusive scan over this coarse bin's 256 counters, 8 per lane
+    uint32_t base = ((uint32_t)cb << 8) + (uint32_t)lane * 8u;
+    uint32_t cnt[8];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t w = hist[(base >> 1) + q];
+        cnt[2 * q] = w & 0xffffu;
+        cnt[2 * q + 1] = w >> 16;
+        tot += cnt[2 * q] + cnt[2 * q + 1];
+    }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    uint32_t excl = incl - tot;
+    // the lane whose range holds rem
+    bool mine = (excl <= rem) && (rem < incl);
+    uint32_t ans = 0;
+    if (mine) {
+        uint32_t acc = excl;
+        for (int q = 0; q < 8; ++q) {
+            acc += cnt[q];
+            if (rem < acc) { ans = base + q; break; }
+        }
+    }
+    unsigned ball = __ballot_sync(0xffffffffu, mine);
+    int src = ball ? (__ffs(ball) - 1) : 0;
+    return __shfl_sync(0xffffffffu, ans, src);
+}
+
+__global__ void __launch_bounds__(U16_NT, 1)
+k_boxstats_u16(const uint16_t* __restrict__ img, int64_t pitch, const uint8_t* __restrict__ mask,
+               int W, int H, int B, int Mx, double k, int maxiter,
+               double* __restrict__ bkg_out, double* __restrict__ rms_out, int* __restrict__ valid_out,
+               float* __restrict__ quant_out)
+{
+    extern __shared__ uint32_t hist[];                    // U16_WORDS
+    __shared__ unsigned long long pc[257], ps1[257], ps2[257];
+    __shared__ unsigned long long cc_s[256], cs1_s[256], cs2_s[256];
+    __shared__ uint32_t red_min[32], red_max[32], red_n[32];
+
+    const int box = blockIdx.x;
+    const int bi = box % Mx, bj = box / Mx;
+    const int x0 = bi * B, x1 = min(x0 + B, W);
+    const int y0 = bj * B, y1 = min(y0 + B, H);
+    const int bw = x1 - x0, bh = y1 - y0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int w = tid; w < U16_WORDS; w += U16_NT) hist[w] = 0u;
+    __syncthreads();
+
+    uint32_t vmin = 0xffffffffu, vmax = 0u, ngood = 0u;
+    // 8-pixel chunks along each row; rows spread over the CTA
+    const int cpr = (bw + 7) >> 3;              // chunks per row
+    const int nchunks = cpr * bh;
+    const bool vec = ((((uintptr_t)img) & 15) == 0) && ((pitch & 7) == 0) && ((x0 & 7) == 0);
+    for (int c = tid; c < nchunks; c += U16_NT) {
+        const int ry = c / cpr, rc = c - ry * cpr;
+        const int y = y0 + ry, xs = x0 + rc * 8;
+        const uint16_t* row = img + (int64_t)y * pitch;
+        uint16_t v[8];
+        int nv = min(8, x1 - xs);
+        if (vec && nv == 8) {
+            uint4 q = __ldg(reinterpret_cast<const uint4*>(row + xs));
+            v[0] = q.x & 0xffff; v[1] = q.x >> 16; v[2] = q.y & 0xffff; v[3] = q.y >> 16;
+            v[4] = q.z & 0xffff; v[5] = q.z >> 16; v[6] = q.w & 0xffff; v[7] = q.w >> 16;
+        } else {
+            for (int e = 0; e < 8; ++e) v[e] = e < nv ? __ldg(row + xs + e) : 0;
+        }
+        for (int e = 0; e < nv; ++e) {
+            if (mask && mask[(int64_t)y * W + xs + e]) continue;
+            uint32_t u = v[e];
+            atomicAdd(&hist[u >> 1], (u & 1u) ? 65536u : 1u);
+            vmin = min(vmin, u);
+            vmax = max(vmax, u);
+            ++ngood;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        ngood += __shfl_xor_sync(0xffffffffu, ngood, o);
+    }
+    if (lane == 0) { red_min[warp] = vmin; red_max[warp] = vmax; red_n[warp] = ngood; }
+    __syncthreads();
+    if (warp == 0) {
+        vmin = red_min[lane]; vmax = red_max[lane]; ngood = red_n[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+            vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            ngood += __shfl_xor_sync(0xffffffffu, ngood, o);
+        }
+        if (lane == 0) { red_min[0] = vmin; red_max[0] = vmax; red_n[0] = ngood; }
+    }
+    __syncthreads();
+    vmin = red_min[0]; vmax = red_max[0]; ngood = red_n[0];
+    const bool valid = ngood > 0 && 2u * ngood >= (uint32_t)(bw * bh);
+
+    if (ngood == 0 || vmin == vmax) {
+        // empty box, or a constant one (the only case where one 16-bit
+        // counter could have wrapped): statistics are immediate
+        if (tid == 0) {
+            double med = ngood ? (double)vmin : 0.0;
+            double b, r;
+            box_result(med, med, 0.0, &b, &r);
+            bkg_out[box] = valid ? b : 0.0;
+            rms_out[box] = valid ? r : 0.0;
+            valid_out[box] = valid;
+            if (quant_out)
+                for (int q = 0; q < 5; ++q) quant_out[(int64_t)q * gridDim.x + box] = (float)med;
+        }
+        return;
+    }
+
+    // coarse summaries: 256 bins of 256 values
+    for (int cb = warp; cb < 256; cb += U16_NT / 32) {
+        unsigned long long c = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int widx = cb * 128 + lane + 32 * q;
+            uint32_t w = hist[widx];
+            uint32_t v0 = (uint32_t)widx * 2u, v1 = v0 + 1u;
+            uint32_t n0 = w & 0xffffu, n1 = w >> 16;
+            c += n0 + n1;
+            s1 += (unsigned long long)n0 * v0 + (unsigned long long)n1 * v1;
+            s2 += (unsigned long long)n0 * v0 * v0 + (unsigned long long)n1 * v1 * v1;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) { cc_s[cb] = c; cs1_s[cb] = s1; cs2_s[cb] = s2; }
+    }
+    __syncthreads();
+    if (warp != 0) return;
+
+    // exclusive prefix over the coarse bins (8 per lane)
+    {
+        unsigned long long c[8], s1[8], s2[8];
+        unsigned long long tc = 0, t1 = 0, t2 = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            c[q] = cc_s[lane * 8 + q]; s1[q] = cs1_s[lane * 8 + q]; s2[q] = cs2_s[lane * 8 + q];
+            tc += c[q]; t1 += s1[q]; t2 += s2[q];
+        }
+        unsigned long long ic = tc, i1 = t1, i2 = t2;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long a = __shfl_up_sync(0xffffffffu, ic, o);
+            unsigned long long b = __shfl_up_sync(0xffffffffu, i1, o);
+            unsigned long long d = __shfl_up_sync(0xffffffffu, i2, o);
+            if (lane >= o) { ic += a; i1 += b; i2 += d; }
+        }
+        unsigned long long ec = ic - tc, e1 = i1 - t1, e2 = i2 - t2;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            pc[lane * 8 + q] = ec; ps1[lane * 8 + q] = e1; ps2[lane * 8 + q] = e2;
+            ec += c[q]; e1 += s1[q]; e2 += s2[q];
+        }
+        if (lane == 31) { pc[256] = ec; ps1[256] = e1; ps2[256] = e2; }
+    }
+    __syncwarp();
+
+    // iterative clip on the histogram: the kept set is always the values in
+    // an integer range [a, b]
+    uint32_t a = vmin, b = vmax;
+    HistSums lo = hist_prefix(hist, pc, ps1, ps2, a);
+    HistSums hi = hist_prefix(hist, pc, ps1, ps2, b + 1u);
+    unsigned long long n = hi.c - lo.c, S1 = hi.s1 - lo.s1, S2 = hi.s2 - lo.s2;
+    double med = 0, mean = 0, sd = 0;
+    for (int it = 0;; ++it) {
+        uint32_t m0 = hist_select(hist, pc, lo.c + (n - 1) / 2);
+        uint32_t m1 = (n & 1ull) ? m0 : hist_select(hist, pc, lo.c + n / 2);
+        med = 0.5 * ((double)m0 + (double)m1);
+        mean = (double)S1 / (double)n;
+        // population variance from exact integers: (n S2 - S1^2) / n^2
+        unsigned long long num = n * S2 - S1 * S1;
+        sd = sqrt((double)num / ((double)n * (double)n));
+        if (it >= maxiter) break;
+        double flo = med - k * sd, fhi = med + k * sd;
+        double ca = ceil(flo), cbv = floor(fhi);
+        uint32_t na = ca <= (double)a ? a : (uint32_t)ca;
+        uint32_t nbv = cbv >= (double)b ? b : (cbv < 0 ? 0u : (uint32_t)cbv);
+        if (nbv < na) { na = a; nbv = a; }   // cannot happen for k > 0 (median lies inside)
+        HistSums nlo = hist_prefix(hist, pc, ps1, ps2, na);
+        HistSums nhi = hist_prefix(hist, pc, ps1, ps2, nbv + 1u);
+        unsigned long long nn = nhi.c - nlo.c;
+        if (nn == n) break;                // the kept set did not change
+        a = na; b = nbv; lo = nlo; hi = nhi;
+        n = nn; S1 = nhi.s1 - nlo.s1; S2 = nhi.s2 - nlo.s2;
+    }
+    if (quant_out) {
+        // quantiles of all good values (features for the learned background)
+        const float qs[5] = {0.10f, 0.25f, 0.50f, 0.75f, 0.90f};
+        for (int q = 0; q < 5; ++q) {
+            unsigned long long r = (unsigned long long)floor((double)qs[q] * (double)(ngood - 1) + 0.5);
+            uint32_t v = hist_select(hist, pc, r);
+            if (lane == 0) quant_out[(int64_t)q * gridDim.x + box] = (float)v;
+        }
+    }
+    if (lane == 0) {
+        double bb, rr;
+        box_result(med, mean, sd, &bb, &rr);
+        bkg_out[box] = valid ? bb : 0.0;
+        rms_out[box] = valid ? rr : 0.0;
+        valid_out[box] = valid;
+    }
+}
+
+// ============================================================ float32 box ===
+constexpr int F32_NT = 512;
+
+__device__ __forceinline__ DF block_df_sum(DF v, DF* red)
+{
+    v = df_warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    DF t = lane < (int)(blockDim.x >> 5) ? red[lane] : df_zero();
+    t = df_warp_sum(t);
+    return t;
+}
+
+// first index in [lo, hi) with (double)v[i] >= x (v ascending)
+__device__ __forceinline__ int lower_bound_d(const float* v, int lo, int hi, double x)
+{
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((double)v[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// first index in [lo, hi) with (double)v[i] > x
+__device__ __forceinline__ int upper_bound_d(const float* v, int lo, int hi, double x)
+{
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((double)v[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(F32_NT)
+k_boxstats_f32(const float* __restrict__ img, int64_t pitch, const uint8_t* __restrict__ mask,
+               int W, int H, int B, int Mx, int npad, double k, int maxiter,
+               double* __restrict__ bkg_out, double* __restrict__ rms_out, int* __restrict__ valid_out,
+               float* __restrict__ quant_out)
+{
+    extern __shared__ float vals[];                 // npad
+    __shared__ int ngood_s;
+    __shared__ DF red[32];
+    const int box = blockIdx.x;
+    const int bi = box % Mx, bj = box / Mx;
+    const int x0 = bi * B, x1 = min(x0 + B, W);
+    const int y0 = bj * B, y1 = min(y0 + B, H);
+    const int bw = x1 - x0, bh = y1 - y0;
+    const int tid = threadIdx.x;
+    if (tid == 0) ngood_s = 0;
+    __syncthreads();
+    for (int p = tid; p < bw * bh; p += F32_NT) {
+        int y = y0 + p / bw, x = x0 + p % bw;
+        float v = __ldg(img + (int64_t)y * pitch + x);
+        bool bad = !isfinite(v) || (mask && mask[(int64_t)y * W + x]);
+        if (!bad) vals[atomicAdd(&ngood_s, 1)] = v;
+    }
+    __syncthreads();
+    const int ng = ngood_s;
+    for (int p = ng + tid; p < npad; p += F32_NT) vals[p] = INFINITY;
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int size = 2; size <= npad; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < npad / 2; i += F32_NT) {
+                int lo = 2 * i - (i & (stride - 1));
+                int hi = lo + stride;
+                bool up = ((lo & size) == 0);
+                float a = vals[lo], b = vals[hi];
+                if ((a > b) == up) { vals[lo] = b; vals[hi] = a; }
+            }
+            __syncthreads();
+        }
+    const bool valid = ng > 0 && 2 * ng >= bw * bh;
+    if (ng == 0) {
+        if (tid == 0) { bkg_out[box] = 0; rms_out[box] = 0; valid_out[box] = 0; }
+        if (quant_out && tid < 5) quant_out[(int64_t)tid * gridDim.x + box] = 0.f;
+        return;
+    }
+    int lo = 0, hi = ng;
+    double med = 0, mean = 0, sd = 0;
+    for (int it = 0;; ++it) {
+        int n = hi - lo;
+        med = (n & 1) ? (double)vals[lo + n / 2] : 0.5 * ((double)vals[lo + n / 2 - 1] + (double)vals[lo + n / 2]);
+        DF s = df_zero();
+        for (int i = lo + tid; i < hi; i += F32_NT) df_add(s, vals[i]);
+        s = block_df_sum(s, red);
+        double S = df_value(s);
+        mean = S / (double)n;
+        float mh = (float)mean;
+        float ml = (float)(mean - (double)mh);
+        DF q = df_zero();
+        for (int i = lo + tid; i < hi; i += F32_NT) {
+            float d = (vals[i] - mh) - ml;
+            df_add_prod(q, d, d);
+        }
+        q = block_df_sum(q, red);
+        sd = sqrt(fmax(df_value(q), 0.0) / (double)n);
+        if (it >= maxiter) break;
+        double flo = med - k * sd, fhi = med + k * sd;
+        int nlo = lower_bound_d(vals, lo, hi, flo);
+        int nhi = upper_bound_d(vals, lo, hi, fhi);
+        if (nhi - nlo == n) break;
+        lo = nlo; hi = nhi;
+    }
+    if (tid == 0) {
+        double bb, rr;
+        box_result(med, mean, sd, &bb, &rr);
+        bkg_out[box] = valid ? bb : 0.0;
+        rms_out[box] = valid ? rr : 0.0;
+        valid_out[box] = valid;
+    }
+    if (quant_out && tid < 5) {
+        const float qs[5] = {0.10f, 0.25f, 0.50f, 0.75f, 0.90f};
+        int r = (int)floor((double)qs[tid] * (double)(ng - 1) + 0.5);
+        quant_out[(int64_t)tid * gridDim.x + box] = vals[r];
+    }
+}
+
+// ====================================================== mesh finalisation ===
+constexpr int MF_NT = 1024;
+
+// Fill boxes with < 50 % good pixels from the mean of their valid
+// 8-neighbours (sweep after sweep), then median-filter both meshes over a
+// fsize x fsize window clipped at the mesh edge.  One CTA.
+__global__ void __launch_bounds__(MF_NT)
+k_mesh_finalize(double* bkg, double* rms, int* valid, double* tmp_b, double* tmp_r, int* tmp_v,
+                int Mx, int My, int fsize, float* bkg_out, float* rms_out)
+{
+    __shared__ int missing, any;
+    const int nb = Mx * My, tid = threadIdx.x;
+    if (tid == 0) any = 0;
+    __syncthreads();
+    for (int b = tid; b < nb; b += MF_NT)
+        if (valid[b]) any = 1;
+    __syncthreads();
+    if (!any) {
+        for (int b = tid; b < nb; b += MF_NT) { bkg[b] = 0; rms[b] = 0; valid[b] = 1; }
+        __syncthreads();
+    }
+    for (int sweep = 0; sweep < Mx + My + 2; ++sweep) {
+        if (tid == 0) missing = 0;
+        __syncthreads();
+        for (int b = tid; b < nb; b += MF_NT) {
+            tmp_b[b] = bkg[b]; tmp_r[b] = rms[b]; tmp_v[b] = valid[b];
+            if (valid[b]) continue;
+            int i = b % Mx, j = b / Mx, c = 0;
+            double sb = 0, sr = 0;
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    int ii = i + di, jj = j + dj;
+                    if ((di || dj) && ii >= 0 && ii < Mx && jj >= 0 && jj < My && valid[jj * Mx + ii]) {
+                        sb += bkg[jj * Mx + ii];
+                        sr += rms[jj * Mx + ii];
+                        ++c;
+                    }
+                }
+            if (c) { tmp_b[b] = sb / c; tmp_r[b] = sr / c; tmp_v[b] = 1; }
+            else missing = 1;
+        }
+        __syncthreads();
+        for (int b = tid; b < nb; b += MF_NT) { bkg[b] = tmp_b[b]; rms[b] = tmp_r[b]; valid[b] = tmp_v[b]; }
+        __syncthreads();
+        if (!missing) break;
+    }
+    const int h = fsize / 2;
+    for (int b = tid; b < nb; b += MF_NT) {
+        int i = b % Mx, j = b / Mx;
+        for (int map = 0; map < 2; ++map) {
+            const double* src = map ? rms : bkg;
+            double win[49];
+            int c = 0;
+            for (int jj = j - h; jj <= j + h; ++jj)
+                for (int ii = i - h; ii <= i + h; ++ii)
+                    if (ii >= 0 && ii < Mx && jj >= 0 && jj < My) {
+                        double v = src[jj * Mx + ii];
+                        int p = c++;
+                        while (p > 0 && win[p - 1] > v) { win[p] = win[p - 1]; --p; }
+                        win[p] = v;
+                    }
+            double med = (c & 1) ? win[c / 2] : 0.5 * (win[c / 2 - 1] + win[c / 2]);
+            (map ? rms_out : bkg_out)[b] = (float)med;
+        }
+    }
+}
+
+// ============================================================ spline tables ===
+// natural-spline second derivatives along a line of n nodes (positions from
+// the axis) for values v (stride vs), written to M (stride ms); d, c are
+// scratch of n doubles.  Thomas algorithm on the interior nodes.
+__device__ void spline_line(const Axis& ax, const double* v, int vs, double* M, int ms, double* c, double* d)
+{
+    const int n = ax.n;
+    for (int i = 0; i < n; ++i) M[i * ms] = 0.0;
+    if (n < 3) return;
+    auto pos = [&](int i) -> double {
+        return (i == n - 1) ? (double)ax.tl : (double)ax.t0 + (double)i * (double)ax.B;
+    };
+    // rows r = 1 .. n-2: h0 M[r-1] + 2 (h0 + h1) M[r] + h1 M[r+1] = rhs
+    double bprev = 0, cprev = 0, dprev = 0;
+    for (int r = 1; r <= n - 2; ++r) {
+        double h0 = pos(r) - pos(r - 1), h1 = pos(r + 1) - pos(r);
+        double a = h0, b = 2.0 * (h0 + h1), cc = h1;
+        double rhs = 6.0 * ((v[(r + 1) * vs] - v[r * vs]) / h1 - (v[r * vs] - v[(r - 1) * vs]) / h0);
+        if (r > 1) {
+            double w = a / bprev;
+            b -= w * cprev;
+            rhs -= w * dprev;
+        }
+        c[r] = cc; d[r] = rhs;
+        bprev = b; cprev = cc; dprev = rhs;
+        M[r * ms] = b;   // keep the pivot temporarily
+    }
+    // back substitution
+    double next = 0.0;
+    for (int r = n - 2; r >= 1; --r) {
+        double piv = M[r * ms];
+        double val = (d[r] - c[r] * next) / piv;
+        M[r * ms] = val;
+        next = val;
+    }
+}
+
+// X: along each mesh row; Y: along each mesh column.  Each of the Mx + My
+// lines has its own scratch line of Mx + My doubles in sc and sd.
+__global__ void k_spline_xy(const float* mesh, Axis ax, Axis ay, double* vals, double* colv, double* X,
+                            double* Y, double* scr_c, double* scr_d)
+{
+    const int Mx = ax.n, My = ay.n;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < My) {
+        double* v = vals + (int64_t)t * Mx;
+        for (int i = 0; i < Mx; ++i) v[i] = (double)mesh[t * Mx + i];
+        spline_line(ax, v, 1, X + (int64_t)t * Mx, 1, scr_c + (int64_t)t * (Mx + My), scr_d + (int64_t)t * (Mx + My));
+    }
+    const int u = t - My;
+    if (u >= 0 && u < Mx) {
+        double* col = colv + (int64_t)u * My;
+        for (int j = 0; j < My; ++j) col[j] = (double)mesh[j * Mx + u];
+        spline_line(ay, col, 1, Y + u, Mx, scr_c + (int64_t)(My + u) * (Mx + My),
+                    scr_d + (int64_t)(My + u) * (Mx + My));
+    }
+}
+
+// XY: along each mesh row of Y; then pack (P, X, Y, XY) as float4
+__global__ void k_spline_pack(const float* mesh, Axis ax, Axis ay, const double* X, double* Y, double* XY,
+                              double* scr_c, double* scr_d, float4* tab)
+{
+    const int Mx = ax.n, My = ay.n;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= My) return;
+    spline_line(ax, Y + (int64_t)t * Mx, 1, XY + (int64_t)t * Mx, 1, scr_c + (int64_t)t * (Mx + My),
+                scr_d + (int64_t)t * (Mx + My));
+    for (int i = 0; i < Mx; ++i) {
+        int64_t o = (int64_t)t * Mx + i;
+        tab[o] = make_float4(mesh[o], (float)X[o], (float)Y[o], (float)XY[o]);
+    }
+}
+
+__global__ void k_bkg_maps(SplineTab sb, SplineTab sr, int W, int H, float* bmap, float* rmap)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        float x = (float)(p % W), y = (float)(p / W);
+        if (bmap) bmap[p] = spline_eval(sb, x, y);
+        if (rmap) rmap[p] = spline_eval(sr, x, y);
+    }
+}
+
+// --------------------------------------------------------------- launchers ---
+cudaError_t launch_boxstats(const Image& im, int B, double k, int maxiter, double* bkg, double* rms, int* valid,
+                            float* quant, cudaStream_t st)
+{
+    const int Mx = (im.W + B - 1) / B, My = (im.H + B - 1) / B;
+    if (!im.is_f32) {
+        const size_t smem = U16_WORDS * sizeof(uint32_t);
+        cudaFuncSetAttribute(k_boxstats_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_boxstats_u16<<<Mx * My, U16_NT, smem, st>>>((const uint16_t*)im.data, im.pitch, im.mask, im.W, im.H, B,
+                                                     Mx, k, maxiter, bkg, rms, valid, quant);
+    } else {
+        int npad = 1;
+        while (npad < B * B) npad <<= 1;
+        const size_t smem = (size_t)npad * sizeof(float);
+        cudaFuncSetAttribute(k_boxstats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_boxstats_f32<<<Mx * My, F32_NT, smem, st>>>((const float*)im.data, im.pitch, im.mask, im.W, im.H, B, Mx,
+                                                     npad, k, maxiter, bkg, rms, valid, quant);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mesh_finalize(double* bkg, double* rms, int* valid, double* tmp_b, double* tmp_r, int* tmp_v,
+                                 int Mx, int My, int fsize, float* bkg_out, float* rms_out, cudaStream_t st)
+{
+    k_mesh_finalize<<<1, MF_NT, 0, st>>>(bkg, rms, valid, tmp_b, tmp_r, tmp_v, Mx, My, fsize, bkg_out, rms_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spline_tables(const float* mesh, Axis ax, Axis ay, double* scratch, float4* tab, cudaStream_t st)
+{
+    const int Mx = ax.n, My = ay.n;
+    const int64_t nn = (int64_t)Mx * My;
+    double* vals = scratch;
+    double* colv = vals + nn;
+    double* X = colv + nn;
+    double* Y = X + nn;
+    double* XY = Y + nn;
+    double* sc = XY + nn;
+    double* sd = sc + (int64_t)(Mx + My) * (Mx + My);
+    const int nt = Mx + My;
+    k_spline_xy<<<(nt + 127) / 128, 128, 0, st>>>(mesh, ax, ay, vals, colv, X, Y, sc, sd);
+    k_spline_pack<<<(My + 127) / 128, 128, 0, st>>>(mesh, ax, ay, X, Y, XY, sc, sd, tab);
+    return cudaGetLastError();
+}
+
+size_t spline_scratch_doubles(int Mx, int My)
+{
+    return (size_t)5 * Mx * My + (size_t)2 * (Mx + My) * (Mx + My);
+}
+
+cudaError_t launch_bkg_maps(const SplineTab& sb, const SplineTab& sr, int W, int H, float* bmap, float* rmap,
+                            cudaStream_t st)
+{
+    int64_t n = (int64_t)W * H;
+    int64_t nb_ = (n + 255) / 256;
+    int blocks = (int)(nb_ < 152 * 16 ? nb_ : 152 * 16);
+    k_bkg_maps<<<blocks, 256, 0, st>>>(sb, sr, W, H, bmap, rmap);
+    return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -1,0 +1,356 @@
+// k_measure.cu -- segment moments (first-moment centroid of paper Section
+// 3.2, extended to second moments, bounding box and peak) and circular
+// apertures with exact disc/pixel overlap areas (Section 3.4).
+//
+// One warp per source.  Moments scan the segment's bounding box in the final
+// segmentation map; apertures scan the pixels around the centroid once for
+// all radii.  Every sum is a float-float (compensated) accumulation of FP32
+// products, reduced across the warp in a fixed butterfly order, so results
+// are reproducible run to run and carry about 48 bits -- the float64-class
+// accumulation the paper asks of aperture sums, without FP64 arithmetic
+// (which runs at a small fraction of the FP32 rate on this GPU).
+#include <math.h>
+
+#include "gp_internal.cuh"
+#include "gp_launch.h"
+
+namespace gp {
+
+struct ApSpec {
+    int nr;
+    float r[MAX_NR];
+    float rmax;
+    float gain;
+};
+
+struct MeasureArgs {
+    Image im;
+    SplineTab sb, sr;
+    Comps C;
+    const uint32_t* seg;
+    int capacity;
+    // catalog columns
+    uint32_t* label;
+    int32_t* npix;
+    double *flux_iso, *x, *y, *x2, *y2, *xy;
+    int32_t *xmin, *xmax, *ymin, *ymax;
+    float* peak;
+    int32_t *xpeak, *ypeak;
+    uint32_t* flags;
+    ApSpec ap;
+    double* apflux;
+    double* apferr;
+    uint32_t* apflags;
+};
+
+// integral of sqrt(r^2 - t^2) over [a, b], -r <= a <= b <= r, written with
+// differences formed algebraically (no cancellation between large terms)
+__device__ __forceinline__ float chord_int(float a, float b, float r2)
+{
+    float d = b - a;
+    if (!(d > 0.f)) return 0.f;
+    float ha = sqrtf(fmaxf(r2 - a * a, 0.f));
+    float hb = sqrtf(fmaxf(r2 - b * b, 0.f));
+    float s = ha + hb;
+    float q = s > 0.f ? d * (a + b) / s : 0.f;      // ha - hb
+    float sin_t = fmaf(d, ha, a * q);               // (b ha - a hb), r^2 sin(theta)
+    float cos_t = fmaf(ha, hb, a * b);              // (ha hb + a b), r^2 cos(theta)
+    float theta = atan2f(sin_t, cos_t);             // asin(b/r) - asin(a/r)
+    return 0.5f * (fmaf(d, hb, -a * q) + r2 * theta);
+}
+
+// exact area of disc(0, r) n [x0,x1] x [y0,y1]: integrate the length of
+// [y0,y1] n [-h(x), h(x)] over x, split where h(x) = |y0|, |y1|
+__device__ float disc_rect_area(float x0, float x1, float y0, float y1, float r)
+{
+    const float r2 = r * r;
+    const float a = fmaxf(x0, -r), b = fminf(x1, r);
+    if (!(a < b)) return 0.f;
+    float p[6];
+    p[0] = a;
+    p[5] = b;
+    float c0 = fabsf(y0) < r ? sqrtf(fmaxf(r2 - y0 * y0, 0.f)) : 0.f;
+    float c1 = fabsf(y1) < r ? sqrtf(fmaxf(r2 - y1 * y1, 0.f)) : 0.f;
+    p[1] = fminf(fmaxf(-c0, a), b);
+    p[2] = fminf(fmaxf(c0, a), b);
+    p[3] = fminf(fmaxf(-c1, a), b);
+    p[4] = fminf(fmaxf(c1, a), b);
+    // sort p[1..4]
+#define GP_CSWAP(i, j) { float lo_ = fminf(p[i], p[j]); float hi_ = fmaxf(p[i], p[j]); p[i] = lo_; p[j] = hi_; }
+    GP_CSWAP(1, 2); GP_CSWAP(3, 4); GP_CSWAP(1, 3); GP_CSWAP(2, 4); GP_CSWAP(2, 3);
+#undef GP_CSWAP
+    float area = 0.f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float lo = p[k], hi = p[k + 1];
+        if (!(hi > lo)) continue;
+        float mid = 0.5f * (lo + hi);
+        float h = sqrtf(fmaxf(r2 - mid * mid, 0.f));
+        bool top_h = h < y1, bot_h = -h > y0;
+        float top = top_h ? h : y1, bot = bot_h ? -h : y0;
+        if (!(top > bot)) continue;
+        float gi = (top_h || bot_h) ? chord_int(lo, hi, r2) : 0.f;
+        float w = hi - lo;
+        float itop = top_h ? gi : y1 * w;
+        float ibot = bot_h ? -gi : y0 * w;
+        area += itop - ibot;
+    }
+    return area;
+}
+
+template <bool F32>
+__device__ __forceinline__ float load_px(const Image& im, int x, int y, bool& bad)
+{
+    float v;
+    if (F32) {
+        v = __ldg(reinterpret_cast<const float*>(im.data) + (int64_t)y * im.pitch + x);
+        bad = !isfinite(v);
+    } else {
+        v = (float)__ldg(reinterpret_cast<const uint16_t*>(im.data) + (int64_t)y * im.pitch + x);
+        bad = false;
+    }
+    if (im.mask && im.mask[(int64_t)y * im.W + x]) bad = true;
+    return v;
+}
+
+// Apertures around (cx, cy) for all radii; executed by one full warp.
+// Lane results are combined in a fixed order; lane 0 writes.
+template <bool F32>
+__device__ void aperture_warp(const Image& im, const SplineTab& sb, const SplineTab& sr, const ApSpec& ap,
+                              double cx, double cy, double* flux, double* ferr, uint32_t* aflags)
+{
+    const int lane = threadIdx.x & 31;
+    const int W = im.W, H = im.H;
+    // positions far outside the frame (or NaN) clamp to an empty pixel range
+    const double cxc = fmin(fmax(cx, -4096.0), (double)W + 4096.0);
+    const double cyc = fmin(fmax(cy, -4096.0), (double)H + 4096.0);
+    const double xi_d = floor(cxc), yi_d = floor(cyc);
+    const int xi = (int)xi_d, yi = (int)yi_d;
+    const float xf = (float)(cxc - xi_d), yf = (float)(cyc - yi_d);
+    int xa = (int)floor(cxc - (double)ap.rmax - 0.5), xb = (int)ceil(cxc + (double)ap.rmax + 0.5);
+    int ya = (int)floor(cyc - (double)ap.rmax - 0.5), yb = (int)ceil(cyc + (double)ap.rmax + 0.5);
+    xa = max(xa, 0); ya = max(ya, 0);
+    xb = min(xb, W - 1); yb = min(yb, H - 1);
+    if (!(cx == cxc) || !(cy == cyc)) { xb = -1; yb = -1; }
+    DF f[MAX_NR], v[MAX_NR];
+    uint32_t fl[MAX_NR];
+#pragma unroll
+    for (int k = 0; k < MAX_NR; ++k) { f[k] = df_zero(); v[k] = df_zero(); fl[k] = 0u; }
+    const int bw = xb - xa + 1, bh = yb - ya + 1;
+    const int npx = (bw > 0 && bh > 0) ? bw * bh : 0;
+    for (int q = lane; q < npx; q += 32) {
+        const int y = ya + q / bw, x = xa + q % bw;
+        const float dx0 = (float)(x - xi) - xf - 0.5f, dx1 = dx0 + 1.f;
+        const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
+        const float nx = fmaxf(0.f, fmaxf(dx0, -dx1)), ny = fmaxf(0.f, fmaxf(dy0, -dy1));
+        const float dmin2 = nx * nx + ny * ny;
+        if (dmin2 >= ap.rmax * ap.rmax) continue;
+        const float fx = fmaxf(dx0 * dx0, dx1 * dx1), fy = fmaxf(dy0 * dy0, dy1 * dy1);
+        const float dmax2 = fx + fy;
+        bool bad;
+        float val = load_px<F32>(im, x, y, bad);
+        float m = 0.f, var = 0.f;
+        bool sat = false;
+        if (!bad) {
+            m = val - spline_eval(sb, (float)x, (float)y);
+            float s = spline_eval(sr, (float)x, (float)y);
+            var = s * s;
+            sat = im.sat > 0.f && val >= im.sat;
+        }
+#pragma unroll
+        for (int k = 0; k < MAX_NR; ++k) {
+            if (k >= ap.nr) break;
+            const float r = ap.r[k], r2 = r * r;
+            float A;
+            if (dmin2 >= r2) continue;
+            if (dmax2 <= r2) A = 1.f;
+            else A = disc_rect_area(dx0, dx1, dy0, dy1, r);
+            if (!(A > 0.f)) continue;
+            if (bad) { fl[k] |= GP_FLAG_BAD; continue; }
+            if (sat) fl[k] |= GP_FLAG_SAT;
+            df_add_prod(f[k], A, m);
+            df_add_prod(v[k], A, var);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MAX_NR; ++k) {
+        if (k >= ap.nr) break;
+        DF fs = df_warp_sum(f[k]);
+        DF vs = df_warp_sum(v[k]);
+        uint32_t ff = fl[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ff |= __shfl_xor_sync(0xffffffffu, ff, o);
+        if (lane == 0) {
+            const double r = ap.r[k];
+            if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) ff |= GP_FLAG_TRUNCATED;
+            double F = df_value(fs);
+            double V = df_value(vs);
+            if (ap.gain > 0.f && F > 0.0) V += F / (double)ap.gain;
+            flux[k] = F;
+            ferr[k] = sqrt(fmax(V, 0.0));
+            aflags[k] = ff;
+        }
+    }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_measure(MeasureArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int ncomp = min(*A.C.count, A.C.cap);
+    const int nrow = min(ncomp, A.capacity);
+    const int W = A.im.W;
+    for (int r = wid; r < nrow; r += nw) {
+        const int c = A.C.perm[r];
+        const uint32_t lab = A.C.label[c];
+        const int4 bb = A.C.bbox[c];
+        const int bw = bb.y - bb.x + 1, bh = bb.w - bb.z + 1;
+        const int npx = bw * bh;
+        // pass 1: sums about the box corner
+        DF S = df_zero(), Sx = df_zero(), Sy = df_zero();
+        long long ux = 0, uy = 0;
+        int cnt = 0;
+        float pk = -INFINITY;
+        long long pkL = 0x7fffffffffffffffll;
+        bool sat = false;
+        for (int q = lane; q < npx; q += 32) {
+            const int y = bb.z + q / bw, x = bb.x + q % bw;
+            if (__ldg(A.seg + (int64_t)y * W + x) != lab) continue;
+            bool bad;
+            const float v = load_px<F32>(A.im, x, y, bad);
+            const float m = v - spline_eval(A.sb, (float)x, (float)y);
+            sat |= A.im.sat > 0.f && v >= A.im.sat;
+            const float dx = (float)(x - bb.x), dy = (float)(y - bb.z);
+            df_add(S, m);
+            df_add_prod(Sx, dx, m);
+            df_add_prod(Sy, dy, m);
+            ux += x - bb.x; uy += y - bb.z;
+            ++cnt;
+            const long long L = (long long)y * W + x;
+            if (m > pk || (m == pk && L < pkL)) { pk = m; pkL = L; }
+        }
+        S = df_warp_sum(S); Sx = df_warp_sum(Sx); Sy = df_warp_sum(Sy);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ux += __shfl_xor_sync(0xffffffffu, ux, o);
+            uy += __shfl_xor_sync(0xffffffffu, uy, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            float opk = __shfl_xor_sync(0xffffffffu, pk, o);
+            long long oL = __shfl_xor_sync(0xffffffffu, pkL, o);
+            if (opk > pk || (opk == pk && oL < pkL)) { pk = opk; pkL = oL; }
+        }
+        sat = __any_sync(0xffffffffu, sat);
+        const double Sd = df_value(S);
+        const bool fallback = !(Sd > 0.0);
+        double xc, yc;
+        if (!fallback) {
+            xc = bb.x + df_value(Sx) / Sd;
+            yc = bb.z + df_value(Sy) / Sd;
+        } else {
+            xc = bb.x + (double)ux / cnt;
+            yc = bb.z + (double)uy / cnt;
+        }
+        // pass 2: central second moments
+        const double xi_d = floor(xc), yi_d = floor(yc);
+        const int xi = (int)xi_d, yi = (int)yi_d;
+        const float xf = (float)(xc - xi_d), yf = (float)(yc - yi_d);
+        DF X2 = df_zero(), Y2 = df_zero(), XY = df_zero();
+        for (int q = lane; q < npx; q += 32) {
+            const int y = bb.z + q / bw, x = bb.x + q % bw;
+            if (__ldg(A.seg + (int64_t)y * W + x) != lab) continue;
+            float w = 1.f;
+            if (!fallback) {
+                bool bad;
+                const float v = load_px<F32>(A.im, x, y, bad);
+                w = v - spline_eval(A.sb, (float)x, (float)y);
+            }
+            const float dx = (float)(x - xi) - xf, dy = (float)(y - yi) - yf;
+            df_add_prod(X2, dx * dx, w);
+            df_add_prod(Y2, dy * dy, w);
+            df_add_prod(XY, dx * dy, w);
+        }
+        X2 = df_warp_sum(X2); Y2 = df_warp_sum(Y2); XY = df_warp_sum(XY);
+        if (lane == 0) {
+            const double d = fallback ? (double)cnt : Sd;
+            A.label[r] = lab;
+            A.npix[r] = cnt;
+            A.flux_iso[r] = Sd;
+            A.x[r] = xc; A.y[r] = yc;
+            A.x2[r] = df_value(X2) / d;
+            A.y2[r] = df_value(Y2) / d;
+            A.xy[r] = df_value(XY) / d;
+            A.xmin[r] = bb.x; A.xmax[r] = bb.y; A.ymin[r] = bb.z; A.ymax[r] = bb.w;
+            A.peak[r] = pk;
+            A.xpeak[r] = (int)(pkL % W); A.ypeak[r] = (int)(pkL / W);
+            A.flags[r] = (sat ? GP_FLAG_SAT : 0u) | (fallback ? GP_FLAG_CENTROID_FALLBACK : 0u);
+        }
+        if (A.ap.nr > 0)
+            aperture_warp<F32>(A.im, A.sb, A.sr, A.ap, xc, yc, A.apflux + (int64_t)r * A.ap.nr,
+                               A.apferr + (int64_t)r * A.ap.nr, A.apflags + (int64_t)r * A.ap.nr);
+    }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap, const double* xs,
+                                                  const double* ys, int n, double* flux, double* ferr, uint32_t* fl)
+{
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = wid; i < n; i += nw)
+        aperture_warp<F32>(im, sb, sr, ap, xs[i], ys[i], flux + (int64_t)i * ap.nr, ferr + (int64_t)i * ap.nr,
+                           fl + (int64_t)i * ap.nr);
+}
+
+// --------------------------------------------------------------- launchers ---
+static ApSpec make_ap(const float* radii, int nr, float gain)
+{
+    ApSpec s;
+    s.nr = nr;
+    s.rmax = 0.f;
+    for (int k = 0; k < MAX_NR; ++k) {
+        s.r[k] = k < nr ? radii[k] : 0.f;
+        if (k < nr) s.rmax = fmaxf(s.rmax, radii[k]);
+    }
+    s.gain = gain;
+    return s;
+}
+
+cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab& sr, const Comps& C,
+                           const uint32_t* seg, const gp_catalog& cat, const float* radii, int nr, float gain,
+                           double* apflux, double* apferr, uint32_t* apflags, cudaStream_t st)
+{
+    MeasureArgs A;
+    A.im = im; A.sb = sb; A.sr = sr; A.C = C; A.seg = seg;
+    A.capacity = cat.capacity;
+    A.label = cat.label; A.npix = cat.npix; A.flux_iso = cat.flux_iso;
+    A.x = cat.x; A.y = cat.y; A.x2 = cat.x2; A.y2 = cat.y2; A.xy = cat.xy;
+    A.xmin = cat.xmin; A.xmax = cat.xmax; A.ymin = cat.ymin; A.ymax = cat.ymax;
+    A.peak = cat.peak; A.xpeak = cat.xpeak; A.ypeak = cat.ypeak; A.flags = cat.flags;
+    A.ap = make_ap(radii, nr, gain);
+    A.apflux = apflux; A.apferr = apferr; A.apflags = apflags;
+    const int g = 152 * 8;
+    if (im.is_f32)
+        k_measure<true><<<g, 256, 0, st>>>(A);
+    else
+        k_measure<false><<<g, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,
+                            const double* ys, int n, const float* radii, int nr, float gain, double* flux,
+                            double* ferr, uint32_t* fl, cudaStream_t st)
+{
+    ApSpec ap = make_ap(radii, nr, gain);
+    int64_t g64 = ((int64_t)n * 32 + 255) / 256;
+    int g = (int)(g64 < 152 * 8 ? g64 : 152 * 8);
+    if (g < 1) g = 1;
+    if (im.is_f32)
+        k_aperture<true><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
+    else
+        k_aperture<false><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
+    return cudaGetLastError();
+}
+
+}  // namespace gp
