@@ -529,7 +529,9 @@ double orc_overlap_area(double x0, double x1, double y0, double y1, double r)
         if (!(q > p)) continue;
         double mid = 0.5 * (p + q);
         double h = sqrt(r * r - mid * mid);
-        int top_is_h = h < y1, bot_is_h = -h > y0;
+        /* non-strict: h == y1 inside a piece only happens at a tangent
+         * point (y1 == r), where h <= y1 holds on the whole piece */
+        int top_is_h = h <= y1, bot_is_h = -h >= y0;
         double top = top_is_h ? h : y1, bot = bot_is_h ? -h : y0;
         if (top <= bot) continue;
         double gi = Gint(q, r) - Gint(p, r);

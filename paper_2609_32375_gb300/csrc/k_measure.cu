@@ -86,7 +86,7 @@ __device__ float disc_rect_area(float x0, float x1, float y0, float y1, float r)
         if (!(hi > lo)) continue;
         float mid = 0.5f * (lo + hi);
         float h = sqrtf(fmaxf(r2 - mid * mid, 0.f));
-        bool top_h = h < y1, bot_h = -h > y0;
+        bool top_h = h <= y1, bot_h = -h >= y0;
         float top = top_h ? h : y1, bot = bot_h ? -h : y0;
         if (!(top > bot)) continue;
         float gi = (top_h || bot_h) ? chord_int(lo, hi, r2) : 0.f;

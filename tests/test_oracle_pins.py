@@ -137,6 +137,27 @@ def test_overlap_sums_to_disc_area(r):
         assert abs(tot - math.pi * r * r) < 1e-12 * max(1.0, r * r)
 
 
+@pytest.mark.parametrize("r", [0.5, 1.0, 1.5, 2.5, 4.0, 8.0, 12.5])
+def test_overlap_sums_to_disc_area_at_aligned_centres(r):
+    """Centres on a pixel centre, an edge midpoint and a corner make the
+    circle tangent to pixel edges (y = +-r); the sum must still be pi r^2."""
+    for cx, cy in [(0.0, 0.0), (0.5, 0.0), (0.0, 0.5), (0.5, 0.5)]:
+        R = int(math.ceil(r)) + 2
+        tot = sum(oracle.overlap_area(x - 0.5 - cx, x + 0.5 - cx, y - 0.5 - cy, y + 0.5 - cy, r)
+                  for y in range(-R, R + 1) for x in range(-R, R + 1))
+        assert abs(tot - math.pi * r * r) < 1e-12 * max(1.0, r * r), (cx, cy)
+
+
+def test_overlap_tangent_pixel_against_quadrature():
+    """Pixel [-1/2, 1/2] x [r-1, r] under a disc of radius r tangent to its
+    top edge: area = integral of min(h(x), r) - (r - 1) by quadrature."""
+    from scipy.integrate import quad
+    for r in (1.5, 4.0, 12.5):
+        ref, _ = quad(lambda x: min(math.sqrt(r * r - x * x), r) - (r - 1.0), -0.5, 0.5, epsabs=1e-13)
+        assert oracle.overlap_area(-0.5, 0.5, r - 1.0, r, r) == pytest.approx(ref, abs=1e-12)
+        assert oracle.overlap_area(-0.5, 0.5, -r, 1.0 - r, r) == pytest.approx(ref, abs=1e-12)
+
+
 def test_overlap_interior_exterior_and_small_disc():
     r = 5.0
     for y in range(-7, 8):
