@@ -164,6 +164,8 @@ void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w)
     w.P.npix = cv.take<int>(w.P.cap);
     w.P.bbox = cv.take<int4>(w.P.cap);
     w.P.parent = cv.take<int>(w.P.cap);
+    w.P.proot = cv.take<int>(w.P.cap);
+    w.P.mom = cv.take<Moments>(w.P.cap);
     w.P.agg_min = cv.take<uint32_t>(w.P.cap);
     w.P.agg_npix = cv.take<int>(w.P.cap);
     w.P.agg_bbox = cv.take<int4>(w.P.cap);
@@ -172,6 +174,12 @@ void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w)
     w.C.label = cv.take<uint32_t>(w.C.cap);
     w.C.npix = cv.take<int>(w.C.cap);
     w.C.bbox = cv.take<int4>(w.C.cap);
+    w.C.flux = cv.take<double>(w.C.cap);
+    w.C.xy = cv.take<double2>(w.C.cap);
+    w.C.mom2 = cv.take<double4>(w.C.cap);
+    w.C.peak = cv.take<float>(w.C.cap);
+    w.C.peakL = cv.take<uint32_t>(w.C.cap);
+    w.C.flags = cv.take<uint32_t>(w.C.cap);
     w.C.perm = cv.take<int>(w.C.cap);
     w.C.slots = cv.take<int>(w.C.cap);
     bucket_geometry(npix, &w.C.shift, &w.C.nb);
@@ -284,14 +292,30 @@ SplineTab make_tab(const float4* node, int W, int H, int mesh)
     return s;
 }
 
-gp_status run_spline(Carver& cv, const gp_bkg* b, int W, int H, SplineTab* sb, SplineTab* sr, cudaStream_t st)
+// spline tables of both maps from the (float) meshes in b; adds the number
+// of kernels launched to *nlaunch
+gp_status run_spline(Carver& cv, const gp_bkg* b, int W, int H, SplineTab* sb, SplineTab* sr, int* nlaunch,
+                     cudaStream_t st)
 {
     SplineWork w;
-    carve_spline(cv, b->mx, b->my, w);
+    const bool fused = mesh_fits_smem(b->mx, b->my);
+    if (fused) {
+        w.tab_b = cv.take<float4>((size_t)b->mx * b->my);
+        w.tab_r = cv.take<float4>((size_t)b->mx * b->my);
+    } else {
+        carve_spline(cv, b->mx, b->my, w);
+    }
     if (!cv.ok()) return GP_ERR_OOM;
     Axis ax = make_axis(W, b->mesh), ay = make_axis(H, b->mesh);
-    GP_CUDA(launch_spline_tables(b->bkg_mesh, ax, ay, w.scratch, w.tab_b, st));
-    GP_CUDA(launch_spline_tables(b->rms_mesh, ax, ay, w.scratch, w.tab_r, st));
+    if (fused) {
+        GP_CUDA(launch_mesh_all(nullptr, nullptr, nullptr, ax, ay, 1, 1, b->bkg_mesh, b->rms_mesh, w.tab_b, w.tab_r,
+                                st));
+        *nlaunch += 1;
+    } else {
+        GP_CUDA(launch_spline_tables(b->bkg_mesh, ax, ay, w.scratch, w.tab_b, st));
+        GP_CUDA(launch_spline_tables(b->rms_mesh, ax, ay, w.scratch, w.tab_r, st));
+        *nlaunch += 4;
+    }
     *sb = make_tab(w.tab_b, W, H, b->mesh);
     *sr = make_tab(w.tab_r, W, H, b->mesh);
     return GP_OK;
@@ -315,21 +339,31 @@ gp_status run_background(gp_ctx* ctx, Carver& cv, const gp_image* img, const gp_
     Image im = to_image(img);
     GP_CUDA(launch_boxstats(im, B, (double)p->clip_k, p->clip_maxiter, w.bkg_raw, w.rms_raw, w.valid, nullptr, st));
     mark(ctx, 1, st);
-    GP_CUDA(launch_mesh_finalize(w.bkg_raw, w.rms_raw, w.valid, w.tmp_b, w.tmp_r, w.tmp_v, Mx, My, p->filter_size,
-                                 bkg->bkg_mesh, bkg->rms_mesh, st));
-    ctx->launches += 2;
-    if (sb || bkg->bkg_map || bkg->rms_map) {
-        SplineTab tb, tr;
-        gp_status s = run_spline(cv, bkg, W, H, &tb, &tr, st);
+    ctx->launches += 1;
+    SplineTab tb, tr;
+    if (mesh_fits_smem(Mx, My)) {
+        // fill, median filter and both spline tables in one shared-memory CTA
+        float4* tab_b = cv.take<float4>((size_t)Mx * My);
+        float4* tab_r = cv.take<float4>((size_t)Mx * My);
+        if (!cv.ok()) return oom(cv);
+        GP_CUDA(launch_mesh_all(w.bkg_raw, w.rms_raw, w.valid, make_axis(W, B), make_axis(H, B), p->filter_size, 0,
+                                bkg->bkg_mesh, bkg->rms_mesh, tab_b, tab_r, st));
+        ctx->launches += 1;
+        tb = make_tab(tab_b, W, H, B);
+        tr = make_tab(tab_r, W, H, B);
+    } else {
+        GP_CUDA(launch_mesh_finalize(w.bkg_raw, w.rms_raw, w.valid, w.tmp_b, w.tmp_r, w.tmp_v, Mx, My, p->filter_size,
+                                     bkg->bkg_mesh, bkg->rms_mesh, st));
+        ctx->launches += 1;
+        gp_status s = run_spline(cv, bkg, W, H, &tb, &tr, &ctx->launches, st);
         if (s == GP_ERR_OOM) return oom(cv);
         if (s != GP_OK) return s;
-        ctx->launches += 4;
-        if (bkg->bkg_map || bkg->rms_map) {
-            GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
-            ctx->launches += 1;
-        }
-        if (sb) { *sb = tb; *sr = tr; }
     }
+    if (bkg->bkg_map || bkg->rms_map) {
+        GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
+        ctx->launches += 1;
+    }
+    if (sb) { *sb = tb; *sr = tr; }
     mark(ctx, 2, st);
     return GP_OK;
 }
@@ -514,10 +548,9 @@ gp_status gp_detect(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const g
     SplineTab sb, sr;
     begin_call(ctx, st);
     mark(ctx, 1, st);
-    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, st);
+    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, &ctx->launches, st);
     if (s == GP_ERR_OOM) return oom(cv);
     if (s != GP_OK) return s;
-    ctx->launches += 4;
     mark(ctx, 2, st);
     return run_detect(ctx, cv, img, sb, sr, taps, p, segmap, cat, nullptr, 0, 0.f, nullptr, nullptr, nullptr, st);
 }
@@ -537,10 +570,9 @@ gp_status gp_aperture(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const
     SplineTab sb, sr;
     begin_call(ctx, st);
     mark(ctx, 1, st);
-    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, st);
+    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, &ctx->launches, st);
     if (s == GP_ERR_OOM) return oom(cv);
     if (s != GP_OK) return s;
-    ctx->launches += 4;
     mark_to(ctx, 2, 5, st);
     if (n > 0) {
         GP_CUDA(launch_aperture(to_image(img), sb, sr, x, y, n, p->radii, p->nr, p->gain, flux, fluxerr, flags, st));

@@ -208,6 +208,18 @@ __host__ __device__ __forceinline__ int mirror_idx(int i, int N)
 }
 
 // ---------------------------------------------------- workspace layout ---
+// Partial moments of the pixels of one piece of a segment, relative to an
+// origin (the piece's tile corner): compensated sums of m, dx m, dy m,
+// dx^2 m, dy^2 m, dx dy m; the same unweighted (integers, for segments whose
+// sum is not positive); peak value and its linear index; flag bits.
+struct Moments {
+    float2 s, sx, sy, sxx, syy, sxy;   // (hi, lo) pairs
+    int ux, uy, uxx, uyy, uxy;
+    float peak;
+    uint32_t peakL;
+    uint32_t flags;
+};
+
 // Pieces: the parts of segments that touch a detection-tile edge shared
 // with another tile; they are merged across tiles by union-find.
 struct Pieces {
@@ -217,18 +229,27 @@ struct Pieces {
     int* npix;
     int4* bbox;           // xmin, xmax, ymin, ymax (frame coordinates)
     int* parent;          // union-find over piece ids
+    int* proot;           // union-find root after the merge
     uint32_t* agg_min;    // at a root piece: min linear index of the whole segment
     int* agg_npix;
     int4* agg_bbox;
+    Moments* mom;         // partial moments, origin = the piece's tile corner
 };
 
-// Segments that survive the minarea cut, in no particular order until ranked
+// Segments that survive the minarea cut, in no particular order until ranked,
+// with their finished moments
 struct Comps {
     int* count;           // scalar
     int cap;
     uint32_t* label;
     int* npix;
     int4* bbox;
+    double* flux;         // sum of m
+    double2* xy;          // centroid
+    double4* mom2;        // x2, y2, xy, -
+    float* peak;
+    uint32_t* peakL;
+    uint32_t* flags;
     int* perm;            // rank -> component id
     int* slots;           // bucket scatter space
     int* bcnt;            // per label bucket counts

@@ -14,6 +14,10 @@ cudaError_t launch_mesh_finalize(double* bkg, double* rms, int* valid, double* t
                                  int Mx, int My, int fsize, float* bkg_out, float* rms_out, cudaStream_t st);
 cudaError_t launch_spline_tables(const float* mesh, Axis ax, Axis ay, double* scratch, float4* tab, cudaStream_t st);
 size_t spline_scratch_doubles(int Mx, int My);
+bool mesh_fits_smem(int Mx, int My);
+cudaError_t launch_mesh_all(const double* bkg_raw, const double* rms_raw, const int* valid, Axis ax, Axis ay,
+                            int fsize, int mode, float* bkg_mesh, float* rms_mesh, float4* tab_b, float4* tab_r,
+                            cudaStream_t st);
 cudaError_t launch_bkg_maps(const SplineTab& sb, const SplineTab& sr, int W, int H, float* bmap, float* rmap,
                             cudaStream_t st);
 

@@ -578,6 +578,208 @@ __global__ void k_bkg_maps(SplineTab sb, SplineTab sr, int W, int H, float* bmap
     }
 }
 
+// ====================================================== fused mesh kernel ===
+// One CTA does the whole mesh stage in shared memory when the mesh has at
+// most MESH_SMEM_NODES nodes: invalid-box fill, median filter, and the
+// spline tables of both maps.  The tridiagonal matrix of the natural spline
+// depends only on the node positions, so each axis is factorised once
+// (multipliers and reciprocal pivots) and every line is then solved with
+// FMAs only.
+constexpr int MESH_SMEM_NODES = 4096;
+constexpr int MA_NT = 1024;
+
+// byte offset of the LU scratch in k_mesh_all's shared memory: six double
+// arrays and two int arrays of n entries, rounded up to 16 bytes
+__host__ __device__ __forceinline__ size_t mesh_lu_offset(int n)
+{
+    const size_t end = (size_t)n * (6 * sizeof(double) + 2 * sizeof(int));
+    return (end + 15) & ~(size_t)15;
+}
+
+struct AxisLU {
+    double* w;      // elimination multipliers  (index r = 1..n-2)
+    double* ib;     // reciprocal pivots
+    double* c;      // super-diagonal
+    double* ih;     // 1 / interval width (n-1 entries)
+};
+
+__device__ __forceinline__ double node_pos(const Axis& a, int i)
+{
+    return (i == a.n - 1) ? (double)a.tl : (double)a.t0 + (double)i * (double)a.B;
+}
+
+__device__ void factor_axis(const Axis& a, AxisLU L)
+{
+    const int n = a.n;
+    for (int i = 0; i + 1 < n; ++i) L.ih[i] = 1.0 / (node_pos(a, i + 1) - node_pos(a, i));
+    double bprev = 0, cprev = 0;
+    for (int r = 1; r <= n - 2; ++r) {
+        double h0 = node_pos(a, r) - node_pos(a, r - 1), h1 = node_pos(a, r + 1) - node_pos(a, r);
+        double b = 2.0 * (h0 + h1);
+        double w = 0.0;
+        if (r > 1) {
+            w = h0 / bprev;
+            b -= w * cprev;
+        }
+        L.w[r] = w;
+        L.ib[r] = 1.0 / b;
+        L.c[r] = h1;
+        bprev = b;
+        cprev = h1;
+    }
+}
+
+// second derivatives of one line (values v, stride vs) into M (stride ms)
+__device__ void solve_line(const AxisLU& L, int n, const double* v, int vs, double* M, int ms)
+{
+    M[0] = 0.0;
+    if (n >= 2) M[(n - 1) * ms] = 0.0;
+    if (n < 3) return;
+    double dprev = 0.0;
+    for (int r = 1; r <= n - 2; ++r) {
+        double d = 6.0 * ((v[(r + 1) * vs] - v[r * vs]) * L.ih[r] - (v[r * vs] - v[(r - 1) * vs]) * L.ih[r - 1]);
+        d = fma(-L.w[r], dprev, d);
+        M[r * ms] = d;        // forward-eliminated right-hand side
+        dprev = d;
+    }
+    double next = 0.0;
+    for (int r = n - 2; r >= 1; --r) {
+        double val = fma(-L.c[r], next, M[r * ms]) * L.ib[r];
+        M[r * ms] = val;
+        next = val;
+    }
+}
+
+// mode 0: raw box statistics -> fill, filter, write meshes, tables
+// mode 1: tables only, from the float meshes given in bkg_out / rms_out
+__global__ void __launch_bounds__(MA_NT) k_mesh_all(const double* __restrict__ bkg_raw,
+                                                    const double* __restrict__ rms_raw,
+                                                    const int* __restrict__ valid_raw, Axis ax, Axis ay, int fsize,
+                                                    int mode, float* bkg_out, float* rms_out, float4* tab_b,
+                                                    float4* tab_r)
+{
+    extern __shared__ __align__(16) double sh[];
+    unsigned char* sh_bytes = reinterpret_cast<unsigned char*>(sh);
+    const int Mx = ax.n, My = ay.n, n = Mx * My, tid = threadIdx.x;
+    double* A0 = sh;
+    double* A1 = A0 + n;
+    double* A2 = A1 + n;
+    double* A3 = A2 + n;
+    double* A4 = A3 + n;
+    double* A5 = A4 + n;
+    int* V0 = reinterpret_cast<int*>(A5 + n);
+    int* V1 = V0 + n;
+    const int nl = Mx > My ? Mx : My;
+    // the LU scratch starts at the first 16-byte boundary after V1
+    double* lu = reinterpret_cast<double*>(sh_bytes + mesh_lu_offset(n));
+    AxisLU Lx{lu, lu + nl, lu + 2 * nl, lu + 3 * nl};
+    AxisLU Ly{lu + 4 * nl, lu + 5 * nl, lu + 6 * nl, lu + 7 * nl};
+    __shared__ int missing, any;
+
+    if (tid == 0) factor_axis(ax, Lx);
+    if (tid == 32) factor_axis(ay, Ly);
+    if (mode == 0) {
+        if (tid == 0) any = 0;
+        __syncthreads();
+        for (int b = tid; b < n; b += MA_NT) {
+            A0[b] = bkg_raw[b]; A1[b] = rms_raw[b]; V0[b] = valid_raw[b];
+            if (V0[b]) any = 1;
+        }
+        __syncthreads();
+        if (!any) {
+            for (int b = tid; b < n; b += MA_NT) { A0[b] = 0; A1[b] = 0; V0[b] = 1; }
+            __syncthreads();
+        }
+        // fill invalid boxes from valid 8-neighbours, sweep after sweep
+        for (int sweep = 0; sweep < Mx + My + 2; ++sweep) {
+            if (tid == 0) missing = 0;
+            __syncthreads();
+            for (int b = tid; b < n; b += MA_NT) {
+                A2[b] = A0[b]; A3[b] = A1[b]; V1[b] = V0[b];
+                if (V0[b]) continue;
+                int i = b % Mx, j = b / Mx, c = 0;
+                double sb = 0, sr = 0;
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        int ii = i + di, jj = j + dj;
+                        if ((di || dj) && ii >= 0 && ii < Mx && jj >= 0 && jj < My && V0[jj * Mx + ii]) {
+                            sb += A0[jj * Mx + ii];
+                            sr += A1[jj * Mx + ii];
+                            ++c;
+                        }
+                    }
+                if (c) { A2[b] = sb / c; A3[b] = sr / c; V1[b] = 1; }
+                else missing = 1;
+            }
+            __syncthreads();
+            for (int b = tid; b < n; b += MA_NT) { A0[b] = A2[b]; A1[b] = A3[b]; V0[b] = V1[b]; }
+            __syncthreads();
+            if (!missing) break;
+        }
+        // median filter (window clipped at the mesh edge) -> float meshes
+        const int h = fsize / 2;
+        for (int b = tid; b < n; b += MA_NT) {
+            int i = b % Mx, j = b / Mx;
+            for (int map = 0; map < 2; ++map) {
+                const double* src = map ? A1 : A0;
+                double win[49];
+                int c = 0;
+                for (int jj = j - h; jj <= j + h; ++jj)
+                    for (int ii = i - h; ii <= i + h; ++ii)
+                        if (ii >= 0 && ii < Mx && jj >= 0 && jj < My) {
+                            double v = src[jj * Mx + ii];
+                            int p = c++;
+                            while (p > 0 && win[p - 1] > v) { win[p] = win[p - 1]; --p; }
+                            win[p] = v;
+                        }
+                double med = (c & 1) ? win[c / 2] : 0.5 * (win[c / 2 - 1] + win[c / 2]);
+                (map ? rms_out : bkg_out)[b] = (float)med;
+            }
+        }
+    }
+    __syncthreads();
+    // spline tables, one map at a time, from the float meshes
+    for (int map = 0; map < 2; ++map) {
+        const float* mesh = map ? rms_out : bkg_out;
+        float4* tab = map ? tab_r : tab_b;
+        for (int b = tid; b < n; b += MA_NT) A4[b] = (double)mesh[b];
+        __syncthreads();
+        for (int t = tid; t < My + Mx; t += MA_NT) {
+            if (t < My) solve_line(Lx, Mx, A4 + t * Mx, 1, A0 + t * Mx, 1);      // X
+            else solve_line(Ly, My, A4 + (t - My), Mx, A1 + (t - My), Mx);        // Y
+        }
+        __syncthreads();
+        for (int t = tid; t < My; t += MA_NT) solve_line(Lx, Mx, A1 + t * Mx, 1, A2 + t * Mx, 1);   // XY
+        __syncthreads();
+        for (int b = tid; b < n; b += MA_NT)
+            tab[b] = make_float4(mesh[b], (float)A0[b], (float)A1[b], (float)A2[b]);
+        __syncthreads();
+    }
+}
+
+size_t mesh_all_smem(int Mx, int My)
+{
+    const size_t n = (size_t)Mx * My;
+    const size_t nl = Mx > My ? Mx : My;
+    return mesh_lu_offset((int)n) + 8 * nl * sizeof(double);
+}
+
+bool mesh_fits_smem(int Mx, int My)
+{
+    return (size_t)Mx * My <= (size_t)MESH_SMEM_NODES && mesh_all_smem(Mx, My) <= 220 * 1024;
+}
+
+cudaError_t launch_mesh_all(const double* bkg_raw, const double* rms_raw, const int* valid, Axis ax, Axis ay,
+                            int fsize, int mode, float* bkg_mesh, float* rms_mesh, float4* tab_b, float4* tab_r,
+                            cudaStream_t st)
+{
+    const size_t smem = mesh_all_smem(ax.n, ay.n);
+    cudaFuncSetAttribute(k_mesh_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mesh_all<<<1, MA_NT, smem, st>>>(bkg_raw, rms_raw, valid, ax, ay, fsize, mode, bkg_mesh, rms_mesh, tab_b,
+                                       tab_r);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- launchers ---
 cudaError_t launch_boxstats(const Image& im, int B, double k, int maxiter, double* bkg, double* rms, int* valid,
                             float* quant, cudaStream_t st)

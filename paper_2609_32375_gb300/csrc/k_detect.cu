@@ -1,23 +1,29 @@
 // k_detect.cu -- matched-filter detection and segmentation (paper Section
-// 3.2, with labelled segments in place of the paper's local maxima).
+// 3.2, with labelled segments in place of the paper's local maxima) and the
+// segment moments (its first-moment centroid, extended to second moments,
+// bounding box and peak).
 //
 //  k_detect_tile  one CTA per 64 x 32 tile.  Stages the tile plus a filter
 //                 halo in shared memory as m = I - B (the spline background
-//                 evaluated from per-column node rows), correlates it with
-//                 the normalised kernel, thresholds F > k sigma(p), labels
-//                 the tile's 8-connected components by union-find in shared
-//                 memory (root = minimum index, i.e. the segment's first
-//                 pixel in raster order) and writes the segmentation map.
-//                 Components that do not touch an edge shared with another
-//                 tile are final here; the others become "pieces" whose
+//                 evaluated from per-column node rows; 16-byte vector loads
+//                 on interior tiles), correlates it with the normalised
+//                 kernel (each thread slides down 8 rows of one column),
+//                 thresholds F > k sigma(p), labels the tile's 8-connected
+//                 components by union-find in shared memory (root = minimum
+//                 index = the segment's first pixel in raster order) and
+//                 accumulates each component's moments from the staged m
+//                 (one warp per component, fixed order).  Components that do
+//                 not touch an edge shared with another tile are final here;
+//                 the others become "pieces" with partial moments, and their
 //                 edge pixels are recorded for the merge.
 //  k_merge        unites pieces across tile edges (lock-free union-find
 //                 over piece ids, atomicMin linking).
 //  k_aggregate    sums piece sizes, bounding boxes and minimum indices at
 //                 each union-find root.
-//  k_finalize     emits merged segments, and rewrites the map pixels of
-//                 pieces whose final label differs (other root, or below
-//                 minarea) -- a sparse pass over those pieces' boxes only.
+//  k_finalize     merges the partial moments of each multi-tile segment in
+//                 tile raster order (deterministic), and rewrites the map
+//                 pixels of pieces whose final label differs (other root, or
+//                 below minarea) -- a sparse pass over those pieces only.
 //  k_rank_*       orders segments by label (bucket counts, one scan,
 //                 scatter, in-bucket rank): a deterministic catalog order.
 #include <math.h>
@@ -29,6 +35,7 @@ namespace gp {
 
 constexpr int DT_NT = 256;
 constexpr int KMAX = (2 * HMAX + 1) * (2 * HMAX + 1);
+constexpr int ROWS_PER_THREAD = TNPIX / DT_NT;     // 8: each thread filters 8 rows of one column
 
 struct DetectArgs {
     float K[KMAX];            // normalised taps, kh rows of kw (kernel parameter space)
@@ -46,6 +53,14 @@ struct DetectArgs {
     Comps C;
     int* status;
 };
+
+// mirror without edge repeat, cheap for offsets within one reflection
+__device__ __forceinline__ int mirror_fast(int i, int N)
+{
+    if (i < 0) i = -i;
+    if (i >= N) i = 2 * (N - 1) - i;
+    return (i >= 0 && i < N) ? i : mirror_idx(i, N);
+}
 
 // ------------------------------------------------ shared-memory union-find ---
 __device__ __forceinline__ int sfind(volatile int* lab, int x)
@@ -126,189 +141,360 @@ __device__ __forceinline__ int block_excl_scan(int v, int* warp_tot, int* total)
     return r;
 }
 
-template <bool F32, bool LABEL_ONLY>
+// ------------------------------------------------------------- moments ---
+struct MomAcc {
+    DF s, sx, sy, sxx, syy, sxy;
+    int ux, uy, uxx, uyy, uxy;
+    float peak;
+    uint32_t peakL;
+    uint32_t flags;
+};
+
+__device__ __forceinline__ void mom_zero(MomAcc& a)
+{
+    a.s = a.sx = a.sy = a.sxx = a.syy = a.sxy = df_zero();
+    a.ux = a.uy = a.uxx = a.uyy = a.uxy = 0;
+    a.peak = -INFINITY;
+    a.peakL = 0xffffffffu;
+    a.flags = 0u;
+}
+
+__device__ __forceinline__ void mom_pixel(MomAcc& a, float m, int dx, int dy, uint32_t L, bool sat)
+{
+    const float fx = (float)dx, fy = (float)dy;
+    df_add(a.s, m);
+    df_add_prod(a.sx, fx, m);
+    df_add_prod(a.sy, fy, m);
+    df_add_prod(a.sxx, fx * fx, m);
+    df_add_prod(a.syy, fy * fy, m);
+    df_add_prod(a.sxy, fx * fy, m);
+    a.ux += dx; a.uy += dy;
+    a.uxx += dx * dx; a.uyy += dy * dy; a.uxy += dx * dy;
+    if (m > a.peak || (m == a.peak && L < a.peakL)) { a.peak = m; a.peakL = L; }
+    if (sat) a.flags |= GP_FLAG_SAT;
+}
+
+__device__ __forceinline__ void mom_warp_reduce(MomAcc& a)
+{
+    a.s = df_warp_sum(a.s); a.sx = df_warp_sum(a.sx); a.sy = df_warp_sum(a.sy);
+    a.sxx = df_warp_sum(a.sxx); a.syy = df_warp_sum(a.syy); a.sxy = df_warp_sum(a.sxy);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.ux += __shfl_xor_sync(0xffffffffu, a.ux, o);
+        a.uy += __shfl_xor_sync(0xffffffffu, a.uy, o);
+        a.uxx += __shfl_xor_sync(0xffffffffu, a.uxx, o);
+        a.uyy += __shfl_xor_sync(0xffffffffu, a.uyy, o);
+        a.uxy += __shfl_xor_sync(0xffffffffu, a.uxy, o);
+        a.flags |= __shfl_xor_sync(0xffffffffu, a.flags, o);
+        float op = __shfl_xor_sync(0xffffffffu, a.peak, o);
+        uint32_t oL = __shfl_xor_sync(0xffffffffu, a.peakL, o);
+        if (op > a.peak || (op == a.peak && oL < a.peakL)) { a.peak = op; a.peakL = oL; }
+    }
+}
+
+__device__ __forceinline__ float2 df2(DF d) { return make_float2(d.hi, d.lo); }
+
+// finished moments of a whole segment from sums about the origin (X0, Y0)
+__device__ void mom_finish(double S, double Sx, double Sy, double Sxx, double Syy, double Sxy, long long ux,
+                           long long uy, long long uxx, long long uyy, long long uxy, int npix, int X0, int Y0,
+                           double* flux, double2* xy, double4* m2, uint32_t* flags)
+{
+    *flux = S;
+    if (S > 0.0) {
+        const double mx = Sx / S, my = Sy / S;
+        *xy = make_double2(X0 + mx, Y0 + my);
+        *m2 = make_double4(Sxx / S - mx * mx, Syy / S - my * my, Sxy / S - mx * my, 0.0);
+    } else {
+        const double n = (double)npix;
+        const double mx = (double)ux / n, my = (double)uy / n;
+        *xy = make_double2(X0 + mx, Y0 + my);
+        *m2 = make_double4((double)uxx / n - mx * mx, (double)uyy / n - my * my, (double)uxy / n - mx * my, 0.0);
+        *flags |= GP_FLAG_CENTROID_FALLBACK;
+    }
+}
+
+// ----------------------------------------------------------- tile kernel ---
+struct TileSmem {
+    float m[SH * SW];                 // staged m = I - B
+    int lab[TNPIX];
+    short rid[TNPIX];
+    uint8_t pflag[TNPIX];             // bit 0 bad, bit 1 saturated
+    float4 colv[NJMAX * SW];          // per column and node row: (u_bkg, w_bkg, u_rms, w_rms)
+    float4 rowc[SH];                  // per staged row: (b, c0, c1, -)
+    int2 rowj[SH];
+    int r_npix[MAXROOT];
+    int r_xmin[MAXROOT], r_xmax[MAXROOT], r_ymin[MAXROOT], r_ymax[MAXROOT];
+    int r_pidx[MAXROOT];              // border flag, then local piece index
+    int r_pix[MAXROOT];               // root's tile pixel
+    int r_val[MAXROOT];               // value written to the map
+    int r_rec[MAXROOT];               // piece id (>= 0), -2 - component id, or -1
+    int warp_tot[DT_NT / 32];
+    int jlo, jhi, nroots, npieces, ncomps, pbase, cbase, nnear;
+};
+
+__device__ __forceinline__ float combine_row(const float4& rc, float v0, float v1, float m0, float m1)
+{
+    return fmaf(rc.z, m1, fmaf(rc.y, m0, fmaf(rc.x, v1 - v0, v0)));
+}
+
+__device__ __forceinline__ void stage_cell(TileSmem& S, const DetectArgs& A, int ry, int cx, float v, bool bad,
+                                           int hh, int th, int tw)
+{
+    const int2 j = S.rowj[ry];
+    const float4 n0 = S.colv[j.x * SW + cx], n1 = S.colv[j.y * SW + cx];
+    const float Bv = combine_row(S.rowc[ry], n0.x, n1.x, n0.y, n1.y);
+    S.m[ry * SW + cx] = bad ? 0.f : v - Bv;
+    const int py = ry - hh, px = cx - hh;
+    if (py >= 0 && py < th && px >= 0 && px < tw)
+        S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && A.im.sat > 0.f && v >= A.im.sat) ? 2 : 0);
+}
+
+// F at 8 consecutive rows of one column: slide the kernel window down the
+// column so each staged value is read once per kernel column
+template <int KS>
+__device__ __forceinline__ void filter_column(const TileSmem& S, const DetectArgs& A, int px, int py0, int hh,
+                                              float* F)
+{
+    if (KS > 0) {
+        constexpr int H = KS / 2;
+#pragma unroll
+        for (int i = 0; i < ROWS_PER_THREAD; ++i) F[i] = 0.f;
+        const int c0 = px + hh - H;
+        const int r0 = py0 + hh - H;
+#pragma unroll
+        for (int rr = 0; rr < ROWS_PER_THREAD + KS - 1; ++rr) {
+            float v[KS > 0 ? KS : 1];
+#pragma unroll
+            for (int u = 0; u < KS; ++u) v[u] = S.m[(r0 + rr) * SW + c0 + u];
+#pragma unroll
+            for (int i = 0; i < ROWS_PER_THREAD; ++i) {
+                const int kv = rr - i;
+                if (kv >= 0 && kv < KS) {
+#pragma unroll
+                    for (int u = 0; u < KS; ++u) F[i] = fmaf(A.K[kv * KS + u], v[u], F[i]);
+                }
+            }
+        }
+    } else {
+        for (int i = 0; i < ROWS_PER_THREAD; ++i) {
+            float f = 0.f;
+            const int r0 = py0 + i + hh - A.hy, c0 = px + hh - A.hx;
+            for (int v = 0; v < A.kh; ++v) {
+                const float* row = S.m + (r0 + v) * SW + c0;
+                const float* kr = A.K + v * A.kw;
+                for (int u = 0; u < A.kw; ++u) f = fmaf(kr[u], row[u], f);
+            }
+            F[i] = f;
+        }
+    }
+}
+
+template <bool F32, bool LABEL_ONLY, int KS>
 __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
 {
-    // m over tile + halo; reused after thresholding for per-root records
-    __shared__ __align__(16) float sm_m[SH * SW];
-    __shared__ int lab[TNPIX];
-    __shared__ __align__(16) uint8_t badpx[TNPIX];   // reused as root pixel list
-    __shared__ short rid[TNPIX];
-    __shared__ float4 colv[NJMAX * SW];   // per column and node row: (u_bkg, w_bkg, u_rms, w_rms)
-    __shared__ float4 rowc[SH];            // per staged row: (b, c0, c1, -)
-    __shared__ int2 rowj[SH];
-    __shared__ int jlo_s, jhi_s;
-    __shared__ int warp_tot[DT_NT / 32];
-    __shared__ int nroots_s, npieces_s, ncomps_s, pbase_s, cbase_s;
-    __shared__ int near_s;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
 
-    int* r_val = reinterpret_cast<int*>(sm_m);          // value written to the map
-    int* r_xmin = r_val + MAXROOT;
-    int* r_xmax = r_xmin + MAXROOT;
-    int* r_ymin = r_xmax + MAXROOT;
-    int* r_ymax = r_ymin + MAXROOT;
-    int* r_pidx = r_ymax + MAXROOT;                     // border flag, then local piece index
-    int* r_pix = reinterpret_cast<int*>(badpx);         // root's tile pixel
-
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = A.im.W, H = A.im.H;
     const int tile = blockIdx.x;
     const int ntx = A.T.ntx;
     const int tx = tile % ntx, ty = tile / ntx;
     const int x0 = tx * TX, y0 = ty * TY;
     const int tw = min(TX, W - x0), th = min(TY, H - y0);
+    const int hh = LABEL_ONLY ? 0 : A.hh;
 
     if (!LABEL_ONLY) {
-        const int hh = A.hh;
         const int scols = tw + 2 * hh, srows = th + 2 * hh;
-        if (tid == 0) { jlo_s = 1 << 30; jhi_s = -1; near_s = 0; }
+        if (tid == 0) { S.jlo = 1 << 30; S.jhi = -1; S.nnear = 0; }
         __syncthreads();
-        // node rows needed by the staged rows
-        for (int ry = tid; ry < srows; ry += DT_NT) {
-            int gy = mirror_idx(y0 - hh + ry, H);
-            AxCoef c = axis_coef(A.sb.ay, (float)gy);
-            atomicMin(&jlo_s, c.i);
-            atomicMax(&jhi_s, c.i1);
+        // spline coefficients of the staged rows (and the node rows they need)
+        AxCoef cy;
+        if (tid < srows) {
+            const int gy = mirror_fast(y0 - hh + tid, H);
+            cy = axis_coef(A.sb.ay, (float)gy);
+            atomicMin(&S.jlo, cy.i);
+            atomicMax(&S.jhi, cy.i1);
         }
         __syncthreads();
-        const int jlo = jlo_s;
-        const int nj = jhi_s - jlo + 1;
+        const int jlo = S.jlo;
+        const int nj = S.jhi - jlo + 1;
         if (nj > NJMAX) {   // excluded by the host's mesh >= 16 rule
             if (tid == 0) set_status(A.status, GP_ERR_INTERNAL);
             return;
         }
-        for (int ry = tid; ry < srows; ry += DT_NT) {
-            int gy = mirror_idx(y0 - hh + ry, H);
-            AxCoef c = axis_coef(A.sb.ay, (float)gy);
-            rowc[ry] = make_float4(c.b, c.c0, c.c1, 0.f);
-            rowj[ry] = make_int2(c.i - jlo, c.i1 - jlo);
+        if (tid < srows) {
+            S.rowc[tid] = make_float4(cy.b, cy.c0, cy.c1, 0.f);
+            S.rowj[tid] = make_int2(cy.i - jlo, cy.i1 - jlo);
         }
         for (int q = tid; q < nj * scols; q += DT_NT) {
-            int jj = q / scols, cx = q - jj * scols;
-            int gx = mirror_idx(x0 - hh + cx, W);
-            AxCoef c = axis_coef(A.sb.ax, (float)gx);
-            float2 b = row_eval(A.sb, jlo + jj, c);
-            float2 r = row_eval(A.sr, jlo + jj, c);
-            colv[jj * SW + cx] = make_float4(b.x, b.y, r.x, r.y);
+            const int jj = q / scols, cx = q - jj * scols;
+            const int gx = mirror_fast(x0 - hh + cx, W);
+            const AxCoef c = axis_coef(A.sb.ax, (float)gx);
+            const float2 b = row_eval(A.sb, jlo + jj, c);
+            const float2 r = row_eval(A.sr, jlo + jj, c);
+            S.colv[jj * SW + cx] = make_float4(b.x, b.y, r.x, r.y);
         }
         __syncthreads();
-        // stage m = I - B over tile + halo (mirror border; bad pixels -> 0)
-        for (int q = tid; q < srows * scols; q += DT_NT) {
-            int ry = q / scols, cx = q - ry * scols;
-            int gx = mirror_idx(x0 - hh + cx, W), gy = mirror_idx(y0 - hh + ry, H);
-            float v;
-            bool bad;
-            if (F32) {
-                v = __ldg(reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx);
-                bad = !isfinite(v);
-            } else {
-                v = (float)__ldg(reinterpret_cast<const uint16_t*>(A.im.data) + (int64_t)gy * A.im.pitch + gx);
-                bad = false;
-            }
-            if (A.im.mask && A.im.mask[(int64_t)gy * W + gx]) bad = true;
-            int2 j = rowj[ry];
-            float4 c = rowc[ry];
-            float4 n0 = colv[j.x * SW + cx], n1 = colv[j.y * SW + cx];
-            AxCoef cy; cy.b = c.x; cy.c0 = c.y; cy.c1 = c.z;
-            float Bv = axis_combine(cy, n0.x, n1.x, n0.y, n1.y);
-            sm_m[ry * SW + cx] = bad ? 0.f : v - Bv;
-            int py = ry - hh, px = cx - hh;
-            if (py >= 0 && py < th && px >= 0 && px < tw) badpx[py * TX + px] = bad;
-        }
-        __syncthreads();
-        // matched filter, threshold
-        int nnear = 0;
-        for (int p = tid; p < TNPIX; p += DT_NT) {
-            int py = p / TX, px = p - py * TX;
-            bool fg = false;
-            if (py < th && px < tw) {
-                float F = 0.f;
-                const int r0 = py + hh - A.hy, c0 = px + hh - A.hx;
-                for (int v = 0; v < A.kh; ++v) {
-                    const float* row = sm_m + (r0 + v) * SW + c0;
-                    const float* kr = A.K + v * A.kw;
-                    for (int u = 0; u < A.kw; ++u) F = fmaf(kr[u], row[u], F);
-                }
-                int ry = py + hh, cx = px + hh;
-                int2 j = rowj[ry];
-                float4 c = rowc[ry];
-                float4 n0 = colv[j.x * SW + cx], n1 = colv[j.y * SW + cx];
-                AxCoef cy; cy.b = c.x; cy.c0 = c.y; cy.c1 = c.z;
-                float sig = axis_combine(cy, n0.z, n1.z, n0.w, n1.w);
-                float thr = A.thresh * sig;
-                fg = (F > thr) && !badpx[p];
-                if (fabsf(F - thr) <= 1e-5f * fabsf(thr)) ++nnear;
-                if (A.mask_out) A.mask_out[(int64_t)(y0 + py) * W + x0 + px] = fg ? 1 : 0;
-            }
-            lab[p] = fg ? p : -1;
-        }
-        if (A.nnear) {
+
+        // ---- stage m = I - B over tile + halo (mirror border; bad -> 0)
+        const bool interior = x0 - hh >= 0 && x0 + tw + hh <= W && y0 - hh >= 0 && y0 + th + hh <= H;
+        constexpr int VEC = F32 ? 4 : 8;          // pixels per 16-byte load
+        const bool vec_ok = interior && !A.im.mask && ((((uintptr_t)A.im.data) & 15) == 0) &&
+                            ((A.im.pitch % VEC) == 0);
+        if (vec_ok) {
+            // aligned chunks covering [x0 - hh, x0 + tw + hh); all inside the row
+            // because the tile is interior and x0 is a multiple of the chunk
+            const int xa = (x0 - hh) & ~(VEC - 1);
+            const int nchunk = (x0 + tw + hh - xa + VEC - 1) / VEC;
+            for (int q = tid; q < srows * nchunk; q += DT_NT) {
+                const int ry = q / nchunk, ch = q - ry * nchunk;
+                const int gy = y0 - hh + ry;
+                const int gx0 = xa + ch * VEC;
+                float v[VEC];
+                if (gx0 + VEC <= W) {
+                    if (F32) {
+                        const float4 w = __ldg(reinterpret_cast<const float4*>(
+                            reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx0));
+                        v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+                    } else {
+                        const uint4 w = __ldg(reinterpret_cast<const uint4*>(
+                            reinterpret_cast<const uint16_t*>(A.im.data) + (int64_t)gy * A.im.pitch + gx0));
+                        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) nnear += __shfl_xor_sync(0xffffffffu, nnear, o);
-            if ((tid & 31) == 0 && nnear) atomicAdd(&near_s, nnear);
+                        for (int e = 0; e < 4; ++e) {
+                            v[2 * e] = (float)(u[e] & 0xffffu);
+                            v[2 * e + 1] = (float)(u[e] >> 16);
+                        }
+                    }
+                } else {
+                    // the frame's last chunk of a row may stop short of VEC pixels
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const int gx = gx0 + e < W ? gx0 + e : W - 1;
+                        v[e] = F32 ? __ldg(reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx)
+                                   : (float)__ldg(reinterpret_cast<const uint16_t*>(A.im.data) +
+                                                  (int64_t)gy * A.im.pitch + gx);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const int cx = gx0 + e - (x0 - hh);
+                    if (cx < 0 || cx >= scols) continue;
+                    stage_cell(S, A, ry, cx, v[e], F32 ? !isfinite(v[e]) : false, hh, th, tw);
+                }
+            }
+        } else {
+            for (int q = tid; q < srows * scols; q += DT_NT) {
+                const int ry = q / scols, cx = q - ry * scols;
+                const int gx = mirror_fast(x0 - hh + cx, W), gy = mirror_fast(y0 - hh + ry, H);
+                float v;
+                bool bad;
+                if (F32) {
+                    v = __ldg(reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx);
+                    bad = !isfinite(v);
+                } else {
+                    v = (float)__ldg(reinterpret_cast<const uint16_t*>(A.im.data) + (int64_t)gy * A.im.pitch + gx);
+                    bad = false;
+                }
+                if (A.im.mask && A.im.mask[(int64_t)gy * W + gx]) bad = true;
+                stage_cell(S, A, ry, cx, v, bad, hh, th, tw);
+            }
         }
         __syncthreads();
-        if (A.nnear && tid == 0 && near_s) atomicAdd(A.nnear, near_s);
+
+        // ---- matched filter and threshold: thread = one column, 8 rows
+        {
+            const int px = tid % TX;
+            const int py0 = (tid / TX) * ROWS_PER_THREAD;
+            float F[ROWS_PER_THREAD];
+            filter_column<KS>(S, A, px, py0, hh, F);
+            int nnear = 0;
+#pragma unroll
+            for (int i = 0; i < ROWS_PER_THREAD; ++i) {
+                const int py = py0 + i;
+                const int p = py * TX + px;
+                bool fg = false;
+                if (py < th && px < tw) {
+                    const int ry = py + hh, cx = px + hh;
+                    const int2 j = S.rowj[ry];
+                    const float4 n0 = S.colv[j.x * SW + cx], n1 = S.colv[j.y * SW + cx];
+                    const float sig = combine_row(S.rowc[ry], n0.z, n1.z, n0.w, n1.w);
+                    const float thr = A.thresh * sig;
+                    fg = (F[i] > thr) && !(S.pflag[p] & 1);
+                    if (fabsf(F[i] - thr) <= 1e-5f * fabsf(thr)) ++nnear;
+                    if (A.mask_out) A.mask_out[(int64_t)(y0 + py) * W + x0 + px] = fg ? 1 : 0;
+                }
+                S.lab[p] = fg ? p : -1;
+            }
+            if (A.nnear) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) nnear += __shfl_xor_sync(0xffffffffu, nnear, o);
+                if (lane == 0 && nnear) atomicAdd(&S.nnear, nnear);
+            }
+        }
+        __syncthreads();
+        if (A.nnear && tid == 0 && S.nnear) atomicAdd(A.nnear, S.nnear);
     } else {
         for (int p = tid; p < TNPIX; p += DT_NT) {
-            int py = p / TX, px = p - py * TX;
-            bool fg = py < th && px < tw && A.in_mask[(int64_t)(y0 + py) * W + x0 + px] != 0;
-            lab[p] = fg ? p : -1;
+            const int py = p / TX, px = p - py * TX;
+            const bool fg = py < th && px < tw && A.in_mask[(int64_t)(y0 + py) * W + x0 + px] != 0;
+            S.lab[p] = fg ? p : -1;
+            S.pflag[p] = 0;
         }
         __syncthreads();
     }
 
     // ---- tile-local union-find: link each pixel to its W, NW, N, NE neighbours
     for (int p = tid; p < TNPIX; p += DT_NT) {
-        if (lab[p] < 0) continue;
-        int py = p / TX, px = p - py * TX;
-        if (px > 0 && lab[p - 1] >= 0) sunite(lab, p, p - 1);
+        if (S.lab[p] < 0) continue;
+        const int py = p / TX, px = p - py * TX;
+        if (px > 0 && S.lab[p - 1] >= 0) sunite(S.lab, p, p - 1);
         if (py > 0) {
-            if (px > 0 && lab[p - TX - 1] >= 0) sunite(lab, p, p - TX - 1);
-            if (lab[p - TX] >= 0) sunite(lab, p, p - TX);
-            if (px + 1 < tw && lab[p - TX + 1] >= 0) sunite(lab, p, p - TX + 1);
+            if (px > 0 && S.lab[p - TX - 1] >= 0) sunite(S.lab, p, p - TX - 1);
+            if (S.lab[p - TX] >= 0) sunite(S.lab, p, p - TX);
+            if (px + 1 < tw && S.lab[p - TX + 1] >= 0) sunite(S.lab, p, p - TX + 1);
         }
     }
     __syncthreads();
     for (int p = tid; p < TNPIX; p += DT_NT)
-        if (lab[p] >= 0) lab[p] = sfind(lab, p);
+        if (S.lab[p] >= 0) S.lab[p] = sfind(S.lab, p);
     __syncthreads();
 
     // ---- compact root numbering in raster (= label) order
     {
-        const int per = TNPIX / DT_NT;   // 8 contiguous pixels per thread
         int cnt = 0;
-        for (int e = 0; e < per; ++e) {
-            int p = tid * per + e;
-            cnt += (lab[p] == p);
+        for (int e = 0; e < ROWS_PER_THREAD; ++e) {
+            const int p = tid * ROWS_PER_THREAD + e;
+            cnt += (S.lab[p] == p);
         }
-        int off = block_excl_scan(cnt, warp_tot, &nroots_s);
-        for (int e = 0; e < per; ++e) {
-            int p = tid * per + e;
-            if (lab[p] == p) {
-                rid[p] = (short)off;
-                r_pix[off] = p;
+        int off = block_excl_scan(cnt, S.warp_tot, &S.nroots);
+        for (int e = 0; e < ROWS_PER_THREAD; ++e) {
+            const int p = tid * ROWS_PER_THREAD + e;
+            if (S.lab[p] == p) {
+                S.rid[p] = (short)off;
+                S.r_pix[off] = p;
                 ++off;
             }
         }
     }
     __syncthreads();
-    const int nroots = nroots_s;
+    const int nroots = S.nroots;
     for (int r = tid; r < nroots; r += DT_NT) {
-        r_val[r] = 0; r_xmin[r] = TX; r_xmax[r] = -1; r_ymin[r] = TY; r_ymax[r] = -1; r_pidx[r] = 0;
+        S.r_npix[r] = 0; S.r_xmin[r] = TX; S.r_xmax[r] = -1; S.r_ymin[r] = TY; S.r_ymax[r] = -1; S.r_pidx[r] = 0;
     }
     __syncthreads();
     for (int p = tid; p < TNPIX; p += DT_NT) {
-        int l = lab[p];
+        const int l = S.lab[p];
         if (l < 0) continue;
-        int r = rid[l];
-        int py = p / TX, px = p - py * TX;
-        atomicAdd(r_val + r, 1);
-        atomicMin(r_xmin + r, px); atomicMax(r_xmax + r, px);
-        atomicMin(r_ymin + r, py); atomicMax(r_ymax + r, py);
-        bool border = (px == 0 && x0 > 0) || (px == tw - 1 && x0 + tw < W) ||
-                      (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
-        if (border) r_pidx[r] = 1;
+        const int r = S.rid[l];
+        const int py = p / TX, px = p - py * TX;
+        atomicAdd(S.r_npix + r, 1);
+        atomicMin(S.r_xmin + r, px); atomicMax(S.r_xmax + r, px);
+        atomicMin(S.r_ymin + r, py); atomicMax(S.r_ymax + r, py);
+        const bool border = (px == 0 && x0 > 0) || (px == tw - 1 && x0 + tw < W) ||
+                            (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
+        if (border) S.r_pidx[r] = 1;
     }
     __syncthreads();
 
@@ -316,62 +502,108 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
     int isp[2], isc[2];
     int pc = 0, cc = 0;
     for (int e = 0; e < 2; ++e) {
-        int r = tid * 2 + e;
-        isp[e] = (r < nroots) && r_pidx[r];
-        isc[e] = (r < nroots) && !r_pidx[r] && r_val[r] >= A.minarea;
+        const int r = tid * 2 + e;
+        isp[e] = (r < nroots) && S.r_pidx[r];
+        isc[e] = (r < nroots) && !S.r_pidx[r] && S.r_npix[r] >= A.minarea;
         pc += isp[e]; cc += isc[e];
     }
-    int poff = block_excl_scan(pc, warp_tot, &npieces_s);
-    int coff = block_excl_scan(cc, warp_tot, &ncomps_s);
+    int poff = block_excl_scan(pc, S.warp_tot, &S.npieces);
+    int coff = block_excl_scan(cc, S.warp_tot, &S.ncomps);
     if (tid == 0) {
-        pbase_s = npieces_s ? atomicAdd(A.P.count, npieces_s) : 0;
-        cbase_s = ncomps_s ? atomicAdd(A.C.count, ncomps_s) : 0;
-        A.T.piece_base[tile] = pbase_s;
-        A.T.piece_cnt[tile] = npieces_s;
+        S.pbase = S.npieces ? atomicAdd(A.P.count, S.npieces) : 0;
+        S.cbase = S.ncomps ? atomicAdd(A.C.count, S.ncomps) : 0;
+        A.T.piece_base[tile] = S.pbase;
+        A.T.piece_cnt[tile] = S.npieces;
     }
     __syncthreads();
-    const int pbase = pbase_s, cbase = cbase_s;
+    const int pbase = S.pbase, cbase = S.cbase;
     for (int e = 0; e < 2; ++e) {
-        int r = tid * 2 + e;
+        const int r = tid * 2 + e;
         if (r >= nroots) continue;
-        int p = r_pix[r];
-        int py = p / TX, px = p - py * TX;
-        uint32_t L = (uint32_t)(y0 + py) * (uint32_t)W + (uint32_t)(x0 + px);
-        int4 bb = make_int4(x0 + r_xmin[r], x0 + r_xmax[r], y0 + r_ymin[r], y0 + r_ymax[r]);
-        int npix = r_val[r];
-        int val = 0, pidx = -1;
+        const int p = S.r_pix[r];
+        const int py = p / TX, px = p - py * TX;
+        const uint32_t L = (uint32_t)(y0 + py) * (uint32_t)W + (uint32_t)(x0 + px);
+        const int4 bb = make_int4(x0 + S.r_xmin[r], x0 + S.r_xmax[r], y0 + S.r_ymin[r], y0 + S.r_ymax[r]);
+        const int npix = S.r_npix[r];
+        int val = 0, pidx = -1, rec = -1;
         if (isp[e]) {
-            int id = pbase + poff;
+            const int id = pbase + poff;
             if (id < A.P.cap) {
                 A.P.root[id] = L; A.P.npix[id] = npix; A.P.bbox[id] = bb; A.P.parent[id] = id;
                 A.P.agg_min[id] = L; A.P.agg_npix[id] = npix; A.P.agg_bbox[id] = bb;
                 pidx = poff;
+                rec = id;
             } else {
                 set_status(A.status, GP_ERR_INTERNAL);
             }
             val = (int)(L + 1u);
             ++poff;
         } else if (isc[e]) {
-            int id = cbase + coff;
+            const int id = cbase + coff;
             if (id < A.C.cap) {
                 A.C.label[id] = L + 1u; A.C.npix[id] = npix; A.C.bbox[id] = bb;
+                rec = -2 - id;
             } else {
                 set_status(A.status, GP_ERR_INTERNAL);
             }
             val = (int)(L + 1u);
             ++coff;
         }
-        r_val[r] = val;
-        r_pidx[r] = pidx;
+        S.r_val[r] = val;
+        S.r_pidx[r] = pidx;
+        S.r_rec[r] = rec;
     }
     __syncthreads();
 
+    // ---- moments of each kept component from the staged m (warp per root)
+    if (!LABEL_ONLY) {
+        for (int r = warp; r < nroots; r += DT_NT / 32) {
+            const int rec = S.r_rec[r];
+            if (rec == -1) continue;
+            const int rp = S.r_pix[r];
+            const int bx0 = S.r_xmin[r], by0 = S.r_ymin[r];
+            const int bw = S.r_xmax[r] - bx0 + 1, bh = S.r_ymax[r] - by0 + 1;
+            MomAcc a;
+            mom_zero(a);
+            for (int q = lane; q < bw * bh; q += 32) {
+                const int py = by0 + q / bw, px = bx0 + q % bw;
+                const int p = py * TX + px;
+                if (S.lab[p] != rp) continue;
+                const float m = S.m[(py + hh) * SW + px + hh];
+                const uint32_t L = (uint32_t)(y0 + py) * (uint32_t)W + (uint32_t)(x0 + px);
+                mom_pixel(a, m, px, py, L, (S.pflag[p] & 2) != 0);
+            }
+            mom_warp_reduce(a);
+            if (lane == 0) {
+                if (rec >= 0) {
+                    Moments mo;
+                    mo.s = df2(a.s); mo.sx = df2(a.sx); mo.sy = df2(a.sy);
+                    mo.sxx = df2(a.sxx); mo.syy = df2(a.syy); mo.sxy = df2(a.sxy);
+                    mo.ux = a.ux; mo.uy = a.uy; mo.uxx = a.uxx; mo.uyy = a.uyy; mo.uxy = a.uxy;
+                    mo.peak = a.peak; mo.peakL = a.peakL; mo.flags = a.flags;
+                    A.P.mom[rec] = mo;
+                } else {
+                    const int id = -2 - rec;
+                    uint32_t fl = a.flags;
+                    double flux;
+                    double2 xy;
+                    double4 m2;
+                    mom_finish(df_value(a.s), df_value(a.sx), df_value(a.sy), df_value(a.sxx), df_value(a.syy),
+                               df_value(a.sxy), a.ux, a.uy, a.uxx, a.uyy, a.uxy, S.r_npix[r], x0, y0, &flux, &xy,
+                               &m2, &fl);
+                    A.C.flux[id] = flux; A.C.xy[id] = xy; A.C.mom2[id] = m2;
+                    A.C.peak[id] = a.peak; A.C.peakL[id] = a.peakL; A.C.flags[id] = fl;
+                }
+            }
+        }
+    }
+
     // ---- segmentation map for the tile (coalesced rows)
     for (int p = tid; p < TNPIX; p += DT_NT) {
-        int py = p / TX, px = p - py * TX;
+        const int py = p / TX, px = p - py * TX;
         if (py >= th || px >= tw) continue;
-        int l = lab[p];
-        uint32_t v = l >= 0 ? (uint32_t)r_val[rid[l]] : 0u;
+        const int l = S.lab[p];
+        const uint32_t v = l >= 0 ? (uint32_t)S.r_val[S.rid[l]] : 0u;
         A.seg[(int64_t)(y0 + py) * W + x0 + px] = v;
     }
     // ---- edge records: local piece index of each edge pixel, or -1
@@ -385,8 +617,8 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
         else { px = q - 2 * TY - TX; py = th - 1; ok = px < tw; }                      // rowB
         int16_t v = -1;
         if (ok) {
-            int l = lab[py * TX + px];
-            if (l >= 0) v = (int16_t)r_pidx[rid[l]];
+            const int l = S.lab[py * TX + px];
+            if (l >= 0) v = (int16_t)S.r_pidx[S.rid[l]];
         }
         ed[q] = v;
     }
@@ -405,8 +637,8 @@ __global__ void k_merge(Tiles T, Pieces P, int W, int H, int* status)
         // (independent of whether this tile has pieces)
         const int rt = tile + 1, dn = tile + ntx;
         if (T.piece_cnt[rt] > 0 && T.piece_cnt[dn] > 0) {
-            int a = T.edges[(int64_t)rt * EDGE_PER_TILE + th - 1];
-            int b = T.edges[(int64_t)dn * EDGE_PER_TILE + TY + 0];
+            const int a = T.edges[(int64_t)rt * EDGE_PER_TILE + th - 1];
+            const int b = T.edges[(int64_t)dn * EDGE_PER_TILE + TY + 0];
             if (a >= 0 && b >= 0) gunite(P.parent, T.piece_base[rt] + a, T.piece_base[dn] + b, status);
         }
     }
@@ -417,12 +649,12 @@ __global__ void k_merge(Tiles T, Pieces P, int W, int H, int* status)
         const int nbase = T.piece_base[tile + 1];
         const int16_t* en = T.edges + (int64_t)(tile + 1) * EDGE_PER_TILE;
         for (int i = threadIdx.x; i < th; i += blockDim.x) {
-            int a = e[TY + i];
+            const int a = e[TY + i];
             if (a < 0) continue;
             for (int d = -1; d <= 1; ++d) {
-                int k = i + d;
+                const int k = i + d;
                 if (k < 0 || k >= th) continue;
-                int b = en[k];
+                const int b = en[k];
                 if (b >= 0) gunite(P.parent, base + a, nbase + b, status);
             }
         }
@@ -431,12 +663,12 @@ __global__ void k_merge(Tiles T, Pieces P, int W, int H, int* status)
         const int nbase = T.piece_base[tile + ntx];
         const int16_t* en = T.edges + (int64_t)(tile + ntx) * EDGE_PER_TILE;
         for (int j = threadIdx.x; j < tw; j += blockDim.x) {
-            int a = e[2 * TY + TX + j];
+            const int a = e[2 * TY + TX + j];
             if (a < 0) continue;
             for (int d = -1; d <= 1; ++d) {
-                int k = j + d;
+                const int k = j + d;
                 if (k < 0 || k >= tw) continue;
-                int b = en[2 * TY + k];
+                const int b = en[2 * TY + k];
                 if (b >= 0) gunite(P.parent, base + a, nbase + b, status);
             }
         }
@@ -444,8 +676,8 @@ __global__ void k_merge(Tiles T, Pieces P, int W, int H, int* status)
     if (threadIdx.x == 0 && tx + 1 < ntx && ty + 1 < nty) {
         // bottom-right pixel of this tile and top-left pixel of the diagonal tile
         const int dr = tile + ntx + 1;
-        int a = e[TY + th - 1];
-        int b = T.edges[(int64_t)dr * EDGE_PER_TILE + 0];
+        const int a = e[TY + th - 1];
+        const int b = T.edges[(int64_t)dr * EDGE_PER_TILE + 0];
         if (a >= 0 && b >= 0) gunite(P.parent, base + a, T.piece_base[dr] + b, status);
     }
 }
@@ -455,47 +687,123 @@ __global__ void k_aggregate(Pieces P, int* status)
 {
     const int n = min(*P.count, P.cap);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        int r = gfind(P.parent, p);
+        const int r = gfind(P.parent, p);
+        P.proot[p] = r;
         if (r < 0) { set_status(status, GP_ERR_TIMEOUT); continue; }
         if (r == p) continue;
         atomicMin(P.agg_min + r, P.root[p]);
         atomicAdd(P.agg_npix + r, P.npix[p]);
-        int4 b = P.bbox[p];
+        const int4 b = P.bbox[p];
         int* ab = reinterpret_cast<int*>(P.agg_bbox + r);
         atomicMin(ab + 0, b.x); atomicMax(ab + 1, b.y);
         atomicMin(ab + 2, b.z); atomicMax(ab + 3, b.w);
     }
 }
 
-// one warp per piece: emit merged segments at root pieces; rewrite the map
-// pixels of pieces whose final label differs from their provisional one
-__global__ void k_finalize(Pieces P, Comps C, uint32_t* seg, int W, int minarea, int* status)
+// add a (hi, lo) pair times a small integer
+__device__ __forceinline__ void df_add_scaled(DF& s, float2 v, float k)
+{
+    df_add_prod(s, k, v.x);
+    s.lo = fmaf(k, v.y, s.lo);
+}
+
+__device__ __forceinline__ void df_add_pair(DF& s, float2 v)
+{
+    df_add(s, v.x);
+    s.lo += v.y;
+}
+
+// One warp per piece.  At root pieces of kept segments: merge the partial
+// moments of all the segment's pieces, visiting the tiles of the segment's
+// bounding box in raster order (a fixed order, so the sums are
+// reproducible) and emit the segment.  Every piece whose final label differs
+// from its provisional one rewrites its pixels in the map.
+__global__ void k_finalize(Tiles T, Pieces P, Comps C, uint32_t* seg, int W, int minarea, int* status)
 {
     const int n = min(*P.count, P.cap);
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int p = wid; p < n; p += nw) {
-        int r = gfind(P.parent, p);
-        if (r < 0) { if (lane == 0) set_status(status, GP_ERR_TIMEOUT); continue; }
-        int tot = P.agg_npix[r];
-        uint32_t fin = tot >= minarea ? P.agg_min[r] + 1u : 0u;
-        if (r == p && fin && lane == 0) {
-            int id = atomicAdd(C.count, 1);
-            if (id < C.cap) {
-                C.label[id] = fin; C.npix[id] = tot; C.bbox[id] = P.agg_bbox[r];
-            } else {
-                set_status(status, GP_ERR_INTERNAL);
+        const int r = P.proot[p];
+        if (r < 0) continue;
+        const int tot = P.agg_npix[r];
+        const uint32_t fin = tot >= minarea ? P.agg_min[r] + 1u : 0u;
+        if (r == p && fin) {
+            const int4 bb = P.agg_bbox[r];
+            const int X0 = bb.x, Y0 = bb.z;
+            const int tx0 = bb.x / TX, tx1 = bb.y / TX, ty0 = bb.z / TY, ty1 = bb.w / TY;
+            const int ntw = tx1 - tx0 + 1, nt = ntw * (ty1 - ty0 + 1);
+            DF s = df_zero(), sx = df_zero(), sy = df_zero(), sxx = df_zero(), syy = df_zero(), sxy = df_zero();
+            long long ux = 0, uy = 0, uxx = 0, uyy = 0, uxy = 0;
+            float pk = -INFINITY;
+            uint32_t pkL = 0xffffffffu, fl = 0u;
+            for (int k = lane; k < nt; k += 32) {
+                const int t = (ty0 + k / ntw) * T.ntx + tx0 + k % ntw;
+                const int b0 = T.piece_base[t], cnt = T.piece_cnt[t];
+                for (int q = b0; q < b0 + cnt && q < n; ++q) {
+                    if (P.proot[q] != r) continue;
+                    const Moments mo = P.mom[q];
+                    const uint32_t L = P.root[q];
+                    const int ox = (int)(L % (uint32_t)W) / TX * TX - X0;
+                    const int oy = (int)(L / (uint32_t)W) / TY * TY - Y0;
+                    const float fx = (float)ox, fy = (float)oy;
+                    // shift the sums from the piece's tile corner to (X0, Y0)
+                    df_add_pair(s, mo.s);
+                    df_add_pair(sx, mo.sx); df_add_scaled(sx, mo.s, fx);
+                    df_add_pair(sy, mo.sy); df_add_scaled(sy, mo.s, fy);
+                    df_add_pair(sxx, mo.sxx); df_add_scaled(sxx, mo.sx, 2.f * fx); df_add_scaled(sxx, mo.s, fx * fx);
+                    df_add_pair(syy, mo.syy); df_add_scaled(syy, mo.sy, 2.f * fy); df_add_scaled(syy, mo.s, fy * fy);
+                    df_add_pair(sxy, mo.sxy); df_add_scaled(sxy, mo.sy, fx); df_add_scaled(sxy, mo.sx, fy);
+                    df_add_scaled(sxy, mo.s, fx * fy);
+                    const long long np = P.npix[q];
+                    ux += mo.ux + (long long)ox * np;
+                    uy += mo.uy + (long long)oy * np;
+                    uxx += mo.uxx + 2ll * ox * mo.ux + (long long)ox * ox * np;
+                    uyy += mo.uyy + 2ll * oy * mo.uy + (long long)oy * oy * np;
+                    uxy += mo.uxy + (long long)ox * mo.uy + (long long)oy * mo.ux + (long long)ox * oy * np;
+                    if (mo.peak > pk || (mo.peak == pk && mo.peakL < pkL)) { pk = mo.peak; pkL = mo.peakL; }
+                    fl |= mo.flags;
+                }
+            }
+            s = df_warp_sum(s); sx = df_warp_sum(sx); sy = df_warp_sum(sy);
+            sxx = df_warp_sum(sxx); syy = df_warp_sum(syy); sxy = df_warp_sum(sxy);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ux += __shfl_xor_sync(0xffffffffu, ux, o);
+                uy += __shfl_xor_sync(0xffffffffu, uy, o);
+                uxx += __shfl_xor_sync(0xffffffffu, uxx, o);
+                uyy += __shfl_xor_sync(0xffffffffu, uyy, o);
+                uxy += __shfl_xor_sync(0xffffffffu, uxy, o);
+                fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+                const float op = __shfl_xor_sync(0xffffffffu, pk, o);
+                const uint32_t oL = __shfl_xor_sync(0xffffffffu, pkL, o);
+                if (op > pk || (op == pk && oL < pkL)) { pk = op; pkL = oL; }
+            }
+            if (lane == 0) {
+                const int id = atomicAdd(C.count, 1);
+                if (id < C.cap) {
+                    double flux;
+                    double2 xy;
+                    double4 m2;
+                    mom_finish(df_value(s), df_value(sx), df_value(sy), df_value(sxx), df_value(syy), df_value(sxy),
+                               ux, uy, uxx, uyy, uxy, tot, X0, Y0, &flux, &xy, &m2, &fl);
+                    C.label[id] = fin; C.npix[id] = tot; C.bbox[id] = bb;
+                    C.flux[id] = flux; C.xy[id] = xy; C.mom2[id] = m2;
+                    C.peak[id] = pk; C.peakL[id] = pkL; C.flags[id] = fl;
+                } else {
+                    set_status(status, GP_ERR_INTERNAL);
+                }
             }
         }
-        uint32_t prov = P.root[p] + 1u;
+        const uint32_t prov = P.root[p] + 1u;
         if (fin == prov) continue;
-        int4 b = P.bbox[p];
-        int bw = b.y - b.x + 1, bh = b.w - b.z + 1;
+        const int4 b = P.bbox[p];
+        const int bw = b.y - b.x + 1, bh = b.w - b.z + 1;
         for (int q = lane; q < bw * bh; q += 32) {
-            int y = b.z + q / bw, x = b.x + q % bw;
-            uint32_t* s = seg + (int64_t)y * W + x;
-            if (*s == prov) *s = fin;
+            const int y = b.z + q / bw, x = b.x + q % bw;
+            uint32_t* sp = seg + (int64_t)y * W + x;
+            if (*sp == prov) *sp = fin;
         }
     }
 }
@@ -519,35 +827,35 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(Comps C, int* n_out, int 
     if (tid == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < C.nb; base += SCAN_NT) {
-        int i = base + tid;
-        int v = i < C.nb ? C.bcnt[i] : 0;
+        const int i = base + tid;
+        const int v = i < C.nb ? C.bcnt[i] : 0;
         int incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
         if (lane == 31) wsum[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            int w = wsum[lane];
+            const int w = wsum[lane];
             int wi = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, wi, o);
+                const int t = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += t;
             }
             wsum[lane] = wi - w;
         }
         __syncthreads();
-        int excl = carry + wsum[warp] + incl - v;
+        const int excl = carry + wsum[warp] + incl - v;
         if (i < C.nb) C.boff[i] = excl;
         __syncthreads();
         if (tid == SCAN_NT - 1) carry = excl + v;
         __syncthreads();
     }
     if (tid == 0) {
-        int total = *C.count;
+        const int total = *C.count;
         if (total > C.cap) set_status(status, GP_ERR_INTERNAL);
         if (n_out) *n_out = total;
         if (capacity >= 0 && total > capacity) set_status(status, GP_ERR_CAPACITY);
@@ -558,8 +866,8 @@ __global__ void k_rank_scatter(Comps C)
 {
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        int b = (int)((C.label[c] - 1u) >> C.shift);
-        int s = C.boff[b] + atomicAdd(C.bcur + b, 1);
+        const int b = (int)((C.label[c] - 1u) >> C.shift);
+        const int s = C.boff[b] + atomicAdd(C.bcur + b, 1);
         C.slots[s] = c;
     }
 }
@@ -568,9 +876,9 @@ __global__ void k_rank_place(Comps C)
 {
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        uint32_t l = C.label[c];
-        int b = (int)((l - 1u) >> C.shift);
-        int s0 = C.boff[b], s1 = s0 + C.bcnt[b];
+        const uint32_t l = C.label[c];
+        const int b = (int)((l - 1u) >> C.shift);
+        const int s0 = C.boff[b], s1 = s0 + C.bcnt[b];
         int r = s0;
         for (int s = s0; s < s1; ++s) r += (C.label[C.slots[s]] < l);
         C.perm[r] = c;
@@ -578,9 +886,27 @@ __global__ void k_rank_place(Comps C)
 }
 
 // --------------------------------------------------------------- launchers ---
+template <bool F32, bool LO, int KS>
+static cudaError_t launch_tile(const DetectArgs& A, int ntiles, cudaStream_t st)
+{
+    const size_t smem = sizeof(TileSmem);
+    cudaFuncSetAttribute(k_detect_tile<F32, LO, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_detect_tile<F32, LO, KS><<<ntiles, DT_NT, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <bool F32>
+static cudaError_t launch_tile_ks(const DetectArgs& A, int ntiles, cudaStream_t st)
+{
+    if (A.kw == A.kh && A.kw == 3) return launch_tile<F32, false, 3>(A, ntiles, st);
+    if (A.kw == A.kh && A.kw == 5) return launch_tile<F32, false, 5>(A, ntiles, st);
+    if (A.kw == A.kh && A.kw == 7) return launch_tile<F32, false, 7>(A, ntiles, st);
+    return launch_tile<F32, false, 0>(A, ntiles, st);
+}
+
 cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
-                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
-                                const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C,
+                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
+                                int* nnear, const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C,
                                 int* status, cudaStream_t st)
 {
     DetectArgs A;
@@ -591,13 +917,9 @@ cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const Spli
     A.seg = seg; A.mask_out = mask_out; A.nnear = nnear; A.in_mask = in_mask;
     A.T = T; A.P = P; A.C = C; A.status = status;
     const int ntiles = T.ntx * T.nty;
-    if (in_mask)
-        k_detect_tile<false, true><<<ntiles, DT_NT, 0, st>>>(A);
-    else if (im.is_f32)
-        k_detect_tile<true, false><<<ntiles, DT_NT, 0, st>>>(A);
-    else
-        k_detect_tile<false, false><<<ntiles, DT_NT, 0, st>>>(A);
-    return cudaGetLastError();
+    if (in_mask) return launch_tile<false, true, 0>(A, ntiles, st);
+    if (im.is_f32) return launch_tile_ks<true>(A, ntiles, st);
+    return launch_tile_ks<false>(A, ntiles, st);
 }
 
 cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H,
@@ -607,7 +929,7 @@ cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, uint
     k_merge<<<ntiles, 64, 0, st>>>(T, P, W, H, status);
     const int g = 152 * 8;
     k_aggregate<<<g, 256, 0, st>>>(P, status);
-    k_finalize<<<g, 256, 0, st>>>(P, C, seg, W, minarea, status);
+    k_finalize<<<g, 256, 0, st>>>(T, P, C, seg, W, minarea, status);
     return cudaGetLastError();
 }
 

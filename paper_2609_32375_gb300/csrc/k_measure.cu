@@ -1,14 +1,14 @@
-// k_measure.cu -- segment moments (first-moment centroid of paper Section
-// 3.2, extended to second moments, bounding box and peak) and circular
-// apertures with exact disc/pixel overlap areas (Section 3.4).
+// k_measure.cu -- catalog rows and circular apertures with exact disc/pixel
+// overlap areas (paper Section 3.4).
 //
-// One warp per source.  Moments scan the segment's bounding box in the final
-// segmentation map; apertures scan the pixels around the centroid once for
-// all radii.  Every sum is a float-float (compensated) accumulation of FP32
-// products, reduced across the warp in a fixed butterfly order, so results
-// are reproducible run to run and carry about 48 bits -- the float64-class
-// accumulation the paper asks of aperture sums, without FP64 arithmetic
-// (which runs at a small fraction of the FP32 rate on this GPU).
+// One warp per source.  The segment moments were finished during detection;
+// here each row is written in label order and the apertures scan the pixels
+// around the centroid once for all radii.  Every sum is a float-float
+// (compensated) accumulation of FP32 products, reduced across the warp in a
+// fixed butterfly order, so results are reproducible run to run and carry
+// about 48 bits -- the float64-class accumulation the paper asks of aperture
+// sums, without FP64 arithmetic (which runs at a small fraction of the FP32
+// rate on this GPU).
 #include <math.h>
 
 #include "gp_internal.cuh"
@@ -27,7 +27,6 @@ struct MeasureArgs {
     Image im;
     SplineTab sb, sr;
     Comps C;
-    const uint32_t* seg;
     int capacity;
     // catalog columns
     uint32_t* label;
@@ -193,6 +192,8 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
     }
 }
 
+// One warp per catalog row (segments in label order): copy the segment's
+// finished moments into the row, then the apertures at its centroid.
 template <bool F32>
 __global__ void __launch_bounds__(256) k_measure(MeasureArgs A)
 {
@@ -204,90 +205,23 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs A)
     const int W = A.im.W;
     for (int r = wid; r < nrow; r += nw) {
         const int c = A.C.perm[r];
-        const uint32_t lab = A.C.label[c];
-        const int4 bb = A.C.bbox[c];
-        const int bw = bb.y - bb.x + 1, bh = bb.w - bb.z + 1;
-        const int npx = bw * bh;
-        // pass 1: sums about the box corner
-        DF S = df_zero(), Sx = df_zero(), Sy = df_zero();
-        long long ux = 0, uy = 0;
-        int cnt = 0;
-        float pk = -INFINITY;
-        long long pkL = 0x7fffffffffffffffll;
-        bool sat = false;
-        for (int q = lane; q < npx; q += 32) {
-            const int y = bb.z + q / bw, x = bb.x + q % bw;
-            if (__ldg(A.seg + (int64_t)y * W + x) != lab) continue;
-            bool bad;
-            const float v = load_px<F32>(A.im, x, y, bad);
-            const float m = v - spline_eval(A.sb, (float)x, (float)y);
-            sat |= A.im.sat > 0.f && v >= A.im.sat;
-            const float dx = (float)(x - bb.x), dy = (float)(y - bb.z);
-            df_add(S, m);
-            df_add_prod(Sx, dx, m);
-            df_add_prod(Sy, dy, m);
-            ux += x - bb.x; uy += y - bb.z;
-            ++cnt;
-            const long long L = (long long)y * W + x;
-            if (m > pk || (m == pk && L < pkL)) { pk = m; pkL = L; }
-        }
-        S = df_warp_sum(S); Sx = df_warp_sum(Sx); Sy = df_warp_sum(Sy);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ux += __shfl_xor_sync(0xffffffffu, ux, o);
-            uy += __shfl_xor_sync(0xffffffffu, uy, o);
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            float opk = __shfl_xor_sync(0xffffffffu, pk, o);
-            long long oL = __shfl_xor_sync(0xffffffffu, pkL, o);
-            if (opk > pk || (opk == pk && oL < pkL)) { pk = opk; pkL = oL; }
-        }
-        sat = __any_sync(0xffffffffu, sat);
-        const double Sd = df_value(S);
-        const bool fallback = !(Sd > 0.0);
-        double xc, yc;
-        if (!fallback) {
-            xc = bb.x + df_value(Sx) / Sd;
-            yc = bb.z + df_value(Sy) / Sd;
-        } else {
-            xc = bb.x + (double)ux / cnt;
-            yc = bb.z + (double)uy / cnt;
-        }
-        // pass 2: central second moments
-        const double xi_d = floor(xc), yi_d = floor(yc);
-        const int xi = (int)xi_d, yi = (int)yi_d;
-        const float xf = (float)(xc - xi_d), yf = (float)(yc - yi_d);
-        DF X2 = df_zero(), Y2 = df_zero(), XY = df_zero();
-        for (int q = lane; q < npx; q += 32) {
-            const int y = bb.z + q / bw, x = bb.x + q % bw;
-            if (__ldg(A.seg + (int64_t)y * W + x) != lab) continue;
-            float w = 1.f;
-            if (!fallback) {
-                bool bad;
-                const float v = load_px<F32>(A.im, x, y, bad);
-                w = v - spline_eval(A.sb, (float)x, (float)y);
-            }
-            const float dx = (float)(x - xi) - xf, dy = (float)(y - yi) - yf;
-            df_add_prod(X2, dx * dx, w);
-            df_add_prod(Y2, dy * dy, w);
-            df_add_prod(XY, dx * dy, w);
-        }
-        X2 = df_warp_sum(X2); Y2 = df_warp_sum(Y2); XY = df_warp_sum(XY);
+        const double2 xy = A.C.xy[c];
         if (lane == 0) {
-            const double d = fallback ? (double)cnt : Sd;
-            A.label[r] = lab;
-            A.npix[r] = cnt;
-            A.flux_iso[r] = Sd;
-            A.x[r] = xc; A.y[r] = yc;
-            A.x2[r] = df_value(X2) / d;
-            A.y2[r] = df_value(Y2) / d;
-            A.xy[r] = df_value(XY) / d;
+            const int4 bb = A.C.bbox[c];
+            const double4 m2 = A.C.mom2[c];
+            const uint32_t pL = A.C.peakL[c];
+            A.label[r] = A.C.label[c];
+            A.npix[r] = A.C.npix[c];
+            A.flux_iso[r] = A.C.flux[c];
+            A.x[r] = xy.x; A.y[r] = xy.y;
+            A.x2[r] = m2.x; A.y2[r] = m2.y; A.xy[r] = m2.z;
             A.xmin[r] = bb.x; A.xmax[r] = bb.y; A.ymin[r] = bb.z; A.ymax[r] = bb.w;
-            A.peak[r] = pk;
-            A.xpeak[r] = (int)(pkL % W); A.ypeak[r] = (int)(pkL / W);
-            A.flags[r] = (sat ? GP_FLAG_SAT : 0u) | (fallback ? GP_FLAG_CENTROID_FALLBACK : 0u);
+            A.peak[r] = A.C.peak[c];
+            A.xpeak[r] = (int)(pL % (uint32_t)W); A.ypeak[r] = (int)(pL / (uint32_t)W);
+            A.flags[r] = A.C.flags[c];
         }
         if (A.ap.nr > 0)
-            aperture_warp<F32>(A.im, A.sb, A.sr, A.ap, xc, yc, A.apflux + (int64_t)r * A.ap.nr,
+            aperture_warp<F32>(A.im, A.sb, A.sr, A.ap, xy.x, xy.y, A.apflux + (int64_t)r * A.ap.nr,
                                A.apferr + (int64_t)r * A.ap.nr, A.apflags + (int64_t)r * A.ap.nr);
     }
 }
@@ -322,7 +256,8 @@ cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab
                            double* apflux, double* apferr, uint32_t* apflags, cudaStream_t st)
 {
     MeasureArgs A;
-    A.im = im; A.sb = sb; A.sr = sr; A.C = C; A.seg = seg;
+    A.im = im; A.sb = sb; A.sr = sr; A.C = C;
+    (void)seg;
     A.capacity = cat.capacity;
     A.label = cat.label; A.npix = cat.npix; A.flux_iso = cat.flux_iso;
     A.x = cat.x; A.y = cat.y; A.x2 = cat.x2; A.y2 = cat.y2; A.xy = cat.xy;
