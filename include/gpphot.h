@@ -206,6 +206,29 @@ gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp,
 gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t height,
                         int32_t minarea, uint32_t* segmap, int32_t* n_out, gp_stream stream);
 
+/* gp_background without a context, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it is a deployment form of the
+ * Section 3.1 stage.  Some callers must not call cudaMalloc at all -- a
+ * process whose device memory belongs to a pool it may not bypass, a plugin
+ * loaded into an application that forbids allocations after start-up, a
+ * latency-critical loop that must not take the allocator's locks -- and so
+ * cannot create a gp_ctx, whose workspace is one cudaMalloc.  This entry
+ * point allocates nothing: its scratch is a fixed array inside the library
+ * image (about 172 KB, held on every GPU that loads the library until the
+ * process exits).
+ *  - Runs on the current device.  Same arguments and outputs as
+ *    gp_background (caller-owned meshes and optional maps).
+ *  - Limit: at most 3600 mesh boxes (ceil(width/mesh) * ceil(height/mesh));
+ *    a larger mesh returns GP_ERR_INVALID_ARG with nothing enqueued.
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same scratch, and each call rewrites all of it that
+ *    it reads, so calls in sequence need nothing cleared; calls that overlap
+ *    on the GPU (different streams, no ordering) race on it.
+ *  - Errors are reported like gp_background's (gp_last_error()). */
+gp_status gp_background_static(const gp_image* img, const gp_bkg_params* p, gp_bkg* bkg, gp_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

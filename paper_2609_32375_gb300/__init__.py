@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_workspace_bytes",
-           "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask")
+           "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static")
 
 
 class GpError(RuntimeError):
@@ -134,6 +134,8 @@ def load_library():
         L.gp_extract.restype = st
         L.gp_label_mask.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
         L.gp_label_mask.restype = st
+        L.gp_background_static.argtypes = [C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpBkg), vp]
+        L.gp_background_static.restype = st
         _lib = L
         return L
 

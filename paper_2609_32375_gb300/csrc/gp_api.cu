@@ -642,3 +642,8 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
 }
 
 }  // extern "C"
+
+// message for gp_last_error() from entry points defined in other files
+namespace gp {
+void record_error(const char* msg) { g_err = msg; }
+}  // namespace gp

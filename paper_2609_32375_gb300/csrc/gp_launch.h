@@ -7,6 +7,9 @@
 
 namespace gp {
 
+// set the thread's gp_last_error() message (gp_api.cu)
+void record_error(const char* msg);
+
 // background (k_background.cu)
 cudaError_t launch_boxstats(const Image& im, int B, double k, int maxiter, double* bkg, double* rms, int* valid,
                             float* quant, cudaStream_t st);
