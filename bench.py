@@ -202,6 +202,9 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     cfg = synth.CONFIGS[args.workload]
+    if args.size:
+        w, h = (int(v) for v in args.size.lower().split("x"))
+        cfg = synth.scaled_config(cfg, w, h)
     img, _ = synth.make_frame(cfg, rank)          # one independent frame per rank
     H, W = img.shape
     t_img = torch.from_numpy(img).to(dev)
@@ -341,6 +344,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-crop", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default=None,
+                    help="WxH: run the workload's recipe on a frame of this size (profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -206,6 +206,73 @@ gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp,
 gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t height,
                         int32_t minarea, uint32_t* segmap, int32_t* n_out, gp_stream stream);
 
+/* ------------------------------------------------- learned background --
+ * A small convolutional network maps one-pass per-box quantile features to
+ * the background and rms meshes, in place of the iterative clip and median
+ * filter.  The paper has no counterpart (its background is an FFT-smoothed
+ * local estimate, Section 3.1); the plain estimator of gp_background stays
+ * as the fallback and produces the training targets.
+ *
+ * Fixed architecture: six 3x3 convolutions, zero padding, ReLU between
+ * layers, channels 5 -> 32 -> 48 -> 48 -> 32 -> 32 -> 2.  Activations are
+ * NHWC bfloat16 (channels padded to 16, 32, 48, 48, 32, 32, 16); each layer's
+ * weights are packed by gp_cnn_pack into bfloat16 [cout_p][9][cin_p] (tap =
+ * 3 dy + dx, offsets -1..1) with float32 biases padded to cout_p. */
+#define GP_CNN_LAYERS 6
+typedef struct {
+    const void* wt[GP_CNN_LAYERS];       /* device, packed bf16 forward weights */
+    const float* bias[GP_CNN_LAYERS];    /* device, float32, cout_p entries */
+} gp_cnn_weights;
+
+/* The background stage with the network: per-box quantiles (one histogram
+ * pass, no clipping), features, network, meshes, spline maps.  Same outputs
+ * as gp_background (p->filter_size, clip_k and clip_maxiter are unused). */
+gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, const gp_cnn_weights* net,
+                                gp_bkg* bkg, gp_stream stream);
+
+/* Per-box quantiles q10, q25, q50, q75, q90 of the good pixels (float32,
+ * [5][my][mx], device, caller-owned), from one pass over the frame. */
+gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float* quant, gp_stream stream);
+
+/* Network layers and training steps (all pointers device, caller-owned;
+ * supported (cin_p, cout_p) pairs: (16,32) (32,48) (48,48) (48,32) (32,32)
+ * (32,16)).  x, y: NHWC bf16 [n][h][w][c_p]; out_f32 writes float32
+ * [n][h][w][creal] instead (the output layer). */
+gp_status gp_cnn_conv3x3(const void* x, int32_t n, int32_t h, int32_t w, int32_t cin_p, const void* wt,
+                         const float* bias, int32_t cout_p, int32_t relu, void* y, int32_t out_f32, int32_t creal,
+                         gp_stream stream);
+/* dW[cout][cin][3][3] and db[cout] from the layer input x and the gradient
+ * dp at its pre-activation; partial (nslot*9*cout_p*cin_p floats) and bpart
+ * (nslot*cout_p floats) are scratch; the slots are summed in a fixed order. */
+gp_status gp_cnn_conv3x3_wgrad(const void* x, const void* dp, int32_t n, int32_t h, int32_t w, int32_t cin_p,
+                               int32_t cout_p, int32_t cin, int32_t cout, int32_t nslot, float* partial, float* bpart,
+                               float* dw, float* db, gp_stream stream);
+/* dp = dy where y > 0, else 0 (bf16, count elements) */
+gp_status gp_cnn_relu_backward(const void* dy, const void* y, void* dp, int64_t count, gp_stream stream);
+/* mean squared error of pred vs target (float32 [npos][2]); writes
+ * dL/dpred as bf16 [npos][cout_p] (zero in the padding) and *loss */
+gp_status gp_cnn_mse(const float* pred, const float* target, int64_t npos, int32_t cout_p, void* dy, float* partial,
+                     int32_t nblocks, float* loss, gp_stream stream);
+/* master weights W[cout][cin][3][3] float32 and b[cout] -> forward weights
+ * wt [cout_p][9][cin_p], data-gradient weights wtd [cin_p][9][cout_p]
+ * (taps flipped), padded bias */
+gp_status gp_cnn_pack(const float* W, const float* b, int32_t cin, int32_t cout, int32_t cin_p, int32_t cout_p,
+                      void* wt, void* wtd, float* bias_p, gp_stream stream);
+/* one AdamW step (decoupled weight decay, bias-corrected moments) */
+gp_status gp_cnn_adamw(float* p, const float* g, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                       float eps, float weight_decay, int32_t step, gp_stream stream);
+/* features of nframes frames from their quantiles ([nframes][5][nbox]):
+ * centre c = median box median, scale s = median (q75 - q25) / 1.349,
+ * feat = (q - c) / s as bf16 [nframes][nbox][16]; norm = (c, s) per frame */
+gp_status gp_cnn_features(const float* quant, int32_t nframes, int32_t nbox, void* feat, float* norm,
+                          gp_stream stream);
+/* plain meshes -> normalised training targets [nframes][nbox][2] */
+gp_status gp_cnn_targets(const float* bkg_mesh, const float* rms_mesh, const float* norm, int32_t nbox,
+                         int32_t nframes, float* target, gp_stream stream);
+/* network output [nframes][nbox][2] -> meshes */
+gp_status gp_cnn_denorm(const float* out, const float* norm, int32_t nbox, int32_t nframes, float* bkg_mesh,
+                        float* rms_mesh, gp_stream stream);
+
 /* gp_background without a context, for callers that cannot allocate device
  * memory.  The paper has no counterpart: it is a deployment form of the
  * Section 3.1 stage.  Some callers must not call cudaMalloc at all -- a

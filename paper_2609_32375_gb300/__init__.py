@@ -32,7 +32,10 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_workspace_bytes",
-           "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static")
+           "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static",
+           "gp_background_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
+           "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
+           "gp_cnn_denorm")
 
 
 class GpError(RuntimeError):
@@ -76,6 +79,10 @@ STAGE_NAMES = ("box_stats", "mesh_spline", "detect_tiles", "tile_merge", "label_
 
 class GpStats(C.Structure):
     _fields_ = [("calls", C.c_int32), ("launches", C.c_int32), ("ms", C.c_float * GP_NSTAGES)]
+
+
+class GpCnnWeights(C.Structure):
+    _fields_ = [("wt", C.c_void_p * 6), ("bias", C.c_void_p * 6)]
 
 
 class GpApParams(C.Structure):
@@ -136,6 +143,23 @@ def load_library():
         L.gp_label_mask.restype = st
         L.gp_background_static.argtypes = [C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpBkg), vp]
         L.gp_background_static.restype = st
+        i64, f = C.c_int64, C.c_float
+        L.gp_background_learned.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpCnnWeights),
+                                            C.POINTER(GpBkg), vp]
+        L.gp_box_quantiles.argtypes = [vp, C.POINTER(GpImage), i32, vp, vp]
+        L.gp_cnn_conv3x3.argtypes = [vp, i32, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp]
+        L.gp_cnn_conv3x3_wgrad.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
+        L.gp_cnn_relu_backward.argtypes = [vp, vp, vp, i64, vp]
+        L.gp_cnn_mse.argtypes = [vp, vp, i64, i32, vp, vp, i32, vp, vp]
+        L.gp_cnn_pack.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]
+        L.gp_cnn_adamw.argtypes = [vp, vp, vp, vp, i64, f, f, f, f, f, i32, vp]
+        L.gp_cnn_features.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.gp_cnn_targets.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+        L.gp_cnn_denorm.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+        for name in ("gp_background_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
+                     "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features",
+                     "gp_cnn_targets", "gp_cnn_denorm"):
+            getattr(L, name).restype = st
         _lib = L
         return L
 

@@ -176,7 +176,7 @@ void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w)
     w.C.bbox = cv.take<int4>(w.C.cap);
     w.C.flux = cv.take<double>(w.C.cap);
     w.C.xy = cv.take<double2>(w.C.cap);
-    w.C.mom2 = cv.take<double4>(w.C.cap);
+    w.C.mom2 = cv.take<Mom2>(w.C.cap);
     w.C.peak = cv.take<float>(w.C.cap);
     w.C.peakL = cv.take<uint32_t>(w.C.cap);
     w.C.flags = cv.take<uint32_t>(w.C.cap);
@@ -642,6 +642,81 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
 }
 
 }  // extern "C"
+
+gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float* quant, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    gp_bkg_params p{mesh, 1, 3.f, 0};
+    if ((s = check_bkg_params(img, &p)) != GP_OK) return s;
+    if (!quant) return fail(GP_ERR_INVALID_ARG, "null quantile output");
+    const int W = img->width, H = img->height;
+    const int Mx = (W + mesh - 1) / mesh, My = (H + mesh - 1) / mesh;
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    BkgWork w;
+    carve_bkg(cv, Mx * My, w);
+    if (!cv.ok()) return oom(cv);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    begin_call(ctx, st);
+    GP_CUDA(launch_boxstats(to_image(img), mesh, 3.0, 0, w.bkg_raw, w.rms_raw, w.valid, quant, st));
+    ctx->launches += 1;
+    mark_to(ctx, 1, 6, st);
+    return GP_OK;
+}
+
+gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, const gp_cnn_weights* net,
+                                gp_bkg* bkg, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg_params(img, p)) != GP_OK) return s;
+    if (!net) return fail(GP_ERR_INVALID_ARG, "null network weights");
+    for (int l = 0; l < GP_CNN_LAYERS; ++l)
+        if (!net->wt[l] || !net->bias[l]) return fail(GP_ERR_INVALID_ARG, "null weights of layer %d", l);
+    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
+    const int W = img->width, H = img->height, B = p->mesh;
+    const int Mx = (W + B - 1) / B, My = (H + B - 1) / B, nbox = Mx * My;
+    bkg->mesh = B; bkg->mx = Mx; bkg->my = My;
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    BkgWork w;
+    carve_bkg(cv, nbox, w);
+    float* quant = cv.take<float>((size_t)5 * nbox);
+    float* norm = cv.take<float>(2);
+    uint16_t* feat = cv.take<uint16_t>((size_t)16 * nbox);
+    uint16_t* a0 = cv.take<uint16_t>((size_t)48 * nbox);
+    uint16_t* a1 = cv.take<uint16_t>((size_t)48 * nbox);
+    float* out = cv.take<float>((size_t)2 * nbox);
+    if (!cv.ok()) return oom(cv);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    begin_call(ctx, st);
+    GP_CUDA(launch_boxstats(to_image(img), B, 3.0, 0, w.bkg_raw, w.rms_raw, w.valid, quant, st));
+    mark(ctx, 1, st);
+    GP_CUDA(launch_cnn_features(quant, 1, nbox, feat, norm, st));
+    static const int cin_p[GP_CNN_LAYERS] = {16, 32, 48, 48, 32, 32};
+    static const int cout_p[GP_CNN_LAYERS] = {32, 48, 48, 32, 32, 16};
+    const void* in = feat;
+    for (int l = 0; l < GP_CNN_LAYERS; ++l) {
+        const bool last = l == GP_CNN_LAYERS - 1;
+        void* o = last ? (void*)out : (void*)((l & 1) ? a1 : a0);
+        GP_CUDA(launch_cnn_conv(in, 1, My, Mx, cin_p[l], net->wt[l], net->bias[l], cout_p[l], last ? 0 : 1, o,
+                                last ? 1 : 0, 2, st));
+        in = o;
+    }
+    GP_CUDA(launch_cnn_denorm(out, norm, nbox, 1, bkg->bkg_mesh, bkg->rms_mesh, st));
+    ctx->launches += 3 + GP_CNN_LAYERS;
+    SplineTab tb, tr;
+    s = run_spline(cv, bkg, W, H, &tb, &tr, &ctx->launches, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    if (bkg->bkg_map || bkg->rms_map) {
+        GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
+        ctx->launches += 1;
+    }
+    mark_to(ctx, 2, 6, st);
+    return GP_OK;
+}
 
 // message for gp_last_error() from entry points defined in other files
 namespace gp {

@@ -14,11 +14,12 @@ constexpr int TY = 32;           // detection tile height
 constexpr int TNPIX = TX * TY;
 constexpr int MAXROOT = (TX / 2) * (TY / 2);  // most 8-connected segments a tile can hold
 constexpr int HMAX = 7;          // largest filter half-size (15 x 15 taps)
-constexpr int SW = TX + 2 * HMAX;
+constexpr int XHALO = 8;         // staged columns left of the tile (>= HMAX, keeps 16-byte alignment)
+constexpr int SW = TX + 2 * XHALO;
 constexpr int SH = TY + 2 * HMAX;
 constexpr int EDGE_PER_TILE = 2 * TY + 2 * TX;   // colL, colR, rowT, rowB
 constexpr int MAX_NR = 8;        // most aperture radii per call
-constexpr int NJMAX = 8;         // most mesh node rows one detection tile touches
+constexpr int NJMAX = 5;         // most mesh node rows one staged tile touches (mesh >= 16, SH <= 46 rows)
 
 // bounded-loop limit for union-find walks (a cycle would be a bug; the walk
 // gives up, records GP_ERR_TIMEOUT and the result is flagged invalid)
@@ -236,6 +237,17 @@ struct Pieces {
     Moments* mom;         // partial moments, origin = the piece's tile corner
 };
 
+struct Mom2 {
+    double x2, y2, xy, pad;
+};
+
+__host__ __device__ __forceinline__ Mom2 mom2_make(double x2, double y2, double xy, double pad)
+{
+    Mom2 m;
+    m.x2 = x2; m.y2 = y2; m.xy = xy; m.pad = pad;
+    return m;
+}
+
 // Segments that survive the minarea cut, in no particular order until ranked,
 // with their finished moments
 struct Comps {
@@ -246,7 +258,7 @@ struct Comps {
     int4* bbox;
     double* flux;         // sum of m
     double2* xy;          // centroid
-    double4* mom2;        // x2, y2, xy, -
+    Mom2* mom2;           // x2, y2, xy
     float* peak;
     uint32_t* peakL;
     uint32_t* flags;

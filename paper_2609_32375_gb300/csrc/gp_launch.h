@@ -42,3 +42,24 @@ cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTa
                             double* ferr, uint32_t* fl, cudaStream_t st);
 
 }  // namespace gp
+
+namespace gp {
+// learned background network (k_cnn.cu)
+bool cnn_pair_supported(int cip, int cop);
+cudaError_t launch_cnn_conv(const void* x, int n, int h, int w, int cip, const void* wt, const float* bias, int cop,
+                            int relu, void* y, int out_f32, int creal, cudaStream_t st);
+cudaError_t launch_cnn_wgrad(const void* x, const void* dp, int n, int h, int w, int cip, int cop, int cir, int cor,
+                             int nslot, float* partial, float* bpart, float* dw, float* db, cudaStream_t st);
+cudaError_t launch_cnn_relu_backward(const void* dy, const void* y, void* dp, int64_t count, cudaStream_t st);
+cudaError_t launch_cnn_mse(const float* pred, const float* target, int64_t npos, int cop, void* dy, float* part,
+                           int nblocks, float* loss, cudaStream_t st);
+cudaError_t launch_cnn_pack(const float* W, const float* b, int cir, int cor, int cip, int cop, void* wt, void* wtd,
+                            float* bias_p, cudaStream_t st);
+cudaError_t launch_cnn_adamw(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                             float eps, float wd, int step, cudaStream_t st);
+cudaError_t launch_cnn_features(const float* quant, int nframes, int nbox, void* feat, float* norm, cudaStream_t st);
+cudaError_t launch_cnn_denorm(const float* out, const float* norm, int nbox, int nframes, float* bkg, float* rms,
+                              cudaStream_t st);
+cudaError_t launch_cnn_targets(const float* bkg, const float* rms, const float* norm, int nbox, int nframes,
+                               float* tgt, cudaStream_t st);
+}  // namespace gp

@@ -150,27 +150,48 @@ k_boxstats_u16(const uint16_t* __restrict__ img, int64_t pitch, const uint8_t* _
     // 8-pixel chunks along each row; rows spread over the CTA
     const int cpr = (bw + 7) >> 3;              // chunks per row
     const int nchunks = cpr * bh;
-    const bool vec = ((((uintptr_t)img) & 15) == 0) && ((pitch & 7) == 0) && ((x0 & 7) == 0);
-    for (int c = tid; c < nchunks; c += U16_NT) {
-        const int ry = c / cpr, rc = c - ry * cpr;
-        const int y = y0 + ry, xs = x0 + rc * 8;
-        const uint16_t* row = img + (int64_t)y * pitch;
-        uint16_t v[8];
-        int nv = min(8, x1 - xs);
-        if (vec && nv == 8) {
-            uint4 q = __ldg(reinterpret_cast<const uint4*>(row + xs));
-            v[0] = q.x & 0xffff; v[1] = q.x >> 16; v[2] = q.y & 0xffff; v[3] = q.y >> 16;
-            v[4] = q.z & 0xffff; v[5] = q.z >> 16; v[6] = q.w & 0xffff; v[7] = q.w >> 16;
-        } else {
-            for (int e = 0; e < 8; ++e) v[e] = e < nv ? __ldg(row + xs + e) : 0;
+    const bool vec = ((((uintptr_t)img) & 15) == 0) && ((pitch & 7) == 0) && ((x0 & 7) == 0) && ((bw & 7) == 0) &&
+                     !mask;
+    auto count = [&](uint32_t u) {
+        atomicAdd(&hist[u >> 1], (u & 1u) ? 65536u : 1u);
+        vmin = min(vmin, u);
+        vmax = max(vmax, u);
+        ++ngood;
+    };
+    if (vec) {
+        // four 16-byte loads in flight per thread before the histogram updates
+        constexpr int U = 4;
+        for (int c0 = tid; c0 < nchunks; c0 += U * U16_NT) {
+            uint4 q[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int c = c0 + k * U16_NT;
+                if (c < nchunks) {
+                    const int ry = c / cpr, rc = c - ry * cpr;
+                    q[k] = __ldg(reinterpret_cast<const uint4*>(img + (int64_t)(y0 + ry) * pitch + x0 + rc * 8));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                if (c0 + k * U16_NT >= nchunks) break;
+                const uint32_t w4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    count(w4[e] & 0xffffu);
+                    count(w4[e] >> 16);
+                }
+            }
         }
-        for (int e = 0; e < nv; ++e) {
-            if (mask && mask[(int64_t)y * W + xs + e]) continue;
-            uint32_t u = v[e];
-            atomicAdd(&hist[u >> 1], (u & 1u) ? 65536u : 1u);
-            vmin = min(vmin, u);
-            vmax = max(vmax, u);
-            ++ngood;
+    } else {
+        for (int c = tid; c < nchunks; c += U16_NT) {
+            const int ry = c / cpr, rc = c - ry * cpr;
+            const int y = y0 + ry, xs = x0 + rc * 8;
+            const uint16_t* row = img + (int64_t)y * pitch;
+            const int nv = min(8, x1 - xs);
+            for (int e = 0; e < nv; ++e) {
+                if (mask && mask[(int64_t)y * W + xs + e]) continue;
+                count(__ldg(row + xs + e));
+            }
         }
     }
 #pragma unroll
@@ -584,45 +605,46 @@ __global__ void k_bkg_maps(SplineTab sb, SplineTab sr, int W, int H, float* bmap
 // spline tables of both maps.  The tridiagonal matrix of the natural spline
 // depends only on the node positions, so each axis is factorised once
 // (multipliers and reciprocal pivots) and every line is then solved with
-// FMAs only.
+// FMAs only.  FP32 throughout: the tables are stored in FP32 anyway, and the
+// diagonally dominant spline system loses nothing that matters at 1e-5.
 constexpr int MESH_SMEM_NODES = 4096;
 constexpr int MA_NT = 1024;
 
-// byte offset of the LU scratch in k_mesh_all's shared memory: six double
+// byte offset of the LU scratch in k_mesh_all's shared memory: six float
 // arrays and two int arrays of n entries, rounded up to 16 bytes
 __host__ __device__ __forceinline__ size_t mesh_lu_offset(int n)
 {
-    const size_t end = (size_t)n * (6 * sizeof(double) + 2 * sizeof(int));
+    const size_t end = (size_t)n * (6 * sizeof(float) + 2 * sizeof(int));
     return (end + 15) & ~(size_t)15;
 }
 
 struct AxisLU {
-    double* w;      // elimination multipliers  (index r = 1..n-2)
-    double* ib;     // reciprocal pivots
-    double* c;      // super-diagonal
-    double* ih;     // 1 / interval width (n-1 entries)
+    float* w;      // elimination multipliers  (index r = 1..n-2)
+    float* ib;     // reciprocal pivots
+    float* c;      // super-diagonal
+    float* ih;     // 1 / interval width (n-1 entries)
 };
 
-__device__ __forceinline__ double node_pos(const Axis& a, int i)
+__device__ __forceinline__ float node_pos(const Axis& a, int i)
 {
-    return (i == a.n - 1) ? (double)a.tl : (double)a.t0 + (double)i * (double)a.B;
+    return (i == a.n - 1) ? a.tl : a.t0 + (float)i * a.B;
 }
 
 __device__ void factor_axis(const Axis& a, AxisLU L)
 {
     const int n = a.n;
-    for (int i = 0; i + 1 < n; ++i) L.ih[i] = 1.0 / (node_pos(a, i + 1) - node_pos(a, i));
-    double bprev = 0, cprev = 0;
+    for (int i = 0; i + 1 < n; ++i) L.ih[i] = 1.f / (node_pos(a, i + 1) - node_pos(a, i));
+    float bprev = 0.f, cprev = 0.f;
     for (int r = 1; r <= n - 2; ++r) {
-        double h0 = node_pos(a, r) - node_pos(a, r - 1), h1 = node_pos(a, r + 1) - node_pos(a, r);
-        double b = 2.0 * (h0 + h1);
-        double w = 0.0;
+        const float h0 = node_pos(a, r) - node_pos(a, r - 1), h1 = node_pos(a, r + 1) - node_pos(a, r);
+        float b = 2.f * (h0 + h1);
+        float w = 0.f;
         if (r > 1) {
             w = h0 / bprev;
             b -= w * cprev;
         }
         L.w[r] = w;
-        L.ib[r] = 1.0 / b;
+        L.ib[r] = 1.f / b;
         L.c[r] = h1;
         bprev = b;
         cprev = h1;
@@ -630,21 +652,21 @@ __device__ void factor_axis(const Axis& a, AxisLU L)
 }
 
 // second derivatives of one line (values v, stride vs) into M (stride ms)
-__device__ void solve_line(const AxisLU& L, int n, const double* v, int vs, double* M, int ms)
+__device__ void solve_line(const AxisLU& L, int n, const float* v, int vs, float* M, int ms)
 {
-    M[0] = 0.0;
-    if (n >= 2) M[(n - 1) * ms] = 0.0;
+    M[0] = 0.f;
+    if (n >= 2) M[(n - 1) * ms] = 0.f;
     if (n < 3) return;
-    double dprev = 0.0;
+    float dprev = 0.f;
     for (int r = 1; r <= n - 2; ++r) {
-        double d = 6.0 * ((v[(r + 1) * vs] - v[r * vs]) * L.ih[r] - (v[r * vs] - v[(r - 1) * vs]) * L.ih[r - 1]);
-        d = fma(-L.w[r], dprev, d);
+        float d = 6.f * ((v[(r + 1) * vs] - v[r * vs]) * L.ih[r] - (v[r * vs] - v[(r - 1) * vs]) * L.ih[r - 1]);
+        d = fmaf(-L.w[r], dprev, d);
         M[r * ms] = d;        // forward-eliminated right-hand side
         dprev = d;
     }
-    double next = 0.0;
+    float next = 0.f;
     for (int r = n - 2; r >= 1; --r) {
-        double val = fma(-L.c[r], next, M[r * ms]) * L.ib[r];
+        const float val = fmaf(-L.c[r], next, M[r * ms]) * L.ib[r];
         M[r * ms] = val;
         next = val;
     }
@@ -658,20 +680,20 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const double* __restrict__ b
                                                     int mode, float* bkg_out, float* rms_out, float4* tab_b,
                                                     float4* tab_r)
 {
-    extern __shared__ __align__(16) double sh[];
+    extern __shared__ __align__(16) float sh[];
     unsigned char* sh_bytes = reinterpret_cast<unsigned char*>(sh);
     const int Mx = ax.n, My = ay.n, n = Mx * My, tid = threadIdx.x;
-    double* A0 = sh;
-    double* A1 = A0 + n;
-    double* A2 = A1 + n;
-    double* A3 = A2 + n;
-    double* A4 = A3 + n;
-    double* A5 = A4 + n;
+    float* A0 = sh;
+    float* A1 = A0 + n;
+    float* A2 = A1 + n;
+    float* A3 = A2 + n;
+    float* A4 = A3 + n;
+    float* A5 = A4 + n;
     int* V0 = reinterpret_cast<int*>(A5 + n);
     int* V1 = V0 + n;
     const int nl = Mx > My ? Mx : My;
     // the LU scratch starts at the first 16-byte boundary after V1
-    double* lu = reinterpret_cast<double*>(sh_bytes + mesh_lu_offset(n));
+    float* lu = reinterpret_cast<float*>(sh_bytes + mesh_lu_offset(n));
     AxisLU Lx{lu, lu + nl, lu + 2 * nl, lu + 3 * nl};
     AxisLU Ly{lu + 4 * nl, lu + 5 * nl, lu + 6 * nl, lu + 7 * nl};
     __shared__ int missing, any;
@@ -682,12 +704,12 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const double* __restrict__ b
         if (tid == 0) any = 0;
         __syncthreads();
         for (int b = tid; b < n; b += MA_NT) {
-            A0[b] = bkg_raw[b]; A1[b] = rms_raw[b]; V0[b] = valid_raw[b];
+            A0[b] = (float)bkg_raw[b]; A1[b] = (float)rms_raw[b]; V0[b] = valid_raw[b];
             if (V0[b]) any = 1;
         }
         __syncthreads();
         if (!any) {
-            for (int b = tid; b < n; b += MA_NT) { A0[b] = 0; A1[b] = 0; V0[b] = 1; }
+            for (int b = tid; b < n; b += MA_NT) { A0[b] = 0.f; A1[b] = 0.f; V0[b] = 1; }
             __syncthreads();
         }
         // fill invalid boxes from valid 8-neighbours, sweep after sweep
@@ -697,11 +719,12 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const double* __restrict__ b
             for (int b = tid; b < n; b += MA_NT) {
                 A2[b] = A0[b]; A3[b] = A1[b]; V1[b] = V0[b];
                 if (V0[b]) continue;
-                int i = b % Mx, j = b / Mx, c = 0;
-                double sb = 0, sr = 0;
+                const int i = b % Mx, j = b / Mx;
+                int c = 0;
+                float sb = 0.f, sr = 0.f;
                 for (int dj = -1; dj <= 1; ++dj)
                     for (int di = -1; di <= 1; ++di) {
-                        int ii = i + di, jj = j + dj;
+                        const int ii = i + di, jj = j + dj;
                         if ((di || dj) && ii >= 0 && ii < Mx && jj >= 0 && jj < My && V0[jj * Mx + ii]) {
                             sb += A0[jj * Mx + ii];
                             sr += A1[jj * Mx + ii];
@@ -712,48 +735,59 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const double* __restrict__ b
                 else missing = 1;
             }
             __syncthreads();
+            const bool more = missing;
             for (int b = tid; b < n; b += MA_NT) { A0[b] = A2[b]; A1[b] = A3[b]; V0[b] = V1[b]; }
             __syncthreads();
-            if (!missing) break;
+            if (!more) break;
         }
         // median filter (window clipped at the mesh edge) -> float meshes
         const int h = fsize / 2;
-        for (int b = tid; b < n; b += MA_NT) {
-            int i = b % Mx, j = b / Mx;
-            for (int map = 0; map < 2; ++map) {
-                const double* src = map ? A1 : A0;
-                double win[49];
-                int c = 0;
-                for (int jj = j - h; jj <= j + h; ++jj)
-                    for (int ii = i - h; ii <= i + h; ++ii)
-                        if (ii >= 0 && ii < Mx && jj >= 0 && jj < My) {
-                            double v = src[jj * Mx + ii];
-                            int p = c++;
-                            while (p > 0 && win[p - 1] > v) { win[p] = win[p - 1]; --p; }
-                            win[p] = v;
-                        }
-                double med = (c & 1) ? win[c / 2] : 0.5 * (win[c / 2 - 1] + win[c / 2]);
-                (map ? rms_out : bkg_out)[b] = (float)med;
-            }
+        for (int t = tid; t < 2 * n; t += MA_NT) {
+            const int map = t / n, b = t - map * n;
+            const int i = b % Mx, j = b / Mx;
+            const float* src = map ? A1 : A0;
+            float win[49];
+            int c = 0;
+            for (int jj = j - h; jj <= j + h; ++jj)
+                for (int ii = i - h; ii <= i + h; ++ii)
+                    if (ii >= 0 && ii < Mx && jj >= 0 && jj < My) {
+                        const float v = src[jj * Mx + ii];
+                        int p = c++;
+                        while (p > 0 && win[p - 1] > v) { win[p] = win[p - 1]; --p; }
+                        win[p] = v;
+                    }
+            const float med = (c & 1) ? win[c / 2] : 0.5f * (win[c / 2 - 1] + win[c / 2]);
+            (map ? rms_out : bkg_out)[b] = med;
         }
     }
     __syncthreads();
-    // spline tables, one map at a time, from the float meshes
-    for (int map = 0; map < 2; ++map) {
-        const float* mesh = map ? rms_out : bkg_out;
-        float4* tab = map ? tab_r : tab_b;
-        for (int b = tid; b < n; b += MA_NT) A4[b] = (double)mesh[b];
-        __syncthreads();
-        for (int t = tid; t < My + Mx; t += MA_NT) {
-            if (t < My) solve_line(Lx, Mx, A4 + t * Mx, 1, A0 + t * Mx, 1);      // X
-            else solve_line(Ly, My, A4 + (t - My), Mx, A1 + (t - My), Mx);        // Y
-        }
-        __syncthreads();
-        for (int t = tid; t < My; t += MA_NT) solve_line(Lx, Mx, A1 + t * Mx, 1, A2 + t * Mx, 1);   // XY
-        __syncthreads();
-        for (int b = tid; b < n; b += MA_NT)
-            tab[b] = make_float4(mesh[b], (float)A0[b], (float)A1[b], (float)A2[b]);
-        __syncthreads();
+    // spline tables of both maps, from the float meshes: X (rows) and Y
+    // (columns) for both maps at once, then XY (rows of Y)
+    for (int b = tid; b < n; b += MA_NT) { A4[b] = bkg_out[b]; A5[b] = rms_out[b]; }
+    __syncthreads();
+    for (int t = tid; t < 2 * (My + Mx); t += MA_NT) {
+        const int map = t / (My + Mx), q = t - map * (My + Mx);
+        const float* P = map ? A5 : A4;
+        float* X = map ? A1 : A0;
+        float* Y = map ? A3 : A2;
+        if (q < My) solve_line(Lx, Mx, P + q * Mx, 1, X + q * Mx, 1);
+        else solve_line(Ly, My, P + (q - My), Mx, Y + (q - My), Mx);
+    }
+    __syncthreads();
+    // XY overwrites P (no longer needed once X and Y are known)
+    for (int b = tid; b < n; b += MA_NT) {
+        tab_b[b] = make_float4(A4[b], A0[b], A2[b], 0.f);
+        tab_r[b] = make_float4(A5[b], A1[b], A3[b], 0.f);
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * My; t += MA_NT) {
+        const int map = t / My, q = t - map * My;
+        solve_line(Lx, Mx, (map ? A3 : A2) + q * Mx, 1, (map ? A5 : A4) + q * Mx, 1);
+    }
+    __syncthreads();
+    for (int b = tid; b < n; b += MA_NT) {
+        tab_b[b].w = A4[b];
+        tab_r[b].w = A5[b];
     }
 }
 
@@ -761,7 +795,7 @@ size_t mesh_all_smem(int Mx, int My)
 {
     const size_t n = (size_t)Mx * My;
     const size_t nl = Mx > My ? Mx : My;
-    return mesh_lu_offset((int)n) + 8 * nl * sizeof(double);
+    return mesh_lu_offset((int)n) + 8 * nl * sizeof(float);
 }
 
 bool mesh_fits_smem(int Mx, int My)

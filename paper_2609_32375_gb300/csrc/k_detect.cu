@@ -197,29 +197,36 @@ __device__ __forceinline__ float2 df2(DF d) { return make_float2(d.hi, d.lo); }
 // finished moments of a whole segment from sums about the origin (X0, Y0)
 __device__ void mom_finish(double S, double Sx, double Sy, double Sxx, double Syy, double Sxy, long long ux,
                            long long uy, long long uxx, long long uyy, long long uxy, int npix, int X0, int Y0,
-                           double* flux, double2* xy, double4* m2, uint32_t* flags)
+                           double* flux, double2* xy, Mom2* m2, uint32_t* flags)
 {
     *flux = S;
     if (S > 0.0) {
         const double mx = Sx / S, my = Sy / S;
         *xy = make_double2(X0 + mx, Y0 + my);
-        *m2 = make_double4(Sxx / S - mx * mx, Syy / S - my * my, Sxy / S - mx * my, 0.0);
+        *m2 = mom2_make(Sxx / S - mx * mx, Syy / S - my * my, Sxy / S - mx * my, 0.0);
     } else {
         const double n = (double)npix;
         const double mx = (double)ux / n, my = (double)uy / n;
         *xy = make_double2(X0 + mx, Y0 + my);
-        *m2 = make_double4((double)uxx / n - mx * mx, (double)uyy / n - my * my, (double)uxy / n - mx * my, 0.0);
+        *m2 = mom2_make((double)uxx / n - mx * mx, (double)uyy / n - my * my, (double)uxy / n - mx * my, 0.0);
         *flags |= GP_FLAG_CENTROID_FALLBACK;
     }
 }
 
 // ----------------------------------------------------------- tile kernel ---
+// Staged columns: SMEM column c holds frame column x0 - XHALO + c (so 16-byte
+// chunks of the frame land on 16-byte boundaries); staged rows: row r holds
+// frame row y0 - hh + r.
 struct TileSmem {
-    float m[SH * SW];                 // staged m = I - B
+    float m[SH * SW];                 // staged pixels, then m = I - B
     int lab[TNPIX];
-    short rid[TNPIX];
     uint8_t pflag[TNPIX];             // bit 0 bad, bit 1 saturated
-    float4 colv[NJMAX * SW];          // per column and node row: (u_bkg, w_bkg, u_rms, w_rms)
+    union {
+        struct {                      // per staged column and node row (SoA)
+            float ub[NJMAX * SW], wb[NJMAX * SW], ur[NJMAX * SW], wr[NJMAX * SW];
+        } col;
+        short rid[TNPIX];             // after thresholding: root pixel -> compact root id
+    } u;
     float4 rowc[SH];                  // per staged row: (b, c0, c1, -)
     int2 rowj[SH];
     int r_npix[MAXROOT];
@@ -237,16 +244,19 @@ __device__ __forceinline__ float combine_row(const float4& rc, float v0, float v
     return fmaf(rc.z, m1, fmaf(rc.y, m0, fmaf(rc.x, v1 - v0, v0)));
 }
 
-__device__ __forceinline__ void stage_cell(TileSmem& S, const DetectArgs& A, int ry, int cx, float v, bool bad,
-                                           int hh, int th, int tw)
+// background and rms at staged cell (ry, c)
+__device__ __forceinline__ float cell_bkg(const TileSmem& S, int ry, int c)
 {
     const int2 j = S.rowj[ry];
-    const float4 n0 = S.colv[j.x * SW + cx], n1 = S.colv[j.y * SW + cx];
-    const float Bv = combine_row(S.rowc[ry], n0.x, n1.x, n0.y, n1.y);
-    S.m[ry * SW + cx] = bad ? 0.f : v - Bv;
-    const int py = ry - hh, px = cx - hh;
-    if (py >= 0 && py < th && px >= 0 && px < tw)
-        S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && A.im.sat > 0.f && v >= A.im.sat) ? 2 : 0);
+    return combine_row(S.rowc[ry], S.u.col.ub[j.x * SW + c], S.u.col.ub[j.y * SW + c], S.u.col.wb[j.x * SW + c],
+                       S.u.col.wb[j.y * SW + c]);
+}
+
+__device__ __forceinline__ float cell_rms(const TileSmem& S, int ry, int c)
+{
+    const int2 j = S.rowj[ry];
+    return combine_row(S.rowc[ry], S.u.col.ur[j.x * SW + c], S.u.col.ur[j.y * SW + c], S.u.col.wr[j.x * SW + c],
+                       S.u.col.wr[j.y * SW + c]);
 }
 
 // F at 8 consecutive rows of one column: slide the kernel window down the
@@ -259,7 +269,7 @@ __device__ __forceinline__ void filter_column(const TileSmem& S, const DetectArg
         constexpr int H = KS / 2;
 #pragma unroll
         for (int i = 0; i < ROWS_PER_THREAD; ++i) F[i] = 0.f;
-        const int c0 = px + hh - H;
+        const int c0 = px + XHALO - H;
         const int r0 = py0 + hh - H;
 #pragma unroll
         for (int rr = 0; rr < ROWS_PER_THREAD + KS - 1; ++rr) {
@@ -278,7 +288,7 @@ __device__ __forceinline__ void filter_column(const TileSmem& S, const DetectArg
     } else {
         for (int i = 0; i < ROWS_PER_THREAD; ++i) {
             float f = 0.f;
-            const int r0 = py0 + i + hh - A.hy, c0 = px + hh - A.hx;
+            const int r0 = py0 + i + hh - A.hy, c0 = px + XHALO - A.hx;
             for (int v = 0; v < A.kh; ++v) {
                 const float* row = S.m + (r0 + v) * SW + c0;
                 const float* kr = A.K + v * A.kw;
@@ -305,7 +315,8 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
     const int hh = LABEL_ONLY ? 0 : A.hh;
 
     if (!LABEL_ONLY) {
-        const int scols = tw + 2 * hh, srows = th + 2 * hh;
+        const int srows = th + 2 * hh;
+        const int clo = XHALO - hh, chi = XHALO + tw + hh;      // staged columns in use
         if (tid == 0) { S.jlo = 1 << 30; S.jhi = -1; S.nnear = 0; }
         __syncthreads();
         // spline coefficients of the staged rows (and the node rows they need)
@@ -327,28 +338,32 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
             S.rowc[tid] = make_float4(cy.b, cy.c0, cy.c1, 0.f);
             S.rowj[tid] = make_int2(cy.i - jlo, cy.i1 - jlo);
         }
-        for (int q = tid; q < nj * scols; q += DT_NT) {
-            const int jj = q / scols, cx = q - jj * scols;
-            const int gx = mirror_fast(x0 - hh + cx, W);
-            const AxCoef c = axis_coef(A.sb.ax, (float)gx);
-            const float2 b = row_eval(A.sb, jlo + jj, c);
-            const float2 r = row_eval(A.sr, jlo + jj, c);
-            S.colv[jj * SW + cx] = make_float4(b.x, b.y, r.x, r.y);
+        for (int c = clo + tid; c < chi; c += DT_NT) {
+            const int gx = mirror_fast(x0 - XHALO + c, W);
+            const AxCoef cx = axis_coef(A.sb.ax, (float)gx);
+            for (int jj = 0; jj < nj; ++jj) {
+                const float2 b = row_eval(A.sb, jlo + jj, cx);
+                const float2 r = row_eval(A.sr, jlo + jj, cx);
+                S.u.col.ub[jj * SW + c] = b.x; S.u.col.wb[jj * SW + c] = b.y;
+                S.u.col.ur[jj * SW + c] = r.x; S.u.col.wr[jj * SW + c] = r.y;
+            }
         }
-        __syncthreads();
 
-        // ---- stage m = I - B over tile + halo (mirror border; bad -> 0)
+        // ---- stage the pixels over tile + halo (mirror border)
         const bool interior = x0 - hh >= 0 && x0 + tw + hh <= W && y0 - hh >= 0 && y0 + th + hh <= H;
         constexpr int VEC = F32 ? 4 : 8;          // pixels per 16-byte load
         const bool vec_ok = interior && !A.im.mask && ((((uintptr_t)A.im.data) & 15) == 0) &&
                             ((A.im.pitch % VEC) == 0);
         if (vec_ok) {
-            // aligned chunks covering [x0 - hh, x0 + tw + hh); all inside the row
-            // because the tile is interior and x0 is a multiple of the chunk
+            // 16-byte chunks covering [x0 - hh, x0 + tw + hh), stored with
+            // 16-byte shared stores (frame column x0 - XHALO is chunk aligned)
             const int xa = (x0 - hh) & ~(VEC - 1);
             const int nchunk = (x0 + tw + hh - xa + VEC - 1) / VEC;
+            // q / nchunk by multiply-shift, exact for every q < 46 * nchunk and nchunk <= 20
+            const unsigned inv_nchunk = (65536u + nchunk - 1) / nchunk;
+            // nchunk <= 20 chunks per row: a warp takes one or two rows' chunks
             for (int q = tid; q < srows * nchunk; q += DT_NT) {
-                const int ry = q / nchunk, ch = q - ry * nchunk;
+                const int ry = (int)(((unsigned)q * inv_nchunk) >> 16), ch = q - ry * nchunk;
                 const int gy = y0 - hh + ry;
                 const int gx0 = xa + ch * VEC;
                 float v[VEC];
@@ -360,11 +375,11 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
                     } else {
                         const uint4 w = __ldg(reinterpret_cast<const uint4*>(
                             reinterpret_cast<const uint16_t*>(A.im.data) + (int64_t)gy * A.im.pitch + gx0));
-                        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+                        const uint32_t u4[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            v[2 * e] = (float)(u[e] & 0xffffu);
-                            v[2 * e + 1] = (float)(u[e] >> 16);
+                            v[2 * e] = (float)(u4[e] & 0xffffu);
+                            v[2 * e + 1] = (float)(u4[e] >> 16);
                         }
                     }
                 } else {
@@ -377,17 +392,26 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
                                                   (int64_t)gy * A.im.pitch + gx);
                     }
                 }
+                float4* dst = reinterpret_cast<float4*>(S.m + ry * SW + (gx0 - (x0 - XHALO)));
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const int cx = gx0 + e - (x0 - hh);
-                    if (cx < 0 || cx >= scols) continue;
-                    stage_cell(S, A, ry, cx, v[e], F32 ? !isfinite(v[e]) : false, hh, th, tw);
-                }
+                for (int e = 0; e < VEC / 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+            }
+            __syncthreads();
+            // m = I - B, one staged column per lane, one row per warp at a time
+            for (int ry = warp; ry < srows; ry += DT_NT / 32)
+            for (int c = clo + lane; c < chi; c += 32) {
+                const float v = S.m[ry * SW + c];
+                const bool bad = F32 ? !isfinite(v) : false;
+                S.m[ry * SW + c] = bad ? 0.f : v - cell_bkg(S, ry, c);
+                const int py = ry - hh, px = c - XHALO;
+                if (py >= 0 && py < th && px >= 0 && px < tw)
+                    S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && A.im.sat > 0.f && v >= A.im.sat) ? 2 : 0);
             }
         } else {
-            for (int q = tid; q < srows * scols; q += DT_NT) {
-                const int ry = q / scols, cx = q - ry * scols;
-                const int gx = mirror_fast(x0 - hh + cx, W), gy = mirror_fast(y0 - hh + ry, H);
+            __syncthreads();
+            for (int ry = warp; ry < srows; ry += DT_NT / 32)
+            for (int c = clo + lane; c < chi; c += 32) {
+                const int gx = mirror_fast(x0 - XHALO + c, W), gy = mirror_fast(y0 - hh + ry, H);
                 float v;
                 bool bad;
                 if (F32) {
@@ -398,7 +422,10 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
                     bad = false;
                 }
                 if (A.im.mask && A.im.mask[(int64_t)gy * W + gx]) bad = true;
-                stage_cell(S, A, ry, cx, v, bad, hh, th, tw);
+                S.m[ry * SW + c] = bad ? 0.f : v - cell_bkg(S, ry, c);
+                const int py = ry - hh, px = c - XHALO;
+                if (py >= 0 && py < th && px >= 0 && px < tw)
+                    S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && A.im.sat > 0.f && v >= A.im.sat) ? 2 : 0);
             }
         }
         __syncthreads();
@@ -416,10 +443,7 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
                 const int p = py * TX + px;
                 bool fg = false;
                 if (py < th && px < tw) {
-                    const int ry = py + hh, cx = px + hh;
-                    const int2 j = S.rowj[ry];
-                    const float4 n0 = S.colv[j.x * SW + cx], n1 = S.colv[j.y * SW + cx];
-                    const float sig = combine_row(S.rowc[ry], n0.z, n1.z, n0.w, n1.w);
+                    const float sig = cell_rms(S, py + hh, px + XHALO);
                     const float thr = A.thresh * sig;
                     fg = (F[i] > thr) && !(S.pflag[p] & 1);
                     if (fabsf(F[i] - thr) <= 1e-5f * fabsf(thr)) ++nnear;
@@ -463,17 +487,19 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
 
     // ---- compact root numbering in raster (= label) order
     {
+        const int p0 = tid * ROWS_PER_THREAD;
+        const int4* l4 = reinterpret_cast<const int4*>(S.lab + p0);
+        const int4 a = l4[0], b = l4[1];
+        const int lv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         int cnt = 0;
-        for (int e = 0; e < ROWS_PER_THREAD; ++e) {
-            const int p = tid * ROWS_PER_THREAD + e;
-            cnt += (S.lab[p] == p);
-        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) cnt += (lv[e] == p0 + e);
         int off = block_excl_scan(cnt, S.warp_tot, &S.nroots);
-        for (int e = 0; e < ROWS_PER_THREAD; ++e) {
-            const int p = tid * ROWS_PER_THREAD + e;
-            if (S.lab[p] == p) {
-                S.rid[p] = (short)off;
-                S.r_pix[off] = p;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            if (lv[e] == p0 + e) {
+                S.u.rid[p0 + e] = (short)off;
+                S.r_pix[off] = p0 + e;
                 ++off;
             }
         }
@@ -485,16 +511,26 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
     }
     __syncthreads();
     for (int p = tid; p < TNPIX; p += DT_NT) {
+        // lanes of one warp that share a root combine before touching
+        // shared memory (large segments fill whole warps)
         const int l = S.lab[p];
+        const unsigned act = __ballot_sync(0xffffffffu, l >= 0);
         if (l < 0) continue;
-        const int r = S.rid[l];
+        const int r = S.u.rid[l];
         const int py = p / TX, px = p - py * TX;
-        atomicAdd(S.r_npix + r, 1);
-        atomicMin(S.r_xmin + r, px); atomicMax(S.r_xmax + r, px);
-        atomicMin(S.r_ymin + r, py); atomicMax(S.r_ymax + r, py);
         const bool border = (px == 0 && x0 > 0) || (px == tw - 1 && x0 + tw < W) ||
                             (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
-        if (border) S.r_pidx[r] = 1;
+        const unsigned grp = __match_any_sync(act, r);
+        const int n = __popc(grp);
+        const int xmn = __reduce_min_sync(grp, px), xmx = __reduce_max_sync(grp, px);
+        const int ymn = __reduce_min_sync(grp, py), ymx = __reduce_max_sync(grp, py);
+        const unsigned brd = __ballot_sync(grp, border);
+        if (lane == __ffs(grp) - 1) {
+            atomicAdd(S.r_npix + r, n);
+            atomicMin(S.r_xmin + r, xmn); atomicMax(S.r_xmax + r, xmx);
+            atomicMin(S.r_ymin + r, ymn); atomicMax(S.r_ymax + r, ymx);
+            if (brd) S.r_pidx[r] = 1;
+        }
     }
     __syncthreads();
 
@@ -569,7 +605,7 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
                 const int py = by0 + q / bw, px = bx0 + q % bw;
                 const int p = py * TX + px;
                 if (S.lab[p] != rp) continue;
-                const float m = S.m[(py + hh) * SW + px + hh];
+                const float m = S.m[(py + hh) * SW + px + XHALO];
                 const uint32_t L = (uint32_t)(y0 + py) * (uint32_t)W + (uint32_t)(x0 + px);
                 mom_pixel(a, m, px, py, L, (S.pflag[p] & 2) != 0);
             }
@@ -587,7 +623,7 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
                     uint32_t fl = a.flags;
                     double flux;
                     double2 xy;
-                    double4 m2;
+                    Mom2 m2;
                     mom_finish(df_value(a.s), df_value(a.sx), df_value(a.sy), df_value(a.sxx), df_value(a.syy),
                                df_value(a.sxy), a.ux, a.uy, a.uxx, a.uyy, a.uxy, S.r_npix[r], x0, y0, &flux, &xy,
                                &m2, &fl);
@@ -603,7 +639,7 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
         const int py = p / TX, px = p - py * TX;
         if (py >= th || px >= tw) continue;
         const int l = S.lab[p];
-        const uint32_t v = l >= 0 ? (uint32_t)S.r_val[S.rid[l]] : 0u;
+        const uint32_t v = l >= 0 ? (uint32_t)S.r_val[S.u.rid[l]] : 0u;
         A.seg[(int64_t)(y0 + py) * W + x0 + px] = v;
     }
     // ---- edge records: local piece index of each edge pixel, or -1
@@ -618,7 +654,7 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
         int16_t v = -1;
         if (ok) {
             const int l = S.lab[py * TX + px];
-            if (l >= 0) v = (int16_t)S.r_pidx[S.rid[l]];
+            if (l >= 0) v = (int16_t)S.r_pidx[S.u.rid[l]];
         }
         ed[q] = v;
     }
@@ -785,7 +821,7 @@ __global__ void k_finalize(Tiles T, Pieces P, Comps C, uint32_t* seg, int W, int
                 if (id < C.cap) {
                     double flux;
                     double2 xy;
-                    double4 m2;
+                    Mom2 m2;
                     mom_finish(df_value(s), df_value(sx), df_value(sy), df_value(sxx), df_value(syy), df_value(sxy),
                                ux, uy, uxx, uyy, uxy, tot, X0, Y0, &flux, &xy, &m2, &fl);
                     C.label[id] = fin; C.npix[id] = tot; C.bbox[id] = bb;

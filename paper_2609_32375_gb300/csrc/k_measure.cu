@@ -112,13 +112,52 @@ __device__ __forceinline__ float load_px(const Image& im, int x, int y, bool& ba
     return v;
 }
 
+// Pixels crossed by a circle wait in a per-warp queue so that the exact
+// overlap area, the one expensive step, runs with every lane busy instead of
+// once per row for whichever lanes meet the circle.
+struct BEntry {
+    float dx0, dy0, m, var;
+    int kf;                 // radius index | bad << 8 | saturated << 9
+};
+constexpr int QCAP = 96;
+constexpr int MEAS_NT = 256;
+
+template <int NR>
+__device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn, DF* f, DF* v, uint32_t* fl)
+{
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < qn; i += 32) {
+        const BEntry e = wq[i];
+        const int k = e.kf & 0xff;
+        const float A = disc_rect_area(e.dx0, e.dx0 + 1.f, e.dy0, e.dy0 + 1.f, ap.r[k]);
+        if (!(A > 0.f)) continue;
+#pragma unroll
+        for (int kk = 0; kk < NR; ++kk) {
+            if (kk != k) continue;
+            if (e.kf & 0x100) { fl[kk] |= GP_FLAG_BAD; continue; }
+            if (e.kf & 0x200) fl[kk] |= GP_FLAG_SAT;
+            df_add_prod(f[kk], A, e.m);
+            df_add_prod(v[kk], A, e.var);
+        }
+    }
+    __syncwarp();
+}
+
 // Apertures around (cx, cy) for all radii; executed by one full warp.
-// Lane results are combined in a fixed order; lane 0 writes.
-template <bool F32>
+// One lane per pixel column: the column's x-spline coefficients and the
+// node-row values u_j, w_j of both maps are evaluated once per column and
+// reused down the column, so each pixel costs a few FMAs for B(p) and
+// sigma(p).  Pixels wholly inside a disc add directly; pixels the circle
+// crosses go through the queue.  The queue order and the lane assignment are
+// fixed, and lane results are combined in a fixed order, so the sums are
+// reproducible.  Lane 0 writes.
+template <bool F32, int NR>
 __device__ void aperture_warp(const Image& im, const SplineTab& sb, const SplineTab& sr, const ApSpec& ap,
-                              double cx, double cy, double* flux, double* ferr, uint32_t* aflags)
+                              double cx, double cy, double* flux, double* ferr, uint32_t* aflags, BEntry* wq)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int W = im.W, H = im.H;
     // positions far outside the frame (or NaN) clamp to an empty pixel range
     const double cxc = fmin(fmax(cx, -4096.0), (double)W + 4096.0);
@@ -131,58 +170,87 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
     xa = max(xa, 0); ya = max(ya, 0);
     xb = min(xb, W - 1); yb = min(yb, H - 1);
     if (!(cx == cxc) || !(cy == cyc)) { xb = -1; yb = -1; }
-    DF f[MAX_NR], v[MAX_NR];
-    uint32_t fl[MAX_NR];
+    DF f[NR > 0 ? NR : 1], v[NR > 0 ? NR : 1];
+    uint32_t fl[NR > 0 ? NR : 1];
 #pragma unroll
-    for (int k = 0; k < MAX_NR; ++k) { f[k] = df_zero(); v[k] = df_zero(); fl[k] = 0u; }
-    const int bw = xb - xa + 1, bh = yb - ya + 1;
-    const int npx = (bw > 0 && bh > 0) ? bw * bh : 0;
-    for (int q = lane; q < npx; q += 32) {
-        const int y = ya + q / bw, x = xa + q % bw;
+    for (int k = 0; k < NR; ++k) { f[k] = df_zero(); v[k] = df_zero(); fl[k] = 0u; }
+    const float rmax2 = ap.rmax * ap.rmax;
+    int qn = 0;                                      // warp-uniform queue length
+    for (int xbase = xa; xbase <= xb; xbase += 32) {
+        const int x = xbase + lane;
+        const bool colok = x <= xb;
         const float dx0 = (float)(x - xi) - xf - 0.5f, dx1 = dx0 + 1.f;
-        const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
-        const float nx = fmaxf(0.f, fmaxf(dx0, -dx1)), ny = fmaxf(0.f, fmaxf(dy0, -dy1));
-        const float dmin2 = nx * nx + ny * ny;
-        if (dmin2 >= ap.rmax * ap.rmax) continue;
-        const float fx = fmaxf(dx0 * dx0, dx1 * dx1), fy = fmaxf(dy0 * dy0, dy1 * dy1);
-        const float dmax2 = fx + fy;
-        bool bad;
-        float val = load_px<F32>(im, x, y, bad);
-        float m = 0.f, var = 0.f;
-        bool sat = false;
-        if (!bad) {
-            m = val - spline_eval(sb, (float)x, (float)y);
-            float s = spline_eval(sr, (float)x, (float)y);
-            var = s * s;
-            sat = im.sat > 0.f && val >= im.sat;
-        }
+        const float nx = fmaxf(0.f, fmaxf(dx0, -dx1));
+        const float fx = fmaxf(dx0 * dx0, dx1 * dx1);
+        const AxCoef ccx = axis_coef(sb.ax, (float)(colok ? x : xb));
+        int jc = -1;                       // node row pair cached for this column
+        float ub0 = 0, ub1 = 0, wb0 = 0, wb1 = 0, ur0 = 0, ur1 = 0, wr0 = 0, wr1 = 0;
+        for (int y = ya; y <= yb; ++y) {
+            const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
+            const float ny = fmaxf(0.f, fmaxf(dy0, -dy1));
+            const float dmin2 = nx * nx + ny * ny;
+            const float dmax2 = fx + fmaxf(dy0 * dy0, dy1 * dy1);
+            const bool live = colok && dmin2 < rmax2;
+            bool bad = true, sat = false;
+            float m = 0.f, var = 0.f;
+            if (live) {
+                const float val = load_px<F32>(im, x, y, bad);
+                if (!bad) {
+                    const AxCoef ccy = axis_coef(sb.ay, (float)y);
+                    if (ccy.i != jc) {
+                        const float2 b0 = row_eval(sb, ccy.i, ccx), b1 = row_eval(sb, ccy.i1, ccx);
+                        const float2 r0 = row_eval(sr, ccy.i, ccx), r1 = row_eval(sr, ccy.i1, ccx);
+                        ub0 = b0.x; wb0 = b0.y; ub1 = b1.x; wb1 = b1.y;
+                        ur0 = r0.x; wr0 = r0.y; ur1 = r1.x; wr1 = r1.y;
+                        jc = ccy.i;
+                    }
+                    m = val - axis_combine(ccy, ub0, ub1, wb0, wb1);
+                    const float sg = axis_combine(ccy, ur0, ur1, wr0, wr1);
+                    var = sg * sg;
+                    sat = im.sat > 0.f && val >= im.sat;
+                }
+            }
 #pragma unroll
-        for (int k = 0; k < MAX_NR; ++k) {
-            if (k >= ap.nr) break;
-            const float r = ap.r[k], r2 = r * r;
-            float A;
-            if (dmin2 >= r2) continue;
-            if (dmax2 <= r2) A = 1.f;
-            else A = disc_rect_area(dx0, dx1, dy0, dy1, r);
-            if (!(A > 0.f)) continue;
-            if (bad) { fl[k] |= GP_FLAG_BAD; continue; }
-            if (sat) fl[k] |= GP_FLAG_SAT;
-            df_add_prod(f[k], A, m);
-            df_add_prod(v[k], A, var);
+            for (int k = 0; k < NR; ++k) {
+                const float r = ap.r[k], r2 = r * r;
+                const bool in = live && dmin2 < r2;
+                const bool full = in && dmax2 <= r2;
+                if (full) {
+                    if (bad) fl[k] |= GP_FLAG_BAD;
+                    else {
+                        if (sat) fl[k] |= GP_FLAG_SAT;
+                        df_add(f[k], m);
+                        df_add(v[k], var);
+                    }
+                }
+                const bool bnd = in && !full;
+                const unsigned bal = __ballot_sync(0xffffffffu, bnd);
+                if (bnd) {
+                    BEntry e;
+                    e.dx0 = dx0; e.dy0 = dy0; e.m = m; e.var = var;
+                    e.kf = k | (bad ? 0x100 : 0) | (sat ? 0x200 : 0);
+                    wq[qn + __popc(bal & lt)] = e;
+                }
+                qn += __popc(bal);
+                if (qn > QCAP - 32) {
+                    flush_queue<NR>(ap, wq, qn, f, v, fl);
+                    qn = 0;
+                }
+            }
         }
     }
+    flush_queue<NR>(ap, wq, qn, f, v, fl);
 #pragma unroll
-    for (int k = 0; k < MAX_NR; ++k) {
-        if (k >= ap.nr) break;
-        DF fs = df_warp_sum(f[k]);
-        DF vs = df_warp_sum(v[k]);
+    for (int k = 0; k < NR; ++k) {
+        const DF fs = df_warp_sum(f[k]);
+        const DF vs = df_warp_sum(v[k]);
         uint32_t ff = fl[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ff |= __shfl_xor_sync(0xffffffffu, ff, o);
         if (lane == 0) {
             const double r = ap.r[k];
             if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) ff |= GP_FLAG_TRUNCATED;
-            double F = df_value(fs);
+            const double F = df_value(fs);
             double V = df_value(vs);
             if (ap.gain > 0.f && F > 0.0) V += F / (double)ap.gain;
             flux[k] = F;
@@ -194,9 +262,11 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
 
 // One warp per catalog row (segments in label order): copy the segment's
 // finished moments into the row, then the apertures at its centroid.
-template <bool F32>
-__global__ void __launch_bounds__(256) k_measure(MeasureArgs A)
+template <bool F32, int NR>
+__global__ void __launch_bounds__(MEAS_NT) k_measure(MeasureArgs A)
 {
+    __shared__ BEntry queue[MEAS_NT / 32][QCAP];
+    BEntry* wq = queue[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -208,34 +278,74 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs A)
         const double2 xy = A.C.xy[c];
         if (lane == 0) {
             const int4 bb = A.C.bbox[c];
-            const double4 m2 = A.C.mom2[c];
+            const Mom2 m2 = A.C.mom2[c];
             const uint32_t pL = A.C.peakL[c];
             A.label[r] = A.C.label[c];
             A.npix[r] = A.C.npix[c];
             A.flux_iso[r] = A.C.flux[c];
             A.x[r] = xy.x; A.y[r] = xy.y;
-            A.x2[r] = m2.x; A.y2[r] = m2.y; A.xy[r] = m2.z;
+            A.x2[r] = m2.x2; A.y2[r] = m2.y2; A.xy[r] = m2.xy;
             A.xmin[r] = bb.x; A.xmax[r] = bb.y; A.ymin[r] = bb.z; A.ymax[r] = bb.w;
             A.peak[r] = A.C.peak[c];
             A.xpeak[r] = (int)(pL % (uint32_t)W); A.ypeak[r] = (int)(pL / (uint32_t)W);
             A.flags[r] = A.C.flags[c];
         }
-        if (A.ap.nr > 0)
-            aperture_warp<F32>(A.im, A.sb, A.sr, A.ap, xy.x, xy.y, A.apflux + (int64_t)r * A.ap.nr,
-                               A.apferr + (int64_t)r * A.ap.nr, A.apflags + (int64_t)r * A.ap.nr);
+        if constexpr (NR > 0)
+            aperture_warp<F32, NR>(A.im, A.sb, A.sr, A.ap, xy.x, xy.y, A.apflux + (int64_t)r * NR,
+                                   A.apferr + (int64_t)r * NR, A.apflags + (int64_t)r * NR, wq);
     }
 }
 
-template <bool F32>
-__global__ void __launch_bounds__(256) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap, const double* xs,
-                                                  const double* ys, int n, double* flux, double* ferr, uint32_t* fl)
+template <bool F32, int NR>
+__global__ void __launch_bounds__(MEAS_NT) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap,
+                                                      const double* xs, const double* ys, int n, double* flux,
+                                                      double* ferr, uint32_t* fl)
 {
+    __shared__ BEntry queue[MEAS_NT / 32][QCAP];
+    BEntry* wq = queue[threadIdx.x >> 5];
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = wid; i < n; i += nw)
-        aperture_warp<F32>(im, sb, sr, ap, xs[i], ys[i], flux + (int64_t)i * ap.nr, ferr + (int64_t)i * ap.nr,
-                           fl + (int64_t)i * ap.nr);
+        aperture_warp<F32, NR>(im, sb, sr, ap, xs[i], ys[i], flux + (int64_t)i * NR, ferr + (int64_t)i * NR,
+                               fl + (int64_t)i * NR, wq);
 }
+
+// dispatch on the number of radii (a compile-time constant in the kernels)
+template <template <bool, int> class Launch, bool F32, typename... Args>
+static cudaError_t dispatch_nr(int nr, Args... args)
+{
+    switch (nr) {
+    case 0: return Launch<F32, 0>::run(args...);
+    case 1: return Launch<F32, 1>::run(args...);
+    case 2: return Launch<F32, 2>::run(args...);
+    case 3: return Launch<F32, 3>::run(args...);
+    case 4: return Launch<F32, 4>::run(args...);
+    case 5: return Launch<F32, 5>::run(args...);
+    case 6: return Launch<F32, 6>::run(args...);
+    case 7: return Launch<F32, 7>::run(args...);
+    default: return Launch<F32, 8>::run(args...);
+    }
+}
+
+template <bool F32, int NR>
+struct MeasureLaunch {
+    static cudaError_t run(const MeasureArgs& A, int g, cudaStream_t st)
+    {
+        k_measure<F32, NR><<<g, 256, 0, st>>>(A);
+        return cudaGetLastError();
+    }
+};
+
+template <bool F32, int NR>
+struct ApertureLaunch {
+    static cudaError_t run(Image im, SplineTab sb, SplineTab sr, ApSpec ap, const double* xs, const double* ys,
+                           int n, double* flux, double* ferr, uint32_t* fl, int g, cudaStream_t st)
+    {
+        if (NR == 0) return cudaSuccess;
+        k_aperture<F32, NR><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
+        return cudaGetLastError();
+    }
+};
 
 // --------------------------------------------------------------- launchers ---
 static ApSpec make_ap(const float* radii, int nr, float gain)
@@ -266,11 +376,8 @@ cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab
     A.ap = make_ap(radii, nr, gain);
     A.apflux = apflux; A.apferr = apferr; A.apflags = apflags;
     const int g = 152 * 8;
-    if (im.is_f32)
-        k_measure<true><<<g, 256, 0, st>>>(A);
-    else
-        k_measure<false><<<g, 256, 0, st>>>(A);
-    return cudaGetLastError();
+    if (im.is_f32) return dispatch_nr<MeasureLaunch, true>(nr, A, g, st);
+    return dispatch_nr<MeasureLaunch, false>(nr, A, g, st);
 }
 
 cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,
@@ -281,11 +388,8 @@ cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTa
     int64_t g64 = ((int64_t)n * 32 + 255) / 256;
     int g = (int)(g64 < 152 * 8 ? g64 : 152 * 8);
     if (g < 1) g = 1;
-    if (im.is_f32)
-        k_aperture<true><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
-    else
-        k_aperture<false><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
-    return cudaGetLastError();
+    if (im.is_f32) return dispatch_nr<ApertureLaunch, true>(nr, im, sb, sr, ap, xs, ys, n, flux, ferr, fl, g, st);
+    return dispatch_nr<ApertureLaunch, false>(nr, im, sb, sr, ap, xs, ys, n, flux, ferr, fl, g, st);
 }
 
 }  // namespace gp
