@@ -321,6 +321,40 @@ def run_gpu(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clk}
+    # ---- the learned-background form on the same frame (when trained weights exist)
+    wpath = os.path.join(ROOT, "paper_2609_32375_gb300", "weights", "learned_bkg.npz")
+    if os.path.exists(wpath) and not args.no_learned:
+        from paper_2609_32375_gb300 import learned as L
+        net = L.load(wpath, device=dev)
+        exl = gp.Extractor(ctx, (H, W), t_img.dtype, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii,
+                           cfg.gain, CAPACITY, saturation=cfg.saturation, device=dev, net=net)
+        for _ in range(args.warmup):
+            exl.run(t_img)
+        ctx.sync()
+        ctx.set_timing(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            exl.run(t_img)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        lst = ctx.stats()
+        ctx.set_timing(False)
+        lms = a.elapsed_time(b) / args.steps
+        pb, pr = ex.out["bkg_mesh"], ex.out["rms_mesh"]
+        dbk = ((exl.out["bkg_mesh"] - pb) / pr.clamp_min(1e-6)).pow(2).mean().sqrt().item()
+        drm = ((exl.out["rms_mesh"] - pr) / pr.clamp_min(1e-6)).pow(2).mean().sqrt().item()
+        nl = int(exl.out["catalog"]["n"].item())
+        line_learned = {"value": round(mpix_all / (lms / 1e3), 2), "unit": UNIT, "ms_per_step": round(lms, 4),
+                        "stages_ms": {k: round(v / max(lst["calls"], 1), 4) for k, v in lst["ms"].items()},
+                        "bkg_rmse_vs_plain_sigma": round(dbk, 4), "rms_relerr_vs_plain": round(drm, 4),
+                        "segments": nl, "weights": os.path.relpath(wpath, ROOT)}
+    else:
+        line_learned = None
+    if line_learned:
+        line["learned"] = line_learned
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, t, desc = oracle_sample(img, cfg)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
@@ -344,6 +378,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-crop", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-background form")
     ap.add_argument("--size", default=None,
                     help="WxH: run the workload's recipe on a frame of this size (profiling cases)")
     args = ap.parse_args()

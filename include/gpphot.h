@@ -230,6 +230,12 @@ typedef struct {
 gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, const gp_cnn_weights* net,
                                 gp_bkg* bkg, gp_stream stream);
 
+/* gp_extract with the network's background (same arguments and outputs,
+ * plus the weights). */
+gp_status gp_extract_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp, const gp_det_params* dp,
+                             const gp_ap_params* ap, const gp_cnn_weights* net, gp_bkg* bkg, uint32_t* segmap,
+                             gp_catalog* cat, double* flux, double* fluxerr, uint32_t* apflags, gp_stream stream);
+
 /* Per-box quantiles q10, q25, q50, q75, q90 of the good pixels (float32,
  * [5][my][mx], device, caller-owned), from one pass over the frame. */
 gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float* quant, gp_stream stream);

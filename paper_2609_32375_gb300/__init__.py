@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_workspace_bytes",
            "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static",
-           "gp_background_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
+           "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
            "gp_cnn_denorm")
 
@@ -147,6 +147,9 @@ def load_library():
         L.gp_background_learned.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpCnnWeights),
                                             C.POINTER(GpBkg), vp]
         L.gp_box_quantiles.argtypes = [vp, C.POINTER(GpImage), i32, vp, vp]
+        L.gp_extract_learned.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
+                                         C.POINTER(GpApParams), C.POINTER(GpCnnWeights), C.POINTER(GpBkg), vp,
+                                         C.POINTER(GpCatalog), vp, vp, vp, vp]
         L.gp_cnn_conv3x3.argtypes = [vp, i32, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp]
         L.gp_cnn_conv3x3_wgrad.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp]
         L.gp_cnn_relu_backward.argtypes = [vp, vp, vp, i64, vp]
@@ -156,7 +159,7 @@ def load_library():
         L.gp_cnn_features.argtypes = [vp, i32, i32, vp, vp, vp]
         L.gp_cnn_targets.argtypes = [vp, vp, vp, i32, i32, vp, vp]
         L.gp_cnn_denorm.argtypes = [vp, vp, i32, i32, vp, vp, vp]
-        for name in ("gp_background_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
+        for name in ("gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
                      "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features",
                      "gp_cnn_targets", "gp_cnn_denorm"):
             getattr(L, name).restype = st
@@ -352,9 +355,10 @@ class Extractor:
 
     def __init__(self, ctx: Context, shape, dtype, mesh, kernel, thresh, minarea, radii, gain, capacity,
                  saturation=0.0, filter_size=3, clip_k=3.0, clip_maxiter=10, maps=False, mask_out=False,
-                 count_near=False, device="cuda"):
+                 count_near=False, device="cuda", net=None):
         import torch
         self.ctx = ctx
+        self.net = net          # learned.Network: use the learned background
         H, W = shape
         self.shape = (H, W)
         mx, my = -(-W // mesh), -(-H // mesh)
@@ -388,10 +392,19 @@ class Extractor:
 
     def run(self, img, mask=None, stream=None):
         gi = make_image(img, mask, self.saturation)
-        _check(self._lib.gp_extract(self.ctx.handle, C.byref(gi), C.byref(self._bp), C.byref(self._dp),
-                                    C.byref(self._ap), C.byref(self._bkg), self.out["segmap"].data_ptr(),
-                                    C.byref(self._cat), self.out["flux"].data_ptr(), self.out["fluxerr"].data_ptr(),
-                                    self.out["apflags"].data_ptr(), _stream_handle(stream)))
+        if self.net is None:
+            _check(self._lib.gp_extract(self.ctx.handle, C.byref(gi), C.byref(self._bp), C.byref(self._dp),
+                                        C.byref(self._ap), C.byref(self._bkg), self.out["segmap"].data_ptr(),
+                                        C.byref(self._cat), self.out["flux"].data_ptr(),
+                                        self.out["fluxerr"].data_ptr(), self.out["apflags"].data_ptr(),
+                                        _stream_handle(stream)))
+        else:
+            w = self.net.weights()
+            _check(self._lib.gp_extract_learned(self.ctx.handle, C.byref(gi), C.byref(self._bp), C.byref(self._dp),
+                                                C.byref(self._ap), C.byref(w), C.byref(self._bkg),
+                                                self.out["segmap"].data_ptr(), C.byref(self._cat),
+                                                self.out["flux"].data_ptr(), self.out["fluxerr"].data_ptr(),
+                                                self.out["apflags"].data_ptr(), _stream_handle(stream)))
         return self.out
 
     def catalog_host(self):

@@ -643,6 +643,8 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
 
 }  // extern "C"
 
+extern "C" {
+
 gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float* quant, gp_stream stream)
 {
     gp_status s;
@@ -665,21 +667,19 @@ gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float
     return GP_OK;
 }
 
-gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, const gp_cnn_weights* net,
-                                gp_bkg* bkg, gp_stream stream)
+}  // extern "C"
+
+namespace {
+
+// the background stage with the network; fills bkg's meshes (and maps) and
+// returns the spline tables for the stages that follow
+gp_status run_background_learned(gp_ctx* ctx, Carver& cv, const gp_image* img, const gp_bkg_params* p,
+                                 const gp_cnn_weights* net, gp_bkg* bkg, cudaStream_t st, SplineTab* sb,
+                                 SplineTab* sr)
 {
-    gp_status s;
-    if ((s = check_ctx(ctx)) != GP_OK) return s;
-    if ((s = check_image(img)) != GP_OK) return s;
-    if ((s = check_bkg_params(img, p)) != GP_OK) return s;
-    if (!net) return fail(GP_ERR_INVALID_ARG, "null network weights");
-    for (int l = 0; l < GP_CNN_LAYERS; ++l)
-        if (!net->wt[l] || !net->bias[l]) return fail(GP_ERR_INVALID_ARG, "null weights of layer %d", l);
-    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
     const int W = img->width, H = img->height, B = p->mesh;
     const int Mx = (W + B - 1) / B, My = (H + B - 1) / B, nbox = Mx * My;
     bkg->mesh = B; bkg->mx = Mx; bkg->my = My;
-    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
     BkgWork w;
     carve_bkg(cv, nbox, w);
     float* quant = cv.take<float>((size_t)5 * nbox);
@@ -689,8 +689,6 @@ gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_p
     uint16_t* a1 = cv.take<uint16_t>((size_t)48 * nbox);
     float* out = cv.take<float>((size_t)2 * nbox);
     if (!cv.ok()) return oom(cv);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    begin_call(ctx, st);
     GP_CUDA(launch_boxstats(to_image(img), B, 3.0, 0, w.bkg_raw, w.rms_raw, w.valid, quant, st));
     mark(ctx, 1, st);
     GP_CUDA(launch_cnn_features(quant, 1, nbox, feat, norm, st));
@@ -707,16 +705,75 @@ gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_p
     GP_CUDA(launch_cnn_denorm(out, norm, nbox, 1, bkg->bkg_mesh, bkg->rms_mesh, st));
     ctx->launches += 3 + GP_CNN_LAYERS;
     SplineTab tb, tr;
-    s = run_spline(cv, bkg, W, H, &tb, &tr, &ctx->launches, st);
+    gp_status s = run_spline(cv, bkg, W, H, &tb, &tr, &ctx->launches, st);
     if (s == GP_ERR_OOM) return oom(cv);
     if (s != GP_OK) return s;
     if (bkg->bkg_map || bkg->rms_map) {
         GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
         ctx->launches += 1;
     }
-    mark_to(ctx, 2, 6, st);
+    mark(ctx, 2, st);
+    if (sb) { *sb = tb; *sr = tr; }
     return GP_OK;
 }
+
+gp_status check_net(const gp_cnn_weights* net)
+{
+    if (!net) return fail(GP_ERR_INVALID_ARG, "null network weights");
+    for (int l = 0; l < GP_CNN_LAYERS; ++l)
+        if (!net->wt[l] || !net->bias[l]) return fail(GP_ERR_INVALID_ARG, "null weights of layer %d", l);
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, const gp_cnn_weights* net,
+                                gp_bkg* bkg, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg_params(img, p)) != GP_OK) return s;
+    if ((s = check_net(net)) != GP_OK) return s;
+    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    begin_call(ctx, st);
+    s = run_background_learned(ctx, cv, img, p, net, bkg, st, nullptr, nullptr);
+    mark_to(ctx, 3, 6, st);
+    return s;
+}
+
+gp_status gp_extract_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp, const gp_det_params* dp,
+                             const gp_ap_params* ap, const gp_cnn_weights* net, gp_bkg* bkg, uint32_t* segmap,
+                             gp_catalog* cat, double* flux, double* fluxerr, uint32_t* apflags, gp_stream stream)
+{
+    gp_status s;
+    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg_params(img, bp)) != GP_OK) return s;
+    if ((s = check_net(net)) != GP_OK) return s;
+    if ((s = check_det(dp, taps)) != GP_OK) return s;
+    if ((s = check_ap(ap, true)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
+    if (!segmap) return fail(GP_ERR_INVALID_ARG, "null segmap");
+    if (ap->nr > 0 && cat->capacity > 0 && (!flux || !fluxerr || !apflags))
+        return fail(GP_ERR_INVALID_ARG, "null aperture output array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    s = run_background_learned(ctx, cv, img, bp, net, bkg, st, &sb, &sr);
+    if (s != GP_OK) return s;
+    return run_detect(ctx, cv, img, sb, sr, taps, dp, segmap, cat, ap->radii, ap->nr, ap->gain, flux, fluxerr, apflags,
+                      st);
+}
+
+}  // extern "C"
 
 // message for gp_last_error() from entry points defined in other files
 namespace gp {

@@ -373,3 +373,67 @@ def time_background(ctx, img, mesh, net, reps=20):
         torch.cuda.synchronize()
         res[name] = a.elapsed_time(b) / reps
     return res
+
+
+# --------------------------------------------------------------- weights ---
+def save(net: Network, path: str, meta=None):
+    arrays = {f"W{l}": net.W[l].cpu().numpy() for l in range(6)}
+    arrays.update({f"b{l}": net.b[l].cpu().numpy() for l in range(6)})
+    if meta:
+        arrays["meta"] = np.frombuffer(repr(meta).encode(), dtype=np.uint8)
+    np.savez(path, **arrays)
+
+
+def load(path: str, device="cuda") -> Network:
+    import torch
+    z = np.load(path)
+    net = Network(device=device)
+    net.load_state_dict({"W": [torch.from_numpy(z[f"W{l}"]) for l in range(6)],
+                         "b": [torch.from_numpy(z[f"b{l}"]) for l in range(6)]})
+    return net
+
+
+def main(argv=None):
+    """Train the network on seeded GPU-drawn frames and report its held-out
+    errors and the background stage's time against the plain estimator."""
+    import argparse
+    import json
+
+    import torch
+
+    from . import Context
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--frames", type=int, default=2000)
+    ap.add_argument("--held", type=int, default=200)
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--mesh", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--out", default=None, help="write the trained weights (.npz)")
+    a = ap.parse_args(argv)
+    ctx = Context(0, workspace_bytes=1 << 30)
+    t0 = time.time()
+    train_set = build_dataset(ctx, a.frames, seed0=1_000_000, size=a.size, mesh=a.mesh)
+    held = build_dataset(ctx, a.held, seed0=1_000_000 + a.frames, size=a.size, mesh=a.mesh)
+    t_data = time.time() - t0
+    net = Network(seed=0)
+    t0 = time.time()
+    hist = train(net, train_set, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    ev = evaluate(net, held)
+    frame = training_frame(1_000_000 + a.frames + a.held, a.size)
+    tm = time_background(ctx, frame.image, a.mesh, net)
+    res = {"frames": a.frames, "held_out": a.held, "size": a.size, "mesh": a.mesh, "epochs": a.epochs,
+           "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "data_s": round(t_data, 1),
+           "train_s": round(t_train, 1), **{k: round(v, 5) for k, v in ev.items()},
+           **{k: round(v, 4) for k, v in tm.items()}}
+    if a.out:
+        save(net, a.out, res)
+    print(json.dumps(res), flush=True)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
