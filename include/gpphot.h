@@ -279,6 +279,125 @@ gp_status gp_cnn_targets(const float* bkg_mesh, const float* rms_mesh, const flo
 gp_status gp_cnn_denorm(const float* out, const float* norm, int32_t nbox, int32_t nframes, float* bkg_mesh,
                         float* rms_mesh, gp_stream stream);
 
+/* ------------------------------------------------------- batched frames --
+ * Several frames in one call.  The paper runs one frame per call; a frame of
+ * a few megapixels leaves most of a GB300 idle, so here every stage runs as
+ * one launch over all the frames of the call (grid y = frame).  Frames share
+ * the parameters and the dtype; each has its own inputs, outputs and status
+ * word, and its results are bit-identical to gp_extract's on that frame
+ * alone (same kernels, same per-frame arithmetic and reduction order).
+ *  - 1 <= n <= GP_MAX_BATCH; all frames GP_U16 or all GP_F32.
+ *  - dp->nnear and dp->mask_out are not written (per-frame outputs that the
+ *    batch does not carry).
+ *  - net: NULL for the clipped estimator, else the learned background (one
+ *    network pass over all frames when they share one mesh geometry).
+ *  - Workspace: the sum of gp_workspace_bytes over the frames plus 256 KB
+ *    suffices for the plain background.
+ *  - Each frame's status word (device int32) must be zero on entry; after the
+ *    stream completes it is 0 or the frame's first error (GP_ERR_CAPACITY:
+ *    more segments than catalog rows; GP_ERR_TIMEOUT / GP_ERR_INTERNAL: see
+ *    gp_ctx_sync).  The return value covers argument checks and launches. */
+#define GP_MAX_BATCH 64
+typedef struct {
+    gp_image image;        /* device */
+    gp_bkg bkg;            /* bkg_mesh, rms_mesh required (device); maps nullable */
+    uint32_t* segmap;      /* device width*height */
+    gp_catalog cat;        /* device columns and device count */
+    double* flux;          /* device capacity*nr; nullable when nr = 0 or capacity = 0 */
+    double* fluxerr;
+    uint32_t* apflags;
+    int32_t* status;       /* device word, zero on entry */
+} gp_frame;
+
+gp_status gp_extract_batch(gp_ctx* ctx, gp_frame* frames, int32_t n, const gp_bkg_params* bp,
+                           const gp_det_params* dp, const gp_ap_params* ap, const gp_cnn_weights* net,
+                           gp_stream stream);
+
+/* --------------------------------------------------------- request server --
+ * A long-lived loop that takes frames from host memory and returns their
+ * catalogs, with continuous batching.  The paper processes one frame per
+ * call and bounds how many frames run at once by device memory over a
+ * frame's peak footprint (Section 6.4); the server makes that bound an
+ * admission rule: a request is admitted when its device footprint (pixels,
+ * segmentation map, workspace, results) fits the memory budget and an
+ * execution slot is free, so frames that arrive while others run start as
+ * soon as memory and a slot free up.  Small frames waiting together run as
+ * one batched launch (gp_extract_batch); each slot has its own stream, so one
+ * unit's host-to-device copy overlaps another's kernels.  A frame's results
+ * are bit-identical to gp_extract's on it alone.
+ *  - One worker thread owns all device work; submit, wait, release and stats
+ *    may be called from any thread.
+ *  - Requests are admitted in arrival order (a request that does not fit
+ *    waits, and so do the ones behind it).
+ *  - The request's host pixels must stay valid until its result is ready;
+ *    pinned host memory lets the copy run asynchronously.
+ *  - Results live in the server's pinned host memory until released. */
+typedef struct gp_server gp_server;
+
+typedef struct {
+    int32_t device;
+    size_t hbm_budget;        /* device bytes for work in flight (one allocation at create) */
+    size_t host_budget;       /* pinned host bytes for results (one allocation at create) */
+    int32_t slots;            /* units in flight at once, one stream each: 1 .. 16 */
+    int64_t batch_pixels;     /* frames of at most this many pixels may share a launch */
+    int32_t max_batch;        /* frames per launch, 1 .. GP_MAX_BATCH */
+    gp_bkg_params bkg;
+    gp_det_params det;        /* kernel taps copied at create; nnear and mask_out ignored */
+    gp_ap_params ap;          /* radii copied at create */
+    const gp_cnn_weights* net;  /* device weights (must outlive the server), or NULL: clipped estimator */
+} gp_server_config;
+
+typedef struct {
+    gp_image image;           /* HOST pixels and optional host mask (pitch = width) */
+    int32_t capacity;         /* catalog rows, >= 1 */
+    int32_t want_segmap;      /* nonzero: copy the segmentation map back */
+} gp_request;
+
+typedef struct {
+    int32_t status;           /* this frame's gp_status */
+    int32_t n;                /* segments found; rows filled = min(n, capacity) */
+    gp_catalog cat;           /* host columns (cat.n points at n), valid until release */
+    const double* flux;       /* host capacity*nr */
+    const double* fluxerr;
+    const uint32_t* apflags;
+    const uint32_t* segmap;   /* host width*height, or NULL */
+    const float* bkg_mesh;    /* host my*mx */
+    const float* rms_mesh;
+    int32_t mesh, mx, my;
+    int32_t batch;            /* frames in the launch this frame ran in */
+    double latency_ms;        /* submit to result ready (host clock) */
+    double queue_ms;          /* submit to admission */
+} gp_result;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t units;            /* launches of the pipeline (a frame or a batch) */
+    int64_t batched_frames;   /* frames that ran in a batch of two or more */
+    double mpix;              /* megapixels of completed frames */
+    double wall_s;            /* first submit to last completion */
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* latency of completed frames */
+    size_t budget, peak_bytes;                /* device budget and its peak use */
+    int32_t peak_inflight;    /* most units in flight at once */
+} gp_server_report;
+
+gp_status gp_server_create(const gp_server_config* cfg, gp_server** out);
+/* GP_ERR_OOM when the request could never fit the budgets */
+gp_status gp_server_submit(gp_server* s, const gp_request* req, uint64_t* ticket);
+/* the footprint the admission rule charges for this request run alone:
+ * device bytes (pixels, mask, segmentation map, workspace, result block) and
+ * pinned host bytes (result block, segmentation map if wanted) */
+gp_status gp_server_request_bytes(const gp_server* s, const gp_request* req, size_t* device_bytes,
+                                  size_t* host_bytes);
+/* waits for the result (timeout_ms < 0: no limit; GP_ERR_TIMEOUT when it
+ * expires first); returns the frame's own status */
+gp_status gp_server_wait(gp_server* s, uint64_t ticket, int32_t timeout_ms, gp_result* out);
+/* frees the result's host memory; its pointers become invalid */
+gp_status gp_server_release(gp_server* s, uint64_t ticket);
+/* counters and latency percentiles since create or the last reset */
+gp_status gp_server_stats(gp_server* s, gp_server_report* out, int32_t reset);
+/* finishes the work in flight, fails the requests not yet admitted, frees */
+void gp_server_destroy(gp_server* s);
+
 /* gp_background without a context, for callers that cannot allocate device
  * memory.  The paper has no counterpart: it is a deployment form of the
  * Section 3.1 stage.  Some callers must not call cudaMalloc at all -- a

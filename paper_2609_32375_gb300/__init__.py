@@ -35,7 +35,8 @@ EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "g
            "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static",
            "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
-           "gp_cnn_denorm")
+           "gp_cnn_denorm", "gp_extract_batch", "gp_server_create", "gp_server_submit", "gp_server_wait",
+           "gp_server_release", "gp_server_stats", "gp_server_destroy", "gp_server_request_bytes")
 
 
 class GpError(RuntimeError):
@@ -87,6 +88,38 @@ class GpCnnWeights(C.Structure):
 
 class GpApParams(C.Structure):
     _fields_ = [("radii", C.POINTER(C.c_float)), ("nr", C.c_int32), ("gain", C.c_float)]
+
+
+GP_MAX_BATCH = 64
+
+
+class GpFrame(C.Structure):
+    _fields_ = [("image", GpImage), ("bkg", GpBkg), ("segmap", C.c_void_p), ("cat", GpCatalog),
+                ("flux", C.c_void_p), ("fluxerr", C.c_void_p), ("apflags", C.c_void_p), ("status", C.c_void_p)]
+
+
+class GpServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("hbm_budget", C.c_size_t), ("host_budget", C.c_size_t),
+                ("slots", C.c_int32), ("batch_pixels", C.c_int64), ("max_batch", C.c_int32),
+                ("bkg", GpBkgParams), ("det", GpDetParams), ("ap", GpApParams), ("net", C.c_void_p)]
+
+
+class GpRequest(C.Structure):
+    _fields_ = [("image", GpImage), ("capacity", C.c_int32), ("want_segmap", C.c_int32)]
+
+
+class GpResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("cat", GpCatalog), ("flux", C.c_void_p),
+                ("fluxerr", C.c_void_p), ("apflags", C.c_void_p), ("segmap", C.c_void_p), ("bkg_mesh", C.c_void_p),
+                ("rms_mesh", C.c_void_p), ("mesh", C.c_int32), ("mx", C.c_int32), ("my", C.c_int32),
+                ("batch", C.c_int32), ("latency_ms", C.c_double), ("queue_ms", C.c_double)]
+
+
+class GpServerReport(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("units", C.c_int64),
+                ("batched_frames", C.c_int64), ("mpix", C.c_double), ("wall_s", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("max_ms", C.c_double),
+                ("budget", C.c_size_t), ("peak_bytes", C.c_size_t), ("peak_inflight", C.c_int32)]
 
 
 CATALOG_COLUMNS = (("label", "uint32"), ("npix", "int32"), ("flux_iso", "float64"), ("x", "float64"),
@@ -159,6 +192,20 @@ def load_library():
         L.gp_cnn_features.argtypes = [vp, i32, i32, vp, vp, vp]
         L.gp_cnn_targets.argtypes = [vp, vp, vp, i32, i32, vp, vp]
         L.gp_cnn_denorm.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+        L.gp_extract_batch.argtypes = [vp, C.POINTER(GpFrame), i32, C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
+                                       C.POINTER(GpApParams), C.POINTER(GpCnnWeights), vp]
+        L.gp_server_create.argtypes = [C.POINTER(GpServerConfig), C.POINTER(C.c_void_p)]
+        L.gp_server_submit.argtypes = [vp, C.POINTER(GpRequest), C.POINTER(C.c_uint64)]
+        L.gp_server_wait.argtypes = [vp, C.c_uint64, i32, C.POINTER(GpResult)]
+        L.gp_server_release.argtypes = [vp, C.c_uint64]
+        L.gp_server_stats.argtypes = [vp, C.POINTER(GpServerReport), i32]
+        L.gp_server_destroy.argtypes = [vp]
+        L.gp_server_destroy.restype = None
+        L.gp_server_request_bytes.argtypes = [vp, C.POINTER(GpRequest), C.POINTER(C.c_size_t),
+                                              C.POINTER(C.c_size_t)]
+        for name in ("gp_extract_batch", "gp_server_create", "gp_server_submit", "gp_server_wait",
+                     "gp_server_release", "gp_server_stats", "gp_server_request_bytes"):
+            getattr(L, name).restype = st
         for name in ("gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
                      "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features",
                      "gp_cnn_targets", "gp_cnn_denorm"):
@@ -417,3 +464,215 @@ class Extractor:
         cat["fluxerr"] = self.out["fluxerr"][:m, :nr].cpu().numpy()
         cat["apflags"] = self.out["apflags"][:m, :nr].cpu().numpy()
         return n, cat
+
+
+class BatchExtractor:
+    """Pre-allocated outputs for gp_extract_batch over a list of frame
+    shapes (one dtype): `run(images)` extracts them all in one batched call.
+    `outs[f]` has the layout of Extractor.out; `status` holds each frame's
+    device status word."""
+
+    def __init__(self, ctx: Context, shapes, dtype, mesh, kernel, thresh, minarea, radii, gain, capacity,
+                 saturation=0.0, filter_size=3, clip_k=3.0, clip_maxiter=10, device="cuda", net=None):
+        import torch
+        self.ctx = ctx
+        self.net = net
+        self._k, kp = _taps(kernel)
+        self._r, rp = _radii(radii)
+        nr = self._r.size
+        self.saturation = float(saturation)
+        self.shapes = [tuple(s) for s in shapes]
+        n = len(self.shapes)
+        if not 1 <= n <= GP_MAX_BATCH:
+            raise ValueError(f"batch of {n} frames outside [1, {GP_MAX_BATCH}]")
+        caps = capacity if isinstance(capacity, (list, tuple)) else [capacity] * n
+        self.status = torch.zeros(n, dtype=torch.int32, device=device)
+        self.outs, self._cats = [], []
+        for (H, W), cap in zip(self.shapes, caps):
+            mx, my = -(-W // mesh), -(-H // mesh)
+            cols, cat = allocate_catalog(cap, device)
+            o = {"bkg_mesh": torch.empty((my, mx), dtype=torch.float32, device=device),
+                 "rms_mesh": torch.empty((my, mx), dtype=torch.float32, device=device), "mesh": mesh,
+                 "segmap": torch.empty((H, W), dtype=torch.int32, device=device), "catalog": cols,
+                 "flux": torch.zeros((max(cap, 1), max(nr, 1)), dtype=torch.float64, device=device)}
+            o["fluxerr"] = torch.zeros_like(o["flux"])
+            o["apflags"] = torch.zeros((max(cap, 1), max(nr, 1)), dtype=torch.int32, device=device)
+            self.outs.append(o)
+            self._cats.append(cat)
+        self._bp = GpBkgParams(mesh, filter_size, clip_k, clip_maxiter)
+        self._dp = GpDetParams(kp, self._k.shape[1], self._k.shape[0], float(thresh), int(minarea), None, None)
+        self._ap = GpApParams(rp, nr, float(gain))
+        self._frames = (GpFrame * n)()
+        self._lib = load_library()
+
+    def run(self, images, stream=None):
+        if len(images) != len(self.shapes):
+            raise ValueError("one image per frame shape")
+        self.status.zero_()
+        for f, (img, o) in enumerate(zip(images, self.outs)):
+            if tuple(img.shape) != self.shapes[f]:
+                raise ValueError(f"frame {f}: shape {tuple(img.shape)} != {self.shapes[f]}")
+            my, mx = o["bkg_mesh"].shape
+            fr = self._frames[f]
+            fr.image = make_image(img, None, self.saturation)
+            fr.bkg = GpBkg(o["mesh"], mx, my, o["bkg_mesh"].data_ptr(), o["rms_mesh"].data_ptr(), None, None)
+            fr.segmap = o["segmap"].data_ptr()
+            fr.cat = self._cats[f]
+            fr.flux, fr.fluxerr, fr.apflags = o["flux"].data_ptr(), o["fluxerr"].data_ptr(), o["apflags"].data_ptr()
+            fr.status = self.status.data_ptr() + 4 * f
+        w = self.net.weights() if self.net is not None else None
+        _check(self._lib.gp_extract_batch(self.ctx.handle, self._frames, len(self.shapes), C.byref(self._bp),
+                                          C.byref(self._dp), C.byref(self._ap),
+                                          C.byref(w) if w is not None else None, _stream_handle(stream)))
+        return self.outs
+
+    def catalog_host(self, f):
+        o = self.outs[f]
+        n = int(o["catalog"]["n"].item())
+        m = min(n, self._cats[f].capacity)
+        cat = {k: v[:m].cpu().numpy() for k, v in o["catalog"].items() if k != "n"}
+        nr = self._r.size
+        cat["flux"] = o["flux"][:m, :nr].cpu().numpy()
+        cat["fluxerr"] = o["fluxerr"][:m, :nr].cpu().numpy()
+        cat["apflags"] = o["apflags"][:m, :nr].cpu().numpy()
+        return n, cat
+
+
+def _host_image(img, mask=None, saturation=0.0):
+    """GpImage for a host frame (numpy array or CPU tensor, 2-D, contiguous
+    rows) and the objects that keep its memory alive."""
+    keep = []
+    if hasattr(img, "numpy") and not isinstance(img, np.ndarray):
+        if img.is_cuda:
+            raise ValueError("server requests take host frames")
+        keep.append(img)
+        ptr, dt, shape, stride = img.data_ptr(), str(img.dtype).replace("torch.", ""), tuple(img.shape), img.stride(0)
+    else:
+        a = np.asarray(img)
+        if a.ndim != 2 or a.strides[1] != a.itemsize:
+            a = np.ascontiguousarray(a)
+        keep.append(a)
+        ptr, dt, shape, stride = a.ctypes.data, str(a.dtype), a.shape, a.strides[0] // a.itemsize
+    if dt not in ("uint16", "float32"):
+        raise ValueError(f"unsupported dtype {dt}")
+    mptr = None
+    if mask is not None:
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        if m.shape != shape:
+            raise ValueError("mask shape differs from the image")
+        keep.append(m)
+        mptr = m.ctypes.data
+    H, W = shape
+    return GpImage(ptr, GP_U16 if dt == "uint16" else GP_F32, W, H, stride, mptr, float(saturation)), keep
+
+
+def _np_view(ptr, n, dtype):
+    dt = np.dtype(dtype)
+    if n == 0 or not ptr:
+        return np.zeros(0, dt)
+    buf = (C.c_char * (n * dt.itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dt, count=n)
+
+
+class Server:
+    """The request server (gp_server_*): frames from host memory in,
+    catalogs out, with continuous batching under a device-memory budget.
+
+    submit() returns a ticket at once; result() waits for it, copies the
+    catalog into numpy arrays and frees the server's copy."""
+
+    def __init__(self, device=0, hbm_budget=8 << 30, host_budget=1 << 30, slots=4, batch_pixels=4 << 20,
+                 max_batch=16, mesh=64, filter_size=3, clip_k=3.0, clip_maxiter=10, kernel=None, thresh=1.5,
+                 minarea=5, radii=(3.0,), gain=0.0, net=None):
+        L = load_library()
+        self._k, kp = _taps(kernel)
+        self._r, rp = _radii(radii)
+        self.net = net
+        self._w = net.weights() if net is not None else None
+        cfg = GpServerConfig(int(device), int(hbm_budget), int(host_budget), int(slots), int(batch_pixels),
+                             int(max_batch), GpBkgParams(mesh, filter_size, clip_k, clip_maxiter),
+                             GpDetParams(kp, self._k.shape[1], self._k.shape[0], float(thresh), int(minarea), None,
+                                         None),
+                             GpApParams(rp, self._r.size, float(gain)),
+                             C.cast(C.pointer(self._w), C.c_void_p) if self._w is not None else None)
+        h = C.c_void_p()
+        _check(L.gp_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._keep = {}
+        self._shape = {}
+        self.nr = self._r.size
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().gp_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, img, capacity, mask=None, saturation=0.0, want_segmap=False) -> int:
+        gi, keep = _host_image(img, mask, saturation)
+        req = GpRequest(gi, int(capacity), 1 if want_segmap else 0)
+        t = C.c_uint64()
+        _check(load_library().gp_server_submit(self._h, C.byref(req), C.byref(t)))
+        self._keep[t.value] = keep
+        self._shape[t.value] = (gi.height, gi.width, int(capacity))
+        return t.value
+
+    def request_bytes(self, img, capacity, want_segmap=False):
+        """(device bytes, host bytes) the admission rule charges for this
+        request alone."""
+        gi, keep = _host_image(img)
+        req = GpRequest(gi, int(capacity), 1 if want_segmap else 0)
+        d, h = C.c_size_t(), C.c_size_t()
+        _check(load_library().gp_server_request_bytes(self._h, C.byref(req), C.byref(d), C.byref(h)))
+        return d.value, h.value
+
+    def wait(self, ticket, timeout_ms=-1) -> GpResult:
+        res = GpResult()
+        st = load_library().gp_server_wait(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(res))
+        if st == GP_ERR_TIMEOUT and res.batch == 0:
+            raise GpError(st, load_library().gp_last_error().decode(errors="replace"))
+        return res
+
+    def release(self, ticket):
+        _check(load_library().gp_server_release(self._h, C.c_uint64(ticket)))
+        self._keep.pop(ticket, None)
+        self._shape.pop(ticket, None)
+
+    def result(self, ticket, timeout_ms=-1):
+        """Wait, copy the result to numpy arrays, release.  Returns a dict:
+        status, n, catalog (columns of the rows filled, with flux, fluxerr,
+        apflags), bkg/rms meshes, segmap (if asked), batch, latency_ms,
+        queue_ms."""
+        res = self.wait(ticket, timeout_ms)
+        H, W, cap = self._shape[ticket]
+        m = min(max(res.n, 0), cap) if res.status in (GP_OK, GP_ERR_CAPACITY) else 0
+        out = {"status": res.status, "n": res.n, "batch": res.batch, "latency_ms": res.latency_ms,
+               "queue_ms": res.queue_ms}
+        if res.status in (GP_OK, GP_ERR_CAPACITY):
+            cat = {}
+            for name, dt in CATALOG_COLUMNS:
+                cat[name] = _np_view(getattr(res.cat, name), m, dt).copy()
+            nr = self.nr
+            cat["flux"] = _np_view(res.flux, m * nr, "float64").reshape(m, nr).copy()
+            cat["fluxerr"] = _np_view(res.fluxerr, m * nr, "float64").reshape(m, nr).copy()
+            cat["apflags"] = _np_view(res.apflags, m * nr, "uint32").reshape(m, nr).copy()
+            out["catalog"] = cat
+            out["bkg_mesh"] = _np_view(res.bkg_mesh, res.mx * res.my, "float32").reshape(res.my, res.mx).copy()
+            out["rms_mesh"] = _np_view(res.rms_mesh, res.mx * res.my, "float32").reshape(res.my, res.mx).copy()
+            if res.segmap:
+                out["segmap"] = _np_view(res.segmap, H * W, "uint32").reshape(H, W).copy()
+        else:
+            out["error"] = load_library().gp_last_error().decode(errors="replace")
+        self.release(ticket)
+        return out
+
+    def stats(self, reset=False):
+        r = GpServerReport()
+        _check(load_library().gp_server_stats(self._h, C.byref(r), 1 if reset else 0))
+        return {k: getattr(r, k) for k, _ in GpServerReport._fields_}

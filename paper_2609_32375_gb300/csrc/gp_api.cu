@@ -7,9 +7,11 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "gp_internal.cuh"
 #include "gp_launch.h"
+#include "gp_pipeline.h"
 
 using namespace gp;
 
@@ -29,6 +31,7 @@ struct gp_ctx {
     int nrec;              // calls recorded since the last gp_ctx_stats
     int slot;              // slot of the current call
     int launches;          // kernels launched by the current / last call
+    ArgStage stage;        // pinned staging of batched calls' argument records
 };
 
 namespace {
@@ -78,115 +81,7 @@ void mark_to(gp_ctx* ctx, int from, int to, cudaStream_t st)
     for (int k = from; k <= to; ++k) mark(ctx, k, st);
 }
 
-constexpr size_t ALIGN = 256;
 constexpr size_t STATUS_BYTES = 256;
-
-// bump allocator over the arena; sizes are accumulated even past the end so
-// that the total requirement can be reported
-struct Carver {
-    char* base;
-    size_t cap;
-    size_t off = 0;
-    template <class T>
-    T* take(size_t n)
-    {
-        off = (off + ALIGN - 1) & ~(ALIGN - 1);
-        T* p = reinterpret_cast<T*>(base + off);
-        off += n * sizeof(T);
-        return p;
-    }
-    bool ok() const { return off <= cap; }
-};
-
-struct BkgWork {
-    double *bkg_raw, *rms_raw, *tmp_b, *tmp_r;
-    int *valid, *tmp_v;
-};
-
-struct SplineWork {
-    double* scratch;
-    float4 *tab_b, *tab_r;
-};
-
-struct DetWork {
-    Tiles T;
-    Pieces P;
-    Comps C;
-    int* counters;   // [0] pieces, [1] comps
-};
-
-int piece_cap_for(int64_t npix) { return (int)std::max<int64_t>(65536, npix / 64); }
-int comp_cap_for(int64_t npix, int capacity)
-{
-    int64_t c = std::max<int64_t>(65536, npix / 32);
-    if (capacity > c) c = capacity;
-    return (int)std::min<int64_t>(c, 1ll << 30);
-}
-
-void bucket_geometry(int64_t npix, int* shift, int* nb)
-{
-    int s = 0;
-    while (((npix - 1) >> s) + 1 > 65536) ++s;
-    *shift = s;
-    *nb = (int)(((npix - 1) >> s) + 1);
-}
-
-void carve_bkg(Carver& cv, int nbox, BkgWork& w)
-{
-    w.bkg_raw = cv.take<double>(nbox);
-    w.rms_raw = cv.take<double>(nbox);
-    w.tmp_b = cv.take<double>(nbox);
-    w.tmp_r = cv.take<double>(nbox);
-    w.valid = cv.take<int>(nbox);
-    w.tmp_v = cv.take<int>(nbox);
-}
-
-void carve_spline(Carver& cv, int Mx, int My, SplineWork& w)
-{
-    w.scratch = cv.take<double>(spline_scratch_doubles(Mx, My));
-    w.tab_b = cv.take<float4>((size_t)Mx * My);
-    w.tab_r = cv.take<float4>((size_t)Mx * My);
-}
-
-void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w)
-{
-    const int64_t npix = (int64_t)W * H;
-    w.T.ntx = (W + TX - 1) / TX;
-    w.T.nty = (H + TY - 1) / TY;
-    const int64_t ntiles = (int64_t)w.T.ntx * w.T.nty;
-    w.T.edges = cv.take<int16_t>((size_t)ntiles * EDGE_PER_TILE);
-    w.T.piece_base = cv.take<int>(ntiles);
-    w.T.piece_cnt = cv.take<int>(ntiles);
-    w.counters = cv.take<int>(64);
-    w.P.count = w.counters + 0;
-    w.P.cap = piece_cap_for(npix);
-    w.P.root = cv.take<uint32_t>(w.P.cap);
-    w.P.npix = cv.take<int>(w.P.cap);
-    w.P.bbox = cv.take<int4>(w.P.cap);
-    w.P.parent = cv.take<int>(w.P.cap);
-    w.P.proot = cv.take<int>(w.P.cap);
-    w.P.mom = cv.take<Moments>(w.P.cap);
-    w.P.agg_min = cv.take<uint32_t>(w.P.cap);
-    w.P.agg_npix = cv.take<int>(w.P.cap);
-    w.P.agg_bbox = cv.take<int4>(w.P.cap);
-    w.C.count = w.counters + 32;
-    w.C.cap = comp_cap_for(npix, capacity);
-    w.C.label = cv.take<uint32_t>(w.C.cap);
-    w.C.npix = cv.take<int>(w.C.cap);
-    w.C.bbox = cv.take<int4>(w.C.cap);
-    w.C.flux = cv.take<double>(w.C.cap);
-    w.C.xy = cv.take<double2>(w.C.cap);
-    w.C.mom2 = cv.take<Mom2>(w.C.cap);
-    w.C.peak = cv.take<float>(w.C.cap);
-    w.C.peakL = cv.take<uint32_t>(w.C.cap);
-    w.C.flags = cv.take<uint32_t>(w.C.cap);
-    w.C.perm = cv.take<int>(w.C.cap);
-    w.C.slots = cv.take<int>(w.C.cap);
-    bucket_geometry(npix, &w.C.shift, &w.C.nb);
-    w.C.bcnt = cv.take<int>(w.C.nb);
-    w.C.boff = cv.take<int>(w.C.nb);
-    w.C.bcur = cv.take<int>(w.C.nb);
-}
 
 gp_status check_ctx(gp_ctx* ctx)
 {
@@ -283,15 +178,6 @@ gp_status check_cat(const gp_catalog* c)
     return GP_OK;
 }
 
-SplineTab make_tab(const float4* node, int W, int H, int mesh)
-{
-    SplineTab s;
-    s.node = node;
-    s.ax = make_axis(W, mesh);
-    s.ay = make_axis(H, mesh);
-    return s;
-}
-
 // spline tables of both maps from the (float) meshes in b; adds the number
 // of kernels launched to *nlaunch
 gp_status run_spline(Carver& cv, const gp_bkg* b, int W, int H, SplineTab* sb, SplineTab* sr, int* nlaunch,
@@ -327,47 +213,6 @@ gp_status oom(const Carver& cv)
                 cv.cap + STATUS_BYTES);
 }
 
-gp_status run_background(gp_ctx* ctx, Carver& cv, const gp_image* img, const gp_bkg_params* p, gp_bkg* bkg,
-                         cudaStream_t st, SplineTab* sb, SplineTab* sr)
-{
-    const int W = img->width, H = img->height, B = p->mesh;
-    const int Mx = (W + B - 1) / B, My = (H + B - 1) / B;
-    bkg->mesh = B; bkg->mx = Mx; bkg->my = My;
-    BkgWork w;
-    carve_bkg(cv, Mx * My, w);
-    if (!cv.ok()) return oom(cv);
-    Image im = to_image(img);
-    GP_CUDA(launch_boxstats(im, B, (double)p->clip_k, p->clip_maxiter, w.bkg_raw, w.rms_raw, w.valid, nullptr, st));
-    mark(ctx, 1, st);
-    ctx->launches += 1;
-    SplineTab tb, tr;
-    if (mesh_fits_smem(Mx, My)) {
-        // fill, median filter and both spline tables in one shared-memory CTA
-        float4* tab_b = cv.take<float4>((size_t)Mx * My);
-        float4* tab_r = cv.take<float4>((size_t)Mx * My);
-        if (!cv.ok()) return oom(cv);
-        GP_CUDA(launch_mesh_all(w.bkg_raw, w.rms_raw, w.valid, make_axis(W, B), make_axis(H, B), p->filter_size, 0,
-                                bkg->bkg_mesh, bkg->rms_mesh, tab_b, tab_r, st));
-        ctx->launches += 1;
-        tb = make_tab(tab_b, W, H, B);
-        tr = make_tab(tab_r, W, H, B);
-    } else {
-        GP_CUDA(launch_mesh_finalize(w.bkg_raw, w.rms_raw, w.valid, w.tmp_b, w.tmp_r, w.tmp_v, Mx, My, p->filter_size,
-                                     bkg->bkg_mesh, bkg->rms_mesh, st));
-        ctx->launches += 1;
-        gp_status s = run_spline(cv, bkg, W, H, &tb, &tr, &ctx->launches, st);
-        if (s == GP_ERR_OOM) return oom(cv);
-        if (s != GP_OK) return s;
-    }
-    if (bkg->bkg_map || bkg->rms_map) {
-        GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
-        ctx->launches += 1;
-    }
-    if (sb) { *sb = tb; *sr = tr; }
-    mark(ctx, 2, st);
-    return GP_OK;
-}
-
 gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineTab& sb, const SplineTab& sr,
                      const float* taps, const gp_det_params* p, uint32_t* segmap, gp_catalog* cat,
                      const float* radii, int nr, float gain, double* flux, double* fluxerr, uint32_t* apflags,
@@ -378,9 +223,7 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     carve_det(cv, W, H, cat->capacity, w);
     if (!cv.ok()) return oom(cv);
     Image im = to_image(img);
-    GP_CUDA(cudaMemsetAsync(w.counters, 0, 64 * sizeof(int), st));
-    GP_CUDA(cudaMemsetAsync(w.C.bcnt, 0, (size_t)w.C.nb * sizeof(int), st));
-    GP_CUDA(cudaMemsetAsync(w.C.bcur, 0, (size_t)w.C.nb * sizeof(int), st));
+    GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
     if (p->nnear) GP_CUDA(cudaMemsetAsync(p->nnear, 0, sizeof(int), st));
     GP_CUDA(launch_detect_tiles(im, sb, sr, taps, p->kw, p->kh, p->thresh, p->minarea, segmap, p->mask_out, p->nnear,
                                 nullptr, w.T, w.P, w.C, ctx->dstatus, st));
@@ -393,6 +236,109 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     mark(ctx, 6, st);
     ctx->launches += 1 + 3 + 4 + 1;
     return GP_OK;
+}
+
+void ctx_mark(void* ud, int k, cudaStream_t st) { mark(static_cast<gp_ctx*>(ud), k, st); }
+
+Exec ctx_exec(gp_ctx* ctx, cudaStream_t st)
+{
+    Exec ex;
+    ex.cv = Carver{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    ex.st = st;
+    ex.stage = &ctx->stage;
+    ex.mark = ctx_mark;
+    ex.mark_ud = ctx;
+    return ex;
+}
+
+// parameters shared by the frames of a call (dp, ap may be null for the
+// background alone; taps already normalised by check_det)
+Params make_params(const gp_bkg_params* bp, const float* taps, const gp_det_params* dp, const gp_ap_params* ap,
+                   const gp_cnn_weights* net)
+{
+    Params P;
+    memset(&P, 0, sizeof P);
+    P.bp = *bp;
+    if (dp) {
+        for (int i = 0; i < dp->kw * dp->kh; ++i) P.taps[i] = taps[i];
+        P.kw = dp->kw; P.kh = dp->kh;
+        P.thresh = dp->thresh;
+        P.minarea = dp->minarea;
+    }
+    if (ap) {
+        P.nr = ap->nr;
+        for (int k = 0; k < ap->nr; ++k) P.radii[k] = ap->radii[k];
+        P.gain = ap->gain;
+    }
+    P.net = net;
+    return P;
+}
+
+FrameIO frame_io(const gp_image* img, const gp_bkg* bkg, uint32_t* segmap, const gp_catalog* cat, double* flux,
+                 double* fluxerr, uint32_t* apflags, const gp_det_params* dp, int* status)
+{
+    FrameIO F;
+    memset(&F, 0, sizeof F);
+    F.img = *img;
+    F.bkg = *bkg;
+    F.segmap = segmap;
+    if (cat) F.cat = *cat;
+    F.apflux = flux; F.apferr = fluxerr; F.apflags = apflags;
+    if (dp) { F.mask_out = dp->mask_out; F.nnear = dp->nnear; }
+    F.status = status;
+    return F;
+}
+
+gp_status pipeline_result(gp_status s, const Exec& ex, gp_ctx* ctx)
+{
+    ctx->launches += ex.launches;
+    if (s == GP_ERR_OOM)
+        return fail(GP_ERR_OOM, "workspace needs %zu bytes, the context arena has %zu", ex.cv.off + STATUS_BYTES,
+                    ex.cv.cap + STATUS_BYTES);
+    return s;
+}
+
+gp_status check_net(const gp_cnn_weights* net);
+
+// the background stage of one frame into bkg (clipped or learned)
+gp_status background_call(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p, const gp_cnn_weights* net,
+                          gp_bkg* bkg, gp_stream stream)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    begin_call(ctx, st);
+    Exec ex = ctx_exec(ctx, st);
+    const Params P = make_params(p, nullptr, nullptr, nullptr, net);
+    FrameIO F = frame_io(img, bkg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, ctx->dstatus);
+    gp_status s = pipeline_result(run_background_only(ex, 1, &F, P), ex, ctx);
+    bkg->mesh = F.bkg.mesh; bkg->mx = F.bkg.mx; bkg->my = F.bkg.my;
+    return s;
+}
+
+gp_status extract_call(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp, const gp_det_params* dp,
+                       const gp_ap_params* ap, const gp_cnn_weights* net, gp_bkg* bkg, uint32_t* segmap,
+                       gp_catalog* cat, double* flux, double* fluxerr, uint32_t* apflags, gp_stream stream)
+{
+    gp_status s;
+    float taps[KMAX];
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg_params(img, bp)) != GP_OK) return s;
+    if (net && (s = check_net(net)) != GP_OK) return s;
+    if ((s = check_det(dp, taps)) != GP_OK) return s;
+    if ((s = check_ap(ap, true)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
+    if (!segmap) return fail(GP_ERR_INVALID_ARG, "null segmap");
+    if (ap->nr > 0 && cat->capacity > 0 && (!flux || !fluxerr || !apflags))
+        return fail(GP_ERR_INVALID_ARG, "null aperture output array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    begin_call(ctx, st);
+    Exec ex = ctx_exec(ctx, st);
+    const Params P = make_params(bp, taps, dp, ap, net);
+    FrameIO F = frame_io(img, bkg, segmap, cat, flux, fluxerr, apflags, dp, ctx->dstatus);
+    s = pipeline_result(run_extract(ex, 1, &F, P), ex, ctx);
+    bkg->mesh = F.bkg.mesh; bkg->mx = F.bkg.mx; bkg->my = F.bkg.my;
+    return s;
 }
 
 }  // namespace
@@ -447,6 +393,7 @@ void gp_ctx_destroy(gp_ctx* ctx)
     if (ctx->ev_made)
         for (int i = 0; i < RING; ++i)
             for (int k = 0; k < NMARK; ++k) cudaEventDestroy(ctx->ev[i][k]);
+    ctx->stage.release();
     cudaFree(ctx->arena);
     delete ctx;
 }
@@ -524,12 +471,7 @@ gp_status gp_background(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* p
     if ((s = check_image(img)) != GP_OK) return s;
     if ((s = check_bkg_params(img, p)) != GP_OK) return s;
     if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
-    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    begin_call(ctx, st);
-    s = run_background(ctx, cv, img, p, bkg, st, nullptr, nullptr);
-    mark_to(ctx, 3, 6, st);
-    return s;
+    return background_call(ctx, img, p, nullptr, bkg, stream);
 }
 
 gp_status gp_detect(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* p, uint32_t* segmap,
@@ -586,26 +528,7 @@ gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp, 
                      const gp_ap_params* ap, gp_bkg* bkg, uint32_t* segmap, gp_catalog* cat, double* flux,
                      double* fluxerr, uint32_t* apflags, gp_stream stream)
 {
-    gp_status s;
-    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
-    if ((s = check_ctx(ctx)) != GP_OK) return s;
-    if ((s = check_image(img)) != GP_OK) return s;
-    if ((s = check_bkg_params(img, bp)) != GP_OK) return s;
-    if ((s = check_det(dp, taps)) != GP_OK) return s;
-    if ((s = check_ap(ap, true)) != GP_OK) return s;
-    if ((s = check_cat(cat)) != GP_OK) return s;
-    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
-    if (!segmap) return fail(GP_ERR_INVALID_ARG, "null segmap");
-    if (ap->nr > 0 && cat->capacity > 0 && (!flux || !fluxerr || !apflags))
-        return fail(GP_ERR_INVALID_ARG, "null aperture output array");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
-    SplineTab sb, sr;
-    begin_call(ctx, st);
-    s = run_background(ctx, cv, img, bp, bkg, st, &sb, &sr);
-    if (s != GP_OK) return s;
-    return run_detect(ctx, cv, img, sb, sr, taps, dp, segmap, cat, ap->radii, ap->nr, ap->gain, flux, fluxerr, apflags,
-                      st);
+    return extract_call(ctx, img, bp, dp, ap, nullptr, bkg, segmap, cat, flux, fluxerr, apflags, stream);
 }
 
 gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t height, int32_t minarea,
@@ -628,8 +551,7 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
     SplineTab none{};
     begin_call(ctx, st);
     mark_to(ctx, 1, 2, st);
-    GP_CUDA(cudaMemsetAsync(w.counters, 0, 64 * sizeof(int), st));
-    GP_CUDA(cudaMemsetAsync(w.C.bcnt, 0, (size_t)w.C.nb * sizeof(int), st));
+    GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
     GP_CUDA(launch_detect_tiles(im, none, none, nullptr, 1, 1, 1.f, minarea, segmap, nullptr, nullptr, mask, w.T, w.P,
                                 w.C, ctx->dstatus, st));
     mark(ctx, 3, st);
@@ -671,52 +593,6 @@ gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float
 
 namespace {
 
-// the background stage with the network; fills bkg's meshes (and maps) and
-// returns the spline tables for the stages that follow
-gp_status run_background_learned(gp_ctx* ctx, Carver& cv, const gp_image* img, const gp_bkg_params* p,
-                                 const gp_cnn_weights* net, gp_bkg* bkg, cudaStream_t st, SplineTab* sb,
-                                 SplineTab* sr)
-{
-    const int W = img->width, H = img->height, B = p->mesh;
-    const int Mx = (W + B - 1) / B, My = (H + B - 1) / B, nbox = Mx * My;
-    bkg->mesh = B; bkg->mx = Mx; bkg->my = My;
-    BkgWork w;
-    carve_bkg(cv, nbox, w);
-    float* quant = cv.take<float>((size_t)5 * nbox);
-    float* norm = cv.take<float>(2);
-    uint16_t* feat = cv.take<uint16_t>((size_t)16 * nbox);
-    uint16_t* a0 = cv.take<uint16_t>((size_t)48 * nbox);
-    uint16_t* a1 = cv.take<uint16_t>((size_t)48 * nbox);
-    float* out = cv.take<float>((size_t)2 * nbox);
-    if (!cv.ok()) return oom(cv);
-    GP_CUDA(launch_boxstats(to_image(img), B, 3.0, 0, w.bkg_raw, w.rms_raw, w.valid, quant, st));
-    mark(ctx, 1, st);
-    GP_CUDA(launch_cnn_features(quant, 1, nbox, feat, norm, st));
-    static const int cin_p[GP_CNN_LAYERS] = {16, 32, 48, 48, 32, 32};
-    static const int cout_p[GP_CNN_LAYERS] = {32, 48, 48, 32, 32, 16};
-    const void* in = feat;
-    for (int l = 0; l < GP_CNN_LAYERS; ++l) {
-        const bool last = l == GP_CNN_LAYERS - 1;
-        void* o = last ? (void*)out : (void*)((l & 1) ? a1 : a0);
-        GP_CUDA(launch_cnn_conv(in, 1, My, Mx, cin_p[l], net->wt[l], net->bias[l], cout_p[l], last ? 0 : 1, o,
-                                last ? 1 : 0, 2, st));
-        in = o;
-    }
-    GP_CUDA(launch_cnn_denorm(out, norm, nbox, 1, bkg->bkg_mesh, bkg->rms_mesh, st));
-    ctx->launches += 3 + GP_CNN_LAYERS;
-    SplineTab tb, tr;
-    gp_status s = run_spline(cv, bkg, W, H, &tb, &tr, &ctx->launches, st);
-    if (s == GP_ERR_OOM) return oom(cv);
-    if (s != GP_OK) return s;
-    if (bkg->bkg_map || bkg->rms_map) {
-        GP_CUDA(launch_bkg_maps(tb, tr, W, H, bkg->bkg_map, bkg->rms_map, st));
-        ctx->launches += 1;
-    }
-    mark(ctx, 2, st);
-    if (sb) { *sb = tb; *sr = tr; }
-    return GP_OK;
-}
-
 gp_status check_net(const gp_cnn_weights* net)
 {
     if (!net) return fail(GP_ERR_INVALID_ARG, "null network weights");
@@ -738,44 +614,69 @@ gp_status gp_background_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_p
     if ((s = check_bkg_params(img, p)) != GP_OK) return s;
     if ((s = check_net(net)) != GP_OK) return s;
     if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
-    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    begin_call(ctx, st);
-    s = run_background_learned(ctx, cv, img, p, net, bkg, st, nullptr, nullptr);
-    mark_to(ctx, 3, 6, st);
-    return s;
+    return background_call(ctx, img, p, net, bkg, stream);
 }
 
 gp_status gp_extract_learned(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp, const gp_det_params* dp,
                              const gp_ap_params* ap, const gp_cnn_weights* net, gp_bkg* bkg, uint32_t* segmap,
                              gp_catalog* cat, double* flux, double* fluxerr, uint32_t* apflags, gp_stream stream)
 {
+    if (!net) return fail(GP_ERR_INVALID_ARG, "null network weights");
+    return extract_call(ctx, img, bp, dp, ap, net, bkg, segmap, cat, flux, fluxerr, apflags, stream);
+}
+
+gp_status gp_extract_batch(gp_ctx* ctx, gp_frame* frames, int32_t n, const gp_bkg_params* bp,
+                           const gp_det_params* dp, const gp_ap_params* ap, const gp_cnn_weights* net,
+                           gp_stream stream)
+{
     gp_status s;
-    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
+    float taps[KMAX];
     if ((s = check_ctx(ctx)) != GP_OK) return s;
-    if ((s = check_image(img)) != GP_OK) return s;
-    if ((s = check_bkg_params(img, bp)) != GP_OK) return s;
-    if ((s = check_net(net)) != GP_OK) return s;
+    if (!frames) return fail(GP_ERR_INVALID_ARG, "null frame array");
+    if (n < 1 || n > GP_MAX_BATCH) return fail(GP_ERR_INVALID_ARG, "n = %d outside [1, %d]", n, GP_MAX_BATCH);
+    if (net && (s = check_net(net)) != GP_OK) return s;
     if ((s = check_det(dp, taps)) != GP_OK) return s;
     if ((s = check_ap(ap, true)) != GP_OK) return s;
-    if ((s = check_cat(cat)) != GP_OK) return s;
-    if (!bkg || !bkg->bkg_mesh || !bkg->rms_mesh) return fail(GP_ERR_INVALID_ARG, "null background output meshes");
-    if (!segmap) return fail(GP_ERR_INVALID_ARG, "null segmap");
-    if (ap->nr > 0 && cat->capacity > 0 && (!flux || !fluxerr || !apflags))
-        return fail(GP_ERR_INVALID_ARG, "null aperture output array");
+    for (int f = 0; f < n; ++f) {
+        const gp_frame& x = frames[f];
+        if ((s = check_image(&x.image)) != GP_OK) return fail(s, "frame %d: %s", f, gp_last_error());
+        if (x.image.dtype != frames[0].image.dtype) return fail(GP_ERR_INVALID_ARG, "frame %d: dtype differs", f);
+        if ((s = check_bkg_params(&x.image, bp)) != GP_OK) return s;
+        if ((s = check_cat(&x.cat)) != GP_OK) return fail(s, "frame %d: %s", f, gp_last_error());
+        if (!x.bkg.bkg_mesh || !x.bkg.rms_mesh) return fail(GP_ERR_INVALID_ARG, "frame %d: null meshes", f);
+        if (!x.segmap || !x.status) return fail(GP_ERR_INVALID_ARG, "frame %d: null segmap or status", f);
+        if (ap->nr > 0 && x.cat.capacity > 0 && (!x.flux || !x.fluxerr || !x.apflags))
+            return fail(GP_ERR_INVALID_ARG, "frame %d: null aperture output array", f);
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
-    SplineTab sb, sr;
+    if (n > 1) {
+        cudaError_t e = ctx->stage.init((size_t)512 << 10);
+        if (e != cudaSuccess) return cuda_fail(e, "pinned argument staging");
+    }
     begin_call(ctx, st);
-    s = run_background_learned(ctx, cv, img, bp, net, bkg, st, &sb, &sr);
-    if (s != GP_OK) return s;
-    return run_detect(ctx, cv, img, sb, sr, taps, dp, segmap, cat, ap->radii, ap->nr, ap->gain, flux, fluxerr, apflags,
-                      st);
+    Exec ex = ctx_exec(ctx, st);
+    const Params P = make_params(bp, taps, dp, ap, net);
+    std::vector<FrameIO> F(n);
+    for (int f = 0; f < n; ++f) {
+        const gp_frame& x = frames[f];
+        F[f] = frame_io(&x.image, &x.bkg, x.segmap, &x.cat, x.flux, x.fluxerr, x.apflags, nullptr, x.status);
+    }
+    s = pipeline_result(run_extract(ex, n, F.data(), P), ex, ctx);
+    for (int f = 0; f < n; ++f) {
+        frames[f].bkg.mesh = F[f].bkg.mesh; frames[f].bkg.mx = F[f].bkg.mx; frames[f].bkg.my = F[f].bkg.my;
+    }
+    return s;
 }
 
 }  // extern "C"
 
-// message for gp_last_error() from entry points defined in other files
+// argument checks and gp_last_error() messages for entry points defined in
+// other files
 namespace gp {
 void record_error(const char* msg) { g_err = msg; }
+gp_status validate_image(const gp_image* img) { return check_image(img); }
+gp_status validate_bkg_params(const gp_image* img, const gp_bkg_params* p) { return check_bkg_params(img, p); }
+gp_status validate_det_params(const gp_det_params* p, float* taps) { return check_det(p, taps); }
+gp_status validate_ap_params(const gp_ap_params* p) { return check_ap(p, true); }
+gp_status validate_net(const gp_cnn_weights* net) { return check_net(net); }
 }  // namespace gp

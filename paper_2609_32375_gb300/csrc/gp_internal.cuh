@@ -287,4 +287,114 @@ struct Image {
     int is_f32;
 };
 
+// ------------------------------------------------ per-frame arguments ---
+// Every kernel of the pipeline runs either one frame, its arguments passed
+// by value (`one`, a __grid_constant__ parameter, so taking its address
+// makes no copy), or a batch of frames whose argument records sit in a
+// device array (`batch`), one per frame: the grid's y index is the frame,
+// and blocks beyond a smaller frame's extent return at once.  A batch of
+// small frames thus runs each stage as a single launch.
+template <class T>
+__device__ __forceinline__ const T& frame_args(const T* __restrict__ batch, const T& one)
+{
+    return batch ? batch[blockIdx.y] : one;
+}
+
+// most frames in one batched launch
+constexpr int MAX_BATCH = 64;
+
+// per-box statistics (k_boxstats_*)
+struct BoxArgs {
+    const void* img;
+    int64_t pitch;
+    const uint8_t* mask;
+    int W, H, B, Mx, nbox, npad;
+    double k;
+    int maxiter;
+    double* bkg;
+    double* rms;
+    int* valid;
+    float* quant;
+};
+
+// mesh fill, median filter and spline tables in shared memory (k_mesh_all)
+struct MeshArgs {
+    const double* bkg_raw;
+    const double* rms_raw;
+    const int* valid;
+    Axis ax, ay;
+    int fsize, mode;
+    float* bkg_mesh;
+    float* rms_mesh;
+    float4* tab_b;
+    float4* tab_r;
+};
+
+constexpr int KMAX = (2 * HMAX + 1) * (2 * HMAX + 1);
+
+// tile detection (k_detect_tile)
+struct DetectArgs {
+    float K[KMAX];            // normalised taps, kh rows of kw
+    Image im;
+    SplineTab sb, sr;
+    int kw, kh, hx, hy, hh;   // taps, half sizes, staged halo
+    float thresh;
+    int minarea;
+    uint32_t* seg;
+    uint8_t* mask_out;
+    int* nnear;
+    const uint8_t* in_mask;   // labelling of a given mask
+    Tiles T;
+    Pieces P;
+    Comps C;
+    int* status;
+};
+
+// tile merge, piece aggregation and finalisation (k_merge, k_aggregate,
+// k_finalize)
+struct ResolveArgs {
+    Tiles T;
+    Pieces P;
+    Comps C;
+    uint32_t* seg;
+    int W, H, minarea;
+    int* status;
+};
+
+// label ranking (k_rank_*)
+struct RankArgs {
+    Comps C;
+    int* n_out;
+    int capacity;
+    int place;
+    int* status;
+};
+
+struct ApSpec {
+    int nr;
+    float r[MAX_NR];
+    float rmax;
+    float gain;
+};
+
+// catalog rows and apertures (k_measure)
+struct MeasureArgs {
+    Image im;
+    SplineTab sb, sr;
+    Comps C;
+    int capacity;
+    // catalog columns
+    uint32_t* label;
+    int32_t* npix;
+    double *flux_iso, *x, *y, *x2, *y2, *xy;
+    int32_t *xmin, *xmax, *ymin, *ymax;
+    float* peak;
+    int32_t *xpeak, *ypeak;
+    uint32_t* flags;
+    ApSpec ap;
+    double* apflux;
+    double* apferr;
+    uint32_t* apflags;
+};
+
 }  // namespace gp

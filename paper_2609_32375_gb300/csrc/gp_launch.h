@@ -41,6 +41,34 @@ cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTa
                             const double* ys, int n, const float* radii, int nr, float gain, double* flux,
                             double* ferr, uint32_t* fl, cudaStream_t st);
 
+// Batch-capable forms.  Each takes one frame's argument record (`one`, used
+// alone when batch == nullptr) or a device array of nframes records, one per
+// frame (the grid's y index); frames of one batch share what the launch
+// dispatches on (dtype, filter size, number of radii, mode), taken from `one`.
+BoxArgs box_args(const Image& im, int B, double k, int maxiter, double* bkg, double* rms, int* valid, float* quant);
+cudaError_t launch_boxstats_any(const BoxArgs& one, const BoxArgs* batch, int nframes, int maxbox, int is_f32,
+                                cudaStream_t st);
+MeshArgs mesh_args(const double* bkg_raw, const double* rms_raw, const int* valid, Axis ax, Axis ay, int fsize,
+                   int mode, float* bkg_mesh, float* rms_mesh, float4* tab_b, float4* tab_r);
+size_t mesh_all_smem(int Mx, int My);
+cudaError_t launch_mesh_all_any(const MeshArgs& one, const MeshArgs* batch, int nframes, size_t smem,
+                                cudaStream_t st);
+DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw, int kh,
+                       float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
+                       const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C, int* status);
+cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
+                              cudaStream_t st);
+ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H, int minarea,
+                         int* status);
+cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch, int nframes, int maxtiles,
+                               cudaStream_t st);
+RankArgs rank_args(const Comps& C, int* n_out, int capacity, bool place, int* status);
+cudaError_t launch_rank_any(const RankArgs& one, const RankArgs* batch, int nframes, cudaStream_t st);
+MeasureArgs measure_args(const Image& im, const SplineTab& sb, const SplineTab& sr, const Comps& C,
+                         const gp_catalog& cat, const float* radii, int nr, float gain, double* apflux,
+                         double* apferr, uint32_t* apflags);
+cudaError_t launch_measure_any(const MeasureArgs& one, const MeasureArgs* batch, int nframes, cudaStream_t st);
+
 }  // namespace gp
 
 namespace gp {

@@ -125,12 +125,20 @@ __device__ uint32_t hist_select(const uint32_t* hist, const unsigned long long* 
     return __shfl_sync(0xffffffffu, ans, src);
 }
 
-__global__ void __launch_bounds__(U16_NT, 1)
-k_boxstats_u16(const uint16_t* __restrict__ img, int64_t pitch, const uint8_t* __restrict__ mask,
-               int W, int H, int B, int Mx, double k, int maxiter,
-               double* __restrict__ bkg_out, double* __restrict__ rms_out, int* __restrict__ valid_out,
-               float* __restrict__ quant_out)
+__global__ void __launch_bounds__(U16_NT, 1) k_boxstats_u16(const BoxArgs* __restrict__ batch, const __grid_constant__ BoxArgs one)
 {
+    const BoxArgs& A = frame_args(batch, one);
+    if ((int)blockIdx.x >= A.nbox) return;
+    const uint16_t* __restrict__ img = static_cast<const uint16_t*>(A.img);
+    const int64_t pitch = A.pitch;
+    const uint8_t* __restrict__ mask = A.mask;
+    const int W = A.W, H = A.H, B = A.B, Mx = A.Mx, nbox = A.nbox;
+    const double k = A.k;
+    const int maxiter = A.maxiter;
+    double* __restrict__ bkg_out = A.bkg;
+    double* __restrict__ rms_out = A.rms;
+    int* __restrict__ valid_out = A.valid;
+    float* __restrict__ quant_out = A.quant;
     extern __shared__ uint32_t hist[];                    // U16_WORDS
     __shared__ unsigned long long pc[257], ps1[257], ps2[257];
     __shared__ unsigned long long cc_s[256], cs1_s[256], cs2_s[256];
@@ -227,7 +235,7 @@ k_boxstats_u16(const uint16_t* __restrict__ img, int64_t pitch, const uint8_t* _
             rms_out[box] = valid ? r : 0.0;
             valid_out[box] = valid;
             if (quant_out)
-                for (int q = 0; q < 5; ++q) quant_out[(int64_t)q * gridDim.x + box] = (float)med;
+                for (int q = 0; q < 5; ++q) quant_out[(int64_t)q * nbox + box] = (float)med;
         }
         return;
     }
@@ -317,7 +325,7 @@ k_boxstats_u16(const uint16_t* __restrict__ img, int64_t pitch, const uint8_t* _
         for (int q = 0; q < 5; ++q) {
             unsigned long long r = (unsigned long long)floor((double)qs[q] * (double)(ngood - 1) + 0.5);
             uint32_t v = hist_select(hist, pc, r);
-            if (lane == 0) quant_out[(int64_t)q * gridDim.x + box] = (float)v;
+            if (lane == 0) quant_out[(int64_t)q * nbox + box] = (float)v;
         }
     }
     if (lane == 0) {
@@ -364,12 +372,20 @@ __device__ __forceinline__ int upper_bound_d(const float* v, int lo, int hi, dou
     return lo;
 }
 
-__global__ void __launch_bounds__(F32_NT)
-k_boxstats_f32(const float* __restrict__ img, int64_t pitch, const uint8_t* __restrict__ mask,
-               int W, int H, int B, int Mx, int npad, double k, int maxiter,
-               double* __restrict__ bkg_out, double* __restrict__ rms_out, int* __restrict__ valid_out,
-               float* __restrict__ quant_out)
+__global__ void __launch_bounds__(F32_NT) k_boxstats_f32(const BoxArgs* __restrict__ batch, const __grid_constant__ BoxArgs one)
 {
+    const BoxArgs& A = frame_args(batch, one);
+    if ((int)blockIdx.x >= A.nbox) return;
+    const float* __restrict__ img = static_cast<const float*>(A.img);
+    const int64_t pitch = A.pitch;
+    const uint8_t* __restrict__ mask = A.mask;
+    const int W = A.W, H = A.H, B = A.B, Mx = A.Mx, nbox = A.nbox, npad = A.npad;
+    const double k = A.k;
+    const int maxiter = A.maxiter;
+    double* __restrict__ bkg_out = A.bkg;
+    double* __restrict__ rms_out = A.rms;
+    int* __restrict__ valid_out = A.valid;
+    float* __restrict__ quant_out = A.quant;
     extern __shared__ float vals[];                 // npad
     __shared__ int ngood_s;
     __shared__ DF red[32];
@@ -406,7 +422,7 @@ k_boxstats_f32(const float* __restrict__ img, int64_t pitch, const uint8_t* __re
     const bool valid = ng > 0 && 2 * ng >= bw * bh;
     if (ng == 0) {
         if (tid == 0) { bkg_out[box] = 0; rms_out[box] = 0; valid_out[box] = 0; }
-        if (quant_out && tid < 5) quant_out[(int64_t)tid * gridDim.x + box] = 0.f;
+        if (quant_out && tid < 5) quant_out[(int64_t)tid * nbox + box] = 0.f;
         return;
     }
     int lo = 0, hi = ng;
@@ -445,7 +461,7 @@ k_boxstats_f32(const float* __restrict__ img, int64_t pitch, const uint8_t* __re
     if (quant_out && tid < 5) {
         const float qs[5] = {0.10f, 0.25f, 0.50f, 0.75f, 0.90f};
         int r = (int)floor((double)qs[tid] * (double)(ng - 1) + 0.5);
-        quant_out[(int64_t)tid * gridDim.x + box] = vals[r];
+        quant_out[(int64_t)tid * nbox + box] = vals[r];
     }
 }
 
@@ -674,12 +690,19 @@ __device__ void solve_line(const AxisLU& L, int n, const float* v, int vs, float
 
 // mode 0: raw box statistics -> fill, filter, write meshes, tables
 // mode 1: tables only, from the float meshes given in bkg_out / rms_out
-__global__ void __launch_bounds__(MA_NT) k_mesh_all(const double* __restrict__ bkg_raw,
-                                                    const double* __restrict__ rms_raw,
-                                                    const int* __restrict__ valid_raw, Axis ax, Axis ay, int fsize,
-                                                    int mode, float* bkg_out, float* rms_out, float4* tab_b,
-                                                    float4* tab_r)
+__global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__ batch,
+                                                    const __grid_constant__ MeshArgs one)
 {
+    const MeshArgs& MA = frame_args(batch, one);
+    const double* __restrict__ bkg_raw = MA.bkg_raw;
+    const double* __restrict__ rms_raw = MA.rms_raw;
+    const int* __restrict__ valid_raw = MA.valid;
+    const Axis ax = MA.ax, ay = MA.ay;
+    const int fsize = MA.fsize, mode = MA.mode;
+    float* bkg_out = MA.bkg_mesh;
+    float* rms_out = MA.rms_mesh;
+    float4* tab_b = MA.tab_b;
+    float4* tab_r = MA.tab_r;
     extern __shared__ __align__(16) float sh[];
     unsigned char* sh_bytes = reinterpret_cast<unsigned char*>(sh);
     const int Mx = ax.n, My = ay.n, n = Mx * My, tid = threadIdx.x;
@@ -803,36 +826,71 @@ bool mesh_fits_smem(int Mx, int My)
     return (size_t)Mx * My <= (size_t)MESH_SMEM_NODES && mesh_all_smem(Mx, My) <= 220 * 1024;
 }
 
+MeshArgs mesh_args(const double* bkg_raw, const double* rms_raw, const int* valid, Axis ax, Axis ay, int fsize,
+                   int mode, float* bkg_mesh, float* rms_mesh, float4* tab_b, float4* tab_r)
+{
+    MeshArgs a;
+    a.bkg_raw = bkg_raw; a.rms_raw = rms_raw; a.valid = valid;
+    a.ax = ax; a.ay = ay; a.fsize = fsize; a.mode = mode;
+    a.bkg_mesh = bkg_mesh; a.rms_mesh = rms_mesh; a.tab_b = tab_b; a.tab_r = tab_r;
+    return a;
+}
+
+// smem = the largest frame's mesh_all_smem
+cudaError_t launch_mesh_all_any(const MeshArgs& one, const MeshArgs* batch, int nframes, size_t smem, cudaStream_t st)
+{
+    cudaFuncSetAttribute(k_mesh_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mesh_all<<<dim3(1, nframes), MA_NT, smem, st>>>(batch, one);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mesh_all(const double* bkg_raw, const double* rms_raw, const int* valid, Axis ax, Axis ay,
                             int fsize, int mode, float* bkg_mesh, float* rms_mesh, float4* tab_b, float4* tab_r,
                             cudaStream_t st)
 {
-    const size_t smem = mesh_all_smem(ax.n, ay.n);
-    cudaFuncSetAttribute(k_mesh_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mesh_all<<<1, MA_NT, smem, st>>>(bkg_raw, rms_raw, valid, ax, ay, fsize, mode, bkg_mesh, rms_mesh, tab_b,
-                                       tab_r);
-    return cudaGetLastError();
+    const MeshArgs a = mesh_args(bkg_raw, rms_raw, valid, ax, ay, fsize, mode, bkg_mesh, rms_mesh, tab_b, tab_r);
+    return launch_mesh_all_any(a, nullptr, 1, mesh_all_smem(ax.n, ay.n), st);
 }
 
 // --------------------------------------------------------------- launchers ---
+BoxArgs box_args(const Image& im, int B, double k, int maxiter, double* bkg, double* rms, int* valid, float* quant)
+{
+    BoxArgs a;
+    a.img = im.data; a.pitch = im.pitch; a.mask = im.mask;
+    a.W = im.W; a.H = im.H; a.B = B;
+    a.Mx = (im.W + B - 1) / B;
+    a.nbox = a.Mx * ((im.H + B - 1) / B);
+    int npad = 1;
+    while (npad < B * B) npad <<= 1;
+    a.npad = npad;
+    a.k = k; a.maxiter = maxiter;
+    a.bkg = bkg; a.rms = rms; a.valid = valid; a.quant = quant;
+    return a;
+}
+
+// one frame (batch == nullptr) or nframes frames whose arguments are in the
+// device array batch; maxbox = the largest frame's box count
+cudaError_t launch_boxstats_any(const BoxArgs& one, const BoxArgs* batch, int nframes, int maxbox, int is_f32,
+                                cudaStream_t st)
+{
+    dim3 grid(maxbox, nframes);
+    if (!is_f32) {
+        const size_t smem = U16_WORDS * sizeof(uint32_t);
+        cudaFuncSetAttribute(k_boxstats_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_boxstats_u16<<<grid, U16_NT, smem, st>>>(batch, one);
+    } else {
+        const size_t smem = (size_t)(batch ? 16384 : one.npad) * sizeof(float);
+        cudaFuncSetAttribute(k_boxstats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_boxstats_f32<<<grid, F32_NT, smem, st>>>(batch, one);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_boxstats(const Image& im, int B, double k, int maxiter, double* bkg, double* rms, int* valid,
                             float* quant, cudaStream_t st)
 {
-    const int Mx = (im.W + B - 1) / B, My = (im.H + B - 1) / B;
-    if (!im.is_f32) {
-        const size_t smem = U16_WORDS * sizeof(uint32_t);
-        cudaFuncSetAttribute(k_boxstats_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_boxstats_u16<<<Mx * My, U16_NT, smem, st>>>((const uint16_t*)im.data, im.pitch, im.mask, im.W, im.H, B,
-                                                     Mx, k, maxiter, bkg, rms, valid, quant);
-    } else {
-        int npad = 1;
-        while (npad < B * B) npad <<= 1;
-        const size_t smem = (size_t)npad * sizeof(float);
-        cudaFuncSetAttribute(k_boxstats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_boxstats_f32<<<Mx * My, F32_NT, smem, st>>>((const float*)im.data, im.pitch, im.mask, im.W, im.H, B, Mx,
-                                                     npad, k, maxiter, bkg, rms, valid, quant);
-    }
-    return cudaGetLastError();
+    const BoxArgs a = box_args(im, B, k, maxiter, bkg, rms, valid, quant);
+    return launch_boxstats_any(a, nullptr, 1, a.nbox, im.is_f32, st);
 }
 
 cudaError_t launch_mesh_finalize(double* bkg, double* rms, int* valid, double* tmp_b, double* tmp_r, int* tmp_v,

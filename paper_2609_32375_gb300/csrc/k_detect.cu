@@ -34,25 +34,7 @@
 namespace gp {
 
 constexpr int DT_NT = 256;
-constexpr int KMAX = (2 * HMAX + 1) * (2 * HMAX + 1);
 constexpr int ROWS_PER_THREAD = TNPIX / DT_NT;     // 8: each thread filters 8 rows of one column
-
-struct DetectArgs {
-    float K[KMAX];            // normalised taps, kh rows of kw (kernel parameter space)
-    Image im;
-    SplineTab sb, sr;
-    int kw, kh, hx, hy, hh;   // taps, half sizes, staged halo
-    float thresh;
-    int minarea;
-    uint32_t* seg;
-    uint8_t* mask_out;
-    int* nnear;
-    const uint8_t* in_mask;   // labelling of a given mask
-    Tiles T;
-    Pieces P;
-    Comps C;
-    int* status;
-};
 
 // mirror without edge repeat, cheap for offsets within one reflection
 __device__ __forceinline__ int mirror_fast(int i, int N)
@@ -299,16 +281,29 @@ __device__ __forceinline__ void filter_column(const TileSmem& S, const DetectArg
     }
 }
 
-template <bool F32, bool LABEL_ONLY, int KS>
-__global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
+// the frame's arguments: the kernel parameter itself for a single frame (a
+// compile-time choice, so the taps stay in the constant bank), else the
+// batch record of frame blockIdx.y
+template <bool BATCH>
+__device__ __forceinline__ const DetectArgs& detect_args(const DetectArgs* __restrict__ batch, const DetectArgs& one)
+{
+    if constexpr (BATCH) return batch[blockIdx.y];
+    else return one;
+}
+
+template <bool F32, bool LABEL_ONLY, int KS, bool BATCH>
+__global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restrict__ batch,
+                                                       const __grid_constant__ DetectArgs one)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
+    const DetectArgs& A = detect_args<BATCH>(batch, one);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = A.im.W, H = A.im.H;
     const int tile = blockIdx.x;
     const int ntx = A.T.ntx;
+    if (BATCH && tile >= ntx * A.T.nty) return;
     const int tx = tile % ntx, ty = tile / ntx;
     const int x0 = tx * TX, y0 = ty * TY;
     const int tw = min(TX, W - x0), th = min(TY, H - y0);
@@ -661,10 +656,16 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(DetectArgs A)
 }
 
 // ------------------------------------------------------------ tile merge ---
-__global__ void k_merge(Tiles T, Pieces P, int W, int H, int* status)
+__global__ void k_merge(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    const ResolveArgs& R = frame_args(batch, one);
+    const Tiles& T = R.T;
+    const Pieces& P = R.P;
+    const int W = R.W, H = R.H;
+    int* status = R.status;
     const int tile = blockIdx.x;
     const int ntx = T.ntx, nty = T.nty;
+    if (tile >= ntx * nty) return;
     const int tx = tile % ntx, ty = tile / ntx;
     const int tw = min(TX, W - tx * TX), th = min(TY, H - ty * TY);
     if (threadIdx.x == 0 && tx + 1 < ntx && ty + 1 < nty) {
@@ -719,8 +720,11 @@ __global__ void k_merge(Tiles T, Pieces P, int W, int H, int* status)
 }
 
 // --------------------------------------------------------- piece resolve ---
-__global__ void k_aggregate(Pieces P, int* status)
+__global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    const ResolveArgs& R = frame_args(batch, one);
+    const Pieces& P = R.P;
+    int* status = R.status;
     const int n = min(*P.count, P.cap);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const int r = gfind(P.parent, p);
@@ -754,8 +758,15 @@ __device__ __forceinline__ void df_add_pair(DF& s, float2 v)
 // bounding box in raster order (a fixed order, so the sums are
 // reproducible) and emit the segment.  Every piece whose final label differs
 // from its provisional one rewrites its pixels in the map.
-__global__ void k_finalize(Tiles T, Pieces P, Comps C, uint32_t* seg, int W, int minarea, int* status)
+__global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    const ResolveArgs& R = frame_args(batch, one);
+    const Tiles& T = R.T;
+    const Pieces& P = R.P;
+    const Comps& C = R.C;
+    uint32_t* seg = R.seg;
+    const int W = R.W, minarea = R.minarea;
+    int* status = R.status;
     const int n = min(*P.count, P.cap);
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -845,8 +856,9 @@ __global__ void k_finalize(Tiles T, Pieces P, Comps C, uint32_t* seg, int W, int
 }
 
 // ------------------------------------------------------------------ rank ---
-__global__ void k_rank_count(Comps C)
+__global__ void k_rank_count(const RankArgs* __restrict__ batch, const __grid_constant__ RankArgs one)
 {
+    const Comps& C = frame_args(batch, one).C;
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         atomicAdd(C.bcnt + ((C.label[c] - 1u) >> C.shift), 1);
@@ -855,8 +867,14 @@ __global__ void k_rank_count(Comps C)
 constexpr int SCAN_NT = 1024;
 
 // exclusive scan of the bucket counts (one CTA); publishes the segment count
-__global__ void __launch_bounds__(SCAN_NT) k_rank_scan(Comps C, int* n_out, int capacity, int* status)
+__global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restrict__ batch,
+                                                       const __grid_constant__ RankArgs one)
 {
+    const RankArgs& R = frame_args(batch, one);
+    const Comps& C = R.C;
+    int* n_out = R.n_out;
+    const int capacity = R.capacity;
+    int* status = R.status;
     __shared__ int wsum[SCAN_NT / 32];
     __shared__ int carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -898,8 +916,9 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(Comps C, int* n_out, int 
     }
 }
 
-__global__ void k_rank_scatter(Comps C)
+__global__ void k_rank_scatter(const RankArgs* __restrict__ batch, const __grid_constant__ RankArgs one)
 {
+    const Comps& C = frame_args(batch, one).C;
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const int b = (int)((C.label[c] - 1u) >> C.shift);
@@ -908,8 +927,9 @@ __global__ void k_rank_scatter(Comps C)
     }
 }
 
-__global__ void k_rank_place(Comps C)
+__global__ void k_rank_place(const RankArgs* __restrict__ batch, const __grid_constant__ RankArgs one)
 {
+    const Comps& C = frame_args(batch, one).C;
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const uint32_t l = C.label[c];
@@ -923,27 +943,34 @@ __global__ void k_rank_place(Comps C)
 
 // --------------------------------------------------------------- launchers ---
 template <bool F32, bool LO, int KS>
-static cudaError_t launch_tile(const DetectArgs& A, int ntiles, cudaStream_t st)
+static cudaError_t launch_tile(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
+                               cudaStream_t st)
 {
     const size_t smem = sizeof(TileSmem);
-    cudaFuncSetAttribute(k_detect_tile<F32, LO, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_detect_tile<F32, LO, KS><<<ntiles, DT_NT, smem, st>>>(A);
+    if (batch) {
+        cudaFuncSetAttribute(k_detect_tile<F32, LO, KS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_detect_tile<F32, LO, KS, true><<<dim3(maxtiles, nframes), DT_NT, smem, st>>>(batch, one);
+    } else {
+        cudaFuncSetAttribute(k_detect_tile<F32, LO, KS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_detect_tile<F32, LO, KS, false><<<maxtiles, DT_NT, smem, st>>>(nullptr, one);
+    }
     return cudaGetLastError();
 }
 
 template <bool F32>
-static cudaError_t launch_tile_ks(const DetectArgs& A, int ntiles, cudaStream_t st)
+static cudaError_t launch_tile_ks(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
+                                  cudaStream_t st)
 {
-    if (A.kw == A.kh && A.kw == 3) return launch_tile<F32, false, 3>(A, ntiles, st);
-    if (A.kw == A.kh && A.kw == 5) return launch_tile<F32, false, 5>(A, ntiles, st);
-    if (A.kw == A.kh && A.kw == 7) return launch_tile<F32, false, 7>(A, ntiles, st);
-    return launch_tile<F32, false, 0>(A, ntiles, st);
+    if (one.kw == one.kh && one.kw == 3) return launch_tile<F32, false, 3>(one, batch, nframes, maxtiles, st);
+    if (one.kw == one.kh && one.kw == 5) return launch_tile<F32, false, 5>(one, batch, nframes, maxtiles, st);
+    if (one.kw == one.kh && one.kw == 7) return launch_tile<F32, false, 7>(one, batch, nframes, maxtiles, st);
+    return launch_tile<F32, false, 0>(one, batch, nframes, maxtiles, st);
 }
 
-cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
-                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
-                                int* nnear, const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C,
-                                int* status, cudaStream_t st)
+DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw, int kh,
+                       float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
+                       const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C, int* status)
 {
     DetectArgs A;
     for (int i = 0; i < KMAX; ++i) A.K[i] = (taps && i < kw * kh) ? taps[i] : 0.f;
@@ -952,33 +979,83 @@ cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const Spli
     A.thresh = thresh; A.minarea = minarea;
     A.seg = seg; A.mask_out = mask_out; A.nnear = nnear; A.in_mask = in_mask;
     A.T = T; A.P = P; A.C = C; A.status = status;
-    const int ntiles = T.ntx * T.nty;
-    if (in_mask) return launch_tile<false, true, 0>(A, ntiles, st);
-    if (im.is_f32) return launch_tile_ks<true>(A, ntiles, st);
-    return launch_tile_ks<false>(A, ntiles, st);
+    return A;
+}
+
+// every frame of a batch shares `one`'s dtype, kernel size and mode
+// (labelling a given mask or detecting); maxtiles = the largest frame's tiles
+cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
+                              cudaStream_t st)
+{
+    if (one.in_mask) return launch_tile<false, true, 0>(one, batch, nframes, maxtiles, st);
+    if (one.im.is_f32) return launch_tile_ks<true>(one, batch, nframes, maxtiles, st);
+    return launch_tile_ks<false>(one, batch, nframes, maxtiles, st);
+}
+
+cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
+                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
+                                int* nnear, const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C,
+                                int* status, cudaStream_t st)
+{
+    const DetectArgs A = detect_args(im, sb, sr, taps, kw, kh, thresh, minarea, seg, mask_out, nnear, in_mask, T, P,
+                                     C, status);
+    return launch_detect_any(A, nullptr, 1, T.ntx * T.nty, st);
+}
+
+ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H, int minarea,
+                         int* status)
+{
+    ResolveArgs R;
+    R.T = T; R.P = P; R.C = C; R.seg = seg; R.W = W; R.H = H; R.minarea = minarea; R.status = status;
+    return R;
+}
+
+// grid of the grid-stride kernels: about 152 x 8 CTAs over the whole batch
+static int stride_grid(int per_frame, int nframes)
+{
+    const int g = per_frame / nframes;
+    return g < 16 ? 16 : g;
+}
+
+cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch, int nframes, int maxtiles,
+                               cudaStream_t st)
+{
+    k_merge<<<dim3(maxtiles, nframes), 64, 0, st>>>(batch, one);
+    const dim3 g(stride_grid(152 * 8, nframes), nframes);
+    k_aggregate<<<g, 256, 0, st>>>(batch, one);
+    k_finalize<<<g, 256, 0, st>>>(batch, one);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H,
                            int minarea, int* status, cudaStream_t st)
 {
-    const int ntiles = T.ntx * T.nty;
-    k_merge<<<ntiles, 64, 0, st>>>(T, P, W, H, status);
-    const int g = 152 * 8;
-    k_aggregate<<<g, 256, 0, st>>>(P, status);
-    k_finalize<<<g, 256, 0, st>>>(T, P, C, seg, W, minarea, status);
+    return launch_resolve_any(resolve_args(T, P, C, seg, W, H, minarea, status), nullptr, 1, T.ntx * T.nty, st);
+}
+
+RankArgs rank_args(const Comps& C, int* n_out, int capacity, bool place, int* status)
+{
+    RankArgs R;
+    R.C = C; R.n_out = n_out; R.capacity = capacity; R.place = place ? 1 : 0; R.status = status;
+    return R;
+}
+
+// every frame of a batch shares `one`'s place flag
+cudaError_t launch_rank_any(const RankArgs& one, const RankArgs* batch, int nframes, cudaStream_t st)
+{
+    const dim3 g(stride_grid(152 * 4, nframes), nframes);
+    k_rank_count<<<g, 256, 0, st>>>(batch, one);
+    k_rank_scan<<<dim3(1, nframes), SCAN_NT, 0, st>>>(batch, one);
+    if (one.place) {
+        k_rank_scatter<<<g, 256, 0, st>>>(batch, one);
+        k_rank_place<<<g, 256, 0, st>>>(batch, one);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_rank(const Comps& C, int* n_out, int capacity, bool place, int* status, cudaStream_t st)
 {
-    const int g = 152 * 4;
-    k_rank_count<<<g, 256, 0, st>>>(C);
-    k_rank_scan<<<1, SCAN_NT, 0, st>>>(C, n_out, capacity, status);
-    if (place) {
-        k_rank_scatter<<<g, 256, 0, st>>>(C);
-        k_rank_place<<<g, 256, 0, st>>>(C);
-    }
-    return cudaGetLastError();
+    return launch_rank_any(rank_args(C, n_out, capacity, place, status), nullptr, 1, st);
 }
 
 }  // namespace gp

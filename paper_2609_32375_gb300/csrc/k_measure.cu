@@ -9,343 +9,9 @@
 // about 48 bits -- the float64-class accumulation the paper asks of aperture
 // sums, without FP64 arithmetic (which runs at a small fraction of the FP32
 // rate on this GPU).
-#include <math.h>
-
-#include "gp_internal.cuh"
-#include "gp_launch.h"
+#include "k_measure_impl.cuh"
 
 namespace gp {
-
-struct ApSpec {
-    int nr;
-    float r[MAX_NR];
-    float rmax;
-    float gain;
-};
-
-struct MeasureArgs {
-    Image im;
-    SplineTab sb, sr;
-    Comps C;
-    int capacity;
-    // catalog columns
-    uint32_t* label;
-    int32_t* npix;
-    double *flux_iso, *x, *y, *x2, *y2, *xy;
-    int32_t *xmin, *xmax, *ymin, *ymax;
-    float* peak;
-    int32_t *xpeak, *ypeak;
-    uint32_t* flags;
-    ApSpec ap;
-    double* apflux;
-    double* apferr;
-    uint32_t* apflags;
-};
-
-// integral of sqrt(r^2 - t^2) over [a, b], -r <= a <= b <= r, written with
-// differences formed algebraically (no cancellation between large terms)
-__device__ __forceinline__ float chord_int(float a, float b, float r2)
-{
-    float d = b - a;
-    if (!(d > 0.f)) return 0.f;
-    float ha = sqrtf(fmaxf(r2 - a * a, 0.f));
-    float hb = sqrtf(fmaxf(r2 - b * b, 0.f));
-    float s = ha + hb;
-    float q = s > 0.f ? d * (a + b) / s : 0.f;      // ha - hb
-    float sin_t = fmaf(d, ha, a * q);               // (b ha - a hb), r^2 sin(theta)
-    float cos_t = fmaf(ha, hb, a * b);              // (ha hb + a b), r^2 cos(theta)
-    float theta = atan2f(sin_t, cos_t);             // asin(b/r) - asin(a/r)
-    return 0.5f * (fmaf(d, hb, -a * q) + r2 * theta);
-}
-
-// exact area of disc(0, r) n [x0,x1] x [y0,y1]: integrate the length of
-// [y0,y1] n [-h(x), h(x)] over x, split where h(x) = |y0|, |y1|
-__device__ float disc_rect_area(float x0, float x1, float y0, float y1, float r)
-{
-    const float r2 = r * r;
-    const float a = fmaxf(x0, -r), b = fminf(x1, r);
-    if (!(a < b)) return 0.f;
-    float p[6];
-    p[0] = a;
-    p[5] = b;
-    float c0 = fabsf(y0) < r ? sqrtf(fmaxf(r2 - y0 * y0, 0.f)) : 0.f;
-    float c1 = fabsf(y1) < r ? sqrtf(fmaxf(r2 - y1 * y1, 0.f)) : 0.f;
-    p[1] = fminf(fmaxf(-c0, a), b);
-    p[2] = fminf(fmaxf(c0, a), b);
-    p[3] = fminf(fmaxf(-c1, a), b);
-    p[4] = fminf(fmaxf(c1, a), b);
-    // sort p[1..4]
-#define GP_CSWAP(i, j) { float lo_ = fminf(p[i], p[j]); float hi_ = fmaxf(p[i], p[j]); p[i] = lo_; p[j] = hi_; }
-    GP_CSWAP(1, 2); GP_CSWAP(3, 4); GP_CSWAP(1, 3); GP_CSWAP(2, 4); GP_CSWAP(2, 3);
-#undef GP_CSWAP
-    float area = 0.f;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        float lo = p[k], hi = p[k + 1];
-        if (!(hi > lo)) continue;
-        float mid = 0.5f * (lo + hi);
-        float h = sqrtf(fmaxf(r2 - mid * mid, 0.f));
-        bool top_h = h <= y1, bot_h = -h >= y0;
-        float top = top_h ? h : y1, bot = bot_h ? -h : y0;
-        if (!(top > bot)) continue;
-        float gi = (top_h || bot_h) ? chord_int(lo, hi, r2) : 0.f;
-        float w = hi - lo;
-        float itop = top_h ? gi : y1 * w;
-        float ibot = bot_h ? -gi : y0 * w;
-        area += itop - ibot;
-    }
-    return area;
-}
-
-template <bool F32>
-__device__ __forceinline__ float load_px(const Image& im, int x, int y, bool& bad)
-{
-    float v;
-    if (F32) {
-        v = __ldg(reinterpret_cast<const float*>(im.data) + (int64_t)y * im.pitch + x);
-        bad = !isfinite(v);
-    } else {
-        v = (float)__ldg(reinterpret_cast<const uint16_t*>(im.data) + (int64_t)y * im.pitch + x);
-        bad = false;
-    }
-    if (im.mask && im.mask[(int64_t)y * im.W + x]) bad = true;
-    return v;
-}
-
-// Pixels crossed by a circle wait in a per-warp queue so that the exact
-// overlap area, the one expensive step, runs with every lane busy instead of
-// once per row for whichever lanes meet the circle.
-struct BEntry {
-    float dx0, dy0, m, var;
-    int kf;                 // radius index | bad << 8 | saturated << 9
-};
-constexpr int QCAP = 96;
-constexpr int MEAS_NT = 256;
-
-template <int NR>
-__device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn, DF* f, DF* v, uint32_t* fl)
-{
-    __syncwarp();
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < qn; i += 32) {
-        const BEntry e = wq[i];
-        const int k = e.kf & 0xff;
-        const float A = disc_rect_area(e.dx0, e.dx0 + 1.f, e.dy0, e.dy0 + 1.f, ap.r[k]);
-        if (!(A > 0.f)) continue;
-#pragma unroll
-        for (int kk = 0; kk < NR; ++kk) {
-            if (kk != k) continue;
-            if (e.kf & 0x100) { fl[kk] |= GP_FLAG_BAD; continue; }
-            if (e.kf & 0x200) fl[kk] |= GP_FLAG_SAT;
-            df_add_prod(f[kk], A, e.m);
-            df_add_prod(v[kk], A, e.var);
-        }
-    }
-    __syncwarp();
-}
-
-// Apertures around (cx, cy) for all radii; executed by one full warp.
-// One lane per pixel column: the column's x-spline coefficients and the
-// node-row values u_j, w_j of both maps are evaluated once per column and
-// reused down the column, so each pixel costs a few FMAs for B(p) and
-// sigma(p).  Pixels wholly inside a disc add directly; pixels the circle
-// crosses go through the queue.  The queue order and the lane assignment are
-// fixed, and lane results are combined in a fixed order, so the sums are
-// reproducible.  Lane 0 writes.
-template <bool F32, int NR>
-__device__ void aperture_warp(const Image& im, const SplineTab& sb, const SplineTab& sr, const ApSpec& ap,
-                              double cx, double cy, double* flux, double* ferr, uint32_t* aflags, BEntry* wq)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int W = im.W, H = im.H;
-    // positions far outside the frame (or NaN) clamp to an empty pixel range
-    const double cxc = fmin(fmax(cx, -4096.0), (double)W + 4096.0);
-    const double cyc = fmin(fmax(cy, -4096.0), (double)H + 4096.0);
-    const double xi_d = floor(cxc), yi_d = floor(cyc);
-    const int xi = (int)xi_d, yi = (int)yi_d;
-    const float xf = (float)(cxc - xi_d), yf = (float)(cyc - yi_d);
-    int xa = (int)floor(cxc - (double)ap.rmax - 0.5), xb = (int)ceil(cxc + (double)ap.rmax + 0.5);
-    int ya = (int)floor(cyc - (double)ap.rmax - 0.5), yb = (int)ceil(cyc + (double)ap.rmax + 0.5);
-    xa = max(xa, 0); ya = max(ya, 0);
-    xb = min(xb, W - 1); yb = min(yb, H - 1);
-    if (!(cx == cxc) || !(cy == cyc)) { xb = -1; yb = -1; }
-    DF f[NR > 0 ? NR : 1], v[NR > 0 ? NR : 1];
-    uint32_t fl[NR > 0 ? NR : 1];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) { f[k] = df_zero(); v[k] = df_zero(); fl[k] = 0u; }
-    const float rmax2 = ap.rmax * ap.rmax;
-    int qn = 0;                                      // warp-uniform queue length
-    for (int xbase = xa; xbase <= xb; xbase += 32) {
-        const int x = xbase + lane;
-        const bool colok = x <= xb;
-        const float dx0 = (float)(x - xi) - xf - 0.5f, dx1 = dx0 + 1.f;
-        const float nx = fmaxf(0.f, fmaxf(dx0, -dx1));
-        const float fx = fmaxf(dx0 * dx0, dx1 * dx1);
-        const AxCoef ccx = axis_coef(sb.ax, (float)(colok ? x : xb));
-        int jc = -1;                       // node row pair cached for this column
-        float ub0 = 0, ub1 = 0, wb0 = 0, wb1 = 0, ur0 = 0, ur1 = 0, wr0 = 0, wr1 = 0;
-        for (int y = ya; y <= yb; ++y) {
-            const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
-            const float ny = fmaxf(0.f, fmaxf(dy0, -dy1));
-            const float dmin2 = nx * nx + ny * ny;
-            const float dmax2 = fx + fmaxf(dy0 * dy0, dy1 * dy1);
-            const bool live = colok && dmin2 < rmax2;
-            bool bad = true, sat = false;
-            float m = 0.f, var = 0.f;
-            if (live) {
-                const float val = load_px<F32>(im, x, y, bad);
-                if (!bad) {
-                    const AxCoef ccy = axis_coef(sb.ay, (float)y);
-                    if (ccy.i != jc) {
-                        const float2 b0 = row_eval(sb, ccy.i, ccx), b1 = row_eval(sb, ccy.i1, ccx);
-                        const float2 r0 = row_eval(sr, ccy.i, ccx), r1 = row_eval(sr, ccy.i1, ccx);
-                        ub0 = b0.x; wb0 = b0.y; ub1 = b1.x; wb1 = b1.y;
-                        ur0 = r0.x; wr0 = r0.y; ur1 = r1.x; wr1 = r1.y;
-                        jc = ccy.i;
-                    }
-                    m = val - axis_combine(ccy, ub0, ub1, wb0, wb1);
-                    const float sg = axis_combine(ccy, ur0, ur1, wr0, wr1);
-                    var = sg * sg;
-                    sat = im.sat > 0.f && val >= im.sat;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const float r = ap.r[k], r2 = r * r;
-                const bool in = live && dmin2 < r2;
-                const bool full = in && dmax2 <= r2;
-                if (full) {
-                    if (bad) fl[k] |= GP_FLAG_BAD;
-                    else {
-                        if (sat) fl[k] |= GP_FLAG_SAT;
-                        df_add(f[k], m);
-                        df_add(v[k], var);
-                    }
-                }
-                const bool bnd = in && !full;
-                const unsigned bal = __ballot_sync(0xffffffffu, bnd);
-                if (bnd) {
-                    BEntry e;
-                    e.dx0 = dx0; e.dy0 = dy0; e.m = m; e.var = var;
-                    e.kf = k | (bad ? 0x100 : 0) | (sat ? 0x200 : 0);
-                    wq[qn + __popc(bal & lt)] = e;
-                }
-                qn += __popc(bal);
-                if (qn > QCAP - 32) {
-                    flush_queue<NR>(ap, wq, qn, f, v, fl);
-                    qn = 0;
-                }
-            }
-        }
-    }
-    flush_queue<NR>(ap, wq, qn, f, v, fl);
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        const DF fs = df_warp_sum(f[k]);
-        const DF vs = df_warp_sum(v[k]);
-        uint32_t ff = fl[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ff |= __shfl_xor_sync(0xffffffffu, ff, o);
-        if (lane == 0) {
-            const double r = ap.r[k];
-            if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) ff |= GP_FLAG_TRUNCATED;
-            const double F = df_value(fs);
-            double V = df_value(vs);
-            if (ap.gain > 0.f && F > 0.0) V += F / (double)ap.gain;
-            flux[k] = F;
-            ferr[k] = sqrt(fmax(V, 0.0));
-            aflags[k] = ff;
-        }
-    }
-}
-
-// One warp per catalog row (segments in label order): copy the segment's
-// finished moments into the row, then the apertures at its centroid.
-template <bool F32, int NR>
-__global__ void __launch_bounds__(MEAS_NT) k_measure(MeasureArgs A)
-{
-    __shared__ BEntry queue[MEAS_NT / 32][QCAP];
-    BEntry* wq = queue[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int ncomp = min(*A.C.count, A.C.cap);
-    const int nrow = min(ncomp, A.capacity);
-    const int W = A.im.W;
-    for (int r = wid; r < nrow; r += nw) {
-        const int c = A.C.perm[r];
-        const double2 xy = A.C.xy[c];
-        if (lane == 0) {
-            const int4 bb = A.C.bbox[c];
-            const Mom2 m2 = A.C.mom2[c];
-            const uint32_t pL = A.C.peakL[c];
-            A.label[r] = A.C.label[c];
-            A.npix[r] = A.C.npix[c];
-            A.flux_iso[r] = A.C.flux[c];
-            A.x[r] = xy.x; A.y[r] = xy.y;
-            A.x2[r] = m2.x2; A.y2[r] = m2.y2; A.xy[r] = m2.xy;
-            A.xmin[r] = bb.x; A.xmax[r] = bb.y; A.ymin[r] = bb.z; A.ymax[r] = bb.w;
-            A.peak[r] = A.C.peak[c];
-            A.xpeak[r] = (int)(pL % (uint32_t)W); A.ypeak[r] = (int)(pL / (uint32_t)W);
-            A.flags[r] = A.C.flags[c];
-        }
-        if constexpr (NR > 0)
-            aperture_warp<F32, NR>(A.im, A.sb, A.sr, A.ap, xy.x, xy.y, A.apflux + (int64_t)r * NR,
-                                   A.apferr + (int64_t)r * NR, A.apflags + (int64_t)r * NR, wq);
-    }
-}
-
-template <bool F32, int NR>
-__global__ void __launch_bounds__(MEAS_NT) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap,
-                                                      const double* xs, const double* ys, int n, double* flux,
-                                                      double* ferr, uint32_t* fl)
-{
-    __shared__ BEntry queue[MEAS_NT / 32][QCAP];
-    BEntry* wq = queue[threadIdx.x >> 5];
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = wid; i < n; i += nw)
-        aperture_warp<F32, NR>(im, sb, sr, ap, xs[i], ys[i], flux + (int64_t)i * NR, ferr + (int64_t)i * NR,
-                               fl + (int64_t)i * NR, wq);
-}
-
-// dispatch on the number of radii (a compile-time constant in the kernels)
-template <template <bool, int> class Launch, bool F32, typename... Args>
-static cudaError_t dispatch_nr(int nr, Args... args)
-{
-    switch (nr) {
-    case 0: return Launch<F32, 0>::run(args...);
-    case 1: return Launch<F32, 1>::run(args...);
-    case 2: return Launch<F32, 2>::run(args...);
-    case 3: return Launch<F32, 3>::run(args...);
-    case 4: return Launch<F32, 4>::run(args...);
-    case 5: return Launch<F32, 5>::run(args...);
-    case 6: return Launch<F32, 6>::run(args...);
-    case 7: return Launch<F32, 7>::run(args...);
-    default: return Launch<F32, 8>::run(args...);
-    }
-}
-
-template <bool F32, int NR>
-struct MeasureLaunch {
-    static cudaError_t run(const MeasureArgs& A, int g, cudaStream_t st)
-    {
-        k_measure<F32, NR><<<g, 256, 0, st>>>(A);
-        return cudaGetLastError();
-    }
-};
-
-template <bool F32, int NR>
-struct ApertureLaunch {
-    static cudaError_t run(Image im, SplineTab sb, SplineTab sr, ApSpec ap, const double* xs, const double* ys,
-                           int n, double* flux, double* ferr, uint32_t* fl, int g, cudaStream_t st)
-    {
-        if (NR == 0) return cudaSuccess;
-        k_aperture<F32, NR><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
-        return cudaGetLastError();
-    }
-};
 
 // --------------------------------------------------------------- launchers ---
 static ApSpec make_ap(const float* radii, int nr, float gain)
@@ -361,13 +27,12 @@ static ApSpec make_ap(const float* radii, int nr, float gain)
     return s;
 }
 
-cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab& sr, const Comps& C,
-                           const uint32_t* seg, const gp_catalog& cat, const float* radii, int nr, float gain,
-                           double* apflux, double* apferr, uint32_t* apflags, cudaStream_t st)
+MeasureArgs measure_args(const Image& im, const SplineTab& sb, const SplineTab& sr, const Comps& C,
+                         const gp_catalog& cat, const float* radii, int nr, float gain, double* apflux,
+                         double* apferr, uint32_t* apflags)
 {
     MeasureArgs A;
     A.im = im; A.sb = sb; A.sr = sr; A.C = C;
-    (void)seg;
     A.capacity = cat.capacity;
     A.label = cat.label; A.npix = cat.npix; A.flux_iso = cat.flux_iso;
     A.x = cat.x; A.y = cat.y; A.x2 = cat.x2; A.y2 = cat.y2; A.xy = cat.xy;
@@ -375,9 +40,27 @@ cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab
     A.peak = cat.peak; A.xpeak = cat.xpeak; A.ypeak = cat.ypeak; A.flags = cat.flags;
     A.ap = make_ap(radii, nr, gain);
     A.apflux = apflux; A.apferr = apferr; A.apflags = apflags;
-    const int g = 152 * 8;
-    if (im.is_f32) return dispatch_nr<MeasureLaunch, true>(nr, A, g, st);
-    return dispatch_nr<MeasureLaunch, false>(nr, A, g, st);
+    return A;
+}
+
+// every frame of a batch shares `one`'s dtype and number of radii
+cudaError_t launch_measure_any(const MeasureArgs& one, const MeasureArgs* batch, int nframes, cudaStream_t st)
+{
+    int g = 152 * 8 / nframes;
+    if (g < 16) g = 16;
+    const dim3 grid(g, nframes);
+    if (batch) return launch_measure_batched(one, batch, grid, st);
+    if (one.im.is_f32) return dispatch_nr<MeasureLaunch, true>(one.ap.nr, one, grid, st);
+    return dispatch_nr<MeasureLaunch, false>(one.ap.nr, one, grid, st);
+}
+
+cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab& sr, const Comps& C,
+                           const uint32_t* seg, const gp_catalog& cat, const float* radii, int nr, float gain,
+                           double* apflux, double* apferr, uint32_t* apflags, cudaStream_t st)
+{
+    (void)seg;
+    return launch_measure_any(measure_args(im, sb, sr, C, cat, radii, nr, gain, apflux, apferr, apflags), nullptr, 1,
+                              st);
 }
 
 cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,

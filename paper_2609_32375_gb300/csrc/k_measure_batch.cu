@@ -1,0 +1,13 @@
+// k_measure_batch.cu -- the batched instances of k_measure (one launch
+// over the frames of a batch, grid y = frame; see k_measure_impl.cuh).
+#include "k_measure_impl.cuh"
+
+namespace gp {
+
+cudaError_t launch_measure_batched(const MeasureArgs& one, const MeasureArgs* batch, dim3 grid, cudaStream_t st)
+{
+    if (one.im.is_f32) return dispatch_nr<MeasureBatchLaunch, true>(one.ap.nr, one, batch, grid, st);
+    return dispatch_nr<MeasureBatchLaunch, false>(one.ap.nr, one, batch, grid, st);
+}
+
+}  // namespace gp

@@ -31,26 +31,26 @@ def test_library_exports_every_declared_symbol():
     assert set(decl) <= exported
 
 
+STRUCTS = {"gp_image": gp.GpImage, "gp_bkg_params": gp.GpBkgParams, "gp_bkg": gp.GpBkg,
+           "gp_det_params": gp.GpDetParams, "gp_catalog": gp.GpCatalog, "gp_ap_params": gp.GpApParams,
+           "gp_stats": gp.GpStats, "gp_cnn_weights": gp.GpCnnWeights, "gp_frame": gp.GpFrame,
+           "gp_server_config": gp.GpServerConfig, "gp_request": gp.GpRequest, "gp_result": gp.GpResult,
+           "gp_server_report": gp.GpServerReport}
+
+
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "layout.c"
-    fields = {
-        "gp_image": [f for f, _ in gp.GpImage._fields_], "gp_bkg_params": [f for f, _ in gp.GpBkgParams._fields_],
-        "gp_bkg": [f for f, _ in gp.GpBkg._fields_], "gp_det_params": [f for f, _ in gp.GpDetParams._fields_],
-        "gp_catalog": [f for f, _ in gp.GpCatalog._fields_], "gp_ap_params": [f for f, _ in gp.GpApParams._fields_],
-    }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gpphot.h"', "int main(void){"]
-    for s, fs in fields.items():
+    for s, cls in STRUCTS.items():
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
-        for f in fs:
+        for f, _ in cls._fields_:
             lines.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
     lines.append("return 0;}")
     prog.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
-    py = {"gp_image": gp.GpImage, "gp_bkg_params": gp.GpBkgParams, "gp_bkg": gp.GpBkg,
-          "gp_det_params": gp.GpDetParams, "gp_catalog": gp.GpCatalog, "gp_ap_params": gp.GpApParams}
-    for s, cls in py.items():
+    for s, cls in STRUCTS.items():
         assert int(got[s]) == C.sizeof(cls), s
         for f, _ in cls._fields_:
             assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
