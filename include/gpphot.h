@@ -367,6 +367,9 @@ typedef struct {
     int32_t batch;            /* frames in the launch this frame ran in */
     double latency_ms;        /* submit to result ready (host clock) */
     double queue_ms;          /* submit to admission */
+    float h2d_ms;             /* the unit's input copies (device clock; shared by a batch's frames) */
+    float run_ms;             /* the unit's pipeline kernels */
+    float d2h_ms;             /* the unit's result copies */
 } gp_result;
 
 typedef struct {

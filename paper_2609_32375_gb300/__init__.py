@@ -112,7 +112,8 @@ class GpResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("cat", GpCatalog), ("flux", C.c_void_p),
                 ("fluxerr", C.c_void_p), ("apflags", C.c_void_p), ("segmap", C.c_void_p), ("bkg_mesh", C.c_void_p),
                 ("rms_mesh", C.c_void_p), ("mesh", C.c_int32), ("mx", C.c_int32), ("my", C.c_int32),
-                ("batch", C.c_int32), ("latency_ms", C.c_double), ("queue_ms", C.c_double)]
+                ("batch", C.c_int32), ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("h2d_ms", C.c_float), ("run_ms", C.c_float), ("d2h_ms", C.c_float)]
 
 
 class GpServerReport(C.Structure):
@@ -653,7 +654,7 @@ class Server:
         H, W, cap = self._shape[ticket]
         m = min(max(res.n, 0), cap) if res.status in (GP_OK, GP_ERR_CAPACITY) else 0
         out = {"status": res.status, "n": res.n, "batch": res.batch, "latency_ms": res.latency_ms,
-               "queue_ms": res.queue_ms}
+               "queue_ms": res.queue_ms, "h2d_ms": res.h2d_ms, "run_ms": res.run_ms, "d2h_ms": res.d2h_ms}
         if res.status in (GP_OK, GP_ERR_CAPACITY):
             cat = {}
             for name, dt in CATALOG_COLUMNS:

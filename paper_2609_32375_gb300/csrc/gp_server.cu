@@ -174,6 +174,7 @@ struct Slot {
     cudaStream_t st = nullptr;
     ArgStage stage;
     Unit* unit = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // unit start, inputs in, pipeline done, results out
 };
 
 }  // namespace
@@ -344,6 +345,7 @@ gp_status gp_server::launch(Unit* u)
     char* dws = dbase + off;
 
     // inputs
+    cudaEventRecord(sl.ev[0], st);
     for (int f = 0; f < n; ++f) {
         Req* q = u->frames[f];
         const size_t row = (size_t)q->W * q->esize;
@@ -385,6 +387,7 @@ gp_status gp_server::launch(Unit* u)
         x.apflags = at<uint32_t>(r, L[f].apflags);
         x.status = at<int>(r, 0);
     }
+    cudaEventRecord(sl.ev[1], st);
     Exec ex;
     ex.cv = Carver{dws, ws_bytes};
     ex.st = st;
@@ -394,6 +397,7 @@ gp_status gp_server::launch(Unit* u)
         return srv_fail(GP_ERR_INTERNAL, "unit workspace of %zu bytes short of the %zu carved", ws_bytes, ex.cv.off);
     if (s != GP_OK) return s;
     // results back: the unit's result blocks in one copy, then the wanted maps
+    cudaEventRecord(sl.ev[2], st);
     e = cudaMemcpyAsync(hbase, dbase, n * u->rb, cudaMemcpyDeviceToHost, st);
     size_t hoff = u->seg_host_off;
     for (int f = 0; f < n && e == cudaSuccess; ++f) {
@@ -404,6 +408,7 @@ gp_status gp_server::launch(Unit* u)
         hoff += (size_t)q->npix * 4;
     }
     if (e != cudaSuccess) return srv_fail(GP_ERR_CUDA, "result copy: %s", cudaGetErrorString(e));
+    cudaEventRecord(sl.ev[3], st);
     auto* arg = new std::pair<gp_server*, Unit*>(this, u);
     e = cudaLaunchHostFunc(st, on_unit_done, arg);
     if (e != cudaSuccess) {
@@ -422,6 +427,11 @@ void gp_server::finish(Unit* u)
     char* hbase = hpool + u->host_off;
     const int n = (int)u->frames.size();
     size_t hoff = u->seg_host_off;
+    float t_in = 0.f, t_run = 0.f, t_out = 0.f;
+    const cudaEvent_t* ev = slots[u->slot].ev;
+    if (cudaEventElapsedTime(&t_in, ev[0], ev[1]) != cudaSuccess || cudaEventElapsedTime(&t_run, ev[1], ev[2]) !=
+        cudaSuccess || cudaEventElapsedTime(&t_out, ev[2], ev[3]) != cudaSuccess)
+        t_in = t_run = t_out = -1.f;
     for (int f = 0; f < n; ++f) {
         Req* q = u->frames[f];
         char* r = hbase + f * u->rb;
@@ -456,6 +466,9 @@ void gp_server::finish(Unit* u)
             hoff += (size_t)q->npix * 4;
         }
         res.batch = n;
+        res.h2d_ms = t_in;
+        res.run_ms = t_run;
+        res.d2h_ms = t_out;
         res.latency_ms = ms_between(q->t_submit, now);
         res.queue_ms = ms_between(q->t_submit, q->t_admit);
         if (res.status == GP_ERR_CAPACITY) q->msg = "more segments than catalog rows (see n)";
@@ -581,6 +594,8 @@ gp_status gp_server_create(const gp_server_config* cfg, gp_server** out)
     auto undo = [&](gp_status st, const char* what, cudaError_t err) {
         for (Slot& sl : sv->slots) {
             sl.stage.release();
+            for (cudaEvent_t& x : sl.ev)
+                if (x) cudaEventDestroy(x);
             if (sl.st) cudaStreamDestroy(sl.st);
         }
         if (sv->dpool) cudaFree(sv->dpool);
@@ -597,6 +612,7 @@ gp_status gp_server_create(const gp_server_config* cfg, gp_server** out)
     sv->slots.resize(cfg->slots);
     for (Slot& sl : sv->slots) {
         e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&sl.ev[k]);
         if (e == cudaSuccess) e = sl.stage.init((size_t)512 << 10);
         if (e != cudaSuccess) return undo(GP_ERR_CUDA, "slot streams", e);
     }
@@ -783,6 +799,8 @@ void gp_server_destroy(gp_server* s)
     for (Slot& sl : s->slots) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         sl.stage.release();
+        for (cudaEvent_t& x : sl.ev)
+            if (x) cudaEventDestroy(x);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
     cudaFree(s->dpool);

@@ -33,6 +33,7 @@
 
 namespace gp {
 
+static_assert(TX == 64, "row masks hold one 64-pixel tile row");
 constexpr int DT_NT = 256;
 constexpr int ROWS_PER_THREAD = TNPIX / DT_NT;     // 8: each thread filters 8 rows of one column
 
@@ -217,9 +218,16 @@ struct TileSmem {
     int r_pix[MAXROOT];               // root's tile pixel
     int r_val[MAXROOT];               // value written to the map
     int r_rec[MAXROOT];               // piece id (>= 0), -2 - component id, or -1
+    uint32_t rmask[2 * TY];           // foreground bits per tile row (two 32-pixel halves)
     int warp_tot[DT_NT / 32];
     int jlo, jhi, nroots, npieces, ncomps, pbase, cbase, nnear;
 };
+
+// the 64 foreground bits of tile row y (bit x = pixel x)
+__device__ __forceinline__ uint64_t row_mask(const TileSmem& S, int y)
+{
+    return (uint64_t)S.rmask[2 * y] | ((uint64_t)S.rmask[2 * y + 1] << 32);
+}
 
 __device__ __forceinline__ float combine_row(const float4& rc, float v0, float v1, float m0, float m1)
 {
@@ -239,6 +247,95 @@ __device__ __forceinline__ float cell_rms(const TileSmem& S, int ry, int c)
     const int2 j = S.rowj[ry];
     return combine_row(S.rowc[ry], S.u.col.ur[j.x * SW + c], S.u.col.ur[j.y * SW + c], S.u.col.wr[j.x * SW + c],
                        S.u.col.wr[j.y * SW + c]);
+}
+
+// A 16-byte chunk q of the staged window (row q / nchunk, chunk q % nchunk)
+// as raw bits: 8 uint16 pixels or 4 float32 pixels.  The frame's last chunk
+// of a row may stop short of the vector width: those lanes repeat the last
+// column (they lie outside the columns in use).
+template <bool F32>
+__device__ __forceinline__ uint4 load_chunk(const Image& im, int xa, int nchunk, unsigned inv_nchunk, int gy0, int q)
+{
+    constexpr int VEC = F32 ? 4 : 8;
+    const int ry = (int)(((unsigned)q * inv_nchunk) >> 16), ch = q - ry * nchunk;
+    const int64_t row = (int64_t)(gy0 + ry) * im.pitch;
+    const int gx0 = xa + ch * VEC, W = im.W;
+    if (gx0 + VEC <= W) {
+        if (F32) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(im.data) + row + gx0));
+            return make_uint4(__float_as_uint(w.x), __float_as_uint(w.y), __float_as_uint(w.z), __float_as_uint(w.w));
+        }
+        return __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const uint16_t*>(im.data) + row + gx0));
+    }
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (F32) {
+            const int gx = gx0 + e < W ? gx0 + e : W - 1;
+            w[e] = __float_as_uint(__ldg(reinterpret_cast<const float*>(im.data) + row + gx));
+        } else {
+            const int ga = gx0 + 2 * e < W ? gx0 + 2 * e : W - 1, gb = gx0 + 2 * e + 1 < W ? gx0 + 2 * e + 1 : W - 1;
+            const uint16_t* px = reinterpret_cast<const uint16_t*>(im.data) + row;
+            w[e] = (uint32_t)__ldg(px + ga) | ((uint32_t)__ldg(px + gb) << 16);
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+struct StageGeo {
+    int xa, nchunk;
+    unsigned inv_nchunk;
+    int clo, chi, hh, th, tw, c_org;   // c_org: frame column of staged column 0
+};
+
+// m = I - B of one chunk from its raw bits, the spline background taken
+// from the per-column node-row values (16-byte shared loads: a chunk starts
+// on a 4-column boundary); columns outside the ones in use get 0.  Bad
+// (non-finite) and saturated pixels of the tile are flagged.
+template <bool F32>
+__device__ __forceinline__ void stage_chunk(TileSmem& S, float sat, const StageGeo& g, uint4 raw, int q)
+{
+    constexpr int VEC = F32 ? 4 : 8;
+    const int ry = (int)(((unsigned)q * g.inv_nchunk) >> 16), ch = q - ry * g.nchunk;
+    const int c0 = g.xa + ch * VEC - g.c_org;
+    float v[VEC];
+    const uint32_t u4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (F32) {
+            v[e] = __uint_as_float(u4[e]);
+        } else {
+            v[2 * e] = (float)(u4[e] & 0xffffu);
+            v[2 * e + 1] = (float)(u4[e] >> 16);
+        }
+    }
+    const float4 rc = S.rowc[ry];
+    const int2 j = S.rowj[ry];
+    const int py = ry - g.hh;
+    const bool row_in = py >= 0 && py < g.th;
+#pragma unroll
+    for (int k = 0; k < VEC / 4; ++k) {
+        const int c = c0 + 4 * k;
+        const float4 u0 = *reinterpret_cast<const float4*>(S.u.col.ub + j.x * SW + c);
+        const float4 u1 = *reinterpret_cast<const float4*>(S.u.col.ub + j.y * SW + c);
+        const float4 w0 = *reinterpret_cast<const float4*>(S.u.col.wb + j.x * SW + c);
+        const float4 w1 = *reinterpret_cast<const float4*>(S.u.col.wb + j.y * SW + c);
+        const float a0[4] = {u0.x, u0.y, u0.z, u0.w}, a1[4] = {u1.x, u1.y, u1.z, u1.w};
+        const float b0[4] = {w0.x, w0.y, w0.z, w0.w}, b1[4] = {w1.x, w1.y, w1.z, w1.w};
+        float m[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float val = v[4 * k + e];
+            const int cc = c + e;
+            const bool bad = F32 ? !isfinite(val) : false;
+            const bool use = cc >= g.clo && cc < g.chi;
+            m[e] = (bad || !use) ? 0.f : val - combine_row(rc, a0[e], a1[e], b0[e], b1[e]);
+            const int px = cc - XHALO;
+            if (row_in && use && px >= 0 && px < g.tw)
+                S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && sat > 0.f && val >= sat) ? 2 : 0);
+        }
+        *reinterpret_cast<float4*>(S.m + ry * SW + c) = make_float4(m[0], m[1], m[2], m[3]);
+    }
 }
 
 // F at 8 consecutive rows of one column: slide the kernel window down the
@@ -333,77 +430,45 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
             S.rowc[tid] = make_float4(cy.b, cy.c0, cy.c1, 0.f);
             S.rowj[tid] = make_int2(cy.i - jlo, cy.i1 - jlo);
         }
-        for (int c = clo + tid; c < chi; c += DT_NT) {
-            const int gx = mirror_fast(x0 - XHALO + c, W);
-            const AxCoef cx = axis_coef(A.sb.ax, (float)gx);
-            for (int jj = 0; jj < nj; ++jj) {
-                const float2 b = row_eval(A.sb, jlo + jj, cx);
-                const float2 r = row_eval(A.sr, jlo + jj, cx);
-                S.u.col.ub[jj * SW + c] = b.x; S.u.col.wb[jj * SW + c] = b.y;
-                S.u.col.ur[jj * SW + c] = r.x; S.u.col.wr[jj * SW + c] = r.y;
-            }
-        }
-
-        // ---- stage the pixels over tile + halo (mirror border)
+        // ---- stage the pixels over tile + halo (mirror border) as m = I - B
         const bool interior = x0 - hh >= 0 && x0 + tw + hh <= W && y0 - hh >= 0 && y0 + th + hh <= H;
         constexpr int VEC = F32 ? 4 : 8;          // pixels per 16-byte load
         const bool vec_ok = interior && !A.im.mask && ((((uintptr_t)A.im.data) & 15) == 0) &&
                             ((A.im.pitch % VEC) == 0);
+        // 16-byte chunks covering [x0 - hh, x0 + tw + hh); frame column
+        // x0 - XHALO is chunk aligned, so chunks land on 16-byte boundaries
+        const int xa = (x0 - hh) & ~(VEC - 1);
+        const int nchunk = (x0 + tw + hh - xa + VEC - 1) / VEC;
+        // q / nchunk by multiply-shift, exact for every q < 46 * nchunk and nchunk <= 39
+        const unsigned inv_nchunk = (65536u + nchunk - 1) / nchunk;
+        const int nq = vec_ok ? srows * nchunk : 0;
+        // this thread's first two chunks are read before the column values
+        // are evaluated, so the two global-load latencies overlap
+        uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
+        if (tid < nq) raw0 = load_chunk<F32>(A.im, xa, nchunk, inv_nchunk, y0 - hh, tid);
+        if (tid + DT_NT < nq) raw1 = load_chunk<F32>(A.im, xa, nchunk, inv_nchunk, y0 - hh, tid + DT_NT);
+
+        // spline values of node rows jlo.. at every staged column in use,
+        // one (node row, column) pair per thread
+        const int ncol = chi - clo;
+        for (int q = tid; q < nj * ncol; q += DT_NT) {
+            const int jj = q / ncol, c = clo + q - jj * ncol;
+            const int gx = mirror_fast(x0 - XHALO + c, W);
+            const AxCoef cx = axis_coef(A.sb.ax, (float)gx);
+            const float2 b = row_eval(A.sb, jlo + jj, cx);
+            const float2 r = row_eval(A.sr, jlo + jj, cx);
+            S.u.col.ub[jj * SW + c] = b.x; S.u.col.wb[jj * SW + c] = b.y;
+            S.u.col.ur[jj * SW + c] = r.x; S.u.col.wr[jj * SW + c] = r.y;
+        }
+        __syncthreads();
+
         if (vec_ok) {
-            // 16-byte chunks covering [x0 - hh, x0 + tw + hh), stored with
-            // 16-byte shared stores (frame column x0 - XHALO is chunk aligned)
-            const int xa = (x0 - hh) & ~(VEC - 1);
-            const int nchunk = (x0 + tw + hh - xa + VEC - 1) / VEC;
-            // q / nchunk by multiply-shift, exact for every q < 46 * nchunk and nchunk <= 20
-            const unsigned inv_nchunk = (65536u + nchunk - 1) / nchunk;
-            // nchunk <= 20 chunks per row: a warp takes one or two rows' chunks
-            for (int q = tid; q < srows * nchunk; q += DT_NT) {
-                const int ry = (int)(((unsigned)q * inv_nchunk) >> 16), ch = q - ry * nchunk;
-                const int gy = y0 - hh + ry;
-                const int gx0 = xa + ch * VEC;
-                float v[VEC];
-                if (gx0 + VEC <= W) {
-                    if (F32) {
-                        const float4 w = __ldg(reinterpret_cast<const float4*>(
-                            reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx0));
-                        v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
-                    } else {
-                        const uint4 w = __ldg(reinterpret_cast<const uint4*>(
-                            reinterpret_cast<const uint16_t*>(A.im.data) + (int64_t)gy * A.im.pitch + gx0));
-                        const uint32_t u4[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            v[2 * e] = (float)(u4[e] & 0xffffu);
-                            v[2 * e + 1] = (float)(u4[e] >> 16);
-                        }
-                    }
-                } else {
-                    // the frame's last chunk of a row may stop short of VEC pixels
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        const int gx = gx0 + e < W ? gx0 + e : W - 1;
-                        v[e] = F32 ? __ldg(reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx)
-                                   : (float)__ldg(reinterpret_cast<const uint16_t*>(A.im.data) +
-                                                  (int64_t)gy * A.im.pitch + gx);
-                    }
-                }
-                float4* dst = reinterpret_cast<float4*>(S.m + ry * SW + (gx0 - (x0 - XHALO)));
-#pragma unroll
-                for (int e = 0; e < VEC / 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-            }
-            __syncthreads();
-            // m = I - B, one staged column per lane, one row per warp at a time
-            for (int ry = warp; ry < srows; ry += DT_NT / 32)
-            for (int c = clo + lane; c < chi; c += 32) {
-                const float v = S.m[ry * SW + c];
-                const bool bad = F32 ? !isfinite(v) : false;
-                S.m[ry * SW + c] = bad ? 0.f : v - cell_bkg(S, ry, c);
-                const int py = ry - hh, px = c - XHALO;
-                if (py >= 0 && py < th && px >= 0 && px < tw)
-                    S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && A.im.sat > 0.f && v >= A.im.sat) ? 2 : 0);
-            }
+            const StageGeo g{xa, nchunk, inv_nchunk, clo, chi, hh, th, tw, x0 - XHALO};
+            if (tid < nq) stage_chunk<F32>(S, A.im.sat, g, raw0, tid);
+            if (tid + DT_NT < nq) stage_chunk<F32>(S, A.im.sat, g, raw1, tid + DT_NT);
+            for (int q = tid + 2 * DT_NT; q < nq; q += DT_NT)
+                stage_chunk<F32>(S, A.im.sat, g, load_chunk<F32>(A.im, xa, nchunk, inv_nchunk, y0 - hh, q), q);
         } else {
-            __syncthreads();
             for (int ry = warp; ry < srows; ry += DT_NT / 32)
             for (int c = clo + lane; c < chi; c += 32) {
                 const int gx = mirror_fast(x0 - XHALO + c, W), gy = mirror_fast(y0 - hh + ry, H);
@@ -444,7 +509,9 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
                     if (fabsf(F[i] - thr) <= 1e-5f * fabsf(thr)) ++nnear;
                     if (A.mask_out) A.mask_out[(int64_t)(y0 + py) * W + x0 + px] = fg ? 1 : 0;
                 }
-                S.lab[p] = fg ? p : -1;
+                // the warp holds 32 consecutive pixels of this row
+                const unsigned bits = __ballot_sync(0xffffffffu, fg);
+                if (lane == 0) S.rmask[2 * py + (px >> 5)] = bits;
             }
             if (A.nnear) {
 #pragma unroll
@@ -458,26 +525,66 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         for (int p = tid; p < TNPIX; p += DT_NT) {
             const int py = p / TX, px = p - py * TX;
             const bool fg = py < th && px < tw && A.in_mask[(int64_t)(y0 + py) * W + x0 + px] != 0;
-            S.lab[p] = fg ? p : -1;
+            const unsigned bits = __ballot_sync(0xffffffffu, fg);     // 32 consecutive pixels of row py
+            if (lane == 0) S.rmask[2 * py + (px >> 5)] = bits;
             S.pflag[p] = 0;
         }
         __syncthreads();
     }
 
-    // ---- tile-local union-find: link each pixel to its W, NW, N, NE neighbours
+    // ---- tile-local labelling on horizontal runs.  Every foreground pixel
+    // points at the first pixel of its run (the run's minimum index); only
+    // run heads take part in the union-find.  A run is united with each run
+    // of the row above that it touches (8-connectivity) at one site per
+    // contact: the first column of each vertical overlap (V), and a pixel
+    // whose only contact is diagonal (NW: the upper run ends at x - 1; NE:
+    // it starts at x + 1).  Each overlap of a lower run R and an upper run Q
+    // is one maximal interval of D & U, so V covers every overlapping pair;
+    // a diagonal pair without overlap has U[x] = 0 and D[x -/+ 1] = 0 at its
+    // contact, so NW / NE cover the rest.
     for (int p = tid; p < TNPIX; p += DT_NT) {
-        if (S.lab[p] < 0) continue;
         const int py = p / TX, px = p - py * TX;
-        if (px > 0 && S.lab[p - 1] >= 0) sunite(S.lab, p, p - 1);
-        if (py > 0) {
-            if (px > 0 && S.lab[p - TX - 1] >= 0) sunite(S.lab, p, p - TX - 1);
-            if (S.lab[p - TX] >= 0) sunite(S.lab, p, p - TX);
-            if (px + 1 < tw && S.lab[p - TX + 1] >= 0) sunite(S.lab, p, p - TX + 1);
+        const uint64_t M = row_mask(S, py);
+        int v = -1;
+        if ((M >> px) & 1ull) {
+            const uint64_t z = ~M & ((1ull << px) - 1ull);        // background pixels left of px
+            v = py * TX + (z ? 64 - __clzll((long long)z) : 0);
+        }
+        S.lab[p] = v;
+    }
+    __syncthreads();
+    {
+        const int y = tid >> 3;                 // this row against the row above
+        const int xs = (tid & 7) * 8;           // 8 of its 64 columns
+        if (y > 0 && y < th) {
+            const uint64_t D = row_mask(S, y), U = row_mask(S, y - 1);
+            const uint64_t O = D & U;
+            const uint64_t V = O & ~(O << 1);
+            const uint64_t NW = D & ~U & (U << 1) & ~(D << 1);
+            const uint64_t NE = D & ~U & (U >> 1) & ~(D >> 1);
+            uint32_t sites = (uint32_t)(((V | NW | NE) >> xs) & 0xffu);
+            while (sites) {
+                const int x = xs + __ffs(sites) - 1;
+                sites &= sites - 1;
+                const int p = y * TX + x;
+                if ((V >> x) & 1ull) sunite(S.lab, p, p - TX);
+                if ((NW >> x) & 1ull) sunite(S.lab, p, p - TX - 1);
+                if ((NE >> x) & 1ull) sunite(S.lab, p, p - TX + 1);
+            }
         }
     }
     __syncthreads();
-    for (int p = tid; p < TNPIX; p += DT_NT)
-        if (S.lab[p] >= 0) S.lab[p] = sfind(S.lab, p);
+    // roots of the run heads, then every pixel through its run head
+    for (int p = tid; p < TNPIX; p += DT_NT) {
+        const int py = p / TX, px = p - py * TX;
+        const uint64_t M = row_mask(S, py);
+        if (((M >> px) & 1ull) && (px == 0 || !((M >> (px - 1)) & 1ull))) S.lab[p] = sfind(S.lab, p);
+    }
+    __syncthreads();
+    for (int p = tid; p < TNPIX; p += DT_NT) {
+        const int l = S.lab[p];
+        if (l >= 0) S.lab[p] = S.lab[l];
+    }
     __syncthreads();
 
     // ---- compact root numbering in raster (= label) order
@@ -505,27 +612,20 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         S.r_npix[r] = 0; S.r_xmin[r] = TX; S.r_xmax[r] = -1; S.r_ymin[r] = TY; S.r_ymax[r] = -1; S.r_pidx[r] = 0;
     }
     __syncthreads();
+    // per-root size, bounding box and tile-border contact, one update per run
     for (int p = tid; p < TNPIX; p += DT_NT) {
-        // lanes of one warp that share a root combine before touching
-        // shared memory (large segments fill whole warps)
-        const int l = S.lab[p];
-        const unsigned act = __ballot_sync(0xffffffffu, l >= 0);
-        if (l < 0) continue;
-        const int r = S.u.rid[l];
         const int py = p / TX, px = p - py * TX;
-        const bool border = (px == 0 && x0 > 0) || (px == tw - 1 && x0 + tw < W) ||
+        const uint64_t M = row_mask(S, py);
+        if (!((M >> px) & 1ull) || (px > 0 && ((M >> (px - 1)) & 1ull))) continue;   // run heads only
+        const int len = __ffsll((long long)~(M >> px)) - 1;                          // M has no bit 63+1
+        const int xe = px + (len > 0 ? len : 64 - px) - 1;
+        const int r = S.u.rid[S.lab[p]];
+        const bool border = (px == 0 && x0 > 0) || (xe == tw - 1 && x0 + tw < W) ||
                             (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
-        const unsigned grp = __match_any_sync(act, r);
-        const int n = __popc(grp);
-        const int xmn = __reduce_min_sync(grp, px), xmx = __reduce_max_sync(grp, px);
-        const int ymn = __reduce_min_sync(grp, py), ymx = __reduce_max_sync(grp, py);
-        const unsigned brd = __ballot_sync(grp, border);
-        if (lane == __ffs(grp) - 1) {
-            atomicAdd(S.r_npix + r, n);
-            atomicMin(S.r_xmin + r, xmn); atomicMax(S.r_xmax + r, xmx);
-            atomicMin(S.r_ymin + r, ymn); atomicMax(S.r_ymax + r, ymx);
-            if (brd) S.r_pidx[r] = 1;
-        }
+        atomicAdd(S.r_npix + r, xe - px + 1);
+        atomicMin(S.r_xmin + r, px); atomicMax(S.r_xmax + r, xe);
+        atomicMin(S.r_ymin + r, py); atomicMax(S.r_ymax + r, py);
+        if (border) S.r_pidx[r] = 1;
     }
     __syncthreads();
 
@@ -538,9 +638,12 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         isc[e] = (r < nroots) && !S.r_pidx[r] && S.r_npix[r] >= A.minarea;
         pc += isp[e]; cc += isc[e];
     }
-    int poff = block_excl_scan(pc, S.warp_tot, &S.npieces);
-    int coff = block_excl_scan(cc, S.warp_tot, &S.ncomps);
+    // one scan of both counts (each at most MAXROOT < 2^16)
+    const int both = block_excl_scan(pc | (cc << 16), S.warp_tot, &S.npieces);
+    int poff = both & 0xffff, coff = both >> 16;
     if (tid == 0) {
+        S.ncomps = S.npieces >> 16;
+        S.npieces &= 0xffff;
         S.pbase = S.npieces ? atomicAdd(A.P.count, S.npieces) : 0;
         S.cbase = S.ncomps ? atomicAdd(A.C.count, S.ncomps) : 0;
         A.T.piece_base[tile] = S.pbase;

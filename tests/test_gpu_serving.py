@@ -251,3 +251,21 @@ def test_shutdown_with_requests_queued():
     for _ in range(8):
         s.submit(h, 20000)
     s.close()                                # finishes what is in flight, fails the rest, frees
+
+
+
+def test_strided_host_crop_matches_contiguous_copy():
+    """A request may point at a crop of a larger host frame (row pitch >
+    width); the server copies it with its pitch and gives the same results as
+    for a contiguous copy of the crop."""
+    img = make(1500, 900, 81)
+    h = pinned(img)
+    crop = h[100:700, 200:1300]
+    s = server()
+    try:
+        a = s.result(s.submit(crop, 20000, want_segmap=True))
+        b = s.result(s.submit(pinned(np.ascontiguousarray(img[100:700, 200:1300])), 20000, want_segmap=True))
+    finally:
+        s.close()
+    assert a["status"] == b["status"] == gp.GP_OK and a["n"] > 0
+    same(a, b, "strided crop")
