@@ -120,7 +120,7 @@ class ClockSampler:
 # --------------------------------------------------------------- traffic ---
 def kernel_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel (else None)."""
+    on the current sources of that kernel (else None: the kernel changed)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -129,15 +129,16 @@ def kernel_traffic(kernel, workload):
         e = d.get(kernel)
         if not e or e.get("workload") != workload:
             return None
-        src = os.path.join(ROOT, e["source"])
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        return float(e["dram_bytes_per_launch"]) if sha == e.get("source_sha1") else None
+        h = hashlib.sha1()
+        for src in e["sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        return float(e["dram_bytes_per_launch"]) if h.hexdigest() == e.get("sources_sha1") else None
     except Exception:
         return None
 
 
 STAGE_KERNEL = {"box_stats": "k_boxstats_u16", "detect_tiles": "k_detect_tile", "measure": "k_measure",
-                "tile_merge": "k_merge", "label_rank": "k_rank_place", "mesh_spline": "k_mesh_finalize"}
+                "tile_merge": "k_finalize", "label_rank": "k_rank_scan", "mesh_spline": "k_mesh_all"}
 
 
 def algorithmic_bytes(stage, cfg, cat):
