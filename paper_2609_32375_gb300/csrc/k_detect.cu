@@ -497,13 +497,24 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
             float F[ROWS_PER_THREAD];
             filter_column<KS>(S, A, px, py0, hh, F);
             int nnear = 0;
+            // the column's rms node-row values, reloaded only when the row's
+            // node interval changes (the same for the whole warp)
+            int jc = -1;
+            float ru0 = 0.f, ru1 = 0.f, rw0 = 0.f, rw1 = 0.f;
 #pragma unroll
             for (int i = 0; i < ROWS_PER_THREAD; ++i) {
                 const int py = py0 + i;
                 const int p = py * TX + px;
                 bool fg = false;
                 if (py < th && px < tw) {
-                    const float sig = cell_rms(S, py + hh, px + XHALO);
+                    const int2 j = S.rowj[py + hh];          // staged rows 0 .. th + 2 hh - 1 are set
+                    if (j.x != jc) {
+                        const int c = px + XHALO;
+                        ru0 = S.u.col.ur[j.x * SW + c]; ru1 = S.u.col.ur[j.y * SW + c];
+                        rw0 = S.u.col.wr[j.x * SW + c]; rw1 = S.u.col.wr[j.y * SW + c];
+                        jc = j.x;
+                    }
+                    const float sig = combine_row(S.rowc[py + hh], ru0, ru1, rw0, rw1);
                     const float thr = A.thresh * sig;
                     fg = (F[i] > thr) && !(S.pflag[p] & 1);
                     if (fabsf(F[i] - thr) <= 1e-5f * fabsf(thr)) ++nnear;
@@ -574,11 +585,17 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         }
     }
     __syncthreads();
-    // roots of the run heads, then every pixel through its run head
-    for (int p = tid; p < TNPIX; p += DT_NT) {
-        const int py = p / TX, px = p - py * TX;
-        const uint64_t M = row_mask(S, py);
-        if (((M >> px) & 1ull) && (px == 0 || !((M >> (px - 1)) & 1ull))) S.lab[p] = sfind(S.lab, p);
+    // roots of the run heads (thread: 8 columns of one row; heads from the
+    // row mask), then every pixel through its run head
+    {
+        const int y = tid >> 3, xs = (tid & 7) * 8;
+        const uint64_t M = row_mask(S, y);
+        uint32_t heads = (uint32_t)(((M & ~(M << 1)) >> xs) & 0xffu);
+        while (heads) {
+            const int p = y * TX + xs + __ffs(heads) - 1;
+            heads &= heads - 1;
+            S.lab[p] = sfind(S.lab, p);
+        }
     }
     __syncthreads();
     for (int p = tid; p < TNPIX; p += DT_NT) {
@@ -613,19 +630,24 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
     }
     __syncthreads();
     // per-root size, bounding box and tile-border contact, one update per run
-    for (int p = tid; p < TNPIX; p += DT_NT) {
-        const int py = p / TX, px = p - py * TX;
+    // (thread: the run heads among 8 columns of one row)
+    {
+        const int py = tid >> 3, xs = (tid & 7) * 8;
         const uint64_t M = row_mask(S, py);
-        if (!((M >> px) & 1ull) || (px > 0 && ((M >> (px - 1)) & 1ull))) continue;   // run heads only
-        const int len = __ffsll((long long)~(M >> px)) - 1;                          // M has no bit 63+1
-        const int xe = px + (len > 0 ? len : 64 - px) - 1;
-        const int r = S.u.rid[S.lab[p]];
-        const bool border = (px == 0 && x0 > 0) || (xe == tw - 1 && x0 + tw < W) ||
-                            (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
-        atomicAdd(S.r_npix + r, xe - px + 1);
-        atomicMin(S.r_xmin + r, px); atomicMax(S.r_xmax + r, xe);
-        atomicMin(S.r_ymin + r, py); atomicMax(S.r_ymax + r, py);
-        if (border) S.r_pidx[r] = 1;
+        uint32_t heads = (uint32_t)(((M & ~(M << 1)) >> xs) & 0xffu);
+        while (heads) {
+            const int px = xs + __ffs(heads) - 1;
+            heads &= heads - 1;
+            const uint64_t rest = ~(M >> px);                    // first background column at or after px
+            const int xe = rest ? px + __ffsll((long long)rest) - 2 : 63;
+            const int r = S.u.rid[S.lab[py * TX + px]];
+            const bool border = (px == 0 && x0 > 0) || (xe == tw - 1 && x0 + tw < W) ||
+                                (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
+            atomicAdd(S.r_npix + r, xe - px + 1);
+            atomicMin(S.r_xmin + r, px); atomicMax(S.r_xmax + r, xe);
+            atomicMin(S.r_ymin + r, py); atomicMax(S.r_ymax + r, py);
+            if (border) S.r_pidx[r] = 1;
+        }
     }
     __syncthreads();
 
@@ -732,13 +754,28 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         }
     }
 
-    // ---- segmentation map for the tile (coalesced rows)
-    for (int p = tid; p < TNPIX; p += DT_NT) {
-        const int py = p / TX, px = p - py * TX;
-        if (py >= th || px >= tw) continue;
-        const int l = S.lab[p];
-        const uint32_t v = l >= 0 ? (uint32_t)S.r_val[S.u.rid[l]] : 0u;
-        A.seg[(int64_t)(y0 + py) * W + x0 + px] = v;
+    // ---- segmentation map for the tile (coalesced rows; 16-byte stores when
+    // the tile is full width and rows start on 16-byte boundaries)
+    if (tw == TX && (W & 3) == 0 && ((((uintptr_t)A.seg) & 15) == 0)) {
+        for (int p4 = tid; p4 < TNPIX / 4; p4 += DT_NT) {
+            const int py = p4 / (TX / 4), px = (p4 - py * (TX / 4)) * 4;
+            if (py >= th) continue;
+            const int4 l = *reinterpret_cast<const int4*>(S.lab + py * TX + px);
+            uint4 v;
+            v.x = l.x >= 0 ? (uint32_t)S.r_val[S.u.rid[l.x]] : 0u;
+            v.y = l.y >= 0 ? (uint32_t)S.r_val[S.u.rid[l.y]] : 0u;
+            v.z = l.z >= 0 ? (uint32_t)S.r_val[S.u.rid[l.z]] : 0u;
+            v.w = l.w >= 0 ? (uint32_t)S.r_val[S.u.rid[l.w]] : 0u;
+            *reinterpret_cast<uint4*>(A.seg + (int64_t)(y0 + py) * W + x0 + px) = v;
+        }
+    } else {
+        for (int p = tid; p < TNPIX; p += DT_NT) {
+            const int py = p / TX, px = p - py * TX;
+            if (py >= th || px >= tw) continue;
+            const int l = S.lab[p];
+            const uint32_t v = l >= 0 ? (uint32_t)S.r_val[S.u.rid[l]] : 0u;
+            A.seg[(int64_t)(y0 + py) * W + x0 + px] = v;
+        }
     }
     // ---- edge records: local piece index of each edge pixel, or -1
     int16_t* ed = A.T.edges + (int64_t)tile * EDGE_PER_TILE;
