@@ -315,6 +315,8 @@ struct BoxArgs {
     double* rms;
     int* valid;
     float* quant;
+    int* fb_list;     // uint16 boxes the windowed histogram could not finish (appended), or
+    int* fb_count;    // for the full-histogram kernel, the list it works through; null: every box
 };
 
 // mesh fill, median filter and spline tables in shared memory (k_mesh_all)

@@ -195,6 +195,7 @@ struct FrameWork {
     SplineWork sw;
     float4 *tab_b, *tab_r;
     float* quant;
+    int* fb_list;           // uint16 boxes left to the full-histogram kernel
     DetWork dw;
     SplineTab sb, sr;
 };
@@ -244,9 +245,13 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
         if (detect) nz += det_zero_ints(x.W, x.H);
         same_mesh = same_mesh && x.Mx == w[0].Mx && x.My == w[0].My;
     }
-    // ---- workspace
-    int* zero = detect ? cv.take<int>(nz) : nullptr;
-    int* zc = zero;
+    // ---- workspace: one block cleared per call holds the box-statistics
+    // fallback counts (one per frame) and the detection counters
+    const bool u16 = F[0].img.dtype == GP_U16;
+    const int64_t nz_all = 64 + nz;
+    int* zero = cv.take<int>(nz_all);
+    int* fb_count = zero;                   // [f]
+    int* zc = zero + 64;
     float *quant_all = nullptr, *norm = nullptr, *out = nullptr;
     uint16_t *feat = nullptr, *a0 = nullptr, *a1 = nullptr;
     if (learned) {
@@ -263,6 +268,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     for (int f = 0; f < n; ++f) {
         FrameWork& x = w[f];
         carve_bkg(cv, x.nbox, x.bw);
+        x.fb_list = u16 ? cv.take<int>(x.nbox) : nullptr;
         x.quant = learned ? quant_all + qoff : nullptr;
         qoff += (int64_t)5 * x.nbox;
         x.fused = mesh_fits_smem(x.Mx, x.My);
@@ -302,6 +308,10 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
         const Image im = to_image(F[f].img);
         box[f] = box_args(im, B, learned ? 3.0 : (double)P.bp.clip_k, learned ? 0 : P.bp.clip_maxiter, x.bw.bkg_raw,
                           x.bw.rms_raw, x.bw.valid, x.quant);
+        if (u16) {
+            box[f].fb_list = x.fb_list;
+            box[f].fb_count = fb_count + f;
+        }
         maxbox = std::max(maxbox, x.nbox);
         if (x.fused) {
             mesh.push_back(mesh_args(x.bw.bkg_raw, x.bw.rms_raw, x.bw.valid, x.sb.ax, x.sb.ay, P.bp.filter_size,
@@ -342,9 +352,10 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     }
 
     // ---- background: per-box statistics, mesh, spline tables
+    PL_CUDA(cudaMemsetAsync(zero, 0, (size_t)nz_all * sizeof(int), ex.st));
     const int is_f32 = F[0].img.dtype == GP_F32;
     PL_CUDA(launch_boxstats_any(box[0], d_box, n, maxbox, is_f32, ex.st));
-    ex.launches += 1;
+    ex.launches += is_f32 ? 1 : 2;
     ex.at(1);
     if (learned) {
         if (same_mesh) {
@@ -385,7 +396,6 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     }
 
     // ---- detection, segment resolution, catalog order, measurement
-    PL_CUDA(cudaMemsetAsync(zero, 0, (size_t)nz * sizeof(int), ex.st));
     for (int f = 0; f < n; ++f)
         if (F[f].nnear) PL_CUDA(cudaMemsetAsync(F[f].nnear, 0, sizeof(int), ex.st));
     PL_CUDA(launch_detect_any(det[0], d_det, n, maxtiles, ex.st));
@@ -417,7 +427,7 @@ size_t extract_workspace_bytes(int n, const int* W, const int* H, const int* cap
         nz += det_zero_ints(W[f], H[f]);
         nbox_all += (int64_t)((W[f] + mesh - 1) / mesh) * ((H[f] + mesh - 1) / mesh);
     }
-    int* zc = cv.take<int>(nz);
+    int* zc = cv.take<int>(64 + nz) + 64;
     if (learned) {
         cv.take<float>((size_t)5 * nbox_all);
         cv.take<float>((size_t)2 * n);
@@ -430,6 +440,7 @@ size_t extract_workspace_bytes(int n, const int* W, const int* H, const int* cap
         const int Mx = (W[f] + mesh - 1) / mesh, My = (H[f] + mesh - 1) / mesh;
         BkgWork b;
         carve_bkg(cv, Mx * My, b);
+        cv.take<int>((size_t)Mx * My);      // box fallback list
         if (mesh_fits_smem(Mx, My)) {
             cv.take<float4>((size_t)Mx * My);
             cv.take<float4>((size_t)Mx * My);

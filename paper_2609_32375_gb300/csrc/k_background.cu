@@ -125,10 +125,77 @@ __device__ uint32_t hist_select(const uint32_t* hist, const unsigned long long* 
     return __shfl_sync(0xffffffffu, ans, src);
 }
 
+// queries on the full 65,536-bin histogram
+struct FullHist {
+    const uint32_t* hist;
+    const unsigned long long *pc, *ps1, *ps2;
+    bool failed = false;
+    __device__ HistSums prefix(uint32_t v) { return hist_prefix(hist, pc, ps1, ps2, v); }
+    __device__ uint32_t select(unsigned long long r) { return hist_select(hist, pc, r); }
+};
+
+// Iterative k-sigma clip about the median on a histogram (one full warp):
+// the kept set is always the values in an integer range [a, b]; statistics
+// from exact integer sums, median by rank selection.
+template <class Q>
+__device__ __forceinline__ void clip_histogram(Q& q, uint32_t vmin, uint32_t vmax, double k, int maxiter, double* med_o,
+                                               double* mean_o, double* sd_o)
+{
+    uint32_t a = vmin, b = vmax;
+    HistSums lo = q.prefix(a);
+    HistSums hi = q.prefix(b + 1u);
+    unsigned long long n = hi.c - lo.c, S1 = hi.s1 - lo.s1, S2 = hi.s2 - lo.s2;
+    double med = 0, mean = 0, sd = 0;
+    for (int it = 0;; ++it) {
+        uint32_t m0 = q.select(lo.c + (n - 1) / 2);
+        uint32_t m1 = (n & 1ull) ? m0 : q.select(lo.c + n / 2);
+        med = 0.5 * ((double)m0 + (double)m1);
+        mean = (double)S1 / (double)n;
+        // population variance from exact integers: (n S2 - S1^2) / n^2
+        unsigned long long num = n * S2 - S1 * S1;
+        sd = sqrt((double)num / ((double)n * (double)n));
+        if (it >= maxiter) break;
+        double flo = med - k * sd, fhi = med + k * sd;
+        double ca = ceil(flo), cbv = floor(fhi);
+        uint32_t na = ca <= (double)a ? a : (uint32_t)ca;
+        uint32_t nbv = cbv >= (double)b ? b : (cbv < 0 ? 0u : (uint32_t)cbv);
+        if (nbv < na) { na = a; nbv = a; }   // cannot happen for k > 0 (median lies inside)
+        HistSums nlo = q.prefix(na);
+        HistSums nhi = q.prefix(nbv + 1u);
+        unsigned long long nn = nhi.c - nlo.c;
+        if (nn == n || q.failed) break;    // the kept set did not change (or the query failed)
+        a = na; b = nbv; lo = nlo; hi = nhi;
+        n = nn; S1 = nhi.s1 - nlo.s1; S2 = nhi.s2 - nlo.s2;
+    }
+    *med_o = med;
+    *mean_o = mean;
+    *sd_o = sd;
+}
+
+// rank of quantile q of n good values (features for the learned background)
+__device__ __forceinline__ unsigned long long quantile_rank(float q, uint32_t n)
+{
+    return (unsigned long long)floor((double)q * (double)(n - 1) + 0.5);
+}
+
+__device__ void boxstats_u16_box(const BoxArgs& A, int box, uint32_t* hist);
+
+// One CTA per box (or, with A.fb_list set, a persistent grid over the boxes
+// listed there): the full 65,536-bin histogram in shared memory.
 __global__ void __launch_bounds__(U16_NT, 1) k_boxstats_u16(const BoxArgs* __restrict__ batch, const __grid_constant__ BoxArgs one)
 {
     const BoxArgs& A = frame_args(batch, one);
-    if ((int)blockIdx.x >= A.nbox) return;
+    extern __shared__ uint32_t hist[];                    // U16_WORDS
+    const bool listed = A.fb_list != nullptr;
+    const int count = listed ? *A.fb_count : A.nbox;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        __syncthreads();                                  // the previous box is done with the histogram
+        boxstats_u16_box(A, listed ? A.fb_list[i] : i, hist);
+    }
+}
+
+__device__ void boxstats_u16_box(const BoxArgs& A, int box, uint32_t* hist)
+{
     const uint16_t* __restrict__ img = static_cast<const uint16_t*>(A.img);
     const int64_t pitch = A.pitch;
     const uint8_t* __restrict__ mask = A.mask;
@@ -139,12 +206,10 @@ __global__ void __launch_bounds__(U16_NT, 1) k_boxstats_u16(const BoxArgs* __res
     double* __restrict__ rms_out = A.rms;
     int* __restrict__ valid_out = A.valid;
     float* __restrict__ quant_out = A.quant;
-    extern __shared__ uint32_t hist[];                    // U16_WORDS
     __shared__ unsigned long long pc[257], ps1[257], ps2[257];
     __shared__ unsigned long long cc_s[256], cs1_s[256], cs2_s[256];
     __shared__ uint32_t red_min[32], red_max[32], red_n[32];
 
-    const int box = blockIdx.x;
     const int bi = box % Mx, bj = box / Mx;
     const int x0 = bi * B, x1 = min(x0 + B, W);
     const int y0 = bj * B, y1 = min(y0 + B, H);
@@ -291,40 +356,13 @@ __global__ void __launch_bounds__(U16_NT, 1) k_boxstats_u16(const BoxArgs* __res
     }
     __syncwarp();
 
-    // iterative clip on the histogram: the kept set is always the values in
-    // an integer range [a, b]
-    uint32_t a = vmin, b = vmax;
-    HistSums lo = hist_prefix(hist, pc, ps1, ps2, a);
-    HistSums hi = hist_prefix(hist, pc, ps1, ps2, b + 1u);
-    unsigned long long n = hi.c - lo.c, S1 = hi.s1 - lo.s1, S2 = hi.s2 - lo.s2;
-    double med = 0, mean = 0, sd = 0;
-    for (int it = 0;; ++it) {
-        uint32_t m0 = hist_select(hist, pc, lo.c + (n - 1) / 2);
-        uint32_t m1 = (n & 1ull) ? m0 : hist_select(hist, pc, lo.c + n / 2);
-        med = 0.5 * ((double)m0 + (double)m1);
-        mean = (double)S1 / (double)n;
-        // population variance from exact integers: (n S2 - S1^2) / n^2
-        unsigned long long num = n * S2 - S1 * S1;
-        sd = sqrt((double)num / ((double)n * (double)n));
-        if (it >= maxiter) break;
-        double flo = med - k * sd, fhi = med + k * sd;
-        double ca = ceil(flo), cbv = floor(fhi);
-        uint32_t na = ca <= (double)a ? a : (uint32_t)ca;
-        uint32_t nbv = cbv >= (double)b ? b : (cbv < 0 ? 0u : (uint32_t)cbv);
-        if (nbv < na) { na = a; nbv = a; }   // cannot happen for k > 0 (median lies inside)
-        HistSums nlo = hist_prefix(hist, pc, ps1, ps2, na);
-        HistSums nhi = hist_prefix(hist, pc, ps1, ps2, nbv + 1u);
-        unsigned long long nn = nhi.c - nlo.c;
-        if (nn == n) break;                // the kept set did not change
-        a = na; b = nbv; lo = nlo; hi = nhi;
-        n = nn; S1 = nhi.s1 - nlo.s1; S2 = nhi.s2 - nlo.s2;
-    }
+    FullHist fq{hist, pc, ps1, ps2};
+    double med, mean, sd;
+    clip_histogram(fq, vmin, vmax, k, maxiter, &med, &mean, &sd);
     if (quant_out) {
-        // quantiles of all good values (features for the learned background)
         const float qs[5] = {0.10f, 0.25f, 0.50f, 0.75f, 0.90f};
         for (int q = 0; q < 5; ++q) {
-            unsigned long long r = (unsigned long long)floor((double)qs[q] * (double)(ngood - 1) + 0.5);
-            uint32_t v = hist_select(hist, pc, r);
+            uint32_t v = fq.select(quantile_rank(qs[q], ngood));
             if (lane == 0) quant_out[(int64_t)q * nbox + box] = (float)v;
         }
     }
@@ -335,6 +373,338 @@ __global__ void __launch_bounds__(U16_NT, 1) k_boxstats_u16(const BoxArgs* __res
         rms_out[box] = valid ? rr : 0.0;
         valid_out[box] = valid;
     }
+}
+
+// =================================================== uint16 box, window ===
+// The same statistics from a 4,096-bin histogram of a window [w0, w0 + 4096)
+// placed around the median of a sample of the box (every 16th row), plus
+// exact count / sum / sum-of-squares aggregates of the good values below and
+// above the window.  16 KB of shared memory instead of 128 KB, so several
+// boxes run per SM.  The clip and the quantiles need exact per-value counts
+// only where they query; a query that falls outside the window (a prefix at
+// a value strictly inside (vmin, w0) or (w0 + 4096, vmax], a rank below or
+// above it) marks the box, which then goes to the full-histogram kernel.
+// Boxes finished here get bit-identical results: the same integer sums, the
+// same ranks, the same clip loop.
+constexpr int WB_NT = 256;
+constexpr int NWIN = 4096;
+constexpr int WCB = 64;                 // values per coarse bin of the window
+constexpr int NWC = NWIN / WCB;         // 64 coarse bins
+
+struct WinHist {
+    const uint32_t* win;                        // NWIN counters
+    const unsigned long long *pc, *ps1, *ps2;   // NWC + 1 prefixes; [0] = the values below the window
+    uint32_t w0, vmin, vmax;
+    unsigned long long tc, ts1, ts2;            // all good values
+    bool failed = false;
+
+    __device__ HistSums prefix(uint32_t v)
+    {
+        const int lane = threadIdx.x & 31;
+        HistSums r;
+        r.c = r.s1 = r.s2 = 0;
+        if (v <= vmin) return r;
+        if (v > vmax) { r.c = tc; r.s1 = ts1; r.s2 = ts2; return r; }
+        if (v < w0 || v > w0 + NWIN) { failed = true; return r; }
+        const uint32_t d = v - w0, cb = d / WCB;
+        r.c = pc[cb]; r.s1 = ps1[cb]; r.s2 = ps2[cb];
+        if (cb >= NWC) return r;
+        unsigned long long c = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t bin = cb * WCB + 2u * lane + e;
+            if (bin < d) {
+                const unsigned long long nb = win[bin], x = w0 + bin;
+                c += nb; s1 += nb * x; s2 += nb * x * x;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        r.c += c; r.s1 += s1; r.s2 += s2;
+        return r;
+    }
+
+    __device__ uint32_t select(unsigned long long r)
+    {
+        const int lane = threadIdx.x & 31;
+        if (r < pc[0] || r >= pc[NWC]) { failed = true; return w0; }
+        int best = -1;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int cb = 2 * lane + e;
+            if (pc[cb] <= r && pc[cb + 1] > r) best = cb;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        const int cb = best < 0 ? NWC - 1 : best;
+        const unsigned long long rem = r - pc[cb];
+        const uint32_t base = (uint32_t)cb * WCB + 2u * lane;
+        const uint32_t n0 = win[base], n1 = win[base + 1];
+        const uint32_t tot = n0 + n1;
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t excl = incl - tot;
+        const bool mine = (excl <= rem) && (rem < incl);
+        const uint32_t ans = w0 + base + ((rem < (unsigned long long)excl + n0) ? 0u : 1u);
+        const unsigned ball = __ballot_sync(0xffffffffu, mine);
+        const int src = ball ? (__ffs(ball) - 1) : 0;
+        return __shfl_sync(0xffffffffu, ans, src);
+    }
+};
+
+__global__ void __launch_bounds__(WB_NT, 4) k_boxstats_win(const BoxArgs* __restrict__ batch,
+                                                        const __grid_constant__ BoxArgs one)
+{
+    const BoxArgs& A = frame_args(batch, one);
+    const int box = blockIdx.x;
+    if (box >= A.nbox) return;
+    const uint16_t* __restrict__ img = static_cast<const uint16_t*>(A.img);
+    const int64_t pitch = A.pitch;
+    const uint8_t* __restrict__ mask = A.mask;
+    const int W = A.W, H = A.H, B = A.B, Mx = A.Mx, nbox = A.nbox;
+    __shared__ uint32_t win[NWIN];
+    __shared__ uint32_t samp[256];
+    __shared__ unsigned long long pc[NWC + 1], ps1[NWC + 1], ps2[NWC + 1];
+    __shared__ unsigned long long cc_s[NWC], cs1_s[NWC], cs2_s[NWC];
+    __shared__ unsigned long long red64[6][WB_NT / 32];
+    __shared__ uint32_t red_min[WB_NT / 32], red_max[WB_NT / 32], red_n[WB_NT / 32];
+    __shared__ uint32_t s_w0;
+
+    const int bi = box % Mx, bj = box / Mx;
+    const int x0 = bi * B, x1 = min(x0 + B, W);
+    const int y0 = bj * B, y1 = min(y0 + B, H);
+    const int bw = x1 - x0, bh = y1 - y0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cpr = (bw + 7) >> 3;              // 8-pixel chunks per row
+    const bool vec = ((((uintptr_t)img) & 15) == 0) && ((pitch & 7) == 0) && ((x0 & 7) == 0) && ((bw & 7) == 0) &&
+                     !mask;
+
+    for (int w = tid; w < NWIN; w += WB_NT) win[w] = 0u;
+    samp[tid] = 0u;
+    __syncthreads();
+
+    // ---- sample (every 16th row): median coarse value -> window
+    {
+        const int srow = (bh + 15) >> 4;
+        for (int c = tid; c < srow * cpr; c += WB_NT) {
+            const int ry = (c / cpr) * 16, rc = c - (c / cpr) * cpr;
+            const int y = y0 + ry, xs = x0 + rc * 8;
+            const uint16_t* row = img + (int64_t)y * pitch;
+            if (vec) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + xs));
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    atomicAdd(&samp[(w4[e] & 0xffffu) >> 8], 1u);
+                    atomicAdd(&samp[w4[e] >> 24], 1u);
+                }
+            } else {
+                const int nv = min(8, x1 - xs);
+                for (int e = 0; e < nv; ++e) {
+                    if (mask && mask[(int64_t)y * W + xs + e]) continue;
+                    atomicAdd(&samp[__ldg(row + xs + e) >> 8], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // coarse bin holding the sample median (8 bins per lane)
+        uint32_t cnt[8], tot = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { cnt[q] = samp[lane * 8 + q]; tot += cnt[q]; }
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t ns = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t rank = ns ? (ns - 1) / 2 : 0;
+        uint32_t acc = incl - tot;
+        int cb = -1;
+        for (int q = 0; q < 8; ++q) {
+            if (cb < 0 && rank < acc + cnt[q]) cb = lane * 8 + q;
+            acc += cnt[q];
+        }
+        const bool mine = ns && cb >= 0 && (incl - tot) <= rank && rank < incl;
+        const unsigned ball = __ballot_sync(0xffffffffu, mine);
+        const int mcb = ball ? __shfl_sync(0xffffffffu, cb, __ffs(ball) - 1) : 0;
+        if (lane == 0) {
+            const int c = mcb * 256 + 128 - NWIN / 2;
+            s_w0 = (uint32_t)(c < 0 ? 0 : (c > 65536 - NWIN ? 65536 - NWIN : c));
+        }
+    }
+    __syncthreads();
+    const uint32_t w0 = s_w0;
+
+    // ---- window histogram, aggregates outside it, range and count
+    uint32_t vmin = 0xffffffffu, vmax = 0u, ngood = 0u;
+    uint32_t lc = 0, ls1 = 0, hc = 0, hs1 = 0;
+    unsigned long long ls2 = 0, hs2 = 0;
+    auto count = [&](uint32_t u) {
+        vmin = min(vmin, u);
+        vmax = max(vmax, u);
+        ++ngood;
+        const uint32_t d = u - w0;
+        if (d < (uint32_t)NWIN) {
+            atomicAdd(&win[d], 1u);
+        } else if (u < w0) {
+            ++lc; ls1 += u; ls2 += (unsigned long long)u * u;
+        } else {
+            ++hc; hs1 += u; hs2 += (unsigned long long)u * u;
+        }
+    };
+    const int nchunks = cpr * bh;
+    if (vec) {
+        constexpr int U = 4;
+        for (int c0 = tid; c0 < nchunks; c0 += U * WB_NT) {
+            uint4 q[U];
+#pragma unroll
+            for (int kk = 0; kk < U; ++kk) {
+                const int c = c0 + kk * WB_NT;
+                if (c < nchunks) {
+                    const int ry = c / cpr, rc = c - ry * cpr;
+                    q[kk] = __ldg(reinterpret_cast<const uint4*>(img + (int64_t)(y0 + ry) * pitch + x0 + rc * 8));
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < U; ++kk) {
+                if (c0 + kk * WB_NT >= nchunks) break;
+                const uint32_t w4[4] = {q[kk].x, q[kk].y, q[kk].z, q[kk].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    count(w4[e] & 0xffffu);
+                    count(w4[e] >> 16);
+                }
+            }
+        }
+    } else {
+        for (int c = tid; c < nchunks; c += WB_NT) {
+            const int ry = c / cpr, rc = c - ry * cpr;
+            const int y = y0 + ry, xs = x0 + rc * 8;
+            const uint16_t* row = img + (int64_t)y * pitch;
+            const int nv = min(8, x1 - xs);
+            for (int e = 0; e < nv; ++e) {
+                if (mask && mask[(int64_t)y * W + xs + e]) continue;
+                count(__ldg(row + xs + e));
+            }
+        }
+    }
+    unsigned long long agg[6] = {lc, ls1, ls2, hc, hs1, hs2};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        ngood += __shfl_xor_sync(0xffffffffu, ngood, o);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) agg[j] += __shfl_xor_sync(0xffffffffu, agg[j], o);
+    }
+    if (lane == 0) {
+        red_min[warp] = vmin; red_max[warp] = vmax; red_n[warp] = ngood;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) red64[j][warp] = agg[j];
+    }
+    __syncthreads();
+    vmin = 0xffffffffu; vmax = 0u; ngood = 0u;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) agg[j] = 0;
+    for (int w = 0; w < WB_NT / 32; ++w) {
+        vmin = min(vmin, red_min[w]); vmax = max(vmax, red_max[w]); ngood += red_n[w];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) agg[j] += red64[j][w];
+    }
+    const bool valid = ngood > 0 && 2u * ngood >= (uint32_t)(bw * bh);
+    if (ngood == 0 || vmin == vmax) {
+        // empty or constant box: statistics are immediate (as in the full kernel)
+        if (tid == 0) {
+            double med = ngood ? (double)vmin : 0.0;
+            double b, r;
+            box_result(med, med, 0.0, &b, &r);
+            A.bkg[box] = valid ? b : 0.0;
+            A.rms[box] = valid ? r : 0.0;
+            A.valid[box] = valid;
+            if (A.quant)
+                for (int q = 0; q < 5; ++q) A.quant[(int64_t)q * nbox + box] = (float)med;
+        }
+        return;
+    }
+
+    // ---- coarse summaries of the window (64 bins of 64 values)
+    for (int cb = warp; cb < NWC; cb += WB_NT / 32) {
+        unsigned long long c = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t bin = cb * WCB + 2u * lane + e;
+            const unsigned long long nb = win[bin], x = w0 + bin;
+            c += nb; s1 += nb * x; s2 += nb * x * x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) { cc_s[cb] = c; cs1_s[cb] = s1; cs2_s[cb] = s2; }
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    {
+        // prefixes over the coarse bins, starting from the values below the window
+        unsigned long long c[2], s1[2], s2[2], tc = 0, t1 = 0, t2 = 0;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            c[e] = cc_s[2 * lane + e]; s1[e] = cs1_s[2 * lane + e]; s2[e] = cs2_s[2 * lane + e];
+            tc += c[e]; t1 += s1[e]; t2 += s2[e];
+        }
+        unsigned long long ic = tc, i1 = t1, i2 = t2;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long a0 = __shfl_up_sync(0xffffffffu, ic, o);
+            const unsigned long long a1 = __shfl_up_sync(0xffffffffu, i1, o);
+            const unsigned long long a2 = __shfl_up_sync(0xffffffffu, i2, o);
+            if (lane >= o) { ic += a0; i1 += a1; i2 += a2; }
+        }
+        unsigned long long ec = agg[0] + ic - tc, e1 = agg[1] + i1 - t1, e2 = agg[2] + i2 - t2;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            pc[2 * lane + e] = ec; ps1[2 * lane + e] = e1; ps2[2 * lane + e] = e2;
+            ec += c[e]; e1 += s1[e]; e2 += s2[e];
+        }
+        if (lane == 31) { pc[NWC] = ec; ps1[NWC] = e1; ps2[NWC] = e2; }
+    }
+    __syncwarp();
+    WinHist wq;
+    wq.win = win; wq.pc = pc; wq.ps1 = ps1; wq.ps2 = ps2;
+    wq.w0 = w0; wq.vmin = vmin; wq.vmax = vmax;
+    wq.tc = pc[NWC] + agg[3]; wq.ts1 = ps1[NWC] + agg[4]; wq.ts2 = ps2[NWC] + agg[5];
+    double med, mean, sd;
+    clip_histogram(wq, vmin, vmax, A.k, A.maxiter, &med, &mean, &sd);
+    float qv[5];
+    if (A.quant && !wq.failed) {
+        const float qs[5] = {0.10f, 0.25f, 0.50f, 0.75f, 0.90f};
+        for (int q = 0; q < 5; ++q) qv[q] = (float)wq.select(quantile_rank(qs[q], ngood));
+    }
+    if (lane != 0) return;
+    if (wq.failed) {
+        A.fb_list[atomicAdd(A.fb_count, 1)] = box;
+        return;
+    }
+    if (A.quant)
+        for (int q = 0; q < 5; ++q) A.quant[(int64_t)q * nbox + box] = qv[q];
+    double bb, rr;
+    box_result(med, mean, sd, &bb, &rr);
+    A.bkg[box] = valid ? bb : 0.0;
+    A.rms[box] = valid ? rr : 0.0;
+    A.valid[box] = valid;
 }
 
 // ============================================================ float32 box ===
@@ -865,6 +1235,7 @@ BoxArgs box_args(const Image& im, int B, double k, int maxiter, double* bkg, dou
     a.npad = npad;
     a.k = k; a.maxiter = maxiter;
     a.bkg = bkg; a.rms = rms; a.valid = valid; a.quant = quant;
+    a.fb_list = nullptr; a.fb_count = nullptr;
     return a;
 }
 
@@ -874,6 +1245,15 @@ cudaError_t launch_boxstats_any(const BoxArgs& one, const BoxArgs* batch, int nf
                                 cudaStream_t st)
 {
     dim3 grid(maxbox, nframes);
+    if (!is_f32 && one.fb_list) {
+        // windowed histograms, then the full histogram for the boxes they
+        // could not finish (a persistent grid over the fallback lists)
+        k_boxstats_win<<<grid, WB_NT, 0, st>>>(batch, one);
+        const size_t smem = U16_WORDS * sizeof(uint32_t);
+        cudaFuncSetAttribute(k_boxstats_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_boxstats_u16<<<dim3(maxbox < 152 ? maxbox : 152, nframes), U16_NT, smem, st>>>(batch, one);
+        return cudaGetLastError();
+    }
     if (!is_f32) {
         const size_t smem = U16_WORDS * sizeof(uint32_t);
         cudaFuncSetAttribute(k_boxstats_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

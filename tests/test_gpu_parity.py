@@ -79,6 +79,44 @@ def test_background_with_mask_and_nan(ctx):
     assert_close("rms_mesh", out["rms_mesh"].cpu().numpy(), rm, np.abs(rm) + 1e-6)
 
 
+def test_background_windowed_histogram_fallback(ctx):
+    """uint16 boxes whose clip the 4,096-value window cannot serve go to the
+    full histogram: in half of the boxes every 16th row (the rows the window
+    is placed from) is bright, so the window sits far from the true median;
+    the other boxes finish in the window, others again hold a wide range.
+    All must match the oracle."""
+    rng = np.random.default_rng(17)
+    H, W, B = 512, 640, 128
+    img = rng.poisson(1000.0, (H, W)).astype(np.float64)
+    for bj in range(H // B):
+        for bi in range(W // B):
+            y0, x0 = bj * B, bi * B
+            if (bi + bj) % 2 == 0:
+                img[y0:y0 + B:16, x0:x0 + B] = rng.normal(40000.0, 30.0, (B // 16, B))
+            if (bi, bj) == (1, 0):
+                img[y0:y0 + B, x0:x0 + B] += rng.uniform(0, 20000, (B, B))      # wider than the window
+    img = np.clip(np.round(img), 0, 65535).astype(np.uint16)
+    vals, bad = oracle.pixel_values(img)
+    bm, rm, st = oracle.background_meshes(vals, bad, B)
+    out = ctx.gp_background(dev(img), B)
+    ctx.sync()
+    assert_close("bkg_mesh", out["bkg_mesh"].cpu().numpy(), bm, np.abs(bm) + 1e-6)
+    assert_close("rms_mesh", out["rms_mesh"].cpu().numpy(), rm, np.abs(rm) + 1e-6)
+    # The learned background takes its quantiles from the same windowed
+    # histograms (with the same fallback); gp_box_quantiles always uses the
+    # full histogram.  The network fed by either must give identical meshes.
+    from paper_2609_32375_gb300 import learned
+    net = learned.Network(seed=2)
+    t = dev(img)
+    a = learned.background_learned(ctx, t, B, net)
+    q = learned.box_quantiles(ctx, t, B)
+    feat, norm = learned.features(q[None])
+    _, outp = net.forward(feat)
+    bb, rr = learned.denorm(outp, norm)
+    ctx.sync()
+    assert torch.equal(a["bkg_mesh"], bb[0]) and torch.equal(a["rms_mesh"], rr[0])
+
+
 # -------------------------------------------------------------- labelling ---
 def random_masks():
     rng = np.random.default_rng(11)
