@@ -377,6 +377,7 @@ struct ApSpec {
     float r[MAX_NR];
     float rmax;
     float gain;
+    double inv_gain;    // 1 / gain (0 when gain <= 0): Poisson variance F / gain as a product
 };
 
 // catalog rows and apertures (k_measure)

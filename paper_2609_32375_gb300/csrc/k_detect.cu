@@ -178,20 +178,35 @@ __device__ __forceinline__ void mom_warp_reduce(MomAcc& a)
 __device__ __forceinline__ float2 df2(DF d) { return make_float2(d.hi, d.lo); }
 
 // finished moments of a whole segment from sums about the origin (X0, Y0)
+// 1 / x for x > 0: a float32 estimate refined by two float64 Newton steps
+// (error within an ulp of the float64 quotient), because a float64 division
+// is a long sequence on a float64 pipe that runs at a small fraction of the
+// float32 rate; x outside float32's range takes the division
+__device__ __forceinline__ double recip_pos(double x)
+{
+    const float xf = (float)x;
+    if (!(xf > 1e-37f) || !(xf < 1e37f)) return 1.0 / x;
+    double r = (double)(1.0f / xf);
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
 __device__ void mom_finish(double S, double Sx, double Sy, double Sxx, double Syy, double Sxy, long long ux,
                            long long uy, long long uxx, long long uyy, long long uxy, int npix, int X0, int Y0,
                            double* flux, double2* xy, Mom2* m2, uint32_t* flags)
 {
     *flux = S;
     if (S > 0.0) {
-        const double mx = Sx / S, my = Sy / S;
+        const double iS = recip_pos(S);
+        const double mx = Sx * iS, my = Sy * iS;
         *xy = make_double2(X0 + mx, Y0 + my);
-        *m2 = mom2_make(Sxx / S - mx * mx, Syy / S - my * my, Sxy / S - mx * my, 0.0);
+        *m2 = mom2_make(Sxx * iS - mx * mx, Syy * iS - my * my, Sxy * iS - mx * my, 0.0);
     } else {
-        const double n = (double)npix;
-        const double mx = (double)ux / n, my = (double)uy / n;
+        const double in = recip_pos((double)npix);
+        const double mx = (double)ux * in, my = (double)uy * in;
         *xy = make_double2(X0 + mx, Y0 + my);
-        *m2 = mom2_make((double)uxx / n - mx * mx, (double)uyy / n - my * my, (double)uxy / n - mx * my, 0.0);
+        *m2 = mom2_make((double)uxx * in - mx * mx, (double)uyy * in - my * my, (double)uxy * in - mx * my, 0.0);
         *flags |= GP_FLAG_CENTROID_FALLBACK;
     }
 }

@@ -24,6 +24,7 @@ static ApSpec make_ap(const float* radii, int nr, float gain)
         if (k < nr) s.rmax = fmaxf(s.rmax, radii[k]);
     }
     s.gain = gain;
+    s.inv_gain = gain > 0.f ? 1.0 / (double)gain : 0.0;
     return s;
 }
 

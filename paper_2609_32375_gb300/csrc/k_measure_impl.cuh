@@ -207,6 +207,12 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
         }
     }
     flush_queue<NR>(ap, wq, qn, f, v, fl);
+    // Warp sums of every radius (all lanes hold them after the butterflies);
+    // then lane k finishes radius k, so the float64 steps issue once for all
+    // radii (float64 runs at a small fraction of the float32 rate).
+    DF my_f = df_zero(), my_v = df_zero();
+    uint32_t my_fl = 0u;
+    float my_r = 0.f;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const DF fs = df_warp_sum(f[k]);
@@ -214,16 +220,28 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
         uint32_t ff = fl[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ff |= __shfl_xor_sync(0xffffffffu, ff, o);
-        if (lane == 0) {
-            const double r = ap.r[k];
-            if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) ff |= GP_FLAG_TRUNCATED;
-            const double F = df_value(fs);
-            double V = df_value(vs);
-            if (ap.gain > 0.f && F > 0.0) V += F / (double)ap.gain;
-            flux[k] = F;
-            ferr[k] = sqrt(fmax(V, 0.0));
-            aflags[k] = ff;
+        if (lane == k) { my_f = fs; my_v = vs; my_fl = ff; my_r = ap.r[k]; }
+    }
+    if (lane < NR) {
+        const double r = my_r;
+        if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) my_fl |= GP_FLAG_TRUNCATED;
+        const double F = df_value(my_f);
+        double V = df_value(my_v);
+        if (ap.gain > 0.f && F > 0.0) V = fma(F, ap.inv_gain, V);
+        // sqrt(V): a float32 estimate s0, then one Newton step in float64,
+        // s0 + (V - s0^2) / (2 s0); the step is ~1e-7 s0, so a float32
+        // reciprocal leaves ~1e-14 relative error
+        double e = 0.0;
+        if (V > 0.0) {
+            const float s0f = sqrtf((float)V);
+            if (s0f > 0.f) {
+                const double s0 = (double)s0f;
+                e = fma(fma(-s0, s0, V), (double)(0.5f / s0f), s0);
+            }
         }
+        flux[lane] = F;
+        ferr[lane] = e;
+        aflags[lane] = my_fl;
     }
 }
 
