@@ -31,7 +31,8 @@ CAPACITY = 400_000
 
 
 def env_rank():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    from paper_2609_32375_gb300 import replicas
+    return replicas.rank_env()
 
 
 def workload_config(cfg):
@@ -163,9 +164,13 @@ def run_reference(args):
     import synth
     rank, world, _ = env_rank()
     if rank != 0:
-        return 0
+        return 0                  # the oracle runs on rank 0 alone; the other ranks exit without work
     cfg = synth.CONFIGS[args.workload]
+    if args.size:
+        w, h = (int(v) for v in args.size.lower().split("x"))
+        cfg = synth.scaled_config(cfg, w, h)
     img, _ = synth.make_frame(cfg, 0)
+    args.ref_crop = min(args.ref_crop, img.shape[0], img.shape[1])
     times = []
     desc = ""
     mpix = 0.0
@@ -321,18 +326,17 @@ def run_gpu(args):
     import paper_2609_32375_gb300 as gp
     import synth
 
-    rank, world, local = env_rank()
+    from paper_2609_32375_gb300 import replicas
+
+    rank, world, local = replicas.rank_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    dist = replicas.init(world, "nccl", dev)
     cfg = synth.CONFIGS[args.workload]
     if args.size:
         w, h = (int(v) for v in args.size.lower().split("x"))
         cfg = synth.scaled_config(cfg, w, h)
-    img, _ = synth.make_frame(cfg, rank)          # one independent frame per rank
+    img, _ = synth.make_frame(cfg, replicas.frame_seed(rank))     # one independent frame per rank
     H, W = img.shape
     t_img = torch.from_numpy(img).to(dev)
     L = gp.load_library()
@@ -351,8 +355,7 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
@@ -364,21 +367,17 @@ def run_gpu(args):
         ev[i][1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     clk = clocks.stop()
     ctx.sync()
     stats = ctx.stats()
     ctx.set_timing(False)
     total_ms = t0.elapsed_time(t1)
     step_ms = sorted(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
     mpix_all = W * H * world / 1e6
-    value = mpix_all / (ms_per_step / 1e3)
+    value = replicas.job_rate(W * H / 1e6, world, ms_per_step / 1e3)
 
     # ---- end to end from pinned host memory: (a) through the request server,
     # whose slots overlap one frame's copies with another's kernels (the
@@ -394,8 +393,7 @@ def run_gpu(args):
         assert r["status"] == 0 and r["n"] == nsrc, "server result differs from the device-resident run"
     srv.stats(reset=True)
     ne2e = args.e2e_steps or args.steps
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     s0 = time.perf_counter()
     tickets = [srv.submit(h_frame, CAPACITY) for _ in range(ne2e)]
     for tk in tickets:
@@ -405,10 +403,7 @@ def run_gpu(args):
     srv_ms = (time.perf_counter() - s0) * 1e3 / ne2e
     srv_rep = srv.stats()
     srv.close()
-    if dist:
-        t = torch.tensor([srv_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        srv_ms = float(t.item())
+    srv_ms = replicas.max_over_ranks(srv_ms, dist, dev)
     ncopy = min(nsrc, CAPACITY)
     nr = len(cfg.radii)
     cat_cols = [v for k, v in ex.out["catalog"].items() if k != "n"]
@@ -431,8 +426,7 @@ def run_gpu(args):
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()
     torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -440,11 +434,7 @@ def run_gpu(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / ne2e
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(e0.elapsed_time(e1) / ne2e, dist, dev)
     assert int(h_n.item()) == nsrc, "end-to-end run gave a different segment count"
 
     # ---- roofline of the dominant kernel (live stage times over the timed region)
@@ -527,9 +517,7 @@ def run_gpu(args):
                                 "seconds": round(t, 2)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    replicas.finish(dist)
     ctx.close()
     return 0
 
