@@ -8,6 +8,38 @@
 
 namespace gp {
 
+// --------------------------------------------------- float64 reciprocals ---
+// Float64 runs at a small fraction of the float32 rate on this GPU, and a
+// float64 division or square root is a long instruction sequence.  These
+// start from a float32 estimate and refine it with float64 Newton steps
+// (two: within an ulp of the float64 result); arguments outside float32's
+// range take the plain operation.
+
+// 1 / x for x > 0
+__device__ __forceinline__ double recip_pos(double x)
+{
+    const float xf = (float)x;
+    if (!(xf > 1e-37f) || !(xf < 1e37f)) return 1.0 / x;
+    double r = (double)(1.0f / xf);
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
+// sqrt(v) for v >= 0: s <- s + (v - s^2) / (2 s), with 1 / (2 s) taken
+// once in float32 (the steps are tiny, so its error is squared away)
+__device__ __forceinline__ double sqrt_pos(double v)
+{
+    const float vf = (float)v;
+    if (!(vf > 1e-37f) || !(vf < 1e37f)) return v > 0.0 ? sqrt(v) : 0.0;
+    const float s0f = sqrtf(vf);
+    const double h = (double)(0.5f / s0f);
+    double s = (double)s0f;
+    s = fma(fma(-s, s, v), h, s);
+    s = fma(fma(-s, s, v), h, s);
+    return s;
+}
+
 // ------------------------------------------------------------ constants ---
 constexpr int TX = 64;           // detection tile width  (pixels)
 constexpr int TY = 32;           // detection tile height

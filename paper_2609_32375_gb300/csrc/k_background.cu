@@ -29,7 +29,7 @@ namespace gp {
 __device__ __forceinline__ void box_result(double med, double mean, double sd, double* bkg, double* rms)
 {
     double b;
-    if (sd == 0.0 || fabs(mean - med) / sd > 0.3)
+    if (sd == 0.0 || fabs(mean - med) > 0.3 * sd)
         b = med;
     else
         b = 2.5 * med - 1.5 * mean;
@@ -150,10 +150,11 @@ __device__ __forceinline__ void clip_histogram(Q& q, uint32_t vmin, uint32_t vma
         uint32_t m0 = q.select(lo.c + (n - 1) / 2);
         uint32_t m1 = (n & 1ull) ? m0 : q.select(lo.c + n / 2);
         med = 0.5 * ((double)m0 + (double)m1);
-        mean = (double)S1 / (double)n;
+        const double in = recip_pos((double)n);
+        mean = (double)S1 * in;
         // population variance from exact integers: (n S2 - S1^2) / n^2
         unsigned long long num = n * S2 - S1 * S1;
-        sd = sqrt((double)num / ((double)n * (double)n));
+        sd = sqrt_pos((double)num) * in;
         if (it >= maxiter) break;
         double flo = med - k * sd, fhi = med + k * sd;
         double ca = ceil(flo), cbv = floor(fhi);
@@ -638,22 +639,29 @@ __global__ void __launch_bounds__(WB_NT, 4) k_boxstats_win(const BoxArgs* __rest
         return;
     }
 
-    // ---- coarse summaries of the window (64 bins of 64 values)
+    // ---- coarse summaries of the window (64 bins of 64 values).  Within a
+    // coarse bin the count n, sum n d and sum n d^2 of the offsets d < 64
+    // from its first value fit 32 bits (n <= 65,536); the sums of v and v^2
+    // follow from them exactly in 64 bits.
     for (int cb = warp; cb < NWC; cb += WB_NT / 32) {
-        unsigned long long c = 0, s1 = 0, s2 = 0;
+        uint32_t c = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const uint32_t bin = cb * WCB + 2u * lane + e;
-            const unsigned long long nb = win[bin], x = w0 + bin;
-            c += nb; s1 += nb * x; s2 += nb * x * x;
+            const uint32_t d = 2u * lane + e, nb = win[cb * WCB + d];
+            c += nb; d1 += nb * d; d2 += nb * d * d;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             c += __shfl_xor_sync(0xffffffffu, c, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
         }
-        if (lane == 0) { cc_s[cb] = c; cs1_s[cb] = s1; cs2_s[cb] = s2; }
+        if (lane == 0) {
+            const unsigned long long base = w0 + (uint32_t)cb * WCB;
+            cc_s[cb] = c;
+            cs1_s[cb] = base * c + d1;
+            cs2_s[cb] = base * base * c + 2ull * base * d1 + d2;
+        }
     }
     __syncthreads();
     if (warp != 0) return;

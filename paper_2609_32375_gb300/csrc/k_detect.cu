@@ -178,20 +178,6 @@ __device__ __forceinline__ void mom_warp_reduce(MomAcc& a)
 __device__ __forceinline__ float2 df2(DF d) { return make_float2(d.hi, d.lo); }
 
 // finished moments of a whole segment from sums about the origin (X0, Y0)
-// 1 / x for x > 0: a float32 estimate refined by two float64 Newton steps
-// (error within an ulp of the float64 quotient), because a float64 division
-// is a long sequence on a float64 pipe that runs at a small fraction of the
-// float32 rate; x outside float32's range takes the division
-__device__ __forceinline__ double recip_pos(double x)
-{
-    const float xf = (float)x;
-    if (!(xf > 1e-37f) || !(xf < 1e37f)) return 1.0 / x;
-    double r = (double)(1.0f / xf);
-    r = fma(r, fma(-x, r, 1.0), r);
-    r = fma(r, fma(-x, r, 1.0), r);
-    return r;
-}
-
 __device__ void mom_finish(double S, double Sx, double Sy, double Sxx, double Syy, double Sxy, long long ux,
                            long long uy, long long uxx, long long uyy, long long uxy, int npix, int X0, int Y0,
                            double* flux, double2* xy, Mom2* m2, uint32_t* flags)
