@@ -1143,7 +1143,40 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__
         }
         // median filter (window clipped at the mesh edge) -> float meshes
         const int h = fsize / 2;
-        for (int t = tid; t < 2 * n; t += MA_NT) {
+        for (int t = tid; t < 2 * n && fsize == 3; t += MA_NT) {
+            // 3 x 3: the window in registers (absent cells +inf), sorted by
+            // odd-even transposition; the same order statistics as below
+            const int map = t / n, b = t - map * n;
+            const int i = b % Mx, j = b / Mx;
+            const float* src = map ? A1 : A0;
+            float w[9];
+            int c = 0;
+#pragma unroll
+            for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+                for (int di = -1; di <= 1; ++di) {
+                    const int ii = i + di, jj = j + dj;
+                    const bool in = ii >= 0 && ii < Mx && jj >= 0 && jj < My;
+                    w[(dj + 1) * 3 + di + 1] = in ? src[jj * Mx + ii] : INFINITY;
+                    c += in ? 1 : 0;
+                }
+#pragma unroll
+            for (int pass = 0; pass < 9; ++pass)
+#pragma unroll
+                for (int q = pass & 1; q + 1 < 9; q += 2) {
+                    const float lo = fminf(w[q], w[q + 1]), hi = fmaxf(w[q], w[q + 1]);
+                    w[q] = lo;
+                    w[q + 1] = hi;
+                }
+            float m0 = w[0], m1 = w[0];
+#pragma unroll
+            for (int q = 1; q < 9; ++q) {
+                if (q == (c - 1) / 2) m0 = w[q];
+                if (q == c / 2) m1 = w[q];
+            }
+            (map ? rms_out : bkg_out)[b] = (c & 1) ? m1 : 0.5f * (m0 + m1);
+        }
+        for (int t = tid; t < 2 * n && fsize != 3; t += MA_NT) {
             const int map = t / n, b = t - map * n;
             const int i = b % Mx, j = b / Mx;
             const float* src = map ? A1 : A0;

@@ -1007,7 +1007,8 @@ __global__ void k_rank_count(const RankArgs* __restrict__ batch, const __grid_co
 
 constexpr int SCAN_NT = 1024;
 
-// exclusive scan of the bucket counts (one CTA); publishes the segment count
+// exclusive scan of the bucket counts (one CTA, 8 consecutive buckets per
+// thread per pass); publishes the segment count
 __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restrict__ batch,
                                                        const __grid_constant__ RankArgs one)
 {
@@ -1016,15 +1017,21 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restric
     int* n_out = R.n_out;
     const int capacity = R.capacity;
     int* status = R.status;
+    constexpr int PER = 8;
     __shared__ int wsum[SCAN_NT / 32];
-    __shared__ int carry;
+    __shared__ int carry_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < C.nb; base += SCAN_NT) {
-        const int i = base + tid;
-        const int v = i < C.nb ? C.bcnt[i] : 0;
-        int incl = v;
+    int carry = 0;
+    for (int base = 0; base < C.nb; base += SCAN_NT * PER) {
+        const int i0 = base + tid * PER;
+        int v[PER];
+        int tsum = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            v[k] = i0 + k < C.nb ? C.bcnt[i0 + k] : 0;
+            tsum += v[k];
+        }
+        int incl = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1041,13 +1048,17 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restric
                 if (lane >= o) wi += t;
             }
             wsum[lane] = wi - w;
+            if (lane == 31) carry_s = wi;                 // this pass's total
         }
         __syncthreads();
-        const int excl = carry + wsum[warp] + incl - v;
-        if (i < C.nb) C.boff[i] = excl;
-        __syncthreads();
-        if (tid == SCAN_NT - 1) carry = excl + v;
-        __syncthreads();
+        int excl = carry + wsum[warp] + incl - tsum;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (i0 + k < C.nb) C.boff[i0 + k] = excl;
+            excl += v[k];
+        }
+        carry += carry_s;
+        __syncthreads();                                  // wsum and carry_s are reused
     }
     if (tid == 0) {
         const int total = *C.count;
