@@ -1083,34 +1083,39 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__
     float4* tab_r = MA.tab_r;
     extern __shared__ __align__(16) float sh[];
     unsigned char* sh_bytes = reinterpret_cast<unsigned char*>(sh);
+    // shared-memory rows are Ms = Mx | 1 wide (odd), so the row-direction
+    // solves, one row per lane, hit 32 different banks
     const int Mx = ax.n, My = ay.n, n = Mx * My, tid = threadIdx.x;
+    const int Ms = Mx | 1, ns = Ms * My;
     float* A0 = sh;
-    float* A1 = A0 + n;
-    float* A2 = A1 + n;
-    float* A3 = A2 + n;
-    float* A4 = A3 + n;
-    float* A5 = A4 + n;
-    int* V0 = reinterpret_cast<int*>(A5 + n);
-    int* V1 = V0 + n;
+    float* A1 = A0 + ns;
+    float* A2 = A1 + ns;
+    float* A3 = A2 + ns;
+    float* A4 = A3 + ns;
+    float* A5 = A4 + ns;
+    int* V0 = reinterpret_cast<int*>(A5 + ns);
+    int* V1 = V0 + ns;
     const int nl = Mx > My ? Mx : My;
     // the LU scratch starts at the first 16-byte boundary after V1
-    float* lu = reinterpret_cast<float*>(sh_bytes + mesh_lu_offset(n));
+    float* lu = reinterpret_cast<float*>(sh_bytes + mesh_lu_offset(ns));
     AxisLU Lx{lu, lu + nl, lu + 2 * nl, lu + 3 * nl};
     AxisLU Ly{lu + 4 * nl, lu + 5 * nl, lu + 6 * nl, lu + 7 * nl};
     __shared__ int missing, any;
 
-    if (tid == 0) factor_axis(ax, Lx);
-    if (tid == 32) factor_axis(ay, Ly);
     if (mode == 0) {
         if (tid == 0) any = 0;
         __syncthreads();
         for (int b = tid; b < n; b += MA_NT) {
-            A0[b] = (float)bkg_raw[b]; A1[b] = (float)rms_raw[b]; V0[b] = valid_raw[b];
-            if (V0[b]) any = 1;
+            const int sb_ = (b / Mx) * Ms + b % Mx;
+            A0[sb_] = (float)bkg_raw[b]; A1[sb_] = (float)rms_raw[b]; V0[sb_] = valid_raw[b];
+            if (V0[sb_]) any = 1;
         }
         __syncthreads();
         if (!any) {
-            for (int b = tid; b < n; b += MA_NT) { A0[b] = 0.f; A1[b] = 0.f; V0[b] = 1; }
+            for (int b = tid; b < n; b += MA_NT) {
+                const int sb_ = (b / Mx) * Ms + b % Mx;
+                A0[sb_] = 0.f; A1[sb_] = 0.f; V0[sb_] = 1;
+            }
             __syncthreads();
         }
         // fill invalid boxes from valid 8-neighbours, sweep after sweep
@@ -1118,30 +1123,37 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__
             if (tid == 0) missing = 0;
             __syncthreads();
             for (int b = tid; b < n; b += MA_NT) {
-                A2[b] = A0[b]; A3[b] = A1[b]; V1[b] = V0[b];
-                if (V0[b]) continue;
-                const int i = b % Mx, j = b / Mx;
+                const int i = b % Mx, j = b / Mx, sb_ = j * Ms + i;
+                A2[sb_] = A0[sb_]; A3[sb_] = A1[sb_]; V1[sb_] = V0[sb_];
+                if (V0[sb_]) continue;
                 int c = 0;
                 float sb = 0.f, sr = 0.f;
                 for (int dj = -1; dj <= 1; ++dj)
                     for (int di = -1; di <= 1; ++di) {
                         const int ii = i + di, jj = j + dj;
-                        if ((di || dj) && ii >= 0 && ii < Mx && jj >= 0 && jj < My && V0[jj * Mx + ii]) {
-                            sb += A0[jj * Mx + ii];
-                            sr += A1[jj * Mx + ii];
+                        if ((di || dj) && ii >= 0 && ii < Mx && jj >= 0 && jj < My && V0[jj * Ms + ii]) {
+                            sb += A0[jj * Ms + ii];
+                            sr += A1[jj * Ms + ii];
                             ++c;
                         }
                     }
-                if (c) { A2[b] = sb / c; A3[b] = sr / c; V1[b] = 1; }
+                if (c) { A2[sb_] = sb / c; A3[sb_] = sr / c; V1[sb_] = 1; }
                 else missing = 1;
             }
             __syncthreads();
             const bool more = missing;
-            for (int b = tid; b < n; b += MA_NT) { A0[b] = A2[b]; A1[b] = A3[b]; V0[b] = V1[b]; }
+            for (int b = tid; b < n; b += MA_NT) {
+                const int sb_ = (b / Mx) * Ms + b % Mx;
+                A0[sb_] = A2[sb_]; A1[sb_] = A3[sb_]; V0[sb_] = V1[sb_];
+            }
             __syncthreads();
             if (!more) break;
         }
-        // median filter (window clipped at the mesh edge) -> float meshes
+        // median filter (window clipped at the mesh edge) -> float meshes;
+        // meanwhile two threads factor the spline systems (first needed by
+        // the solves further down)
+        if (tid == MA_NT - 32) factor_axis(ax, Lx);
+        if (tid == MA_NT - 64) factor_axis(ay, Ly);
         const int h = fsize / 2;
         for (int t = tid; t < 2 * n && fsize == 3; t += MA_NT) {
             // 3 x 3: the window in registers (absent cells +inf), sorted by
@@ -1157,7 +1169,7 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__
                 for (int di = -1; di <= 1; ++di) {
                     const int ii = i + di, jj = j + dj;
                     const bool in = ii >= 0 && ii < Mx && jj >= 0 && jj < My;
-                    w[(dj + 1) * 3 + di + 1] = in ? src[jj * Mx + ii] : INFINITY;
+                    w[(dj + 1) * 3 + di + 1] = in ? src[jj * Ms + ii] : INFINITY;
                     c += in ? 1 : 0;
                 }
 #pragma unroll
@@ -1185,7 +1197,7 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__
             for (int jj = j - h; jj <= j + h; ++jj)
                 for (int ii = i - h; ii <= i + h; ++ii)
                     if (ii >= 0 && ii < Mx && jj >= 0 && jj < My) {
-                        const float v = src[jj * Mx + ii];
+                        const float v = src[jj * Ms + ii];
                         int p = c++;
                         while (p > 0 && win[p - 1] > v) { win[p] = win[p - 1]; --p; }
                         win[p] = v;
@@ -1197,39 +1209,48 @@ __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__
     __syncthreads();
     // spline tables of both maps, from the float meshes: X (rows) and Y
     // (columns) for both maps at once, then XY (rows of Y)
-    for (int b = tid; b < n; b += MA_NT) { A4[b] = bkg_out[b]; A5[b] = rms_out[b]; }
+    if (mode != 0) {
+        if (tid == 0) factor_axis(ax, Lx);
+        if (tid == 32) factor_axis(ay, Ly);
+    }
+    for (int b = tid; b < n; b += MA_NT) {
+        const int sb_ = (b / Mx) * Ms + b % Mx;
+        A4[sb_] = bkg_out[b]; A5[sb_] = rms_out[b];
+    }
     __syncthreads();
     for (int t = tid; t < 2 * (My + Mx); t += MA_NT) {
         const int map = t / (My + Mx), q = t - map * (My + Mx);
         const float* P = map ? A5 : A4;
         float* X = map ? A1 : A0;
         float* Y = map ? A3 : A2;
-        if (q < My) solve_line(Lx, Mx, P + q * Mx, 1, X + q * Mx, 1);
-        else solve_line(Ly, My, P + (q - My), Mx, Y + (q - My), Mx);
+        if (q < My) solve_line(Lx, Mx, P + q * Ms, 1, X + q * Ms, 1);
+        else solve_line(Ly, My, P + (q - My), Ms, Y + (q - My), Ms);
     }
     __syncthreads();
     // XY overwrites P (no longer needed once X and Y are known)
     for (int b = tid; b < n; b += MA_NT) {
-        tab_b[b] = make_float4(A4[b], A0[b], A2[b], 0.f);
-        tab_r[b] = make_float4(A5[b], A1[b], A3[b], 0.f);
+        const int sb_ = (b / Mx) * Ms + b % Mx;
+        tab_b[b] = make_float4(A4[sb_], A0[sb_], A2[sb_], 0.f);
+        tab_r[b] = make_float4(A5[sb_], A1[sb_], A3[sb_], 0.f);
     }
     __syncthreads();
     for (int t = tid; t < 2 * My; t += MA_NT) {
         const int map = t / My, q = t - map * My;
-        solve_line(Lx, Mx, (map ? A3 : A2) + q * Mx, 1, (map ? A5 : A4) + q * Mx, 1);
+        solve_line(Lx, Mx, (map ? A3 : A2) + q * Ms, 1, (map ? A5 : A4) + q * Ms, 1);
     }
     __syncthreads();
     for (int b = tid; b < n; b += MA_NT) {
-        tab_b[b].w = A4[b];
-        tab_r[b].w = A5[b];
+        const int sb_ = (b / Mx) * Ms + b % Mx;
+        tab_b[b].w = A4[sb_];
+        tab_r[b].w = A5[sb_];
     }
 }
 
 size_t mesh_all_smem(int Mx, int My)
 {
-    const size_t n = (size_t)Mx * My;
+    const size_t ns = (size_t)(Mx | 1) * My;     // odd row stride (see k_mesh_all)
     const size_t nl = Mx > My ? Mx : My;
-    return mesh_lu_offset((int)n) + 8 * nl * sizeof(float);
+    return mesh_lu_offset((int)ns) + 8 * nl * sizeof(float);
 }
 
 bool mesh_fits_smem(int Mx, int My)
