@@ -15,18 +15,26 @@ __device__ __forceinline__ float chord_int(float a, float b, float r2)
 {
     float d = b - a;
     if (!(d > 0.f)) return 0.f;
-    float ha = sqrtf(fmaxf(r2 - a * a, 0.f));
-    float hb = sqrtf(fmaxf(r2 - b * b, 0.f));
+    float ha = sqrtf(fmaxf(fmaf(-a, a, r2), 0.f));
+    float hb = sqrtf(fmaxf(fmaf(-b, b, r2), 0.f));
     float s = ha + hb;
     float q = s > 0.f ? d * (a + b) / s : 0.f;      // ha - hb
     float sin_t = fmaf(d, ha, a * q);               // (b ha - a hb), r^2 sin(theta)
     float cos_t = fmaf(ha, hb, a * b);              // (ha hb + a b), r^2 cos(theta)
     float theta = atan2f(sin_t, cos_t);             // asin(b/r) - asin(a/r)
-    return 0.5f * (fmaf(d, hb, -a * q) + r2 * theta);
+    return 0.5f * fmaf(r2, theta, fmaf(d, hb, -a * q));
 }
 
 // exact area of disc(0, r) n [x0,x1] x [y0,y1]: integrate the length of
-// [y0,y1] n [-h(x), h(x)] over x, split where h(x) = |y0|, |y1|
+// [y0,y1] n [-h(x), h(x)] over x, split where h(x) = |y0|, |y1|.  On each
+// piece the top is y1 or the arc and the bottom y0 or the arc; rectangle parts
+// add directly and only arc-bounded pieces need the arc integral.  Those are
+// collected first: in a pixel that a circle of radius >= 1 crosses there are
+// one or two, so the warp runs the integral once or twice per pixel instead of
+// once per piece.  The roles come from squared comparisons (h^2 = r^2 - x^2).
+// Every product and sum is an explicit operation (fmaf, __fmul_rn,
+// __fadd_rn), so no instance of the kernels contracts it differently and a
+// frame gives the same bits in a batched launch as alone.
 static __device__ float disc_rect_area(float x0, float x1, float y0, float y1, float r)
 {
     const float r2 = r * r;
@@ -35,8 +43,8 @@ static __device__ float disc_rect_area(float x0, float x1, float y0, float y1, f
     float p[6];
     p[0] = a;
     p[5] = b;
-    float c0 = fabsf(y0) < r ? sqrtf(fmaxf(r2 - y0 * y0, 0.f)) : 0.f;
-    float c1 = fabsf(y1) < r ? sqrtf(fmaxf(r2 - y1 * y1, 0.f)) : 0.f;
+    const float c0 = fabsf(y0) < r ? sqrtf(fmaxf(fmaf(-y0, y0, r2), 0.f)) : 0.f;
+    const float c1 = fabsf(y1) < r ? sqrtf(fmaxf(fmaf(-y1, y1, r2), 0.f)) : 0.f;
     p[1] = fminf(fmaxf(-c0, a), b);
     p[2] = fminf(fmaxf(c0, a), b);
     p[3] = fminf(fmaxf(-c1, a), b);
@@ -45,22 +53,33 @@ static __device__ float disc_rect_area(float x0, float x1, float y0, float y1, f
 #define GP_CSWAP(i, j) { float lo_ = fminf(p[i], p[j]); float hi_ = fmaxf(p[i], p[j]); p[i] = lo_; p[j] = hi_; }
     GP_CSWAP(1, 2); GP_CSWAP(3, 4); GP_CSWAP(1, 3); GP_CSWAP(2, 4); GP_CSWAP(2, 3);
 #undef GP_CSWAP
+    const float y02 = y0 * y0, y12 = y1 * y1;
     float area = 0.f;
+    float l0 = 0.f, h0 = 0.f, k0 = 0.f, l1 = 0.f, h1 = 0.f, k1 = 0.f;   // the first two arc pieces
+    int n = 0;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        float lo = p[k], hi = p[k + 1];
+        const float lo = p[k], hi = p[k + 1];
         if (!(hi > lo)) continue;
-        float mid = 0.5f * (lo + hi);
-        float h = sqrtf(fmaxf(r2 - mid * mid, 0.f));
-        bool top_h = h <= y1, bot_h = -h >= y0;
-        float top = top_h ? h : y1, bot = bot_h ? -h : y0;
-        if (!(top > bot)) continue;
-        float gi = (top_h || bot_h) ? chord_int(lo, hi, r2) : 0.f;
-        float w = hi - lo;
-        float itop = top_h ? gi : y1 * w;
-        float ibot = bot_h ? -gi : y0 * w;
-        area += itop - ibot;
+        const float mid = 0.5f * (lo + hi);
+        const float hm2 = fmaxf(fmaf(-mid, mid, r2), 0.f);      // h(mid)^2
+        const bool top_h = y1 >= 0.f && hm2 <= y12;                // the arc is below the top edge
+        const bool bot_h = y0 <= 0.f && hm2 <= y02;                // the arc is above the bottom edge
+        const float w = hi - lo;
+        if (!top_h && !bot_h) { area = __fadd_rn(area, __fmul_rn(y1 - y0, w)); continue; }
+        // an empty piece: the top at or below the bottom
+        const bool empty = (top_h && bot_h) ? !(hm2 > 0.f) : top_h ? !(y0 < 0.f || hm2 > y02)
+                                                                   : !(y1 > 0.f || hm2 > y12);
+        if (empty) continue;
+        area = __fadd_rn(area, __fsub_rn(top_h ? 0.f : __fmul_rn(y1, w), bot_h ? 0.f : __fmul_rn(y0, w)));
+        const float kg = (top_h && bot_h) ? 2.f : 1.f;
+        if (n == 0) { l0 = lo; h0 = hi; k0 = kg; }
+        else if (n == 1) { l1 = lo; h1 = hi; k1 = kg; }
+        else area = fmaf(kg, chord_int(lo, hi, r2), area);         // radii below 1 only
+        ++n;
     }
+    if (n > 0) area = fmaf(k0, chord_int(l0, h0, r2), area);
+    if (n > 1) area = fmaf(k1, chord_int(l1, h1, r2), area);
     return area;
 }
 
@@ -84,7 +103,7 @@ __device__ __forceinline__ float load_px(const Image& im, int x, int y, bool& ba
 // once per row for whichever lanes meet the circle.
 struct BEntry {
     float dx0, dy0, m, var;
-    int kf;                 // radius index | bad << 8 | saturated << 9
+    int kf;                 // mask of the radii crossing the pixel | bad << 8 | saturated << 9
 };
 constexpr int QCAP = 96;
 constexpr int MEAS_NT = 256;
@@ -96,16 +115,20 @@ __device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < qn; i += 32) {
         const BEntry e = wq[i];
-        const int k = e.kf & 0xff;
-        const float A = disc_rect_area(e.dx0, e.dx0 + 1.f, e.dy0, e.dy0 + 1.f, ap.r[k]);
-        if (!(A > 0.f)) continue;
+        unsigned rm = e.kf & 0xffu;                  // the radii whose circle crosses the pixel
+        while (rm) {
+            const int k = __ffs(rm) - 1;
+            rm &= rm - 1u;
+            const float A = disc_rect_area(e.dx0, e.dx0 + 1.f, e.dy0, e.dy0 + 1.f, ap.r[k]);
+            if (!(A > 0.f)) continue;
 #pragma unroll
-        for (int kk = 0; kk < NR; ++kk) {
-            if (kk != k) continue;
-            if (e.kf & 0x100) { fl[kk] |= GP_FLAG_BAD; continue; }
-            if (e.kf & 0x200) fl[kk] |= GP_FLAG_SAT;
-            df_add_prod(f[kk], A, e.m);
-            df_add_prod(v[kk], A, e.var);
+            for (int kk = 0; kk < NR; ++kk) {
+                if (kk != k) continue;
+                if (e.kf & 0x100) { fl[kk] |= GP_FLAG_BAD; continue; }
+                if (e.kf & 0x200) fl[kk] |= GP_FLAG_SAT;
+                df_add_prod(f[kk], A, e.m);
+                df_add_prod(v[kk], A, e.var);
+            }
         }
     }
     __syncwarp();
@@ -155,7 +178,7 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
         for (int y = ya; y <= yb; ++y) {
             const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
             const float ny = fmaxf(0.f, fmaxf(dy0, -dy1));
-            const float dmin2 = nx * nx + ny * ny;
+            const float dmin2 = fmaf(nx, nx, ny * ny);
             const float dmax2 = fx + fmaxf(dy0 * dy0, dy1 * dy1);
             const bool live = colok && dmin2 < rmax2;
             bool bad = true, sat = false;
@@ -177,9 +200,13 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
                     sat = im.sat > 0.f && val >= im.sat;
                 }
             }
+            unsigned bm = 0u;                        // radii whose circle crosses this pixel
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 const float r = ap.r[k], r2 = r * r;
+                // rows that disc k does not reach skip it: ny depends on the row only, so the
+                // branch is the same for the whole warp
+                if (!(ny * ny < r2)) continue;
                 const bool in = live && dmin2 < r2;
                 const bool full = in && dmax2 <= r2;
                 if (full) {
@@ -190,19 +217,21 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
                         df_add(v[k], var);
                     }
                 }
-                const bool bnd = in && !full;
-                const unsigned bal = __ballot_sync(0xffffffffu, bnd);
-                if (bnd) {
-                    BEntry e;
-                    e.dx0 = dx0; e.dy0 = dy0; e.m = m; e.var = var;
-                    e.kf = k | (bad ? 0x100 : 0) | (sat ? 0x200 : 0);
-                    wq[qn + __popc(bal & lt)] = e;
-                }
-                qn += __popc(bal);
-                if (qn > QCAP - 32) {
-                    flush_queue<NR>(ap, wq, qn, f, v, fl);
-                    qn = 0;
-                }
+                if (in && !full) bm |= 1u << k;
+            }
+            // one queue entry per crossed pixel, for all its radii
+            const bool bnd = bm != 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bnd);
+            if (bnd) {
+                BEntry e;
+                e.dx0 = dx0; e.dy0 = dy0; e.m = m; e.var = var;
+                e.kf = (int)bm | (bad ? 0x100 : 0) | (sat ? 0x200 : 0);
+                wq[qn + __popc(bal & lt)] = e;
+            }
+            qn += __popc(bal);
+            if (qn > QCAP - 32) {
+                flush_queue<NR>(ap, wq, qn, f, v, fl);
+                qn = 0;
             }
         }
     }
