@@ -149,17 +149,22 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int W = im.W, H = im.H;
-    // positions far outside the frame (or NaN) clamp to an empty pixel range
-    const double cxc = fmin(fmax(cx, -4096.0), (double)W + 4096.0);
-    const double cyc = fmin(fmax(cy, -4096.0), (double)H + 4096.0);
-    const double xi_d = floor(cxc), yi_d = floor(cyc);
+    // The window comes from the whole and fractional parts of the position,
+    // so the float64 work is one split of each coordinate (every lane issues
+    // it, and float64 runs at a small fraction of the float32 rate).  With
+    // cx = xi + f, a column x can meet the disc of radius rmax only if
+    // xi - ceil(rmax) - 1 <= x <= xi + ceil(rmax) + 2; rows likewise.  Pixels
+    // of the window beyond the disc fail the per-pixel test.  Positions far
+    // outside the frame (or NaN) give an empty window.
+    const bool near = fabsf((float)cx - 0.5f * (float)W) <= 0.5f * (float)W + 4096.f &&
+                      fabsf((float)cy - 0.5f * (float)H) <= 0.5f * (float)H + 4096.f;
+    const double xi_d = floor(near ? cx : 0.0), yi_d = floor(near ? cy : 0.0);
     const int xi = (int)xi_d, yi = (int)yi_d;
-    const float xf = (float)(cxc - xi_d), yf = (float)(cyc - yi_d);
-    int xa = (int)floor(cxc - (double)ap.rmax - 0.5), xb = (int)ceil(cxc + (double)ap.rmax + 0.5);
-    int ya = (int)floor(cyc - (double)ap.rmax - 0.5), yb = (int)ceil(cyc + (double)ap.rmax + 0.5);
-    xa = max(xa, 0); ya = max(ya, 0);
-    xb = min(xb, W - 1); yb = min(yb, H - 1);
-    if (!(cx == cxc) || !(cy == cyc)) { xb = -1; yb = -1; }
+    const float xf = (float)(cx - xi_d), yf = (float)(cy - yi_d);
+    const int rc = (int)ceilf(ap.rmax);
+    const int xa = max(xi - rc - 1, 0), ya = max(yi - rc - 1, 0);
+    int xb = min(xi + rc + 2, W - 1), yb = min(yi + rc + 2, H - 1);
+    if (!near) { xb = -1; yb = -1; }
     DF f[NR > 0 ? NR : 1], v[NR > 0 ? NR : 1];
     uint32_t fl[NR > 0 ? NR : 1];
 #pragma unroll
@@ -178,6 +183,7 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
         for (int y = ya; y <= yb; ++y) {
             const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
             const float ny = fmaxf(0.f, fmaxf(dy0, -dy1));
+            if (!(ny * ny < rmax2)) continue;        // a row beyond the largest disc (the whole warp)
             const float dmin2 = fmaf(nx, nx, ny * ny);
             const float dmax2 = fx + fmaxf(dy0 * dy0, dy1 * dy1);
             const bool live = colok && dmin2 < rmax2;
@@ -288,7 +294,7 @@ __device__ __forceinline__ const MeasureArgs& measure_frame(const MeasureArgs* _
 }
 
 template <bool F32, int NR, bool BATCH>
-__global__ void __launch_bounds__(MEAS_NT) k_measure(const MeasureArgs* __restrict__ batch,
+__global__ void __launch_bounds__(MEAS_NT, 3) k_measure(const MeasureArgs* __restrict__ batch,
                                                      const __grid_constant__ MeasureArgs one)
 {
     const MeasureArgs& A = measure_frame<BATCH>(batch, one);
@@ -324,7 +330,7 @@ __global__ void __launch_bounds__(MEAS_NT) k_measure(const MeasureArgs* __restri
 }
 
 template <bool F32, int NR>
-__global__ void __launch_bounds__(MEAS_NT) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap,
+__global__ void __launch_bounds__(MEAS_NT, 3) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap,
                                                       const double* xs, const double* ys, int n, double* flux,
                                                       double* ferr, uint32_t* fl)
 {
