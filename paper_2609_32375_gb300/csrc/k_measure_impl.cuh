@@ -57,26 +57,32 @@ static __device__ float disc_rect_area(float x0, float x1, float y0, float y1, f
     float area = 0.f;
     float l0 = 0.f, h0 = 0.f, k0 = 0.f, l1 = 0.f, h1 = 0.f, k1 = 0.f;   // the first two arc pieces
     int n = 0;
+    // the pieces without branches: an empty piece (w = 0) adds an exact zero
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const float lo = p[k], hi = p[k + 1];
-        if (!(hi > lo)) continue;
+        const float w = hi - lo;                                   // >= 0: the points are sorted
         const float mid = 0.5f * (lo + hi);
         const float hm2 = fmaxf(fmaf(-mid, mid, r2), 0.f);      // h(mid)^2
         const bool top_h = y1 >= 0.f && hm2 <= y12;                // the arc is below the top edge
         const bool bot_h = y0 <= 0.f && hm2 <= y02;                // the arc is above the bottom edge
-        const float w = hi - lo;
-        if (!top_h && !bot_h) { area = __fadd_rn(area, __fmul_rn(y1 - y0, w)); continue; }
-        // an empty piece: the top at or below the bottom
+        const bool plain = !top_h && !bot_h;
+        // an arc piece is empty when its top is at or below its bottom
         const bool empty = (top_h && bot_h) ? !(hm2 > 0.f) : top_h ? !(y0 < 0.f || hm2 > y02)
                                                                    : !(y1 > 0.f || hm2 > y12);
-        if (empty) continue;
-        area = __fadd_rn(area, __fsub_rn(top_h ? 0.f : __fmul_rn(y1, w), bot_h ? 0.f : __fmul_rn(y0, w)));
+        const bool arc = w > 0.f && !plain && !empty;
+        // rectangle parts: the full height of a plain piece; on an arc piece
+        // the edges that the arc does not replace
+        const float rect = plain ? __fmul_rn(y1 - y0, w)
+                         : arc   ? __fsub_rn(top_h ? 0.f : __fmul_rn(y1, w), bot_h ? 0.f : __fmul_rn(y0, w))
+                                 : 0.f;
+        area = __fadd_rn(area, rect);
         const float kg = (top_h && bot_h) ? 2.f : 1.f;
-        if (n == 0) { l0 = lo; h0 = hi; k0 = kg; }
-        else if (n == 1) { l1 = lo; h1 = hi; k1 = kg; }
-        else area = fmaf(kg, chord_int(lo, hi, r2), area);         // radii below 1 only
-        ++n;
+        const bool s0 = arc && n == 0, s1 = arc && n == 1;
+        l0 = s0 ? lo : l0; h0 = s0 ? hi : h0; k0 = s0 ? kg : k0;
+        l1 = s1 ? lo : l1; h1 = s1 ? hi : h1; k1 = s1 ? kg : k1;
+        if (arc && n >= 2) area = fmaf(kg, chord_int(lo, hi, r2), area);   // radii below 1 only
+        n += arc ? 1 : 0;
     }
     if (n > 0) area = fmaf(k0, chord_int(l0, h0, r2), area);
     if (n > 1) area = fmaf(k1, chord_int(l1, h1, r2), area);
