@@ -234,7 +234,7 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     mark(ctx, 5, st);
     GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
     mark(ctx, 6, st);
-    ctx->launches += 1 + 3 + 4 + 1;
+    ctx->launches += 1 + 4 + 4 + 1;
     return GP_OK;
 }
 
@@ -559,7 +559,7 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
     mark(ctx, 4, st);
     GP_CUDA(launch_rank(w.C, n_out, -1, false, ctx->dstatus, st));
     mark_to(ctx, 5, 6, st);
-    ctx->launches += 1 + 3 + 2;
+    ctx->launches += 1 + 4 + 2;
     return GP_OK;
 }
 

@@ -387,7 +387,7 @@ __device__ void boxstats_u16_box(const BoxArgs& A, int box, uint32_t* hist)
 // above it) marks the box, which then goes to the full-histogram kernel.
 // Boxes finished here get bit-identical results: the same integer sums, the
 // same ranks, the same clip loop.
-constexpr int WB_NT = 256;
+constexpr int WB_NT = 128;
 constexpr int NWIN = 4096;
 constexpr int WCB = 64;                 // values per coarse bin of the window
 constexpr int NWC = NWIN / WCB;         // 64 coarse bins
@@ -461,7 +461,7 @@ struct WinHist {
     }
 };
 
-__global__ void __launch_bounds__(WB_NT, 4) k_boxstats_win(const BoxArgs* __restrict__ batch,
+__global__ void __launch_bounds__(WB_NT, 8) k_boxstats_win(const BoxArgs* __restrict__ batch,
                                                         const __grid_constant__ BoxArgs one)
 {
     const BoxArgs& A = frame_args(batch, one);
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(WB_NT, 4) k_boxstats_win(const BoxArgs* __rest
                      !mask;
 
     for (int w = tid; w < NWIN; w += WB_NT) win[w] = 0u;
-    samp[tid] = 0u;
+    for (int i = tid; i < 256; i += WB_NT) samp[i] = 0u;
     __syncthreads();
 
     // ---- sample (every 16th row): median coarse value -> window

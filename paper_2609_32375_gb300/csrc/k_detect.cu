@@ -197,6 +197,28 @@ __device__ void mom_finish(double S, double Sx, double Sy, double Sxx, double Sy
     }
 }
 
+// A segment's sum S = hi + lo is positive exactly when hi > -lo (a float
+// comparison, exact), the same decision as (double)hi + (double)lo > 0.
+__device__ __forceinline__ bool df_positive(DF d) { return d.hi > -d.lo; }
+
+// Origin of a segment's stored sums: the corner of the detection tile that
+// holds the top-left pixel of its bounding box.
+__device__ __forceinline__ int2 comp_origin(int4 bb) { return make_int2(bb.x / TX * TX, bb.z / TY * TY); }
+
+// A segment with positive sum keeps its raw float-float sums in its own
+// catalog fields until k_mom_finish finishes them: flux holds S, xy holds
+// (Sx, Sy), mom2 holds (Sxx, Syy, Sxy), all about comp_origin.  Finishing
+// them one segment per thread issues the float64 steps once for 32 segments
+// instead of once per segment on a single lane of a warp.
+__device__ __forceinline__ void comp_store_raw(const Comps& C, int id, DF s, DF sx, DF sy, DF sxx, DF syy, DF sxy)
+{
+    reinterpret_cast<float2*>(C.flux)[id] = make_float2(s.hi, s.lo);
+    reinterpret_cast<float4*>(C.xy)[id] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+    float4* m = reinterpret_cast<float4*>(C.mom2 + id);
+    m[0] = make_float4(sxx.hi, sxx.lo, syy.hi, syy.lo);
+    m[1] = make_float4(sxy.hi, sxy.lo, 0.f, 0.f);
+}
+
 // ----------------------------------------------------------- tile kernel ---
 // Staged columns: SMEM column c holds frame column x0 - XHALO + c (so 16-byte
 // chunks of the frame land on 16-byte boundaries); staged rows: row r holds
@@ -742,13 +764,18 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
                 } else {
                     const int id = -2 - rec;
                     uint32_t fl = a.flags;
-                    double flux;
-                    double2 xy;
-                    Mom2 m2;
-                    mom_finish(df_value(a.s), df_value(a.sx), df_value(a.sy), df_value(a.sxx), df_value(a.syy),
-                               df_value(a.sxy), a.ux, a.uy, a.uxx, a.uyy, a.uxy, S.r_npix[r], x0, y0, &flux, &xy,
-                               &m2, &fl);
-                    A.C.flux[id] = flux; A.C.xy[id] = xy; A.C.mom2[id] = m2;
+                    if (df_positive(a.s)) {
+                        // sums about the tile corner (x0, y0), finished by k_mom_finish
+                        comp_store_raw(A.C, id, a.s, a.sx, a.sy, a.sxx, a.syy, a.sxy);
+                    } else {
+                        double flux;
+                        double2 xy;
+                        Mom2 m2;
+                        mom_finish(df_value(a.s), df_value(a.sx), df_value(a.sy), df_value(a.sxx),
+                                   df_value(a.syy), df_value(a.sxy), a.ux, a.uy, a.uxx, a.uyy, a.uxy, S.r_npix[r],
+                                   x0, y0, &flux, &xy, &m2, &fl);
+                        A.C.flux[id] = flux; A.C.xy[id] = xy; A.C.mom2[id] = m2;
+                    }
                     A.C.peak[id] = a.peak; A.C.peakL[id] = a.peakL; A.C.flags[id] = fl;
                 }
             }
@@ -919,7 +946,8 @@ __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_c
         const uint32_t fin = tot >= minarea ? P.agg_min[r] + 1u : 0u;
         if (r == p && fin) {
             const int4 bb = P.agg_bbox[r];
-            const int X0 = bb.x, Y0 = bb.z;
+            const int2 org = comp_origin(bb);
+            const int X0 = org.x, Y0 = org.y;
             const int tx0 = bb.x / TX, tx1 = bb.y / TX, ty0 = bb.z / TY, ty1 = bb.w / TY;
             const int ntw = tx1 - tx0 + 1, nt = ntw * (ty1 - ty0 + 1);
             DF s = df_zero(), sx = df_zero(), sy = df_zero(), sxx = df_zero(), syy = df_zero(), sxy = df_zero();
@@ -971,13 +999,17 @@ __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_c
             if (lane == 0) {
                 const int id = atomicAdd(C.count, 1);
                 if (id < C.cap) {
-                    double flux;
-                    double2 xy;
-                    Mom2 m2;
-                    mom_finish(df_value(s), df_value(sx), df_value(sy), df_value(sxx), df_value(syy), df_value(sxy),
-                               ux, uy, uxx, uyy, uxy, tot, X0, Y0, &flux, &xy, &m2, &fl);
+                    if (df_positive(s)) {
+                        comp_store_raw(C, id, s, sx, sy, sxx, syy, sxy);     // finished by k_mom_finish
+                    } else {
+                        double flux;
+                        double2 xy;
+                        Mom2 m2;
+                        mom_finish(df_value(s), df_value(sx), df_value(sy), df_value(sxx), df_value(syy),
+                                   df_value(sxy), ux, uy, uxx, uyy, uxy, tot, X0, Y0, &flux, &xy, &m2, &fl);
+                        C.flux[id] = flux; C.xy[id] = xy; C.mom2[id] = m2;
+                    }
                     C.label[id] = fin; C.npix[id] = tot; C.bbox[id] = bb;
-                    C.flux[id] = flux; C.xy[id] = xy; C.mom2[id] = m2;
                     C.peak[id] = pk; C.peakL[id] = pkL; C.flags[id] = fl;
                 } else {
                     set_status(status, GP_ERR_INTERNAL);
@@ -993,6 +1025,32 @@ __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_c
             uint32_t* sp = seg + (int64_t)y * W + x;
             if (*sp == prov) *sp = fin;
         }
+    }
+}
+
+// Centroid and second moments of every segment stored with raw sums (one
+// thread per segment); segments with a sum <= 0 were finished where they were
+// found and carry GP_FLAG_CENTROID_FALLBACK.
+__global__ void k_mom_finish(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
+{
+    const ResolveArgs& R = frame_args(batch, one);
+    const Comps& C = R.C;
+    const int n = min(*C.count, C.cap);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+        uint32_t fl = C.flags[id];
+        if (fl & GP_FLAG_CENTROID_FALLBACK) continue;
+        const float2 s = reinterpret_cast<const float2*>(C.flux)[id];
+        const float4 sxy = reinterpret_cast<const float4*>(C.xy)[id];
+        const float4* mr = reinterpret_cast<const float4*>(C.mom2 + id);
+        const float4 m0 = mr[0], m1 = mr[1];
+        const int2 org = comp_origin(C.bbox[id]);
+        double flux;
+        double2 xy;
+        Mom2 m2;
+        mom_finish((double)s.x + (double)s.y, (double)sxy.x + (double)sxy.y, (double)sxy.z + (double)sxy.w,
+                   (double)m0.x + (double)m0.y, (double)m0.z + (double)m0.w, (double)m1.x + (double)m1.y, 0, 0, 0,
+                   0, 0, C.npix[id], org.x, org.y, &flux, &xy, &m2, &fl);
+        C.flux[id] = flux; C.xy[id] = xy; C.mom2[id] = m2;
     }
 }
 
@@ -1176,6 +1234,7 @@ cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch,
     const dim3 g(stride_grid(152 * 8, nframes), nframes);
     k_aggregate<<<g, 256, 0, st>>>(batch, one);
     k_finalize<<<g, 256, 0, st>>>(batch, one);
+    k_mom_finish<<<g, 256, 0, st>>>(batch, one);
     return cudaGetLastError();
 }
 
