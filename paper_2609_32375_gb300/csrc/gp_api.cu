@@ -234,7 +234,7 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     mark(ctx, 5, st);
     GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
     mark(ctx, 6, st);
-    ctx->launches += 1 + 4 + 4 + 1;
+    ctx->launches += 1 + 4 + 4 + 1 + (nr > 0 ? 1 : 0);
     return GP_OK;
 }
 
@@ -518,7 +518,7 @@ gp_status gp_aperture(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const
     mark_to(ctx, 2, 5, st);
     if (n > 0) {
         GP_CUDA(launch_aperture(to_image(img), sb, sr, x, y, n, p->radii, p->nr, p->gain, flux, fluxerr, flags, st));
-        ctx->launches += 1;
+        ctx->launches += 2;
     }
     mark(ctx, 6, st);
     return GP_OK;

@@ -406,7 +406,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     ex.at(5);
     PL_CUDA(launch_measure_any(meas[0], d_meas, n, ex.st));
     ex.at(6);
-    ex.launches += 1 + 4 + 4 + 1;
+    ex.launches += 1 + 4 + 4 + 1 + (P.nr > 0 ? 1 : 0);
     return GP_OK;
 }
 

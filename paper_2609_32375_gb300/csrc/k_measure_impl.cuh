@@ -249,11 +249,11 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
     }
     flush_queue<NR>(ap, wq, qn, f, v, fl);
     // Warp sums of every radius (all lanes hold them after the butterflies);
-    // then lane k finishes radius k, so the float64 steps issue once for all
-    // radii (float64 runs at a small fraction of the float32 rate).
+    // lane k stores radius k's raw float-float sums, and k_ap_finish turns
+    // them into the flux, its error and the edge flag one (source, radius)
+    // per thread, so the float64 steps issue once for 32 results.
     DF my_f = df_zero(), my_v = df_zero();
     uint32_t my_fl = 0u;
-    float my_r = 0.f;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const DF fs = df_warp_sum(f[k]);
@@ -261,29 +261,42 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
         uint32_t ff = fl[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ff |= __shfl_xor_sync(0xffffffffu, ff, o);
-        if (lane == k) { my_f = fs; my_v = vs; my_fl = ff; my_r = ap.r[k]; }
+        if (lane == k) { my_f = fs; my_v = vs; my_fl = ff; }
     }
     if (lane < NR) {
-        const double r = my_r;
-        if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) my_fl |= GP_FLAG_TRUNCATED;
-        const double F = df_value(my_f);
-        double V = df_value(my_v);
-        if (ap.gain > 0.f && F > 0.0) V = fma(F, ap.inv_gain, V);
-        // sqrt(V): a float32 estimate s0, then one Newton step in float64,
-        // s0 + (V - s0^2) / (2 s0); the step is ~1e-7 s0, so a float32
-        // reciprocal leaves ~1e-14 relative error
-        double e = 0.0;
-        if (V > 0.0) {
-            const float s0f = sqrtf((float)V);
-            if (s0f > 0.f) {
-                const double s0 = (double)s0f;
-                e = fma(fma(-s0, s0, V), (double)(0.5f / s0f), s0);
-            }
-        }
-        flux[lane] = F;
-        ferr[lane] = e;
+        reinterpret_cast<float2*>(flux)[lane] = make_float2(my_f.hi, my_f.lo);
+        reinterpret_cast<float2*>(ferr)[lane] = make_float2(my_v.hi, my_v.lo);
         aflags[lane] = my_fl;
     }
+}
+
+// Radius k's results at (cx, cy) from the raw sums in *flux and *ferr: the
+// flux F, its error sqrt(V + F / gain) and the edge flag.
+__device__ __forceinline__ void ap_finish(double cx, double cy, const ApSpec& ap, int k, int W, int H, double* flux,
+                                          double* ferr, uint32_t* fl)
+{
+    const float2 fr = *reinterpret_cast<const float2*>(flux);
+    const float2 vr = *reinterpret_cast<const float2*>(ferr);
+    uint32_t f = *fl;
+    const double r = ap.r[k];
+    if (cx - r < -0.5 || cx + r > W - 0.5 || cy - r < -0.5 || cy + r > H - 0.5) f |= GP_FLAG_TRUNCATED;
+    const double F = (double)fr.x + (double)fr.y;
+    double V = (double)vr.x + (double)vr.y;
+    if (ap.gain > 0.f && F > 0.0) V = fma(F, ap.inv_gain, V);
+    // sqrt(V): a float32 estimate s0, then one Newton step in float64,
+    // s0 + (V - s0^2) / (2 s0); the step is ~1e-7 s0, so a float32
+    // reciprocal leaves ~1e-14 relative error
+    double e = 0.0;
+    if (V > 0.0) {
+        const float s0f = sqrtf((float)V);
+        if (s0f > 0.f) {
+            const double s0 = (double)s0f;
+            e = fma(fma(-s0, s0, V), (double)(0.5f / s0f), s0);
+        }
+    }
+    *flux = F;
+    *ferr = e;
+    *fl = f;
 }
 
 // One warp per catalog row (segments in label order): copy the segment's
@@ -349,6 +362,33 @@ __global__ void __launch_bounds__(MEAS_NT, 3) k_aperture(Image im, SplineTab sb,
                                fl + (int64_t)i * NR, wq);
 }
 
+// the aperture results of the catalog rows (one (row, radius) per thread)
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_ap_finish_rows(const MeasureArgs* __restrict__ batch,
+                                                        const __grid_constant__ MeasureArgs one)
+{
+    const MeasureArgs& A = measure_frame<BATCH>(batch, one);
+    const int nr = A.ap.nr;
+    const int nrow = min(min(*A.C.count, A.C.cap), A.capacity);
+    const int64_t n = (int64_t)nrow * nr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / nr), k = (int)(i - (int64_t)r * nr);
+        ap_finish(A.x[r], A.y[r], A.ap, k, A.im.W, A.im.H, A.apflux + i, A.apferr + i, A.apflags + i);
+    }
+}
+
+// the aperture results of a list of positions
+static __global__ void __launch_bounds__(256) k_ap_finish_list(const double* xs, const double* ys, int n,
+                                                        const __grid_constant__ ApSpec ap, int W,
+                                                        int H, double* flux, double* ferr, uint32_t* fl)
+{
+    const int64_t tot = (int64_t)n * ap.nr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i / ap.nr), k = (int)(i - (int64_t)j * ap.nr);
+        ap_finish(xs[j], ys[j], ap, k, W, H, flux + i, ferr + i, fl + i);
+    }
+}
+
 // dispatch on the number of radii (a compile-time constant in the kernels)
 template <template <bool, int> class Launch, bool F32, typename... Args>
 static cudaError_t dispatch_nr(int nr, Args... args)
@@ -394,6 +434,7 @@ struct ApertureLaunch {
     {
         if (NR == 0) return cudaSuccess;
         k_aperture<F32, NR><<<g, 256, 0, st>>>(im, sb, sr, ap, xs, ys, n, flux, ferr, fl);
+        k_ap_finish_list<<<g, 256, 0, st>>>(xs, ys, n, ap, im.W, im.H, flux, ferr, fl);
         return cudaGetLastError();
     }
 };
