@@ -138,7 +138,7 @@ def kernel_traffic(kernel, workload):
         return None
 
 
-STAGE_KERNEL = {"box_stats": "k_boxstats_u16", "detect_tiles": "k_detect_tile", "measure": "k_measure",
+STAGE_KERNEL = {"box_stats": "k_boxstats_win", "detect_tiles": "k_detect_tile", "measure": "k_measure",
                 "tile_merge": "k_finalize", "label_rank": "k_rank_scan", "mesh_spline": "k_mesh_all"}
 
 
