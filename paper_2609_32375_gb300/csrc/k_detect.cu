@@ -566,6 +566,27 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         __syncthreads();
     }
 
+    // ---- a tile without foreground pixels (most tiles of a sparse field):
+    // the map rows are zero, every edge record is -1 and the tile has no
+    // pieces, exactly what the labelling below would write for it
+    if (!__syncthreads_or(tid < 2 * TY && S.rmask[tid] != 0u)) {
+        if (tid == 0) { A.T.piece_base[tile] = 0; A.T.piece_cnt[tile] = 0; }
+        if (tw == TX && (W & 3) == 0 && ((((uintptr_t)A.seg) & 15) == 0)) {
+            for (int p4 = tid; p4 < TNPIX / 4; p4 += DT_NT) {
+                const int py = p4 / (TX / 4), px = (p4 - py * (TX / 4)) * 4;
+                if (py < th) *reinterpret_cast<uint4*>(A.seg + (int64_t)(y0 + py) * W + x0 + px) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+            for (int p = tid; p < TNPIX; p += DT_NT) {
+                const int py = p / TX, px = p - py * TX;
+                if (py < th && px < tw) A.seg[(int64_t)(y0 + py) * W + x0 + px] = 0u;
+            }
+        }
+        int16_t* ed = A.T.edges + (int64_t)tile * EDGE_PER_TILE;
+        for (int q = tid; q < EDGE_PER_TILE; q += DT_NT) ed[q] = -1;
+        return;
+    }
+
     // ---- tile-local labelling on horizontal runs.  Every foreground pixel
     // points at the first pixel of its run (the run's minimum index); only
     // run heads take part in the union-find.  A run is united with each run
