@@ -1086,8 +1086,10 @@ __global__ void k_rank_count(const RankArgs* __restrict__ batch, const __grid_co
 
 constexpr int SCAN_NT = 1024;
 
-// exclusive scan of the bucket counts (one CTA, 8 consecutive buckets per
-// thread per pass); publishes the segment count
+// exclusive scan of the bucket counts in one pass of one CTA: each thread
+// sums a run of consecutive buckets (16-byte loads), the block scans the run
+// sums, and each thread writes its run's offsets from a second (cached) read;
+// publishes the segment count
 __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restrict__ batch,
                                                        const __grid_constant__ RankArgs one)
 {
@@ -1096,48 +1098,59 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restric
     int* n_out = R.n_out;
     const int capacity = R.capacity;
     int* status = R.status;
-    constexpr int PER = 8;
     __shared__ int wsum[SCAN_NT / 32];
-    __shared__ int carry_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int carry = 0;
-    for (int base = 0; base < C.nb; base += SCAN_NT * PER) {
-        const int i0 = base + tid * PER;
-        int v[PER];
-        int tsum = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            v[k] = i0 + k < C.nb ? C.bcnt[i0 + k] : 0;
-            tsum += v[k];
+    const int nb = C.nb;                                     // <= 65,536
+    const int per = ((nb + SCAN_NT - 1) / SCAN_NT + 3) & ~3; // a multiple of 4 buckets per thread
+    const int b0 = min(tid * per, nb), b1 = min(b0 + per, nb);
+    const bool vec = (((uintptr_t)C.bcnt | (uintptr_t)C.boff) & 15) == 0;
+    int tsum = 0;
+    int i = b0;
+    if (vec) {
+#pragma unroll 4
+        for (; i + 4 <= b1; i += 4) {
+            const int4 q = *reinterpret_cast<const int4*>(C.bcnt + i);
+            tsum += q.x + q.y + q.z + q.w;
         }
-        int incl = tsum;
+    }
+    for (; i < b1; ++i) tsum += C.bcnt[i];
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = wsum[lane];
+        int wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
         }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int w = wsum[lane];
-            int wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += t;
-            }
-            wsum[lane] = wi - w;
-            if (lane == 31) carry_s = wi;                 // this pass's total
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int excl = wsum[warp] + incl - tsum;
+    i = b0;
+    if (vec) {
+#pragma unroll 4
+        for (; i + 4 <= b1; i += 4) {
+            const int4 q = *reinterpret_cast<const int4*>(C.bcnt + i);
+            int4 o;
+            o.x = excl; excl += q.x;
+            o.y = excl; excl += q.y;
+            o.z = excl; excl += q.z;
+            o.w = excl; excl += q.w;
+            *reinterpret_cast<int4*>(C.boff + i) = o;
         }
-        __syncthreads();
-        int excl = carry + wsum[warp] + incl - tsum;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            if (i0 + k < C.nb) C.boff[i0 + k] = excl;
-            excl += v[k];
-        }
-        carry += carry_s;
-        __syncthreads();                                  // wsum and carry_s are reused
+    }
+    for (; i < b1; ++i) {
+        const int v = C.bcnt[i];
+        C.boff[i] = excl;
+        excl += v;
     }
     if (tid == 0) {
         const int total = *C.count;
