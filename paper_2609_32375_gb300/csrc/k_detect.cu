@@ -11,10 +11,12 @@
 //                 thresholds F > k sigma(p), labels the tile's 8-connected
 //                 components by union-find in shared memory (root = minimum
 //                 index = the segment's first pixel in raster order) and
-//                 accumulates each component's moments from the staged m
-//                 (one warp per component, fixed order).  Components that do
-//                 not touch an edge shared with another tile are final here;
-//                 the others become "pieces" with partial moments, and their
+//                 accumulates each component's moment sums from the staged m
+//                 (one warp per component, fixed order).  A tile without
+//                 foreground writes its empty map rows and edge records and
+//                 stops after thresholding.  Components that do not touch an
+//                 edge shared with another tile are final here (raw sums);
+//                 the others become "pieces" with partial sums, and their
 //                 edge pixels are recorded for the merge.
 //  k_merge        unites pieces across tile edges (lock-free union-find
 //                 over piece ids, atomicMin linking).
@@ -24,6 +26,9 @@
 //                 tile raster order (deterministic), and rewrites the map
 //                 pixels of pieces whose final label differs (other root, or
 //                 below minarea) -- a sparse pass over those pieces only.
+//  k_mom_finish   centroid and second moments of every segment from its raw
+//                 sums, one segment per thread (the float64 steps issue once
+//                 for 32 segments).
 //  k_rank_*       orders segments by label (bucket counts, one scan,
 //                 scatter, in-bucket rank): a deterministic catalog order.
 #include <math.h>

@@ -1,9 +1,10 @@
 // k_measure.cu -- catalog rows and circular apertures with exact disc/pixel
 // overlap areas (paper Section 3.4).
 //
-// One warp per source.  The segment moments were finished during detection;
-// here each row is written in label order and the apertures scan the pixels
-// around the centroid once for all radii.  Every sum is a float-float
+// One warp per source.  The segment moments were finished after detection
+// (k_mom_finish); here each row is written in label order and the apertures
+// scan the pixels around the centroid once for all radii, leaving raw sums
+// that k_ap_finish_rows / k_ap_finish_list finish one result per thread.  Every sum is a float-float
 // (compensated) accumulation of FP32 products, reduced across the warp in a
 // fixed butterfly order, so results are reproducible run to run and carry
 // about 48 bits -- the float64-class accumulation the paper asks of aperture

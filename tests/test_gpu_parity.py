@@ -244,6 +244,67 @@ def test_aperture_entry_point(ctx):
     assert np.array_equal(fl.cpu().numpy().astype(np.uint32), rfl)
 
 
+def test_centroid_fallback_for_nonpositive_flux(ctx):
+    """A segment whose own sum of m is <= 0 takes the unweighted centroid
+    and moments (GP_FLAG_CENTROID_FALLBACK).  A one-tap kernel that is a
+    shifted delta detects the pixels two columns and rows up-left of a bright
+    square, where a dark square sits, so that segment's sum is negative."""
+    rng = np.random.default_rng(5)
+    img = (1000 + 20 * rng.standard_normal((256, 320))).round().astype(np.uint16)
+    img[100:112, 150:162] = 9000           # bright: detected through the shifted tap
+    img[98:110, 148:160] = 0               # dark: the detected pixels themselves
+    img[40:48, 60:70] = 6000               # an ordinary positive source beside it
+    k = np.zeros((5, 5), np.float32)
+    k[4, 4] = 1.0                          # F(x, y) = m(x + 2, y + 2)
+
+    class Cfg:
+        name = "shifted-delta kernel"
+        kernel = k
+        thresh = 3.0
+        minarea = 3
+        radii = (3.0, 5.0)
+        gain = 1.0
+        saturation = 0.0
+
+    out = check_detect(ctx, Cfg, img, 64)
+    n = int(out["catalog"]["n"].item())
+    flags = out["catalog"]["flags"][:n].cpu().numpy().astype(np.uint32)
+    flux = out["catalog"]["flux_iso"][:n].cpu().numpy()
+    assert np.any(flux <= 0) and np.any(flux > 0)
+    assert np.all(((flags & gp.GP_FLAG_CENTROID_FALLBACK) != 0) == (flux <= 0))
+
+
+def test_tiles_without_foreground_overwrite_stale_outputs(ctx):
+    """Tiles with no foreground take a short path that writes zero map rows
+    and empty edge records; outputs reused after a crowded frame must match
+    a run into fresh buffers."""
+    cfg, crowded = frame("dense_12288x12304_u16", 21, 1024, 768)
+    sparse = crowded.copy()
+    sky = np.median(crowded)
+    sparse[:, 200:] = np.random.default_rng(3).normal(sky, 4.0, sparse[:, 200:].shape).round().astype(np.uint16)
+    ex = gp.Extractor(ctx, crowded.shape, torch.uint16, 64, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii,
+                      cfg.gain, 50000, saturation=cfg.saturation, device="cuda")
+    ex.run(dev(crowded))
+    ctx.sync()
+    assert int((ex.out["segmap"][:, 512:] != 0).sum()) > 1000
+    ex.run(dev(sparse))
+    ctx.sync()
+    fresh = ctx.gp_extract(dev(sparse), 64, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii, cfg.gain,
+                           capacity=50000, saturation=cfg.saturation)
+    ctx.sync()
+    assert torch.equal(ex.out["segmap"], fresh["segmap"])
+    n = int(fresh["catalog"]["n"].item())
+    assert int(ex.out["catalog"]["n"].item()) == n
+    for k, v in fresh["catalog"].items():
+        if k != "n":
+            assert torch.equal(ex.out["catalog"][k][:n], v[:n]), k
+    # far from the crowded strip (the spline background blends across about
+    # a mesh box there) the frame is plain sky: no segments, where the
+    # crowded frame left many
+    assert int((fresh["segmap"][:, 512:] != 0).sum()) == 0
+    assert int((ex.out["segmap"][:, 512:] != 0).sum()) == 0
+
+
 # ------------------------------------------------------------- edge cases ---
 def test_constant_frame_has_no_detections(ctx):
     img = np.full((200, 300), 1234, np.uint16)
