@@ -647,9 +647,16 @@ __global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restr
         }
     }
     __syncthreads();
-    for (int p = tid; p < TNPIX; p += DT_NT) {
-        const int l = S.lab[p];
-        if (l >= 0) S.lab[p] = S.lab[l];
+    {
+        // foreground pixels only (thread: 8 columns of one row); run heads
+        // hold their roots, which this pass does not change
+        const int py = tid >> 3, xs = (tid & 7) * 8;
+        uint32_t fgb = (uint32_t)((row_mask(S, py) >> xs) & 0xffu);
+        while (fgb) {
+            const int p = py * TX + xs + __ffs(fgb) - 1;
+            fgb &= fgb - 1;
+            S.lab[p] = S.lab[S.lab[p]];
+        }
     }
     __syncthreads();
 
