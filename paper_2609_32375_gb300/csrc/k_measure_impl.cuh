@@ -111,7 +111,7 @@ struct BEntry {
     float dx0, dy0, m, var;
     int kf;                 // mask of the radii crossing the pixel | bad << 8 | saturated << 9
 };
-constexpr int QCAP = 96;
+constexpr int QCAP = 64;      // at most 31 waiting + 32 added by one row
 constexpr int MEAS_NT = 256;
 
 template <int NR>
@@ -241,9 +241,12 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
                 wq[qn + __popc(bal & lt)] = e;
             }
             qn += __popc(bal);
-            if (qn > QCAP - 32) {
-                flush_queue<NR>(ap, wq, qn, f, v, fl);
-                qn = 0;
+            if (qn >= 32) {
+                // one full round of 32 entries; the rest (< 32) moves to the front
+                flush_queue<NR>(ap, wq, 32, f, v, fl);
+                if (lane < qn - 32) wq[lane] = wq[lane + 32];
+                __syncwarp();
+                qn -= 32;
             }
         }
     }
