@@ -48,7 +48,9 @@ MeasureArgs measure_args(const Image& im, const SplineTab& sb, const SplineTab& 
 // every frame of a batch shares `one`'s dtype and number of radii
 cudaError_t launch_measure_any(const MeasureArgs& one, const MeasureArgs* batch, int nframes, cudaStream_t st)
 {
-    int g = 152 * 8 / nframes;
+    // exactly the resident CTAs (3 per SM at the kernel's launch bounds): the
+    // warps' grid-stride loops share the sources with no partial last wave
+    int g = 152 * 3 / nframes;
     if (g < 16) g = 16;
     const dim3 grid(g, nframes);
     if (batch) return launch_measure_batched(one, batch, grid, st);
@@ -74,7 +76,7 @@ cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTa
 {
     ApSpec ap = make_ap(radii, nr, gain);
     int64_t g64 = ((int64_t)n * 32 + 255) / 256;
-    int g = (int)(g64 < 152 * 8 ? g64 : 152 * 8);
+    int g = (int)(g64 < 152 * 3 ? g64 : 152 * 3);
     if (g < 1) g = 1;
     if (im.is_f32) return dispatch_nr<ApertureLaunch, true>(nr, im, sb, sr, ap, xs, ys, n, flux, ferr, fl, g, st);
     return dispatch_nr<ApertureLaunch, false>(nr, im, sb, sr, ap, xs, ys, n, flux, ferr, fl, g, st);
