@@ -957,7 +957,8 @@ __device__ __forceinline__ void df_add_pair(DF& s, float2 v)
 // One warp per piece.  At root pieces of kept segments: merge the partial
 // moments of all the segment's pieces, visiting the tiles of the segment's
 // bounding box in raster order (a fixed order, so the sums are
-// reproducible) and emit the segment.  Every piece whose final label differs
+// reproducible) and emit the segment; a segment of a single piece is emitted
+// from that piece's sums directly (the merge would add zeros to them).  Every piece whose final label differs
 // from its provisional one rewrites its pixels in the map.
 __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
@@ -977,7 +978,38 @@ __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_c
         if (r < 0) continue;
         const int tot = P.agg_npix[r];
         const uint32_t fin = tot >= minarea ? P.agg_min[r] + 1u : 0u;
-        if (r == p && fin) {
+        if (r == p && fin && tot == P.npix[p]) {
+            // a segment of this one piece: its sums, taken about the corner of
+            // its one tile (the segment's origin), are already final
+            if (lane == 0) {
+                const Moments mo = P.mom[p];
+                const int id = atomicAdd(C.count, 1);
+                if (id < C.cap) {
+                    DF s, sx, sy, sxx, syy, sxy;
+                    s.hi = mo.s.x; s.lo = mo.s.y; sx.hi = mo.sx.x; sx.lo = mo.sx.y; sy.hi = mo.sy.x; sy.lo = mo.sy.y;
+                    sxx.hi = mo.sxx.x; sxx.lo = mo.sxx.y; syy.hi = mo.syy.x; syy.lo = mo.syy.y;
+                    sxy.hi = mo.sxy.x; sxy.lo = mo.sxy.y;
+                    const int4 bb = P.agg_bbox[r];
+                    uint32_t fl = mo.flags;
+                    if (df_positive(s)) {
+                        comp_store_raw(C, id, s, sx, sy, sxx, syy, sxy);     // finished by k_mom_finish
+                    } else {
+                        const int2 org = comp_origin(bb);
+                        double flux;
+                        double2 xy;
+                        Mom2 m2;
+                        mom_finish(df_value(s), df_value(sx), df_value(sy), df_value(sxx), df_value(syy),
+                                   df_value(sxy), mo.ux, mo.uy, mo.uxx, mo.uyy, mo.uxy, tot, org.x, org.y, &flux,
+                                   &xy, &m2, &fl);
+                        C.flux[id] = flux; C.xy[id] = xy; C.mom2[id] = m2;
+                    }
+                    C.label[id] = fin; C.npix[id] = tot; C.bbox[id] = bb;
+                    C.peak[id] = mo.peak; C.peakL[id] = mo.peakL; C.flags[id] = fl;
+                } else {
+                    set_status(status, GP_ERR_INTERNAL);
+                }
+            }
+        } else if (r == p && fin) {
             const int4 bb = P.agg_bbox[r];
             const int2 org = comp_origin(bb);
             const int X0 = org.x, Y0 = org.y;
