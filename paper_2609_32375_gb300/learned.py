@@ -5,7 +5,7 @@ maps one-pass per-box quantile features to the background / rms meshes.
 Every layer, loss, gradient and optimiser step runs in the library's CUDA
 kernels (gp_cnn_*); this module only owns the buffers and the schedule.
 Targets come from the plain estimator (gp_background), which stays as the
-fallback and as the judge of the network's error.
+fallback and as the reference for the network's error.
 
 Training frames are drawn on the GPU with a seeded generator: sky level,
 linear gradients, vignetting, moonlight ramps, random-field nebulosity and
