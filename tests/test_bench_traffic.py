@@ -5,7 +5,6 @@ into null rather than report stale counters."""
 import importlib.util
 import json
 import os
-import shutil
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -30,17 +29,17 @@ def test_committed_traffic_is_well_formed():
 
 
 def test_traffic_turns_null_when_a_source_changes(tmp_path):
-    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    kernel, e = next(iter(d.items()))
+    import hashlib
+    src = tmp_path / "csrc" / "k_x.cu"
+    os.makedirs(src.parent)
+    src.write_text("__global__ void k_x() {}\n")
+    entry = {"workload": "w", "dram_bytes_per_launch": 3, "read": 2, "write": 1, "sources": ["csrc/k_x.cu"],
+             "sources_sha1": hashlib.sha1(src.read_bytes()).hexdigest(), "summary": "profiles/x.md"}
     os.makedirs(tmp_path / "profiles")
-    shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
-    for src in e["sources"]:
-        os.makedirs(os.path.dirname(tmp_path / src), exist_ok=True)
-        shutil.copy(os.path.join(ROOT, src), tmp_path / src)
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k_x": entry}))
     b = load_bench(str(tmp_path))
-    assert b.kernel_traffic(kernel, e["workload"]) == float(e["dram_bytes_per_launch"])
-    assert b.kernel_traffic(kernel, "another_workload") is None
-    with open(tmp_path / e["sources"][0], "a") as f:
-        f.write("\n// changed\n")
-    assert b.kernel_traffic(kernel, e["workload"]) is None
-    assert b.kernel_traffic("no_such_kernel", e["workload"]) is None
+    assert b.kernel_traffic("k_x", "w") == 3.0
+    assert b.kernel_traffic("k_x", "another_workload") is None
+    assert b.kernel_traffic("k_y", "w") is None
+    src.write_text("__global__ void k_x() { /* changed */ }\n")
+    assert b.kernel_traffic("k_x", "w") is None
