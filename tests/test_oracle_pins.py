@@ -421,6 +421,27 @@ def test_aperture_constant_image_and_flags():
     assert flags[0, 0] & oracle.FLAG_BAD and flux[0, 0] == pytest.approx(2.0 * (math.pi * 4 - 1), rel=1e-12)
 
 
+def test_aperture_poisson_term_only_for_positive_flux_and_saturation_flag():
+    """err^2 = sum A var + max(F, 0) / gain: a negative sky-subtracted disc
+    adds no Poisson term; a saturated pixel inside a disc flags that disc
+    (and every larger one) without changing the sums."""
+    W, H = 40, 30
+    var = np.full((H, W), 4.0)
+    bad = np.zeros((H, W), np.uint8)
+    img = np.full((H, W), -3.0)
+    flux, err, flags = oracle.apertures(img, var, bad, None, [20.3], [15.1], [4.0], 1.5)
+    area = math.pi * 16.0
+    assert flux[0, 0] == pytest.approx(-3.0 * area, rel=1e-12)
+    assert err[0, 0] ** 2 == pytest.approx(4.0 * area, rel=1e-12)
+    sat = np.zeros((H, W), np.uint8)
+    sat[15, 26] = 1                                   # 5.7 px from the centre: inside r = 7 only
+    img = np.full((H, W), 2.0)
+    f1, e1, fl1 = oracle.apertures(img, var, bad, sat, [20.3], [15.1], [3.0, 7.0], 1.5)
+    f0, e0, fl0 = oracle.apertures(img, var, bad, None, [20.3], [15.1], [3.0, 7.0], 1.5)
+    assert np.array_equal(f1, f0) and np.array_equal(e1, e0)
+    assert not fl1[0, 0] & oracle.FLAG_SAT and fl1[0, 1] & oracle.FLAG_SAT
+
+
 # ----------------------------------------------------- whole-path invariants ---
 def test_constant_sky_has_no_detections():
     img = np.full((256, 320), 1500.0, np.float32)
