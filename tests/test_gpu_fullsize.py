@@ -1,6 +1,6 @@
 """Parity at the full dense workload -- 12288 x 12304 uint16, mesh 256, the
-5x5 filter, k = 1.5, radii 3/6/10 -- in the launch configuration bench.py
-times: the pre-allocated Extractor, catalog capacity 400,000, no optional
+5x5 filter, k = 1.5, radii 3/6/10, and the same recipe on the paper's 14200 x
+10650 frame shape -- in the launch configuration bench.py times: the pre-allocated Extractor, catalog capacity 400,000, no optional
 maps.  The oracle cannot run the whole frame inside a test, so it checks
 sampled outputs it computes one by one:
 
@@ -30,10 +30,18 @@ CAPACITY = 400_000
 CW, CH = 320, 288                                  # crop size (several tiles and boxes)
 
 
-@pytest.fixture(scope="module")
-def run():
+# the frame bench.py measures, and the paper's own 151 MP frame shape
+# (14200 x 10650: ragged detection tiles and mesh boxes at full size) with
+# the same source density
+SHAPES = [None, (14200, 10650)]
+
+
+@pytest.fixture(scope="module", params=SHAPES, ids=["12288x12304", "14200x10650"])
+def run(request):
     cfg = synth.CONFIGS["dense_12288x12304_u16"]
-    img, _ = synth.make_frame(cfg, 0)              # the frame bench.py measures
+    if request.param is not None:
+        cfg = synth.scaled_config(cfg, *request.param)
+    img, _ = synth.make_frame(cfg, 0)
     H, W = img.shape
     L = gp.load_library()
     ctx = gp.Context(0, workspace_bytes=L.gp_workspace_bytes(W, H, cfg.mesh, CAPACITY) + (64 << 20))
