@@ -262,19 +262,12 @@ __device__ __forceinline__ float combine_row(const float4& rc, float v0, float v
     return fmaf(rc.z, m1, fmaf(rc.y, m0, fmaf(rc.x, v1 - v0, v0)));
 }
 
-// background and rms at staged cell (ry, c)
+// background at staged cell (ry, c)
 __device__ __forceinline__ float cell_bkg(const TileSmem& S, int ry, int c)
 {
     const int2 j = S.rowj[ry];
     return combine_row(S.rowc[ry], S.u.col.ub[j.x * SW + c], S.u.col.ub[j.y * SW + c], S.u.col.wb[j.x * SW + c],
                        S.u.col.wb[j.y * SW + c]);
-}
-
-__device__ __forceinline__ float cell_rms(const TileSmem& S, int ry, int c)
-{
-    const int2 j = S.rowj[ry];
-    return combine_row(S.rowc[ry], S.u.col.ur[j.x * SW + c], S.u.col.ur[j.y * SW + c], S.u.col.wr[j.x * SW + c],
-                       S.u.col.wr[j.y * SW + c]);
 }
 
 // A 16-byte chunk q of the staged window (row q / nchunk, chunk q % nchunk)
