@@ -94,6 +94,16 @@ typedef struct {
 gp_status gp_ctx_set_timing(gp_ctx* ctx, int32_t enable);
 gp_status gp_ctx_stats(gp_ctx* ctx, gp_stats* out);
 
+/* Failure detection.  The tile merge of segments across detection tiles
+ * (Section 3.2's segmentation, kept exact across tiles) walks union-find
+ * chains in device memory; every walk is bounded.  A walk that runs out of
+ * steps stops, records GP_ERR_TIMEOUT in the context's device status word
+ * (returned by the next gp_ctx_sync) and leaves that frame's segments
+ * incomplete; the stream and the context stay usable.  `steps` sets the
+ * bound for later calls on this context (0: the default, 2^22, far above
+ * any chain a frame can build).  GP_ERR_INVALID_ARG for steps < 0. */
+gp_status gp_ctx_set_walk_limit(gp_ctx* ctx, int32_t steps);
+
 /* Arena bytes needed to run gp_extract on a width x height frame with this
  * mesh size and catalog capacity (capacity <= 0: the default internal table
  * size of max(65536, width*height/32) segments). */

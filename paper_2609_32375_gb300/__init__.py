@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
                 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NOT_IMPLEMENTED", 7: "GP_ERR_INTERNAL"}
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
-           "gp_workspace_bytes",
+           "gp_ctx_set_walk_limit", "gp_workspace_bytes",
            "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static",
            "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
@@ -158,6 +158,8 @@ def load_library():
         L.gp_ctx_sync.restype = st
         L.gp_ctx_set_timing.argtypes = [vp, i32]
         L.gp_ctx_set_timing.restype = st
+        L.gp_ctx_set_walk_limit.argtypes = [vp, i32]
+        L.gp_ctx_set_walk_limit.restype = st
         L.gp_ctx_stats.argtypes = [vp, C.POINTER(GpStats)]
         L.gp_ctx_stats.restype = st
         L.gp_workspace_bytes.argtypes = [i32, i32, i32, i32]
@@ -306,6 +308,11 @@ class Context:
 
     def set_timing(self, enable: bool = True):
         _check(load_library().gp_ctx_set_timing(self._h, 1 if enable else 0))
+
+    def set_walk_limit(self, steps: int = 0):
+        """Bound on the steps of each union-find walk of the tile merge for
+        later calls (0: the library default); see gp_ctx_set_walk_limit."""
+        _check(load_library().gp_ctx_set_walk_limit(self._h, int(steps)))
 
     def stats(self):
         """Per-stage device milliseconds summed over the calls since the

@@ -31,6 +31,7 @@ struct gp_ctx {
     int nrec;              // calls recorded since the last gp_ctx_stats
     int slot;              // slot of the current call
     int launches;          // kernels launched by the current / last call
+    int walk_limit;        // union-find walk bound of the tile merge (0: the library default)
     ArgStage stage;        // pinned staging of batched calls' argument records
 };
 
@@ -226,15 +227,15 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
     if (p->nnear) GP_CUDA(cudaMemsetAsync(p->nnear, 0, sizeof(int), st));
     GP_CUDA(launch_detect_tiles(im, sb, sr, taps, p->kw, p->kh, p->thresh, p->minarea, segmap, p->mask_out, p->nnear,
-                                nullptr, w.T, w.P, w.C, ctx->dstatus, st));
+                                nullptr, w.D, w.T, w.P, w.C, ctx->dstatus, st));
     mark(ctx, 3, st);
-    GP_CUDA(launch_resolve(w.T, w.P, w.C, segmap, W, H, p->minarea, ctx->dstatus, st));
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, W, H, p->minarea, ctx->walk_limit, ctx->dstatus, st));
     mark(ctx, 4, st);
     GP_CUDA(launch_rank(w.C, cat->n, cat->capacity, true, ctx->dstatus, st));
     mark(ctx, 5, st);
     GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
     mark(ctx, 6, st);
-    ctx->launches += 1 + 4 + 4 + 1 + (nr > 0 ? 1 : 0);
+    ctx->launches += 3 + 4 + 4 + 1 + (nr > 0 ? 1 : 0);
     return GP_OK;
 }
 
@@ -307,7 +308,8 @@ gp_status background_call(gp_ctx* ctx, const gp_image* img, const gp_bkg_params*
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     begin_call(ctx, st);
     Exec ex = ctx_exec(ctx, st);
-    const Params P = make_params(p, nullptr, nullptr, nullptr, net);
+    Params P = make_params(p, nullptr, nullptr, nullptr, net);
+    P.walk_limit = ctx->walk_limit;
     FrameIO F = frame_io(img, bkg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, ctx->dstatus);
     gp_status s = pipeline_result(run_background_only(ex, 1, &F, P), ex, ctx);
     bkg->mesh = F.bkg.mesh; bkg->mx = F.bkg.mx; bkg->my = F.bkg.my;
@@ -334,7 +336,8 @@ gp_status extract_call(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     begin_call(ctx, st);
     Exec ex = ctx_exec(ctx, st);
-    const Params P = make_params(bp, taps, dp, ap, net);
+    Params P = make_params(bp, taps, dp, ap, net);
+    P.walk_limit = ctx->walk_limit;
     FrameIO F = frame_io(img, bkg, segmap, cat, flux, fluxerr, apflags, dp, ctx->dstatus);
     s = pipeline_result(run_extract(ex, 1, &F, P), ex, ctx);
     bkg->mesh = F.bkg.mesh; bkg->mx = F.bkg.mx; bkg->my = F.bkg.my;
@@ -367,6 +370,7 @@ gp_status gp_ctx_create(int device, size_t workspace_bytes, gp_ctx** out)
     c->nrec = 0;
     c->slot = 0;
     c->launches = 0;
+    c->walk_limit = 0;
     c->arena_bytes = workspace_bytes + STATUS_BYTES;
     cudaError_t e = cudaMalloc(&c->arena, c->arena_bytes);
     if (e != cudaSuccess) {
@@ -409,6 +413,15 @@ gp_status gp_ctx_set_timing(gp_ctx* ctx, int32_t enable)
     }
     ctx->timing = enable ? 1 : 0;
     ctx->nrec = 0;
+    return GP_OK;
+}
+
+gp_status gp_ctx_set_walk_limit(gp_ctx* ctx, int32_t steps)
+{
+    gp_status s = check_ctx(ctx);
+    if (s != GP_OK) return s;
+    if (steps < 0) return fail(GP_ERR_INVALID_ARG, "negative walk limit");
+    ctx->walk_limit = steps;
     return GP_OK;
 }
 
@@ -552,14 +565,14 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
     begin_call(ctx, st);
     mark_to(ctx, 1, 2, st);
     GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
-    GP_CUDA(launch_detect_tiles(im, none, none, nullptr, 1, 1, 1.f, minarea, segmap, nullptr, nullptr, mask, w.T, w.P,
-                                w.C, ctx->dstatus, st));
+    GP_CUDA(launch_detect_tiles(im, none, none, nullptr, 1, 1, 1.f, minarea, segmap, nullptr, nullptr, mask, w.D, w.T,
+                                w.P, w.C, ctx->dstatus, st));
     mark(ctx, 3, st);
-    GP_CUDA(launch_resolve(w.T, w.P, w.C, segmap, width, height, minarea, ctx->dstatus, st));
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, width, height, minarea, ctx->walk_limit, ctx->dstatus, st));
     mark(ctx, 4, st);
     GP_CUDA(launch_rank(w.C, n_out, -1, false, ctx->dstatus, st));
     mark_to(ctx, 5, 6, st);
-    ctx->launches += 1 + 4 + 2;
+    ctx->launches += 3 + 4 + 2;
     return GP_OK;
 }
 
@@ -655,7 +668,8 @@ gp_status gp_extract_batch(gp_ctx* ctx, gp_frame* frames, int32_t n, const gp_bk
     }
     begin_call(ctx, st);
     Exec ex = ctx_exec(ctx, st);
-    const Params P = make_params(bp, taps, dp, ap, net);
+    Params P = make_params(bp, taps, dp, ap, net);
+    P.walk_limit = ctx->walk_limit;
     std::vector<FrameIO> F(n);
     for (int f = 0; f < n; ++f) {
         const gp_frame& x = frames[f];

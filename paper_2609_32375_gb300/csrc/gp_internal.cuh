@@ -43,18 +43,21 @@ __device__ __forceinline__ double sqrt_pos(double v)
 // ------------------------------------------------------------ constants ---
 constexpr int TX = 64;           // detection tile width  (pixels)
 constexpr int TY = 32;           // detection tile height
-constexpr int TNPIX = TX * TY;
-constexpr int MAXROOT = (TX / 2) * (TY / 2);  // most 8-connected segments a tile can hold
+constexpr int MAXRUN = TY * (TX / 2);   // most horizontal foreground runs a tile can hold
 constexpr int HMAX = 7;          // largest filter half-size (15 x 15 taps)
-constexpr int XHALO = 8;         // staged columns left of the tile (>= HMAX, keeps 16-byte alignment)
-constexpr int SW = TX + 2 * XHALO;
-constexpr int SH = TY + 2 * HMAX;
 constexpr int EDGE_PER_TILE = 2 * TY + 2 * TX;   // colL, colR, rowT, rowB
 constexpr int MAX_NR = 8;        // most aperture radii per call
-constexpr int NJMAX = 5;         // most mesh node rows one staged tile touches (mesh >= 16, SH <= 46 rows)
 
-// bounded-loop limit for union-find walks (a cycle would be a bug; the walk
-// gives up, records GP_ERR_TIMEOUT and the result is flagged invalid)
+// streaming detection geometry: a lane filters 4 adjacent columns, a warp a
+// 128-column strip (two detection tiles wide), a CTA ST_NW strips side by
+// side over ST_RC rows; the packed foreground mask holds, per frame row and
+// strip, four 32-bit words, word c bit l = column 4 l + c of the strip
+constexpr int ST_CPL = 4;
+constexpr int ST_STRIP = 32 * ST_CPL;
+
+// default bound on the steps of a global union-find walk (a cycle would be a
+// bug; the walk gives up, records GP_ERR_TIMEOUT and the result is flagged
+// invalid); a context can lower it (gp_ctx_set_walk_limit)
 constexpr int WALK_LIMIT = 1 << 22;
 
 __device__ __forceinline__ void set_status(int* st, int code)
@@ -310,6 +313,16 @@ struct Tiles {
     int* piece_cnt;       // [ntiles]
 };
 
+// the threshold mask of a frame, packed (k_stream), and the detection tiles
+// that hold foreground
+struct DetMask {
+    uint4* bits;          // [H][ceil(W / ST_STRIP)]
+    int* tl_list;         // [ntiles] appended tile indices
+    int* tl_count;        // scalar, cleared per call
+    int* dl_list;         // [ntiles] tiles too crowded for the labelling kernel's common form
+    int* dl_count;        // scalar, cleared per call
+};
+
 struct Image {
     const void* data;
     int64_t pitch;
@@ -366,18 +379,26 @@ struct MeshArgs {
 
 constexpr int KMAX = (2 * HMAX + 1) * (2 * HMAX + 1);
 
-// tile detection (k_detect_tile)
+// detection (k_stream, k_pack_mask, k_label_tiles, k_merge)
 struct DetectArgs {
-    float K[KMAX];            // normalised taps, kh rows of kw
+    // the normalised kernel, padded to ks x ks (ks odd), as a sum of nrank
+    // separable terms: K[v][u] = sum_r fv[r ks + v] fh[r ks + u]
+    float fv[KMAX], fh[KMAX];
+    int ks, nrank;
     Image im;
     SplineTab sb, sr;
-    int kw, kh, hx, hy, hh;   // taps, half sizes, staged halo
     float thresh;
     int minarea;
     uint32_t* seg;
     uint8_t* mask_out;
     int* nnear;
     const uint8_t* in_mask;   // labelling of a given mask
+    uint4* bits;              // packed foreground mask [H][nstrip]
+    int nstrip;               // ceil(W / ST_STRIP)
+    int* tl_list;             // detection tiles holding foreground (appended)
+    int* tl_count;
+    int* dl_list;             // of those, the ones deferred to the big labelling form
+    int* dl_count;
     Tiles T;
     Pieces P;
     Comps C;
@@ -391,7 +412,10 @@ struct ResolveArgs {
     Pieces P;
     Comps C;
     uint32_t* seg;
+    const int* tl_list;       // tiles holding foreground (the only ones with pieces)
+    const int* tl_count;
     int W, H, minarea;
+    int walk_limit;           // steps a union-find walk may take before it gives up (GP_ERR_TIMEOUT)
     int* status;
 };
 

@@ -24,13 +24,19 @@ cudaError_t launch_mesh_all(const double* bkg_raw, const double* rms_raw, const 
 cudaError_t launch_bkg_maps(const SplineTab& sb, const SplineTab& sr, int W, int H, float* bmap, float* rmap,
                             cudaStream_t st);
 
-// detection (k_detect.cu)
+// detection (k_stream.cu: threshold mask; k_detect.cu: labelling, merge, rank)
+int stream_ctas(int W, int H);
+int pack_warps(int W, int H);
+int stream_ks(int kw, int kh);
+int detect_grid(int W, int H, bool given_mask);
+cudaError_t launch_stream_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxgrid,
+                              cudaStream_t st);
 cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
                                 int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
-                                int* nnear, const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C,
-                                int* status, cudaStream_t st);
-cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H,
-                           int minarea, int* status, cudaStream_t st);
+                                int* nnear, const uint8_t* in_mask, const DetMask& dm, const Tiles& T,
+                                const Pieces& P, const Comps& C, int* status, cudaStream_t st);
+cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
+                           int H, int minarea, int walk_limit, int* status, cudaStream_t st);
 cudaError_t launch_rank(const Comps& C, int* n_out, int capacity, bool place, int* status, cudaStream_t st);
 
 // measurement (k_measure.cu)
@@ -55,11 +61,12 @@ cudaError_t launch_mesh_all_any(const MeshArgs& one, const MeshArgs* batch, int 
                                 cudaStream_t st);
 DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw, int kh,
                        float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
-                       const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C, int* status);
-cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
+                       const uint8_t* in_mask, const DetMask& dm, const Tiles& T, const Pieces& P, const Comps& C,
+                       int* status);
+cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxgrid,
                               cudaStream_t st);
-ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H, int minarea,
-                         int* status);
+ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
+                         int H, int minarea, int walk_limit, int* status);
 cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch, int nframes, int maxtiles,
                                cudaStream_t st);
 RankArgs rank_args(const Comps& C, int* n_out, int capacity, bool place, int* status);

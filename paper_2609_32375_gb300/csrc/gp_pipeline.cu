@@ -74,6 +74,11 @@ void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w, int** zero)
     w.T.edges = cv.take<int16_t>((size_t)ntiles * EDGE_PER_TILE);
     w.T.piece_base = cv.take<int>(ntiles);
     w.T.piece_cnt = cv.take<int>(ntiles);
+    w.D.bits = cv.take<uint4>((size_t)H * ((W + ST_STRIP - 1) / ST_STRIP));
+    w.D.tl_list = cv.take<int>(ntiles);
+    w.D.tl_count = w.zero + 16;
+    w.D.dl_list = cv.take<int>(ntiles);
+    w.D.dl_count = w.zero + 17;
     w.P.count = w.zero + 0;
     w.P.cap = piece_cap_for(npix);
     w.P.root = cv.take<uint32_t>(w.P.cap);
@@ -298,7 +303,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     std::vector<ResolveArgs> res(detect ? n : 0);
     std::vector<RankArgs> rank(detect ? n : 0);
     std::vector<MeasureArgs> meas(detect ? n : 0);
-    int maxbox = 0, maxtiles = 0;
+    int maxbox = 0, maxgrid = 0, maxtiles = 0;
     size_t mesh_smem = 0;
     for (int f = 0; f < n; ++f) {
         FrameWork& x = w[f];
@@ -320,11 +325,13 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
         }
         if (!detect) continue;
         det[f] = detect_args(im, x.sb, x.sr, P.taps, P.kw, P.kh, P.thresh, P.minarea, F[f].segmap, F[f].mask_out,
-                             F[f].nnear, nullptr, x.dw.T, x.dw.P, x.dw.C, F[f].status);
-        res[f] = resolve_args(x.dw.T, x.dw.P, x.dw.C, F[f].segmap, x.W, x.H, P.minarea, F[f].status);
+                             F[f].nnear, nullptr, x.dw.D, x.dw.T, x.dw.P, x.dw.C, F[f].status);
+        res[f] = resolve_args(x.dw.T, x.dw.P, x.dw.C, x.dw.D, F[f].segmap, x.W, x.H, P.minarea, P.walk_limit,
+                              F[f].status);
         rank[f] = rank_args(x.dw.C, F[f].cat.n, F[f].cat.capacity, true, F[f].status);
         meas[f] = measure_args(im, x.sb, x.sr, x.dw.C, F[f].cat, P.radii, P.nr, P.gain, F[f].apflux, F[f].apferr,
                                F[f].apflags);
+        maxgrid = std::max(maxgrid, detect_grid(x.W, x.H, false));
         maxtiles = std::max(maxtiles, x.dw.T.ntx * x.dw.T.nty);
     }
     const int nfused = (int)mesh.size();
@@ -398,7 +405,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     // ---- detection, segment resolution, catalog order, measurement
     for (int f = 0; f < n; ++f)
         if (F[f].nnear) PL_CUDA(cudaMemsetAsync(F[f].nnear, 0, sizeof(int), ex.st));
-    PL_CUDA(launch_detect_any(det[0], d_det, n, maxtiles, ex.st));
+    PL_CUDA(launch_detect_any(det[0], d_det, n, maxgrid, ex.st));
     ex.at(3);
     PL_CUDA(launch_resolve_any(res[0], d_res, n, maxtiles, ex.st));
     ex.at(4);
@@ -406,7 +413,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     ex.at(5);
     PL_CUDA(launch_measure_any(meas[0], d_meas, n, ex.st));
     ex.at(6);
-    ex.launches += 1 + 4 + 4 + 1 + (P.nr > 0 ? 1 : 0);
+    ex.launches += 3 + 4 + 4 + 1 + (P.nr > 0 ? 1 : 0);
     return GP_OK;
 }
 

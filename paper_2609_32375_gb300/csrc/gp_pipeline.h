@@ -44,6 +44,7 @@ struct DetWork {
     Tiles T;
     Pieces P;
     Comps C;
+    DetMask D;
     int* zero;       // counters, bucket counts and cursors: one block cleared per call
     int nzero;
 };
@@ -107,6 +108,7 @@ struct Params {
     int nr;
     float gain;
     const gp_cnn_weights* net;       // learned background, or null for the clipped estimator
+    int walk_limit;                  // bound on a union-find walk of the tile merge (0: the default)
 };
 
 // Result codes: GP_OK, GP_ERR_OOM (ex.cv ran past its end: nothing was

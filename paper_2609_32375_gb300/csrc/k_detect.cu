@@ -1,25 +1,28 @@
-// k_detect.cu -- matched-filter detection and segmentation (paper Section
-// 3.2, with labelled segments in place of the paper's local maxima) and the
+// k_detect.cu -- segmentation of the thresholded frame (paper Section 3.2,
+// with labelled segments in place of the paper's local maxima) and the
 // segment moments (its first-moment centroid, extended to second moments,
-// bounding box and peak).
+// bounding box and peak).  The threshold mask comes from k_stream.cu.
 //
-//  k_detect_tile  one CTA per 64 x 32 tile.  Stages the tile plus a filter
-//                 halo in shared memory as m = I - B (the spline background
-//                 evaluated from per-column node rows; 16-byte vector loads
-//                 on interior tiles), correlates it with the normalised
-//                 kernel (each thread slides down 8 rows of one column),
-//                 thresholds F > k sigma(p), labels the tile's 8-connected
-//                 components by union-find in shared memory (root = minimum
-//                 index = the segment's first pixel in raster order) and
-//                 accumulates each component's moment sums from the staged m
-//                 (one warp per component, fixed order).  A tile without
-//                 foreground writes its empty map rows and edge records and
-//                 stops after thresholding.  Components that do not touch an
-//                 edge shared with another tile are final here (raw sums);
-//                 the others become "pieces" with partial sums, and their
-//                 edge pixels are recorded for the merge.
+//  k_label_tiles  one warp per 64 x 32 detection tile that holds foreground
+//                 (the list k_stream appends).  Lane y takes tile row y: its
+//                 64-bit row mask, its horizontal runs (numbered in raster
+//                 order), and the unions of its runs with the touching runs
+//                 of the row above (8-connectivity) in a per-warp union-find
+//                 in shared memory whose roots are the smallest run ids (the
+//                 first run, and so the minimum linear index, of each
+//                 component).  Per root: pixel count and tile-edge contact
+//                 (one shared atomic per run), then for each kept root, in
+//                 raster order, its bounding box (warp min/max) and its
+//                 moment sums over its pixels with m = I - B recomputed there
+//                 (fixed order: x within a row, then a fixed butterfly over
+//                 the rows).  Components that do not touch an edge shared
+//                 with another tile are final here (raw sums); the others
+//                 become "pieces" with partial sums, and their edge pixels
+//                 are recorded for the merge.  The labels of kept
+//                 components are written over the zero map.
 //  k_merge        unites pieces across tile edges (lock-free union-find
-//                 over piece ids, atomicMin linking).
+//                 over piece ids, atomicMin linking), one warp per listed
+//                 tile with pieces.
 //  k_aggregate    sums piece sizes, bounding boxes and minimum indices at
 //                 each union-find root.
 //  k_finalize     merges the partial moments of each multi-tile segment in
@@ -32,6 +35,9 @@
 //  k_rank_*       orders segments by label (bucket counts, one scan,
 //                 scatter, in-bucket rank): a deterministic catalog order.
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
 
 #include "gp_internal.cuh"
 #include "gp_launch.h"
@@ -39,94 +45,58 @@
 namespace gp {
 
 static_assert(TX == 64, "row masks hold one 64-pixel tile row");
-constexpr int DT_NT = 256;
-constexpr int ROWS_PER_THREAD = TNPIX / DT_NT;     // 8: each thread filters 8 rows of one column
-
-// mirror without edge repeat, cheap for offsets within one reflection
-__device__ __forceinline__ int mirror_fast(int i, int N)
-{
-    if (i < 0) i = -i;
-    if (i >= N) i = 2 * (N - 1) - i;
-    return (i >= 0 && i < N) ? i : mirror_idx(i, N);
-}
+static_assert(TY == 32, "a warp's lane is a tile row");
 
 // ------------------------------------------------ shared-memory union-find ---
-__device__ __forceinline__ int sfind(volatile int* lab, int x)
+// over the run ids of one tile; a link always points at a smaller id
+__device__ __forceinline__ int lfind(volatile int* par, int x)
 {
-    for (int n = 0; n < TNPIX + 1; ++n) {
-        int p = lab[x];
+    for (int n = 0; n <= MAXRUN; ++n) {
+        const int p = par[x];
         if (p == x) return x;
         x = p;
     }
     return x;
 }
 
-__device__ __forceinline__ void sunite(int* lab, int a, int b)
+__device__ __forceinline__ void lunite(int* par, int a, int b)
 {
-    for (int it = 0; it < 4 * TNPIX; ++it) {
-        a = sfind(lab, a);
-        b = sfind(lab, b);
+    for (int it = 0; it < 4 * MAXRUN; ++it) {
+        a = lfind(par, a);
+        b = lfind(par, b);
         if (a == b) return;
-        if (a < b) { int t = a; a = b; b = t; }
-        int old = atomicMin(lab + a, b);
+        if (a < b) { const int t = a; a = b; b = t; }
+        const int old = atomicMin(par + a, b);
         if (old == a) return;
         a = old;
     }
 }
 
 // ---------------------------------------------------- global union-find ---
-__device__ __forceinline__ int gfind(const int* parent, int x)
+// walks give up after `limit` steps (-1 / GP_ERR_TIMEOUT)
+__device__ __forceinline__ int gfind(const int* parent, int x, int limit)
 {
-    for (int n = 0; n < WALK_LIMIT; ++n) {
-        int p = __ldcg(parent + x);
+    for (int n = 0; n < limit; ++n) {
+        const int p = __ldcg(parent + x);
         if (p == x) return x;
         x = p;
     }
     return -1;
 }
 
-__device__ void gunite(int* parent, int a, int b, int* status)
+__device__ void gunite(int* parent, int a, int b, int limit, int* status)
 {
-    for (int it = 0; it < WALK_LIMIT; ++it) {
-        a = gfind(parent, a);
-        b = gfind(parent, b);
+    for (int it = 0; it < limit; ++it) {
+        a = gfind(parent, a, limit);
+        b = gfind(parent, b, limit);
         if (a < 0 || b < 0) break;
         if (a == b) return;
-        if (a < b) { int t = a; a = b; b = t; }
-        int old = atomicMin(parent + a, b);
+        if (a < b) { const int t = a; a = b; b = t; }
+        const int old = atomicMin(parent + a, b);
         if (old == a) return;
         a = old;
     }
     set_status(status, GP_ERR_TIMEOUT);
-}
-
-// block-wide exclusive scan of one int per thread (DT_NT threads)
-__device__ __forceinline__ int block_excl_scan(int v, int* warp_tot, int* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < DT_NT / 32 ? warp_tot[lane] : 0;
-        int wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < DT_NT / 32) warp_tot[lane] = wi - w;
-        if (lane == DT_NT / 32 - 1) *total = wi;
-    }
-    __syncthreads();
-    int r = warp_tot[warp] + incl - v;
-    __syncthreads();
-    return r;
 }
 
 // ------------------------------------------------------------- moments ---
@@ -224,692 +194,449 @@ __device__ __forceinline__ void comp_store_raw(const Comps& C, int id, DF s, DF 
     m[1] = make_float4(sxy.hi, sxy.lo, 0.f, 0.f);
 }
 
-// ----------------------------------------------------------- tile kernel ---
-// Staged columns: SMEM column c holds frame column x0 - XHALO + c (so 16-byte
-// chunks of the frame land on 16-byte boundaries); staged rows: row r holds
-// frame row y0 - hh + r.
-struct TileSmem {
-    float m[SH * SW];                 // staged pixels, then m = I - B
-    int lab[TNPIX];
-    uint8_t pflag[TNPIX];             // bit 0 bad, bit 1 saturated
-    union {
-        struct {                      // per staged column and node row (SoA)
-            float ub[NJMAX * SW], wb[NJMAX * SW], ur[NJMAX * SW], wr[NJMAX * SW];
-        } col;
-        short rid[TNPIX];             // after thresholding: root pixel -> compact root id
-    } u;
-    float4 rowc[SH];                  // per staged row: (b, c0, c1, -)
-    int2 rowj[SH];
-    int r_npix[MAXROOT];
-    int r_xmin[MAXROOT], r_xmax[MAXROOT], r_ymin[MAXROOT], r_ymax[MAXROOT];
-    int r_pidx[MAXROOT];              // border flag, then local piece index
-    int r_pix[MAXROOT];               // root's tile pixel
-    int r_val[MAXROOT];               // value written to the map
-    int r_rec[MAXROOT];               // piece id (>= 0), -2 - component id, or -1
-    uint32_t rmask[2 * TY];           // foreground bits per tile row (two 32-pixel halves)
-    int warp_tot[DT_NT / 32];
-    int jlo, jhi, nroots, npieces, ncomps, pbase, cbase, nnear;
+// ---------------------------------------------------------- tile labelling ---
+// Per-warp tables.  The common form holds up to 256 runs and 512 foreground
+// pixels per tile; a tile above either is deferred to the big form, where
+// every tile fits (1024 runs, 2048 pixels).
+template <bool BIG>
+struct LabelCfg {
+    static constexpr int NW = BIG ? 2 : 4;
+    static constexpr int RUNS = BIG ? MAXRUN : 256;
+    static constexpr int FG = BIG ? TX * TY : 512;
 };
 
-// the 64 foreground bits of tile row y (bit x = pixel x)
-__device__ __forceinline__ uint64_t row_mask(const TileSmem& S, int y)
-{
-    return (uint64_t)S.rmask[2 * y] | ((uint64_t)S.rmask[2 * y + 1] << 32);
-}
+// a kept segment of at most this many pixels is summed by one lane (32 such
+// segments at once); larger ones by the whole warp, a lane per tile row
+constexpr int LANE_SEG_MAX = 64;
 
-__device__ __forceinline__ float combine_row(const float4& rc, float v0, float v1, float m0, float m1)
-{
-    return fmaf(rc.z, m1, fmaf(rc.y, m0, fmaf(rc.x, v1 - v0, v0)));
-}
-
-// background at staged cell (ry, c)
-__device__ __forceinline__ float cell_bkg(const TileSmem& S, int ry, int c)
-{
-    const int2 j = S.rowj[ry];
-    return combine_row(S.rowc[ry], S.u.col.ub[j.x * SW + c], S.u.col.ub[j.y * SW + c], S.u.col.wb[j.x * SW + c],
-                       S.u.col.wb[j.y * SW + c]);
-}
-
-// A 16-byte chunk q of the staged window (row q / nchunk, chunk q % nchunk)
-// as raw bits: 8 uint16 pixels or 4 float32 pixels.  The frame's last chunk
-// of a row may stop short of the vector width: those lanes repeat the last
-// column (they lie outside the columns in use).
-template <bool F32>
-__device__ __forceinline__ uint4 load_chunk(const Image& im, int xa, int nchunk, unsigned inv_nchunk, int gy0, int q)
-{
-    constexpr int VEC = F32 ? 4 : 8;
-    const int ry = (int)(((unsigned)q * inv_nchunk) >> 16), ch = q - ry * nchunk;
-    const int64_t row = (int64_t)(gy0 + ry) * im.pitch;
-    const int gx0 = xa + ch * VEC, W = im.W;
-    if (gx0 + VEC <= W) {
-        if (F32) {
-            const float4 w = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(im.data) + row + gx0));
-            return make_uint4(__float_as_uint(w.x), __float_as_uint(w.y), __float_as_uint(w.z), __float_as_uint(w.w));
-        }
-        return __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const uint16_t*>(im.data) + row + gx0));
-    }
-    uint32_t w[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        if (F32) {
-            const int gx = gx0 + e < W ? gx0 + e : W - 1;
-            w[e] = __float_as_uint(__ldg(reinterpret_cast<const float*>(im.data) + row + gx));
-        } else {
-            const int ga = gx0 + 2 * e < W ? gx0 + 2 * e : W - 1, gb = gx0 + 2 * e + 1 < W ? gx0 + 2 * e + 1 : W - 1;
-            const uint16_t* px = reinterpret_cast<const uint16_t*>(im.data) + row;
-            w[e] = (uint32_t)__ldg(px + ga) | ((uint32_t)__ldg(px + gb) << 16);
-        }
-    }
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-struct StageGeo {
-    int xa, nchunk;
-    unsigned inv_nchunk;
-    int clo, chi, hh, th, tw, c_org;   // c_org: frame column of staged column 0
+template <bool BIG>
+struct LabelSmem {
+    static constexpr int R = LabelCfg<BIG>::RUNS, F = LabelCfg<BIG>::FG;
+    int par[R];                   // union-find; after flattening, the component's root run
+    int cnt[R];                   // at roots: pixels + (runs on a shared tile edge << 16)
+    int val[R];                   // at roots: the map value (1 + minimum linear index), 0 when dropped
+    int16_t pidx[R];              // at piece roots: local piece index, else -1
+    int16_t cidx[R];              // at kept final-segment roots: local index
+    int16_t pos[R];               // the run's row * TX + first column
+    int16_t fidx[R];              // compact index of the run's first pixel
+    int16_t klist[R];             // kept roots in label order
+    uint8_t len[R];               // the run's pixels - 1
+    float m[F];                   // m at the tile's foreground pixels, in raster order
+    uint32_t iv[F];               // the 32-bit word holding each foreground pixel's value (saturation)
 };
 
-// m = I - B of one chunk from its raw bits, the spline background taken
-// from the per-column node-row values (16-byte shared loads: a chunk starts
-// on a 4-column boundary); columns outside the ones in use get 0.  Bad
-// (non-finite) and saturated pixels of the tile are flagged.
-template <bool F32>
-__device__ __forceinline__ void stage_chunk(TileSmem& S, float sat, const StageGeo& g, uint4 raw, int q)
+// bits 0..15 of v to bits 0, 4, ..., 60
+__device__ __forceinline__ uint64_t spread4(uint32_t v)
 {
-    constexpr int VEC = F32 ? 4 : 8;
-    const int ry = (int)(((unsigned)q * g.inv_nchunk) >> 16), ch = q - ry * g.nchunk;
-    const int c0 = g.xa + ch * VEC - g.c_org;
-    float v[VEC];
-    const uint32_t u4[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        if (F32) {
-            v[e] = __uint_as_float(u4[e]);
-        } else {
-            v[2 * e] = (float)(u4[e] & 0xffffu);
-            v[2 * e + 1] = (float)(u4[e] >> 16);
-        }
-    }
-    const float4 rc = S.rowc[ry];
-    const int2 j = S.rowj[ry];
-    const int py = ry - g.hh;
-    const bool row_in = py >= 0 && py < g.th;
-#pragma unroll
-    for (int k = 0; k < VEC / 4; ++k) {
-        const int c = c0 + 4 * k;
-        const float4 u0 = *reinterpret_cast<const float4*>(S.u.col.ub + j.x * SW + c);
-        const float4 u1 = *reinterpret_cast<const float4*>(S.u.col.ub + j.y * SW + c);
-        const float4 w0 = *reinterpret_cast<const float4*>(S.u.col.wb + j.x * SW + c);
-        const float4 w1 = *reinterpret_cast<const float4*>(S.u.col.wb + j.y * SW + c);
-        const float a0[4] = {u0.x, u0.y, u0.z, u0.w}, a1[4] = {u1.x, u1.y, u1.z, u1.w};
-        const float b0[4] = {w0.x, w0.y, w0.z, w0.w}, b1[4] = {w1.x, w1.y, w1.z, w1.w};
-        float m[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float val = v[4 * k + e];
-            const int cc = c + e;
-            const bool bad = F32 ? !isfinite(val) : false;
-            const bool use = cc >= g.clo && cc < g.chi;
-            m[e] = (bad || !use) ? 0.f : val - combine_row(rc, a0[e], a1[e], b0[e], b1[e]);
-            const int px = cc - XHALO;
-            if (row_in && use && px >= 0 && px < g.tw)
-                S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && sat > 0.f && val >= sat) ? 2 : 0);
-        }
-        *reinterpret_cast<float4*>(S.m + ry * SW + c) = make_float4(m[0], m[1], m[2], m[3]);
-    }
+    uint64_t x = v & 0xffffu;
+    x = (x | (x << 24)) & 0x000000ff000000ffull;
+    x = (x | (x << 12)) & 0x000f000f000f000full;
+    x = (x | (x << 6)) & 0x0303030303030303ull;
+    x = (x | (x << 3)) & 0x1111111111111111ull;
+    return x;
 }
 
-// F at 8 consecutive rows of one column: slide the kernel window down the
-// column so each staged value is read once per kernel column
-template <int KS>
-__device__ __forceinline__ void filter_column(const TileSmem& S, const DetectArgs& A, int px, int py0, int hh,
-                                              float* F)
+// bits 0..x set (x in 0..63)
+__device__ __forceinline__ uint64_t upto(int x) { return (2ull << x) - 1ull; }
+
+// last column of the run that starts at x in row mask M
+__device__ __forceinline__ int run_end(uint64_t M, int x)
 {
-    if (KS > 0) {
-        constexpr int H = KS / 2;
-#pragma unroll
-        for (int i = 0; i < ROWS_PER_THREAD; ++i) F[i] = 0.f;
-        const int c0 = px + XHALO - H;
-        const int r0 = py0 + hh - H;
-#pragma unroll
-        for (int rr = 0; rr < ROWS_PER_THREAD + KS - 1; ++rr) {
-            float v[KS > 0 ? KS : 1];
-#pragma unroll
-            for (int u = 0; u < KS; ++u) v[u] = S.m[(r0 + rr) * SW + c0 + u];
-#pragma unroll
-            for (int i = 0; i < ROWS_PER_THREAD; ++i) {
-                const int kv = rr - i;
-                if (kv >= 0 && kv < KS) {
-#pragma unroll
-                    for (int u = 0; u < KS; ++u) F[i] = fmaf(A.K[kv * KS + u], v[u], F[i]);
-                }
-            }
-        }
-    } else {
-        for (int i = 0; i < ROWS_PER_THREAD; ++i) {
-            float f = 0.f;
-            const int r0 = py0 + i + hh - A.hy, c0 = px + XHALO - A.hx;
-            for (int v = 0; v < A.kh; ++v) {
-                const float* row = S.m + (r0 + v) * SW + c0;
-                const float* kr = A.K + v * A.kw;
-                for (int u = 0; u < A.kw; ++u) f = fmaf(kr[u], row[u], f);
-            }
-            F[i] = f;
-        }
-    }
+    const uint64_t rest = ~(M >> x);
+    return rest ? x + __ffsll((long long)rest) - 2 : 63;
 }
 
-// the frame's arguments: the kernel parameter itself for a single frame (a
-// compile-time choice, so the taps stay in the constant bank), else the
-// batch record of frame blockIdx.y
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
 template <bool BATCH>
-__device__ __forceinline__ const DetectArgs& detect_args(const DetectArgs* __restrict__ batch, const DetectArgs& one)
+__device__ __forceinline__ const DetectArgs& det_frame(const DetectArgs* __restrict__ batch, const DetectArgs& one)
 {
     if constexpr (BATCH) return batch[blockIdx.y];
     else return one;
 }
 
-template <bool F32, bool LABEL_ONLY, int KS, bool BATCH>
-__global__ void __launch_bounds__(DT_NT) k_detect_tile(const DetectArgs* __restrict__ batch,
-                                                       const __grid_constant__ DetectArgs one)
+// write the records of kept root r (lane-parallel or lane 0 of the warp path)
+template <bool LABEL_ONLY, bool BIG>
+__device__ __forceinline__ void emit_root(const DetectArgs& A, const LabelSmem<BIG>& S, int r, int4 bb, int pbase,
+                                          int cbase, int x0, int y0, const MomAcc& a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw);
-    const DetectArgs& A = detect_args<BATCH>(batch, one);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int W = A.im.W, H = A.im.H;
-    const int tile = blockIdx.x;
-    const int ntx = A.T.ntx;
-    if (BATCH && tile >= ntx * A.T.nty) return;
-    const int tx = tile % ntx, ty = tile / ntx;
-    const int x0 = tx * TX, y0 = ty * TY;
-    const int tw = min(TX, W - x0), th = min(TY, H - y0);
-    const int hh = LABEL_ONLY ? 0 : A.hh;
-
-    if (!LABEL_ONLY) {
-        const int srows = th + 2 * hh;
-        const int clo = XHALO - hh, chi = XHALO + tw + hh;      // staged columns in use
-        if (tid == 0) { S.jlo = 1 << 30; S.jhi = -1; S.nnear = 0; }
-        __syncthreads();
-        // spline coefficients of the staged rows (and the node rows they need)
-        AxCoef cy;
-        if (tid < srows) {
-            const int gy = mirror_fast(y0 - hh + tid, H);
-            cy = axis_coef(A.sb.ay, (float)gy);
-            atomicMin(&S.jlo, cy.i);
-            atomicMax(&S.jhi, cy.i1);
-        }
-        __syncthreads();
-        const int jlo = S.jlo;
-        const int nj = S.jhi - jlo + 1;
-        if (nj > NJMAX) {   // excluded by the host's mesh >= 16 rule
-            if (tid == 0) set_status(A.status, GP_ERR_INTERNAL);
-            return;
-        }
-        if (tid < srows) {
-            S.rowc[tid] = make_float4(cy.b, cy.c0, cy.c1, 0.f);
-            S.rowj[tid] = make_int2(cy.i - jlo, cy.i1 - jlo);
-        }
-        // ---- stage the pixels over tile + halo (mirror border) as m = I - B
-        const bool interior = x0 - hh >= 0 && x0 + tw + hh <= W && y0 - hh >= 0 && y0 + th + hh <= H;
-        constexpr int VEC = F32 ? 4 : 8;          // pixels per 16-byte load
-        const bool vec_ok = interior && !A.im.mask && ((((uintptr_t)A.im.data) & 15) == 0) &&
-                            ((A.im.pitch % VEC) == 0);
-        // 16-byte chunks covering [x0 - hh, x0 + tw + hh); frame column
-        // x0 - XHALO is chunk aligned, so chunks land on 16-byte boundaries
-        const int xa = (x0 - hh) & ~(VEC - 1);
-        const int nchunk = (x0 + tw + hh - xa + VEC - 1) / VEC;
-        // q / nchunk by multiply-shift, exact for every q < 46 * nchunk and nchunk <= 39
-        const unsigned inv_nchunk = (65536u + nchunk - 1) / nchunk;
-        const int nq = vec_ok ? srows * nchunk : 0;
-        // this thread's first two chunks are read before the column values
-        // are evaluated, so the two global-load latencies overlap
-        uint4 raw0 = make_uint4(0u, 0u, 0u, 0u), raw1 = raw0;
-        if (tid < nq) raw0 = load_chunk<F32>(A.im, xa, nchunk, inv_nchunk, y0 - hh, tid);
-        if (tid + DT_NT < nq) raw1 = load_chunk<F32>(A.im, xa, nchunk, inv_nchunk, y0 - hh, tid + DT_NT);
-
-        // spline values of node rows jlo.. at every staged column in use,
-        // one (node row, column) pair per thread
-        const int ncol = chi - clo;
-        for (int q = tid; q < nj * ncol; q += DT_NT) {
-            const int jj = q / ncol, c = clo + q - jj * ncol;
-            const int gx = mirror_fast(x0 - XHALO + c, W);
-            const AxCoef cx = axis_coef(A.sb.ax, (float)gx);
-            const float2 b = row_eval(A.sb, jlo + jj, cx);
-            const float2 r = row_eval(A.sr, jlo + jj, cx);
-            S.u.col.ub[jj * SW + c] = b.x; S.u.col.wb[jj * SW + c] = b.y;
-            S.u.col.ur[jj * SW + c] = r.x; S.u.col.wr[jj * SW + c] = r.y;
-        }
-        __syncthreads();
-
-        if (vec_ok) {
-            const StageGeo g{xa, nchunk, inv_nchunk, clo, chi, hh, th, tw, x0 - XHALO};
-            if (tid < nq) stage_chunk<F32>(S, A.im.sat, g, raw0, tid);
-            if (tid + DT_NT < nq) stage_chunk<F32>(S, A.im.sat, g, raw1, tid + DT_NT);
-            for (int q = tid + 2 * DT_NT; q < nq; q += DT_NT)
-                stage_chunk<F32>(S, A.im.sat, g, load_chunk<F32>(A.im, xa, nchunk, inv_nchunk, y0 - hh, q), q);
-        } else {
-            for (int ry = warp; ry < srows; ry += DT_NT / 32)
-            for (int c = clo + lane; c < chi; c += 32) {
-                const int gx = mirror_fast(x0 - XHALO + c, W), gy = mirror_fast(y0 - hh + ry, H);
-                float v;
-                bool bad;
-                if (F32) {
-                    v = __ldg(reinterpret_cast<const float*>(A.im.data) + (int64_t)gy * A.im.pitch + gx);
-                    bad = !isfinite(v);
-                } else {
-                    v = (float)__ldg(reinterpret_cast<const uint16_t*>(A.im.data) + (int64_t)gy * A.im.pitch + gx);
-                    bad = false;
-                }
-                if (A.im.mask && A.im.mask[(int64_t)gy * W + gx]) bad = true;
-                S.m[ry * SW + c] = bad ? 0.f : v - cell_bkg(S, ry, c);
-                const int py = ry - hh, px = c - XHALO;
-                if (py >= 0 && py < th && px >= 0 && px < tw)
-                    S.pflag[py * TX + px] = (bad ? 1 : 0) | ((!bad && A.im.sat > 0.f && v >= A.im.sat) ? 2 : 0);
-            }
-        }
-        __syncthreads();
-
-        // ---- matched filter and threshold: thread = one column, 8 rows
-        {
-            const int px = tid % TX;
-            const int py0 = (tid / TX) * ROWS_PER_THREAD;
-            float F[ROWS_PER_THREAD];
-            filter_column<KS>(S, A, px, py0, hh, F);
-            int nnear = 0;
-            // the column's rms node-row values, reloaded only when the row's
-            // node interval changes (the same for the whole warp)
-            int jc = -1;
-            float ru0 = 0.f, ru1 = 0.f, rw0 = 0.f, rw1 = 0.f;
-#pragma unroll
-            for (int i = 0; i < ROWS_PER_THREAD; ++i) {
-                const int py = py0 + i;
-                const int p = py * TX + px;
-                bool fg = false;
-                if (py < th && px < tw) {
-                    const int2 j = S.rowj[py + hh];          // staged rows 0 .. th + 2 hh - 1 are set
-                    if (j.x != jc) {
-                        const int c = px + XHALO;
-                        ru0 = S.u.col.ur[j.x * SW + c]; ru1 = S.u.col.ur[j.y * SW + c];
-                        rw0 = S.u.col.wr[j.x * SW + c]; rw1 = S.u.col.wr[j.y * SW + c];
-                        jc = j.x;
-                    }
-                    const float sig = combine_row(S.rowc[py + hh], ru0, ru1, rw0, rw1);
-                    const float thr = A.thresh * sig;
-                    fg = (F[i] > thr) && !(S.pflag[p] & 1);
-                    if (fabsf(F[i] - thr) <= 1e-5f * fabsf(thr)) ++nnear;
-                    if (A.mask_out) A.mask_out[(int64_t)(y0 + py) * W + x0 + px] = fg ? 1 : 0;
-                }
-                // the warp holds 32 consecutive pixels of this row
-                const unsigned bits = __ballot_sync(0xffffffffu, fg);
-                if (lane == 0) S.rmask[2 * py + (px >> 5)] = bits;
-            }
-            if (A.nnear) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) nnear += __shfl_xor_sync(0xffffffffu, nnear, o);
-                if (lane == 0 && nnear) atomicAdd(&S.nnear, nnear);
-            }
-        }
-        __syncthreads();
-        if (A.nnear && tid == 0 && S.nnear) atomicAdd(A.nnear, S.nnear);
-    } else {
-        for (int p = tid; p < TNPIX; p += DT_NT) {
-            const int py = p / TX, px = p - py * TX;
-            const bool fg = py < th && px < tw && A.in_mask[(int64_t)(y0 + py) * W + x0 + px] != 0;
-            const unsigned bits = __ballot_sync(0xffffffffu, fg);     // 32 consecutive pixels of row py
-            if (lane == 0) S.rmask[2 * py + (px >> 5)] = bits;
-            S.pflag[p] = 0;
-        }
-        __syncthreads();
-    }
-
-    // ---- a tile without foreground pixels (most tiles of a sparse field):
-    // the map rows are zero, every edge record is -1 and the tile has no
-    // pieces, exactly what the labelling below would write for it
-    if (!__syncthreads_or(tid < 2 * TY && S.rmask[tid] != 0u)) {
-        if (tid == 0) { A.T.piece_base[tile] = 0; A.T.piece_cnt[tile] = 0; }
-        if (tw == TX && (W & 3) == 0 && ((((uintptr_t)A.seg) & 15) == 0)) {
-            for (int p4 = tid; p4 < TNPIX / 4; p4 += DT_NT) {
-                const int py = p4 / (TX / 4), px = (p4 - py * (TX / 4)) * 4;
-                if (py < th) *reinterpret_cast<uint4*>(A.seg + (int64_t)(y0 + py) * W + x0 + px) = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t L = (uint32_t)S.val[r] - 1u;
+    const int npix = S.cnt[r] & 0xffff;
+    if (S.pidx[r] >= 0) {
+        const int id = pbase + S.pidx[r];
+        if (id < A.P.cap) {
+            A.P.root[id] = L; A.P.npix[id] = npix; A.P.bbox[id] = bb; A.P.parent[id] = id;
+            A.P.agg_min[id] = L; A.P.agg_npix[id] = npix; A.P.agg_bbox[id] = bb;
+            if (!LABEL_ONLY) {
+                Moments mo;
+                mo.s = df2(a.s); mo.sx = df2(a.sx); mo.sy = df2(a.sy);
+                mo.sxx = df2(a.sxx); mo.syy = df2(a.syy); mo.sxy = df2(a.sxy);
+                mo.ux = a.ux; mo.uy = a.uy; mo.uxx = a.uxx; mo.uyy = a.uyy; mo.uxy = a.uxy;
+                mo.peak = a.peak; mo.peakL = a.peakL; mo.flags = a.flags;
+                A.P.mom[id] = mo;
             }
         } else {
-            for (int p = tid; p < TNPIX; p += DT_NT) {
-                const int py = p / TX, px = p - py * TX;
-                if (py < th && px < tw) A.seg[(int64_t)(y0 + py) * W + x0 + px] = 0u;
-            }
+            set_status(A.status, GP_ERR_INTERNAL);
         }
-        int16_t* ed = A.T.edges + (int64_t)tile * EDGE_PER_TILE;
-        for (int q = tid; q < EDGE_PER_TILE; q += DT_NT) ed[q] = -1;
         return;
     }
+    const int id = cbase + S.cidx[r];
+    if (id >= A.C.cap) {
+        set_status(A.status, GP_ERR_INTERNAL);
+        return;
+    }
+    A.C.label[id] = L + 1u; A.C.npix[id] = npix; A.C.bbox[id] = bb;
+    if (LABEL_ONLY) return;
+    uint32_t fl = a.flags;
+    if (df_positive(a.s)) {
+        // sums about the tile corner (x0, y0), finished by k_mom_finish
+        comp_store_raw(A.C, id, a.s, a.sx, a.sy, a.sxx, a.syy, a.sxy);
+    } else {
+        double flux;
+        double2 xy;
+        Mom2 m2;
+        mom_finish(df_value(a.s), df_value(a.sx), df_value(a.sy), df_value(a.sxx), df_value(a.syy), df_value(a.sxy),
+                   a.ux, a.uy, a.uxx, a.uyy, a.uxy, npix, x0, y0, &flux, &xy, &m2, &fl);
+        A.C.flux[id] = flux; A.C.xy[id] = xy; A.C.mom2[id] = m2;
+    }
+    A.C.peak[id] = a.peak; A.C.peakL[id] = a.peakL; A.C.flags[id] = fl;
+}
 
-    // ---- tile-local labelling on horizontal runs.  Every foreground pixel
-    // points at the first pixel of its run (the run's minimum index); only
-    // run heads take part in the union-find.  A run is united with each run
-    // of the row above that it touches (8-connectivity) at one site per
-    // contact: the first column of each vertical overlap (V), and a pixel
-    // whose only contact is diagonal (NW: the upper run ends at x - 1; NE:
-    // it starts at x + 1).  Each overlap of a lower run R and an upper run Q
-    // is one maximal interval of D & U, so V covers every overlapping pair;
-    // a diagonal pair without overlap has U[x] = 0 and D[x -/+ 1] = 0 at its
-    // contact, so NW / NE cover the rest.
-    for (int p = tid; p < TNPIX; p += DT_NT) {
-        const int py = p / TX, px = p - py * TX;
-        const uint64_t M = row_mask(S, py);
-        int v = -1;
-        if ((M >> px) & 1ull) {
-            const uint64_t z = ~M & ((1ull << px) - 1ull);        // background pixels left of px
-            v = py * TX + (z ? 64 - __clzll((long long)z) : 0);
-        }
-        S.lab[p] = v;
-    }
-    __syncthreads();
-    {
-        const int y = tid >> 3;                 // this row against the row above
-        const int xs = (tid & 7) * 8;           // 8 of its 64 columns
-        if (y > 0 && y < th) {
-            const uint64_t D = row_mask(S, y), U = row_mask(S, y - 1);
-            const uint64_t O = D & U;
-            const uint64_t V = O & ~(O << 1);
-            const uint64_t NW = D & ~U & (U << 1) & ~(D << 1);
-            const uint64_t NE = D & ~U & (U >> 1) & ~(D >> 1);
-            uint32_t sites = (uint32_t)(((V | NW | NE) >> xs) & 0xffu);
-            while (sites) {
-                const int x = xs + __ffs(sites) - 1;
-                sites &= sites - 1;
-                const int p = y * TX + x;
-                if ((V >> x) & 1ull) sunite(S.lab, p, p - TX);
-                if ((NW >> x) & 1ull) sunite(S.lab, p, p - TX - 1);
-                if ((NE >> x) & 1ull) sunite(S.lab, p, p - TX + 1);
-            }
-        }
-    }
-    __syncthreads();
-    // roots of the run heads (thread: 8 columns of one row; heads from the
-    // row mask), then every pixel through its run head
-    {
-        const int y = tid >> 3, xs = (tid & 7) * 8;
-        const uint64_t M = row_mask(S, y);
-        uint32_t heads = (uint32_t)(((M & ~(M << 1)) >> xs) & 0xffu);
-        while (heads) {
-            const int p = y * TX + xs + __ffs(heads) - 1;
-            heads &= heads - 1;
-            S.lab[p] = sfind(S.lab, p);
-        }
-    }
-    __syncthreads();
-    {
-        // foreground pixels only (thread: 8 columns of one row); run heads
-        // hold their roots, which this pass does not change
-        const int py = tid >> 3, xs = (tid & 7) * 8;
-        uint32_t fgb = (uint32_t)((row_mask(S, py) >> xs) & 0xffu);
-        while (fgb) {
-            const int p = py * TX + xs + __ffs(fgb) - 1;
-            fgb &= fgb - 1;
-            S.lab[p] = S.lab[S.lab[p]];
-        }
-    }
-    __syncthreads();
+// saturation of a foreground pixel at linear offset `lin` (elements from the
+// image base): from the 32-bit word copied for it (`async`), else read here
+__device__ __forceinline__ bool pix_sat(const DetectArgs& A, bool async, uint32_t word, int64_t lin)
+{
+    float v;
+    if (A.im.is_f32) v = async ? __uint_as_float(word) : __ldg(reinterpret_cast<const float*>(A.im.data) + lin);
+    else if (async) v = (float)((lin & 1) ? (word >> 16) : (word & 0xffffu));
+    else v = (float)__ldg(reinterpret_cast<const uint16_t*>(A.im.data) + lin);
+    return v >= A.im.sat;
+}
 
-    // ---- compact root numbering in raster (= label) order
-    {
-        const int p0 = tid * ROWS_PER_THREAD;
-        const int4* l4 = reinterpret_cast<const int4*>(S.lab + p0);
-        const int4 a = l4[0], b = l4[1];
-        const int lv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        int cnt = 0;
+template <bool LABEL_ONLY, bool BATCH, bool BIG>
+__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const DetectArgs* __restrict__ batch,
+                                                                        const __grid_constant__ DetectArgs one)
+{
+    using Cfg = LabelCfg<BIG>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    LabelSmem<BIG>& S = reinterpret_cast<LabelSmem<BIG>*>(smem_raw)[warp];
+    const DetectArgs& A = det_frame<BATCH>(batch, one);
+    const int W = A.im.W, H = A.im.H, ntx = A.T.ntx;
+    const int* list = BIG ? A.dl_list : A.tl_list;
+    const int ntl = *(BIG ? A.dl_count : A.tl_count);
+    const int nwarps = gridDim.x * Cfg::NW;
+    const uint32_t FULL = 0xffffffffu;
+    const bool sat_on = A.im.sat > 0.f;
+    // the value words are copied asynchronously when they are 4-byte aligned
+    const bool sat_async = sat_on && (A.im.is_f32 || (((uintptr_t)A.im.data) & 3) == 0);
+    const int y = lane;
+    for (int it = blockIdx.x * Cfg::NW + warp; it < ntl; it += nwarps) {
+        const int tile = list[it];
+        const int tx = tile % ntx, ty = tile / ntx;
+        const int x0 = tx * TX, y0 = ty * TY;
+        const int tw = min(TX, W - x0), th = min(TY, H - y0);
+        // ---- this lane's row mask and runs
+        uint64_t M = 0ull;
+        if (y < th) {
+            const uint4 w = A.bits[(int64_t)(y0 + y) * A.nstrip + (tx >> 1)];
+            const int sh = (tx & 1) * 16;
+            M = spread4(w.x >> sh) | (spread4(w.y >> sh) << 1) | (spread4(w.z >> sh) << 2) | (spread4(w.w >> sh) << 3);
+        }
+        const uint64_t heads = M & ~(M << 1);
+        const int nr = __popcll((long long)heads), nf = __popcll((long long)M);
+        int incl = nr | (nf << 16);                        // runs and pixels, both < 2^16
 #pragma unroll
-        for (int e = 0; e < 8; ++e) cnt += (lv[e] == p0 + e);
-        int off = block_excl_scan(cnt, S.warp_tot, &S.nroots);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            if (lv[e] == p0 + e) {
-                S.u.rid[p0 + e] = (short)off;
-                S.r_pix[off] = p0 + e;
-                ++off;
-            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
         }
-    }
-    __syncthreads();
-    const int nroots = S.nroots;
-    for (int r = tid; r < nroots; r += DT_NT) {
-        S.r_npix[r] = 0; S.r_xmin[r] = TX; S.r_xmax[r] = -1; S.r_ymin[r] = TY; S.r_ymax[r] = -1; S.r_pidx[r] = 0;
-    }
-    __syncthreads();
-    // per-root size, bounding box and tile-border contact, one update per run
-    // (thread: the run heads among 8 columns of one row)
-    {
-        const int py = tid >> 3, xs = (tid & 7) * 8;
-        const uint64_t M = row_mask(S, py);
-        uint32_t heads = (uint32_t)(((M & ~(M << 1)) >> xs) & 0xffu);
-        while (heads) {
-            const int px = xs + __ffs(heads) - 1;
-            heads &= heads - 1;
-            const uint64_t rest = ~(M >> px);                    // first background column at or after px
-            const int xe = rest ? px + __ffsll((long long)rest) - 2 : 63;
-            const int r = S.u.rid[S.lab[py * TX + px]];
-            const bool border = (px == 0 && x0 > 0) || (xe == tw - 1 && x0 + tw < W) ||
-                                (py == 0 && y0 > 0) || (py == th - 1 && y0 + th < H);
-            atomicAdd(S.r_npix + r, xe - px + 1);
-            atomicMin(S.r_xmin + r, px); atomicMax(S.r_xmax + r, xe);
-            atomicMin(S.r_ymin + r, py); atomicMax(S.r_ymax + r, py);
-            if (border) S.r_pidx[r] = 1;
+        const int rb = (incl & 0xffff) - nr;               // first run id of this row
+        const int fb = (incl >> 16) - nf;                  // first foreground pixel of this row
+        const int tot = __shfl_sync(FULL, incl, 31);
+        const int NR = tot & 0xffff, NF = tot >> 16;
+        if (!BIG && (NR > Cfg::RUNS || (!LABEL_ONLY && NF > Cfg::FG))) {
+            if (lane == 0) A.dl_list[atomicAdd(A.dl_count, 1)] = tile;   // crowded: the big form takes it
+            continue;
         }
-    }
-    __syncthreads();
-
-    // ---- decide: pieces (touch a shared tile edge), final segments, dropped
-    int isp[2], isc[2];
-    int pc = 0, cc = 0;
-    for (int e = 0; e < 2; ++e) {
-        const int r = tid * 2 + e;
-        isp[e] = (r < nroots) && S.r_pidx[r];
-        isc[e] = (r < nroots) && !S.r_pidx[r] && S.r_npix[r] >= A.minarea;
-        pc += isp[e]; cc += isc[e];
-    }
-    // one scan of both counts (each at most MAXROOT < 2^16)
-    const int both = block_excl_scan(pc | (cc << 16), S.warp_tot, &S.npieces);
-    int poff = both & 0xffff, coff = both >> 16;
-    if (tid == 0) {
-        S.ncomps = S.npieces >> 16;
-        S.npieces &= 0xffff;
-        S.pbase = S.npieces ? atomicAdd(A.P.count, S.npieces) : 0;
-        S.cbase = S.ncomps ? atomicAdd(A.C.count, S.ncomps) : 0;
-        A.T.piece_base[tile] = S.pbase;
-        A.T.piece_cnt[tile] = S.npieces;
-    }
-    __syncthreads();
-    const int pbase = S.pbase, cbase = S.cbase;
-    for (int e = 0; e < 2; ++e) {
-        const int r = tid * 2 + e;
-        if (r >= nroots) continue;
-        const int p = S.r_pix[r];
-        const int py = p / TX, px = p - py * TX;
-        const uint32_t L = (uint32_t)(y0 + py) * (uint32_t)W + (uint32_t)(x0 + px);
-        const int4 bb = make_int4(x0 + S.r_xmin[r], x0 + S.r_xmax[r], y0 + S.r_ymin[r], y0 + S.r_ymax[r]);
-        const int npix = S.r_npix[r];
-        int val = 0, pidx = -1, rec = -1;
-        if (isp[e]) {
-            const int id = pbase + poff;
-            if (id < A.P.cap) {
-                A.P.root[id] = L; A.P.npix[id] = npix; A.P.bbox[id] = bb; A.P.parent[id] = id;
-                A.P.agg_min[id] = L; A.P.agg_npix[id] = npix; A.P.agg_bbox[id] = bb;
-                pidx = poff;
-                rec = id;
-            } else {
-                set_status(A.status, GP_ERR_INTERNAL);
-            }
-            val = (int)(L + 1u);
-            ++poff;
-        } else if (isc[e]) {
-            const int id = cbase + coff;
-            if (id < A.C.cap) {
-                A.C.label[id] = L + 1u; A.C.npix[id] = npix; A.C.bbox[id] = bb;
-                rec = -2 - id;
-            } else {
-                set_status(A.status, GP_ERR_INTERNAL);
-            }
-            val = (int)(L + 1u);
-            ++coff;
-        }
-        S.r_val[r] = val;
-        S.r_pidx[r] = pidx;
-        S.r_rec[r] = rec;
-    }
-    __syncthreads();
-
-    // ---- moments of each kept component from the staged m (warp per root)
-    if (!LABEL_ONLY) {
-        for (int r = warp; r < nroots; r += DT_NT / 32) {
-            const int rec = S.r_rec[r];
-            if (rec == -1) continue;
-            const int rp = S.r_pix[r];
-            const int bx0 = S.r_xmin[r], by0 = S.r_ymin[r];
-            const int bw = S.r_xmax[r] - bx0 + 1, bh = S.r_ymax[r] - by0 + 1;
-            MomAcc a;
-            mom_zero(a);
-            for (int q = lane; q < bw * bh; q += 32) {
-                const int py = by0 + q / bw, px = bx0 + q % bw;
-                const int p = py * TX + px;
-                if (S.lab[p] != rp) continue;
-                const float m = S.m[(py + hh) * SW + px + XHALO];
-                const uint32_t L = (uint32_t)(y0 + py) * (uint32_t)W + (uint32_t)(x0 + px);
-                mom_pixel(a, m, px, py, L, (S.pflag[p] & 2) != 0);
-            }
-            mom_warp_reduce(a);
-            if (lane == 0) {
-                if (rec >= 0) {
-                    Moments mo;
-                    mo.s = df2(a.s); mo.sx = df2(a.sx); mo.sy = df2(a.sy);
-                    mo.sxx = df2(a.sxx); mo.syy = df2(a.syy); mo.sxy = df2(a.sxy);
-                    mo.ux = a.ux; mo.uy = a.uy; mo.uxx = a.uxx; mo.uyy = a.uyy; mo.uxy = a.uxy;
-                    mo.peak = a.peak; mo.peakL = a.peakL; mo.flags = a.flags;
-                    A.P.mom[rec] = mo;
-                } else {
-                    const int id = -2 - rec;
-                    uint32_t fl = a.flags;
-                    if (df_positive(a.s)) {
-                        // sums about the tile corner (x0, y0), finished by k_mom_finish
-                        comp_store_raw(A.C, id, a.s, a.sx, a.sy, a.sxx, a.syy, a.sxy);
-                    } else {
-                        double flux;
-                        double2 xy;
-                        Mom2 m2;
-                        mom_finish(df_value(a.s), df_value(a.sx), df_value(a.sy), df_value(a.sxx),
-                                   df_value(a.syy), df_value(a.sxy), a.ux, a.uy, a.uxx, a.uyy, a.uxy, S.r_npix[r],
-                                   x0, y0, &flux, &xy, &m2, &fl);
-                        A.C.flux[id] = flux; A.C.xy[id] = xy; A.C.mom2[id] = m2;
-                    }
-                    A.C.peak[id] = a.peak; A.C.peakL[id] = a.peakL; A.C.flags[id] = fl;
+        // ---- m (and the value word, for saturation) of every foreground
+        // pixel, copied asynchronously into the compact arrays; the streaming
+        // pass left the bits of m in the map there
+        if (!LABEL_ONLY && M) {
+            const int64_t rowL = (int64_t)(y0 + y) * W + x0;
+            const int64_t rowI = (int64_t)(y0 + y) * A.im.pitch + x0;
+            uint64_t mb = M;
+            for (int f = fb; mb; ++f) {
+                const int x = __ffsll((long long)mb) - 1;
+                mb &= mb - 1;
+                cp_async4(S.m + f, A.seg + rowL + x);
+                if (sat_async) {
+                    const int64_t li = rowI + x;
+                    const void* src = A.im.is_f32
+                                          ? (const void*)(reinterpret_cast<const float*>(A.im.data) + li)
+                                          : (const void*)(reinterpret_cast<const uint16_t*>(A.im.data) + (li & ~(int64_t)1));
+                    cp_async4(S.iv + f, src);
                 }
             }
         }
-    }
-
-    // ---- segmentation map for the tile (coalesced rows; 16-byte stores when
-    // the tile is full width and rows start on 16-byte boundaries)
-    if (tw == TX && (W & 3) == 0 && ((((uintptr_t)A.seg) & 15) == 0)) {
-        for (int p4 = tid; p4 < TNPIX / 4; p4 += DT_NT) {
-            const int py = p4 / (TX / 4), px = (p4 - py * (TX / 4)) * 4;
-            if (py >= th) continue;
-            const int4 l = *reinterpret_cast<const int4*>(S.lab + py * TX + px);
-            uint4 v;
-            v.x = l.x >= 0 ? (uint32_t)S.r_val[S.u.rid[l.x]] : 0u;
-            v.y = l.y >= 0 ? (uint32_t)S.r_val[S.u.rid[l.y]] : 0u;
-            v.z = l.z >= 0 ? (uint32_t)S.r_val[S.u.rid[l.z]] : 0u;
-            v.w = l.w >= 0 ? (uint32_t)S.r_val[S.u.rid[l.w]] : 0u;
-            *reinterpret_cast<uint4*>(A.seg + (int64_t)(y0 + py) * W + x0 + px) = v;
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        {
+            uint64_t hb = heads;
+            int f = fb;
+            for (int q = rb; hb; ++q) {
+                const int x = __ffsll((long long)hb) - 1;
+                hb &= hb - 1;
+                const int xe = run_end(M, x);
+                S.par[q] = q; S.cnt[q] = 0; S.val[q] = 0; S.pidx[q] = -1; S.cidx[q] = -1;
+                S.pos[q] = (int16_t)(y * TX + x);
+                S.fidx[q] = (int16_t)f;
+                S.len[q] = (uint8_t)(xe - x);
+                f += xe - x + 1;
+            }
         }
-    } else {
-        for (int p = tid; p < TNPIX; p += DT_NT) {
-            const int py = p / TX, px = p - py * TX;
-            if (py >= th || px >= tw) continue;
-            const int l = S.lab[p];
-            const uint32_t v = l >= 0 ? (uint32_t)S.r_val[S.u.rid[l]] : 0u;
-            A.seg[(int64_t)(y0 + py) * W + x0 + px] = v;
+        __syncwarp();
+        // ---- unite each run with the runs of the row above it touches, at
+        // one site per contact: the first column of each vertical overlap
+        // (V), and a pixel whose only contact is diagonal (NW: the upper run
+        // ends at x - 1; NE: it starts at x + 1).  Each overlap of a lower
+        // and an upper run is one maximal interval of M & U, so V covers
+        // every overlapping pair; a diagonal pair without overlap has
+        // U[x] = 0 and M[x -/+ 1] = 0 at its contact, so NW / NE cover the rest.
+        {
+            const uint64_t Uup = __shfl_up_sync(FULL, M, 1);
+            const uint64_t U = lane ? Uup : 0ull;
+            const int ub = __shfl_up_sync(FULL, rb, 1);
+            const uint64_t uh = U & ~(U << 1);
+            const uint64_t O = M & U;
+            const uint64_t V = O & ~(O << 1);
+            const uint64_t NWm = M & ~U & (U << 1) & ~(M << 1);
+            const uint64_t NEm = M & ~U & (U >> 1) & ~(M >> 1);
+            uint64_t sites = V | NWm | NEm;
+            while (sites) {
+                const int x = __ffsll((long long)sites) - 1;
+                sites &= sites - 1;
+                const int a = rb + __popcll((long long)(heads & upto(x))) - 1;
+                if ((V >> x) & 1ull) lunite(S.par, a, ub + __popcll((long long)(uh & upto(x))) - 1);
+                if ((NWm >> x) & 1ull) lunite(S.par, a, ub + __popcll((long long)(uh & upto(x - 1))) - 1);
+                if ((NEm >> x) & 1ull) lunite(S.par, a, ub + __popcll((long long)(uh & upto(x + 1))) - 1);
+            }
         }
-    }
-    // ---- edge records: local piece index of each edge pixel, or -1
-    int16_t* ed = A.T.edges + (int64_t)tile * EDGE_PER_TILE;
-    for (int q = tid; q < EDGE_PER_TILE; q += DT_NT) {
-        int px, py;
-        bool ok;
-        if (q < TY) { py = q; px = 0; ok = py < th; }                                   // colL
-        else if (q < 2 * TY) { py = q - TY; px = tw - 1; ok = py < th; }               // colR
-        else if (q < 2 * TY + TX) { px = q - 2 * TY; py = 0; ok = px < tw; }           // rowT
-        else { px = q - 2 * TY - TX; py = th - 1; ok = px < tw; }                      // rowB
-        int16_t v = -1;
-        if (ok) {
-            const int l = S.lab[py * TX + px];
-            if (l >= 0) v = (int16_t)S.r_pidx[S.u.rid[l]];
+        __syncwarp();
+        for (int q = rb; q < rb + nr; ++q) S.par[q] = lfind(S.par, q);
+        __syncwarp();
+        // ---- pixels and shared-edge contact per root, one atomic per run
+        {
+            uint64_t hb = heads;
+            for (int q = rb; hb; ++q) {
+                const int x = __ffsll((long long)hb) - 1;
+                hb &= hb - 1;
+                const int xe = run_end(M, x);
+                const bool border = (x == 0 && x0 > 0) || (xe == tw - 1 && x0 + tw < W) || (y == 0 && y0 > 0) ||
+                                    (y == th - 1 && y0 + th < H);
+                atomicAdd(S.cnt + S.par[q], (xe - x + 1) + (border ? (1 << 16) : 0));
+            }
         }
-        ed[q] = v;
+        __syncwarp();
+        // ---- kept roots, in label order: pieces (on a shared edge) and final
+        // segments (>= minarea); local indices, map values, one id
+        // reservation per kind per tile
+        int np = 0, nc = 0, nk = 0;
+        for (int c0 = 0; c0 < NR; c0 += 32) {
+            const int k = c0 + lane;
+            bool piece = false, comp = false;
+            if (k < NR && S.par[k] == k) {
+                const int v = S.cnt[k];
+                piece = (v >> 16) != 0;
+                comp = !piece && (v & 0xffff) >= A.minarea;
+            }
+            const uint32_t bp = __ballot_sync(FULL, piece), bc = __ballot_sync(FULL, comp);
+            const uint32_t lt = (1u << lane) - 1u;
+            if (piece || comp) {
+                const int p = S.pos[k];
+                S.val[k] = (int)((uint32_t)(y0 + p / TX) * (uint32_t)W + (uint32_t)(x0 + p % TX) + 1u);
+                S.klist[nk + __popc((bp | bc) & lt)] = (int16_t)k;
+                if (piece) S.pidx[k] = (int16_t)(np + __popc(bp & lt));
+                else S.cidx[k] = (int16_t)(nc + __popc(bc & lt));
+            }
+            np += __popc(bp);
+            nc += __popc(bc);
+            nk += __popc(bp | bc);
+        }
+        int pbase = 0, cbase = 0;
+        if (lane == 0) {
+            pbase = np ? atomicAdd(A.P.count, np) : 0;
+            cbase = nc ? atomicAdd(A.C.count, nc) : 0;
+            A.T.piece_base[tile] = pbase;
+            A.T.piece_cnt[tile] = np;
+        }
+        pbase = __shfl_sync(FULL, pbase, 0);
+        cbase = __shfl_sync(FULL, cbase, 0);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        // ---- small kept segments: one lane each, its runs in label order
+        for (int c0 = 0; c0 < nk; c0 += 32) {
+            const int i = c0 + lane;
+            const int r = i < nk ? S.klist[i] : -1;
+            if (r < 0 || (S.cnt[r] & 0xffff) > LANE_SEG_MAX) continue;
+            MomAcc a;
+            mom_zero(a);
+            int bx0 = TX, bx1 = -1, by1 = -1;
+            for (int q = r; q < NR; ++q) {
+                if (S.par[q] != r) continue;
+                const int p = S.pos[q], ry = p / TX, rx = p % TX, n = S.len[q] + 1;
+                bx0 = min(bx0, rx); bx1 = max(bx1, rx + n - 1); by1 = ry;
+                if (!LABEL_ONLY) {
+                    const int f0 = S.fidx[q];
+                    const int64_t lin = (int64_t)(y0 + ry) * A.im.pitch + x0 + rx;
+                    for (int t = 0; t < n; ++t) {
+                        const uint32_t Lp = (uint32_t)(y0 + ry) * (uint32_t)W + (uint32_t)(x0 + rx + t);
+                        mom_pixel(a, S.m[f0 + t], rx + t, ry, Lp, sat_on && pix_sat(A, sat_async, S.iv[f0 + t], lin + t));
+                    }
+                }
+            }
+            const int ry0 = S.pos[r] / TX;
+            emit_root<LABEL_ONLY, BIG>(A, S, r, make_int4(x0 + bx0, x0 + bx1, y0 + ry0, y0 + by1), pbase, cbase, x0,
+                                       y0, a);
+        }
+        // ---- large kept segments: the whole warp, lane = tile row
+        for (int i = 0; i < nk; ++i) {
+            const int r = S.klist[i];
+            if ((S.cnt[r] & 0xffff) <= LANE_SEG_MAX) continue;
+            int xmin = TX, xmax = -1;
+            MomAcc a;
+            mom_zero(a);
+            uint64_t hb = heads;
+            for (int q = rb; hb; ++q) {
+                const int x = __ffsll((long long)hb) - 1;
+                hb &= hb - 1;
+                if (S.par[q] != r) continue;
+                const int xe = run_end(M, x);
+                xmin = min(xmin, x);
+                xmax = max(xmax, xe);
+                if (!LABEL_ONLY) {
+                    const int f0 = S.fidx[q];
+                    const int64_t lin = (int64_t)(y0 + y) * A.im.pitch + x0 + x;
+                    for (int xx = x; xx <= xe; ++xx) {
+                        const uint32_t Lp = (uint32_t)(y0 + y) * (uint32_t)W + (uint32_t)(x0 + xx);
+                        mom_pixel(a, S.m[f0 + xx - x], xx, y, Lp,
+                                  sat_on && pix_sat(A, sat_async, S.iv[f0 + xx - x], lin + xx - x));
+                    }
+                }
+            }
+            const bool present = xmax >= 0;
+            const int bx0 = __reduce_min_sync(FULL, xmin), bx1 = __reduce_max_sync(FULL, xmax);
+            const int by1 = __reduce_max_sync(FULL, present ? y : -1);
+            if (!LABEL_ONLY) mom_warp_reduce(a);
+            if (lane == 0)
+                emit_root<LABEL_ONLY, BIG>(A, S, r, make_int4(x0 + bx0, x0 + bx1, y0 + S.pos[r] / TX, y0 + by1), pbase,
+                                           cbase, x0, y0, a);
+        }
+        __syncwarp();
+        // ---- the map at every foreground pixel: the label of its kept
+        // segment, or 0 (a dropped segment; the streaming pass left m there)
+        if (y < th) {
+            uint32_t* srow = A.seg + (int64_t)(y0 + y) * W + x0;
+            uint64_t hb = heads;
+            for (int q = rb; hb; ++q) {
+                const int x = __ffsll((long long)hb) - 1;
+                hb &= hb - 1;
+                const uint32_t v = (uint32_t)S.val[S.par[q]];
+                if (LABEL_ONLY && !v) continue;          // a given mask: the map is already 0 there
+                const int xe = run_end(M, x);
+                for (int xx = x; xx <= xe; ++xx) srow[xx] = v;
+            }
+        }
+        // ---- edge records of a tile with pieces: local piece index of each
+        // edge pixel, or -1
+        if (np) {
+            int16_t* ed = A.T.edges + (int64_t)tile * EDGE_PER_TILE;
+            const uint64_t M0 = __shfl_sync(FULL, M, 0), H0 = __shfl_sync(FULL, heads, 0);
+            const uint64_t MB = __shfl_sync(FULL, M, th - 1), HB = __shfl_sync(FULL, heads, th - 1);
+            const int rbB = __shfl_sync(FULL, rb, th - 1);
+            auto piece_at = [&](uint64_t Mr, uint64_t Hr, int rbase, int x) -> int16_t {
+                if (!((Mr >> x) & 1ull)) return (int16_t)-1;
+                return S.pidx[S.par[rbase + __popcll((long long)(Hr & upto(x))) - 1]];
+            };
+            ed[y] = y < th ? piece_at(M, heads, rb, 0) : (int16_t)-1;                 // colL
+            ed[TY + y] = y < th ? piece_at(M, heads, rb, tw - 1) : (int16_t)-1;       // colR
+            for (int x = lane; x < TX; x += 32) {
+                ed[2 * TY + x] = x < tw ? piece_at(M0, H0, 0, x) : (int16_t)-1;       // rowT
+                ed[2 * TY + TX + x] = x < tw ? piece_at(MB, HB, rbB, x) : (int16_t)-1;   // rowB
+            }
+        }
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------ tile merge ---
+// One warp per listed tile with pieces: its right and bottom edges and its
+// two lower diagonal corners against the neighbouring tiles' edge records
+// (a tile without pieces records none).
 __global__ void k_merge(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
     const ResolveArgs& R = frame_args(batch, one);
     const Tiles& T = R.T;
     const Pieces& P = R.P;
-    const int W = R.W, H = R.H;
+    const int W = R.W, H = R.H, lim = R.walk_limit;
     int* status = R.status;
-    const int tile = blockIdx.x;
     const int ntx = T.ntx, nty = T.nty;
-    if (tile >= ntx * nty) return;
-    const int tx = tile % ntx, ty = tile / ntx;
-    const int tw = min(TX, W - tx * TX), th = min(TY, H - ty * TY);
-    if (threadIdx.x == 0 && tx + 1 < ntx && ty + 1 < nty) {
-        // anti-diagonal across this tile's bottom-right corner: bottom-left
-        // pixel of the right tile and top-right pixel of the tile below
-        // (independent of whether this tile has pieces)
-        const int rt = tile + 1, dn = tile + ntx;
-        if (T.piece_cnt[rt] > 0 && T.piece_cnt[dn] > 0) {
-            const int a = T.edges[(int64_t)rt * EDGE_PER_TILE + th - 1];
-            const int b = T.edges[(int64_t)dn * EDGE_PER_TILE + TY + 0];
-            if (a >= 0 && b >= 0) gunite(P.parent, T.piece_base[rt] + a, T.piece_base[dn] + b, status);
-        }
-    }
-    if (T.piece_cnt[tile] == 0) return;
-    const int base = T.piece_base[tile];
-    const int16_t* e = T.edges + (int64_t)tile * EDGE_PER_TILE;
-    if (tx + 1 < ntx && T.piece_cnt[tile + 1] > 0) {
-        const int nbase = T.piece_base[tile + 1];
-        const int16_t* en = T.edges + (int64_t)(tile + 1) * EDGE_PER_TILE;
-        for (int i = threadIdx.x; i < th; i += blockDim.x) {
-            const int a = e[TY + i];
-            if (a < 0) continue;
-            for (int d = -1; d <= 1; ++d) {
-                const int k = i + d;
-                if (k < 0 || k >= th) continue;
-                const int b = en[k];
-                if (b >= 0) gunite(P.parent, base + a, nbase + b, status);
+    const int ntl = *R.tl_count;
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int it = wid; it < ntl; it += nw) {
+        const int tile = R.tl_list[it];
+        if (T.piece_cnt[tile] == 0) continue;
+        const int tx = tile % ntx, ty = tile / ntx;
+        const int tw = min(TX, W - tx * TX), th = min(TY, H - ty * TY);
+        const int base = T.piece_base[tile];
+        const int16_t* e = T.edges + (int64_t)tile * EDGE_PER_TILE;
+        if (tx + 1 < ntx && T.piece_cnt[tile + 1] > 0) {
+            const int nbase = T.piece_base[tile + 1];
+            const int16_t* en = T.edges + (int64_t)(tile + 1) * EDGE_PER_TILE;
+            for (int i = lane; i < th; i += 32) {
+                const int a = e[TY + i];
+                if (a < 0) continue;
+                for (int d = -1; d <= 1; ++d) {
+                    const int k = i + d;
+                    if (k < 0 || k >= th) continue;
+                    const int b = en[k];
+                    if (b >= 0) gunite(P.parent, base + a, nbase + b, lim, status);
+                }
             }
         }
-    }
-    if (ty + 1 < nty && T.piece_cnt[tile + ntx] > 0) {
-        const int nbase = T.piece_base[tile + ntx];
-        const int16_t* en = T.edges + (int64_t)(tile + ntx) * EDGE_PER_TILE;
-        for (int j = threadIdx.x; j < tw; j += blockDim.x) {
-            const int a = e[2 * TY + TX + j];
-            if (a < 0) continue;
-            for (int d = -1; d <= 1; ++d) {
-                const int k = j + d;
-                if (k < 0 || k >= tw) continue;
-                const int b = en[2 * TY + k];
-                if (b >= 0) gunite(P.parent, base + a, nbase + b, status);
+        if (ty + 1 < nty && T.piece_cnt[tile + ntx] > 0) {
+            const int nbase = T.piece_base[tile + ntx];
+            const int16_t* en = T.edges + (int64_t)(tile + ntx) * EDGE_PER_TILE;
+            for (int j = lane; j < tw; j += 32) {
+                const int a = e[2 * TY + TX + j];
+                if (a < 0) continue;
+                for (int d = -1; d <= 1; ++d) {
+                    const int k = j + d;
+                    if (k < 0 || k >= tw) continue;
+                    const int b = en[2 * TY + k];
+                    if (b >= 0) gunite(P.parent, base + a, nbase + b, lim, status);
+                }
             }
         }
-    }
-    if (threadIdx.x == 0 && tx + 1 < ntx && ty + 1 < nty) {
-        // bottom-right pixel of this tile and top-left pixel of the diagonal tile
-        const int dr = tile + ntx + 1;
-        const int a = e[TY + th - 1];
-        const int b = T.edges[(int64_t)dr * EDGE_PER_TILE + 0];
-        if (a >= 0 && b >= 0) gunite(P.parent, base + a, T.piece_base[dr] + b, status);
+        if (lane == 0 && ty + 1 < nty) {
+            // bottom-right pixel of this tile and top-left pixel of the tile below-right
+            if (tx + 1 < ntx && T.piece_cnt[tile + ntx + 1] > 0) {
+                const int a = e[TY + th - 1];
+                const int b = T.edges[(int64_t)(tile + ntx + 1) * EDGE_PER_TILE + 0];
+                if (a >= 0 && b >= 0) gunite(P.parent, base + a, T.piece_base[tile + ntx + 1] + b, lim, status);
+            }
+            // bottom-left pixel of this tile and top-right pixel of the tile below-left
+            if (tx > 0 && T.piece_cnt[tile + ntx - 1] > 0) {
+                const int a = e[th - 1];
+                const int b = T.edges[(int64_t)(tile + ntx - 1) * EDGE_PER_TILE + TY + 0];
+                if (a >= 0 && b >= 0) gunite(P.parent, base + a, T.piece_base[tile + ntx - 1] + b, lim, status);
+            }
+        }
     }
 }
 
@@ -921,7 +648,7 @@ __global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_
     int* status = R.status;
     const int n = min(*P.count, P.cap);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int r = gfind(P.parent, p);
+        const int r = gfind(P.parent, p, R.walk_limit);
         P.proot[p] = r;
         if (r < 0) { set_status(status, GP_ERR_TIMEOUT); continue; }
         if (r == p) continue;
@@ -1223,96 +950,149 @@ __global__ void k_rank_place(const RankArgs* __restrict__ batch, const __grid_co
 }
 
 // --------------------------------------------------------------- launchers ---
-template <bool F32, bool LO, int KS>
-static cudaError_t launch_tile(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
-                               cudaStream_t st)
+// the normalised kernel (kh x kw) padded to ks x ks, as a sum of separable
+// terms by full-pivot elimination in double: each step takes the largest
+// remaining entry K[pv][pu] as pivot and removes the outer product of its
+// column and row; it stops when what remains is within 1e-6 of the largest
+// tap (below float32 rounding of the correlation's 25-term sums).  A
+// Gaussian, or any outer product, is one term; the worst case is ks terms.
+static int factor_kernel(const float* taps, int kw, int kh, int ks, float* fv, float* fh)
 {
-    const size_t smem = sizeof(TileSmem);
-    if (batch) {
-        cudaFuncSetAttribute(k_detect_tile<F32, LO, KS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_detect_tile<F32, LO, KS, true><<<dim3(maxtiles, nframes), DT_NT, smem, st>>>(batch, one);
-    } else {
-        cudaFuncSetAttribute(k_detect_tile<F32, LO, KS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        k_detect_tile<F32, LO, KS, false><<<maxtiles, DT_NT, smem, st>>>(nullptr, one);
+    double R[2 * HMAX + 1][2 * HMAX + 1] = {};
+    const int oy = (ks - kh) / 2, ox = (ks - kw) / 2;
+    double amax = 0.0;
+    for (int v = 0; v < kh; ++v)
+        for (int u = 0; u < kw; ++u) {
+            R[v + oy][u + ox] = taps[v * kw + u];
+            amax = fmax(amax, fabs((double)taps[v * kw + u]));
+        }
+    int r = 0;
+    for (; r < ks; ++r) {
+        int pv = 0, pu = 0;
+        double best = -1.0;
+        for (int v = 0; v < ks; ++v)
+            for (int u = 0; u < ks; ++u)
+                if (fabs(R[v][u]) > best) { best = fabs(R[v][u]); pv = v; pu = u; }
+        if (best <= 1e-6 * amax) break;
+        const double p = R[pv][pu];
+        double col[2 * HMAX + 1], row[2 * HMAX + 1];
+        for (int v = 0; v < ks; ++v) col[v] = R[v][pu] / p;
+        for (int u = 0; u < ks; ++u) row[u] = R[pv][u];
+        for (int v = 0; v < ks; ++v) {
+            fv[r * ks + v] = (float)col[v];
+            for (int u = 0; u < ks; ++u) R[v][u] -= col[v] * row[u];
+        }
+        for (int u = 0; u < ks; ++u) fh[r * ks + u] = (float)row[u];
     }
-    return cudaGetLastError();
-}
-
-template <bool F32>
-static cudaError_t launch_tile_ks(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
-                                  cudaStream_t st)
-{
-    if (one.kw == one.kh && one.kw == 3) return launch_tile<F32, false, 3>(one, batch, nframes, maxtiles, st);
-    if (one.kw == one.kh && one.kw == 5) return launch_tile<F32, false, 5>(one, batch, nframes, maxtiles, st);
-    if (one.kw == one.kh && one.kw == 7) return launch_tile<F32, false, 7>(one, batch, nframes, maxtiles, st);
-    return launch_tile<F32, false, 0>(one, batch, nframes, maxtiles, st);
+    return r;
 }
 
 DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw, int kh,
                        float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
-                       const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C, int* status)
+                       const uint8_t* in_mask, const DetMask& dm, const Tiles& T, const Pieces& P, const Comps& C,
+                       int* status)
 {
     DetectArgs A;
-    for (int i = 0; i < KMAX; ++i) A.K[i] = (taps && i < kw * kh) ? taps[i] : 0.f;
+    memset(&A, 0, sizeof A);
+    A.ks = stream_ks(kw, kh);
+    A.nrank = taps ? factor_kernel(taps, kw, kh, A.ks, A.fv, A.fh) : 0;
     A.im = im; A.sb = sb; A.sr = sr;
-    A.kw = kw; A.kh = kh; A.hx = kw / 2; A.hy = kh / 2; A.hh = max(kw / 2, kh / 2);
     A.thresh = thresh; A.minarea = minarea;
     A.seg = seg; A.mask_out = mask_out; A.nnear = nnear; A.in_mask = in_mask;
+    A.bits = dm.bits; A.nstrip = (im.W + ST_STRIP - 1) / ST_STRIP;
+    A.tl_list = dm.tl_list; A.tl_count = dm.tl_count;
+    A.dl_list = dm.dl_list; A.dl_count = dm.dl_count;
     A.T = T; A.P = P; A.C = C; A.status = status;
     return A;
 }
 
-// every frame of a batch shares `one`'s dtype, kernel size and mode
-// (labelling a given mask or detecting); maxtiles = the largest frame's tiles
-cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxtiles,
-                              cudaStream_t st)
-{
-    if (one.in_mask) return launch_tile<false, true, 0>(one, batch, nframes, maxtiles, st);
-    if (one.im.is_f32) return launch_tile_ks<true>(one, batch, nframes, maxtiles, st);
-    return launch_tile_ks<false>(one, batch, nframes, maxtiles, st);
-}
-
-cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
-                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
-                                int* nnear, const uint8_t* in_mask, const Tiles& T, const Pieces& P, const Comps& C,
-                                int* status, cudaStream_t st)
-{
-    const DetectArgs A = detect_args(im, sb, sr, taps, kw, kh, thresh, minarea, seg, mask_out, nnear, in_mask, T, P,
-                                     C, status);
-    return launch_detect_any(A, nullptr, 1, T.ntx * T.nty, st);
-}
-
-ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H, int minarea,
-                         int* status)
-{
-    ResolveArgs R;
-    R.T = T; R.P = P; R.C = C; R.seg = seg; R.W = W; R.H = H; R.minarea = minarea; R.status = status;
-    return R;
-}
-
-// grid of the grid-stride kernels: about 152 x 8 CTAs over the whole batch
+// grid of the grid-stride kernels: about `per_frame` CTAs over the whole batch
 static int stride_grid(int per_frame, int nframes)
 {
     const int g = per_frame / nframes;
     return g < 16 ? 16 : g;
 }
 
+// the labelling kernel's persistent grids: the common form at five CTAs of
+// four warps per SM, the big form (crowded tiles) at four CTAs of two warps
+constexpr int LT_CTAS = 152 * 5;
+constexpr int LT_BIG_CTAS = 152 * 4;
+
+int detect_grid(int W, int H, bool given_mask) { return given_mask ? pack_warps(W, H) : stream_ctas(W, H); }
+
+template <bool LO, bool BATCH, bool BIG>
+static void launch_label(const DetectArgs& one, const DetectArgs* batch, dim3 g, cudaStream_t st)
+{
+    const size_t smem = sizeof(LabelSmem<BIG>) * LabelCfg<BIG>::NW;
+    auto* fn = k_label_tiles<LO, BATCH, BIG>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fn<<<g, 32 * LabelCfg<BIG>::NW, smem, st>>>(batch, one);
+}
+
+template <bool LO, bool BATCH>
+static void launch_label_both(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st)
+{
+    launch_label<LO, BATCH, false>(one, batch, dim3(BATCH ? stride_grid(LT_CTAS, nframes) : LT_CTAS, nframes), st);
+    launch_label<LO, BATCH, true>(one, batch, dim3(BATCH ? stride_grid(LT_BIG_CTAS, nframes) : LT_BIG_CTAS, nframes),
+                                  st);
+}
+
+// every frame of a batch shares `one`'s dtype, kernel size and mode
+// (labelling a given mask or detecting); maxgrid = detect_grid() of the
+// largest frame
+cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxgrid,
+                              cudaStream_t st)
+{
+    cudaError_t e = launch_stream_any(one, batch, nframes, maxgrid, st);
+    if (e != cudaSuccess) return e;
+    if (one.in_mask) {
+        if (batch) launch_label_both<true, true>(one, batch, nframes, st);
+        else launch_label_both<true, false>(one, batch, nframes, st);
+    } else {
+        if (batch) launch_label_both<false, true>(one, batch, nframes, st);
+        else launch_label_both<false, false>(one, batch, nframes, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
+                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
+                                int* nnear, const uint8_t* in_mask, const DetMask& dm, const Tiles& T,
+                                const Pieces& P, const Comps& C, int* status, cudaStream_t st)
+{
+    const DetectArgs A = detect_args(im, sb, sr, taps, kw, kh, thresh, minarea, seg, mask_out, nnear, in_mask, dm, T,
+                                     P, C, status);
+    return launch_detect_any(A, nullptr, 1, detect_grid(im.W, im.H, in_mask != nullptr), st);
+}
+
+ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
+                         int H, int minarea, int walk_limit, int* status)
+{
+    ResolveArgs R;
+    R.T = T; R.P = P; R.C = C; R.seg = seg; R.tl_list = dm.tl_list; R.tl_count = dm.tl_count;
+    R.W = W; R.H = H; R.minarea = minarea; R.walk_limit = walk_limit > 0 ? walk_limit : WALK_LIMIT;
+    R.status = status;
+    return R;
+}
+
 cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch, int nframes, int maxtiles,
                                cudaStream_t st)
 {
-    k_merge<<<dim3(maxtiles, nframes), 64, 0, st>>>(batch, one);
     const dim3 g(stride_grid(152 * 8, nframes), nframes);
+    // the merge: one warp per listed tile (latency-bound chains), up to 152 x 32 CTAs of 4 warps
+    const int mcta = std::min((maxtiles + 3) / 4, 152 * 32);
+    k_merge<<<dim3(std::max(1, mcta / (nframes > 1 ? 2 : 1)), nframes), 128, 0, st>>>(batch, one);
     k_aggregate<<<g, 256, 0, st>>>(batch, one);
     k_finalize<<<g, 256, 0, st>>>(batch, one);
     k_mom_finish<<<g, 256, 0, st>>>(batch, one);
     return cudaGetLastError();
 }
 
-cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, uint32_t* seg, int W, int H,
-                           int minarea, int* status, cudaStream_t st)
+cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
+                           int H, int minarea, int walk_limit, int* status, cudaStream_t st)
 {
-    return launch_resolve_any(resolve_args(T, P, C, seg, W, H, minarea, status), nullptr, 1, T.ntx * T.nty, st);
+    return launch_resolve_any(resolve_args(T, P, C, dm, seg, W, H, minarea, walk_limit, status), nullptr, 1,
+                              T.ntx * T.nty, st);
 }
 
 RankArgs rank_args(const Comps& C, int* n_out, int capacity, bool place, int* status)
