@@ -49,12 +49,16 @@ static_assert(TY == 32, "a warp's lane is a tile row");
 
 // ------------------------------------------------ shared-memory union-find ---
 // over the run ids of one tile; a link always points at a smaller id
+// (path halving: a run is re-pointed at its grandparent on the way, which
+// stays an ancestor, so concurrent walks and links remain valid)
 __device__ __forceinline__ int lfind(volatile int* par, int x)
 {
     for (int n = 0; n <= MAXRUN; ++n) {
         const int p = par[x];
         if (p == x) return x;
-        x = p;
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;
+        x = gp;
     }
     return x;
 }
@@ -117,40 +121,92 @@ __device__ __forceinline__ void mom_zero(MomAcc& a)
     a.flags = 0u;
 }
 
-__device__ __forceinline__ void mom_pixel(MomAcc& a, float m, int dx, int dy, uint32_t L, bool sat)
+__device__ __forceinline__ float2 df2(DF d) { return make_float2(d.hi, d.lo); }
+
+// add a (hi, lo) pair times a small integer
+__device__ __forceinline__ void df_add_scaled(DF& s, float2 v, float k)
 {
-    const float fx = (float)dx, fy = (float)dy;
-    df_add(a.s, m);
-    df_add_prod(a.sx, fx, m);
-    df_add_prod(a.sy, fy, m);
-    df_add_prod(a.sxx, fx * fx, m);
-    df_add_prod(a.syy, fy * fy, m);
-    df_add_prod(a.sxy, fx * fy, m);
-    a.ux += dx; a.uy += dy;
-    a.uxx += dx * dx; a.uyy += dy * dy; a.uxy += dx * dy;
+    df_add_prod(s, k, v.x);
+    s.lo = fmaf(k, v.y, s.lo);
+}
+
+__device__ __forceinline__ void df_add_pair(DF& s, float2 v)
+{
+    df_add(s, v.x);
+    s.lo += v.y;
+}
+
+// Moments of one run (row y, columns xs..xe, tile coordinates) from its
+// partial sums r0 = sum m, r1 = sum x m, r2 = sum x^2 m: the row coordinate
+// enters as exact products of the sums by y and y^2, and the unweighted
+// (integer) sums have closed forms.
+__device__ __forceinline__ void mom_fold(MomAcc& a, DF r0, DF r1, DF r2, int xs, int xe, int y)
+{
+    const float fy = (float)y, fy2 = (float)(y * y);
+    df_add_pair(a.s, df2(r0));
+    df_add_pair(a.sx, df2(r1));
+    df_add_pair(a.sxx, df2(r2));
+    df_add_scaled(a.sy, df2(r0), fy);
+    df_add_scaled(a.syy, df2(r0), fy2);
+    df_add_scaled(a.sxy, df2(r1), fy);
+    const int n = xe - xs + 1;
+    const int sx = n * (xs + xe) / 2;
+    const int sxx = (xe * (xe + 1) * (2 * xe + 1) - (xs - 1) * xs * (2 * xs - 1)) / 6;
+    a.ux += sx; a.uy += y * n; a.uxx += sxx; a.uyy += y * y * n; a.uxy += y * sx;
+}
+
+// one pixel of a run: its partial sums, the peak (first pixel in raster
+// order among equal maxima) and the saturation flag
+__device__ __forceinline__ void run_pixel(DF& r0, DF& r1, DF& r2, MomAcc& a, float m, int x, uint32_t L, bool sat)
+{
+    const float fx = (float)x;
+    df_add(r0, m);
+    df_add_prod(r1, fx, m);
+    df_add_prod(r2, fx * fx, m);
     if (m > a.peak || (m == a.peak && L < a.peakL)) { a.peak = m; a.peakL = L; }
     if (sat) a.flags |= GP_FLAG_SAT;
 }
 
-__device__ __forceinline__ void mom_warp_reduce(MomAcc& a)
+// sum of v over lanes base .. base + 2^levels - 1 into lane base (a fixed
+// tree: reproducible); lanes outside the range hold zeros
+__device__ __forceinline__ DF df_tree_sum(DF v, int levels)
 {
-    a.s = df_warp_sum(a.s); a.sx = df_warp_sum(a.sx); a.sy = df_warp_sum(a.sy);
-    a.sxx = df_warp_sum(a.sxx); a.syy = df_warp_sum(a.syy); a.sxy = df_warp_sum(a.sxy);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a.ux += __shfl_xor_sync(0xffffffffu, a.ux, o);
-        a.uy += __shfl_xor_sync(0xffffffffu, a.uy, o);
-        a.uxx += __shfl_xor_sync(0xffffffffu, a.uxx, o);
-        a.uyy += __shfl_xor_sync(0xffffffffu, a.uyy, o);
-        a.uxy += __shfl_xor_sync(0xffffffffu, a.uxy, o);
-        a.flags |= __shfl_xor_sync(0xffffffffu, a.flags, o);
-        float op = __shfl_xor_sync(0xffffffffu, a.peak, o);
-        uint32_t oL = __shfl_xor_sync(0xffffffffu, a.peakL, o);
-        if (op > a.peak || (op == a.peak && oL < a.peakL)) { a.peak = op; a.peakL = oL; }
+    const int lane = threadIdx.x & 31;
+    for (int o = levels > 0 ? 1 << (levels - 1) : 0; o > 0; o >>= 1) {
+        DF w;
+        w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        if (lane + o < 32) v = df_merge(v, w);
     }
+    return v;
 }
 
-__device__ __forceinline__ float2 df2(DF d) { return make_float2(d.hi, d.lo); }
+// float -> unsigned key with the same order (+0 and -0 equal)
+__device__ __forceinline__ uint32_t fkey(float f)
+{
+    const uint32_t b = __float_as_uint(f == 0.f ? 0.f : f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// a segment's sums over the lanes (tile rows) base .. base + 2^levels - 1,
+// complete in lane base
+__device__ __forceinline__ void mom_rows_reduce(MomAcc& a, int levels)
+{
+    const uint32_t FULL = 0xffffffffu;
+    a.s = df_tree_sum(a.s, levels); a.sx = df_tree_sum(a.sx, levels); a.sy = df_tree_sum(a.sy, levels);
+    a.sxx = df_tree_sum(a.sxx, levels); a.syy = df_tree_sum(a.syy, levels); a.sxy = df_tree_sum(a.sxy, levels);
+    a.ux = __reduce_add_sync(FULL, a.ux); a.uy = __reduce_add_sync(FULL, a.uy);
+    a.uxx = __reduce_add_sync(FULL, a.uxx); a.uyy = __reduce_add_sync(FULL, a.uyy);
+    a.uxy = __reduce_add_sync(FULL, a.uxy);
+    a.flags = __reduce_or_sync(FULL, a.flags);
+    const uint32_t k = __reduce_max_sync(FULL, fkey(a.peak));
+    a.peakL = __reduce_min_sync(FULL, fkey(a.peak) == k ? a.peakL : 0xffffffffu);
+    a.peak = fkey_inv(k);
+}
 
 // finished moments of a whole segment from sums about the origin (X0, Y0)
 __device__ void mom_finish(double S, double Sx, double Sy, double Sxx, double Syy, double Sxy, long long ux,
@@ -220,6 +276,9 @@ struct LabelSmem {
     int16_t pos[R];               // the run's row * TX + first column
     int16_t fidx[R];              // compact index of the run's first pixel
     int16_t klist[R];             // kept roots in label order
+    int16_t roff[R];              // at kept roots (per-lane path): first entry of its runs in rlist
+    int16_t rcnt[R];              // at kept roots (per-lane path): its runs
+    int16_t rlist[R];             // runs of the per-lane segments, grouped by segment, in label order
     uint8_t len[R];               // the run's pixels - 1
     float m[F];                   // m at the tile's foreground pixels, in raster order
     uint32_t iv[F];               // the 32-bit word holding each foreground pixel's value (saturation)
@@ -319,7 +378,7 @@ __device__ __forceinline__ bool pix_sat(const DetectArgs& A, bool async, uint32_
 }
 
 template <bool LABEL_ONLY, bool BATCH, bool BIG>
-__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const DetectArgs* __restrict__ batch,
+__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 5) k_label_tiles(const DetectArgs* __restrict__ batch,
                                                                         const __grid_constant__ DetectArgs one)
 {
     using Cfg = LabelCfg<BIG>;
@@ -336,15 +395,27 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const De
     // the value words are copied asynchronously when they are 4-byte aligned
     const bool sat_async = sat_on && (A.im.is_f32 || (((uintptr_t)A.im.data) & 3) == 0);
     const int y = lane;
-    for (int it = blockIdx.x * Cfg::NW + warp; it < ntl; it += nwarps) {
-        const int tile = list[it];
-        const int tx = tile % ntx, ty = tile / ntx;
+    // this lane's row of the mask words of tile t (zeros past the frame)
+    auto mask_row = [&](int t) -> uint4 {
+        if (t < 0) return make_uint4(0u, 0u, 0u, 0u);
+        const int ty_ = t / ntx, tx_ = t - ty_ * ntx;
+        if (ty_ * TY + y >= H) return make_uint4(0u, 0u, 0u, 0u);
+        return A.bits[(int64_t)(ty_ * TY + y) * A.nstrip + (tx_ >> 1)];
+    };
+    // the next tile's list entry and mask row are loaded while this one is
+    // labelled (both are far-memory reads)
+    int it = blockIdx.x * Cfg::NW + warp;
+    int tile = it < ntl ? list[it] : -1;
+    uint4 wcur = mask_row(tile);
+    for (; it < ntl; it += nwarps) {
+        const int tile_n = it + nwarps < ntl ? list[it + nwarps] : -1;
+        const int ty = tile / ntx, tx = tile - ty * ntx;
         const int x0 = tx * TX, y0 = ty * TY;
         const int tw = min(TX, W - x0), th = min(TY, H - y0);
         // ---- this lane's row mask and runs
         uint64_t M = 0ull;
-        if (y < th) {
-            const uint4 w = A.bits[(int64_t)(y0 + y) * A.nstrip + (tx >> 1)];
+        {
+            const uint4 w = wcur;
             const int sh = (tx & 1) * 16;
             M = spread4(w.x >> sh) | (spread4(w.y >> sh) << 1) | (spread4(w.z >> sh) << 2) | (spread4(w.w >> sh) << 3);
         }
@@ -362,6 +433,8 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const De
         const int NR = tot & 0xffff, NF = tot >> 16;
         if (!BIG && (NR > Cfg::RUNS || (!LABEL_ONLY && NF > Cfg::FG))) {
             if (lane == 0) A.dl_list[atomicAdd(A.dl_count, 1)] = tile;   // crowded: the big form takes it
+            wcur = mask_row(tile_n);
+            tile = tile_n;
             continue;
         }
         // ---- m (and the value word, for saturation) of every foreground
@@ -441,6 +514,7 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const De
                 atomicAdd(S.cnt + S.par[q], (xe - x + 1) + (border ? (1 << 16) : 0));
             }
         }
+        const uint4 wnext = mask_row(tile_n);
         __syncwarp();
         // ---- kept roots, in label order: pieces (on a shared edge) and final
         // segments (>= minarea); local indices, map values, one id
@@ -467,75 +541,14 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const De
             nc += __popc(bc);
             nk += __popc(bp | bc);
         }
+        // id reservation (one per kind per tile), consumed after the map and
+        // edge records are written
         int pbase = 0, cbase = 0;
         if (lane == 0) {
             pbase = np ? atomicAdd(A.P.count, np) : 0;
             cbase = nc ? atomicAdd(A.C.count, nc) : 0;
-            A.T.piece_base[tile] = pbase;
-            A.T.piece_cnt[tile] = np;
         }
-        pbase = __shfl_sync(FULL, pbase, 0);
-        cbase = __shfl_sync(FULL, cbase, 0);
         asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncwarp();
-        // ---- small kept segments: one lane each, its runs in label order
-        for (int c0 = 0; c0 < nk; c0 += 32) {
-            const int i = c0 + lane;
-            const int r = i < nk ? S.klist[i] : -1;
-            if (r < 0 || (S.cnt[r] & 0xffff) > LANE_SEG_MAX) continue;
-            MomAcc a;
-            mom_zero(a);
-            int bx0 = TX, bx1 = -1, by1 = -1;
-            for (int q = r; q < NR; ++q) {
-                if (S.par[q] != r) continue;
-                const int p = S.pos[q], ry = p / TX, rx = p % TX, n = S.len[q] + 1;
-                bx0 = min(bx0, rx); bx1 = max(bx1, rx + n - 1); by1 = ry;
-                if (!LABEL_ONLY) {
-                    const int f0 = S.fidx[q];
-                    const int64_t lin = (int64_t)(y0 + ry) * A.im.pitch + x0 + rx;
-                    for (int t = 0; t < n; ++t) {
-                        const uint32_t Lp = (uint32_t)(y0 + ry) * (uint32_t)W + (uint32_t)(x0 + rx + t);
-                        mom_pixel(a, S.m[f0 + t], rx + t, ry, Lp, sat_on && pix_sat(A, sat_async, S.iv[f0 + t], lin + t));
-                    }
-                }
-            }
-            const int ry0 = S.pos[r] / TX;
-            emit_root<LABEL_ONLY, BIG>(A, S, r, make_int4(x0 + bx0, x0 + bx1, y0 + ry0, y0 + by1), pbase, cbase, x0,
-                                       y0, a);
-        }
-        // ---- large kept segments: the whole warp, lane = tile row
-        for (int i = 0; i < nk; ++i) {
-            const int r = S.klist[i];
-            if ((S.cnt[r] & 0xffff) <= LANE_SEG_MAX) continue;
-            int xmin = TX, xmax = -1;
-            MomAcc a;
-            mom_zero(a);
-            uint64_t hb = heads;
-            for (int q = rb; hb; ++q) {
-                const int x = __ffsll((long long)hb) - 1;
-                hb &= hb - 1;
-                if (S.par[q] != r) continue;
-                const int xe = run_end(M, x);
-                xmin = min(xmin, x);
-                xmax = max(xmax, xe);
-                if (!LABEL_ONLY) {
-                    const int f0 = S.fidx[q];
-                    const int64_t lin = (int64_t)(y0 + y) * A.im.pitch + x0 + x;
-                    for (int xx = x; xx <= xe; ++xx) {
-                        const uint32_t Lp = (uint32_t)(y0 + y) * (uint32_t)W + (uint32_t)(x0 + xx);
-                        mom_pixel(a, S.m[f0 + xx - x], xx, y, Lp,
-                                  sat_on && pix_sat(A, sat_async, S.iv[f0 + xx - x], lin + xx - x));
-                    }
-                }
-            }
-            const bool present = xmax >= 0;
-            const int bx0 = __reduce_min_sync(FULL, xmin), bx1 = __reduce_max_sync(FULL, xmax);
-            const int by1 = __reduce_max_sync(FULL, present ? y : -1);
-            if (!LABEL_ONLY) mom_warp_reduce(a);
-            if (lane == 0)
-                emit_root<LABEL_ONLY, BIG>(A, S, r, make_int4(x0 + bx0, x0 + bx1, y0 + S.pos[r] / TX, y0 + by1), pbase,
-                                           cbase, x0, y0, a);
-        }
         __syncwarp();
         // ---- the map at every foreground pixel: the label of its kept
         // segment, or 0 (a dropped segment; the streaming pass left m there)
@@ -569,7 +582,132 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW) k_label_tiles(const De
                 ed[2 * TY + TX + x] = x < tw ? piece_at(MB, HB, rbB, x) : (int16_t)-1;   // rowB
             }
         }
+        if (lane == 0) {
+            A.T.piece_base[tile] = pbase;
+            A.T.piece_cnt[tile] = np;
+        }
+        pbase = __shfl_sync(FULL, pbase, 0);
+        cbase = __shfl_sync(FULL, cbase, 0);
+        // ---- kept segments of at most LANE_SEG_MAX pixels: one lane each (its
+        // runs in label order), when the tile holds several of them
+        int nsmall = 0;
+        for (int c0 = 0; c0 < nk; c0 += 32) {
+            const int i = c0 + lane;
+            nsmall += __popc(__ballot_sync(FULL, i < nk && (S.cnt[S.klist[i]] & 0xffff) <= LANE_SEG_MAX));
+        }
+        const bool lane_path = nsmall >= 4;
+        if (lane_path) {
+            // runs of each small kept segment, in label order: runs are taken
+            // 32 at a time in id order; the lanes holding runs of one segment
+            // find each other (match) and the first of them advances its count
+            for (int c0 = 0; c0 < nk; c0 += 32) {
+                const int i = c0 + lane;
+                if (i < nk) S.rcnt[S.klist[i]] = 0;
+            }
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    // offsets: the segments' runs laid out in kept-root order
+                    int off = 0;
+                    for (int c0 = 0; c0 < nk; c0 += 32) {
+                        const int i = c0 + lane;
+                        const int r = i < nk ? S.klist[i] : -1;
+                        const int c = (r >= 0 && (S.cnt[r] & 0xffff) <= LANE_SEG_MAX) ? S.rcnt[r] : 0;
+                        int inc = c;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t = __shfl_up_sync(FULL, inc, o);
+                            if (lane >= o) inc += t;
+                        }
+                        if (r >= 0) { S.roff[r] = (int16_t)(off + inc - c); S.rcnt[r] = 0; }
+                        off += __shfl_sync(FULL, inc, 31);
+                    }
+                }
+                __syncwarp();
+                for (int c0 = 0; c0 < NR; c0 += 32) {
+                    const int q = c0 + lane;
+                    const int r = q < NR ? S.par[q] : -1;
+                    const bool mine = r >= 0 && S.val[r] != 0 && (S.cnt[r] & 0xffff) <= LANE_SEG_MAX;
+                    const uint32_t peers = __match_any_sync(FULL, mine ? r : -1);
+                    const int rank = __popc(peers & ((1u << lane) - 1u));
+                    const int base = mine ? S.rcnt[r] : 0;
+                    __syncwarp();
+                    if (mine) {
+                        if (pass == 1) S.rlist[S.roff[r] + base + rank] = (int16_t)q;
+                        if (rank == 0) S.rcnt[r] = (int16_t)(base + __popc(peers));
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int c0 = 0; c0 < nk; c0 += 32) {
+                const int i = c0 + lane;
+                const int r = i < nk ? S.klist[i] : -1;
+                if (r < 0 || (S.cnt[r] & 0xffff) > LANE_SEG_MAX) continue;
+                MomAcc a;
+                mom_zero(a);
+                int bx0 = TX, bx1 = -1, by1 = -1;
+                const int e0 = S.roff[r], e1 = e0 + S.rcnt[r];
+                for (int e = e0; e < e1; ++e) {
+                    const int q = S.rlist[e];
+                    const int p = S.pos[q], ry = p / TX, rx = p % TX, n = S.len[q] + 1;
+                    bx0 = min(bx0, rx); bx1 = max(bx1, rx + n - 1); by1 = ry;
+                    if (!LABEL_ONLY) {
+                        const int f0 = S.fidx[q];
+                        const int64_t lin = (int64_t)(y0 + ry) * A.im.pitch + x0 + rx;
+                        const uint32_t L0 = (uint32_t)(y0 + ry) * (uint32_t)W + (uint32_t)(x0 + rx);
+                        DF r0 = df_zero(), r1 = df_zero(), r2 = df_zero();
+                        for (int t = 0; t < n; ++t)
+                            run_pixel(r0, r1, r2, a, S.m[f0 + t], rx + t, L0 + t,
+                                      sat_on && pix_sat(A, sat_async, S.iv[f0 + t], lin + t));
+                        mom_fold(a, r0, r1, r2, rx, rx + n - 1, ry);
+                    }
+                }
+                const int ry0 = S.pos[r] / TX;
+                emit_root<LABEL_ONLY, BIG>(A, S, r, make_int4(x0 + bx0, x0 + bx1, y0 + ry0, y0 + by1), pbase, cbase,
+                                           x0, y0, a);
+            }
+        }
+        // ---- the other kept segments: the whole warp, lane = tile row; the
+        // sums meet in the segment's first row by a tree over its rows
+        for (int i = 0; i < nk; ++i) {
+            const int r = S.klist[i];
+            if (lane_path && (S.cnt[r] & 0xffff) <= LANE_SEG_MAX) continue;
+            int xmin = TX, xmax = -1;
+            MomAcc a;
+            mom_zero(a);
+            uint64_t hb = heads;
+            for (int q = rb; hb; ++q) {
+                const int x = __ffsll((long long)hb) - 1;
+                hb &= hb - 1;
+                if (S.par[q] != r) continue;
+                const int xe = run_end(M, x);
+                xmin = min(xmin, x);
+                xmax = max(xmax, xe);
+                if (!LABEL_ONLY) {
+                    const int f0 = S.fidx[q];
+                    const int64_t lin = (int64_t)(y0 + y) * A.im.pitch + x0 + x;
+                    const uint32_t L0 = (uint32_t)(y0 + y) * (uint32_t)W + (uint32_t)(x0 + x);
+                    DF r0 = df_zero(), r1 = df_zero(), r2 = df_zero();
+                    for (int t = 0; t <= xe - x; ++t)
+                        run_pixel(r0, r1, r2, a, S.m[f0 + t], x + t, L0 + t,
+                                  sat_on && pix_sat(A, sat_async, S.iv[f0 + t], lin + t));
+                    mom_fold(a, r0, r1, r2, x, xe, y);
+                }
+            }
+            const bool present = xmax >= 0;
+            const int ry0 = S.pos[r] / TX;
+            const int bx0 = __reduce_min_sync(FULL, xmin), bx1 = __reduce_max_sync(FULL, xmax);
+            const int by1 = __reduce_max_sync(FULL, present ? y : -1);
+            if (!LABEL_ONLY) {
+                const int span = by1 - ry0 + 1;
+                mom_rows_reduce(a, span <= 1 ? 0 : 32 - __clz(span - 1));
+            }
+            if (lane == ry0)
+                emit_root<LABEL_ONLY, BIG>(A, S, r, make_int4(x0 + bx0, x0 + bx1, y0 + ry0, y0 + by1), pbase, cbase,
+                                           x0, y0, a);
+        }
         __syncwarp();
+        wcur = wnext;
+        tile = tile_n;
     }
 }
 
@@ -659,19 +797,6 @@ __global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_
         atomicMin(ab + 0, b.x); atomicMax(ab + 1, b.y);
         atomicMin(ab + 2, b.z); atomicMax(ab + 3, b.w);
     }
-}
-
-// add a (hi, lo) pair times a small integer
-__device__ __forceinline__ void df_add_scaled(DF& s, float2 v, float k)
-{
-    df_add_prod(s, k, v.x);
-    s.lo = fmaf(k, v.y, s.lo);
-}
-
-__device__ __forceinline__ void df_add_pair(DF& s, float2 v)
-{
-    df_add(s, v.x);
-    s.lo += v.y;
 }
 
 // One warp per piece.  At root pieces of kept segments: merge the partial

@@ -34,8 +34,11 @@
 //           where the CTA is inside the frame and rows are aligned, else
 //           element loads at mirrored coordinates), one group ahead in
 //           registers.
-// The ring keeps three groups (the filter pass of a group also reads the
-// previous group's rows, and a warp may already write the next one).
+// The ring keeps two groups.  The filter pass reads other lanes' columns only
+// in the current group's rows (a warp writes the next group's rows after the
+// barrier that ends every warp's pass over them); the previous group's rows
+// it reads (a pixel's own m for the map) are the lane's own columns, which
+// no other lane writes.
 // Instances: k_stream_u16.cu and k_stream_f32.cu; launch: k_stream.cu.
 #pragma once
 #include <cuda.h>
@@ -73,7 +76,7 @@ struct StreamSmem {
     static constexpr int G = StreamCfg<KS>::G;
     static constexpr int ROWS = ST_RC + 2 * HMAX + 16;    // row table entries (>= groups * G)
     static constexpr size_t ring = 0;
-    static constexpr size_t ring_bytes = sizeof(float) * 3 * G * ST_RW;
+    static constexpr size_t ring_bytes = sizeof(float) * 2 * G * ST_RW;
     static constexpr size_t rowc = ring + ring_bytes;
     static constexpr size_t rowj = rowc + sizeof(float4) * ROWS;
     static constexpr size_t thr = (rowj + sizeof(int2) * ROWS + 15) & ~(size_t)15;     // k sigma of a group's output rows
@@ -403,8 +406,8 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
     const bool edge_l = X0 - ST_HALO < 0, edge_r = X0 + ST_COLS + ST_HALO > W;
 
     for (int g = 0; g < ng; ++g) {
-        float* rg = ring + (g % 3) * G * ST_RW;               // this group's m rows
-        const float* rp = ring + ((g + 2) % 3) * G * ST_RW;   // the previous group's
+        float* rg = ring + (g & 1) * G * ST_RW;               // this group's m rows
+        const float* rp = ring + ((g + 1) & 1) * G * ST_RW;   // the previous group's
         const unsigned char* sg = stg + (g % ST_STAGES) * 3 * boxb;
         bool timed_out = false;
         if (TMA) timed_out = !mbar_wait(bar + g % ST_STAGES, (uint32_t)((g / ST_STAGES) & 1));
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
                     const int k = g * G + s, r = r0 + s;
                     if (k >= nin || (r >= 0 && r < Hf)) continue;
                     const int ks = mirror_idx(r, Hf) - (Y0 - H);
-                    const float* src = ring + ((ks / G) % 3) * G * ST_RW + (ks % G) * ST_RW;
+                    const float* src = ring + ((ks / G) & 1) * G * ST_RW + (ks % G) * ST_RW;
                     for (int c = tid; c < ST_RW; c += ST_NT) rg[s * ST_RW + c] = src[c];
                 }
                 __syncthreads();
