@@ -16,8 +16,8 @@
 // ST_NW strips side by side over ST_RC output rows.  Input rows are taken in
 // groups of G (a multiple of the kernel size): each warp turns its columns of
 // a group into m rows in a shared-memory ring (two halves of G rows, 528
-// columns: the CTA's 512 and 8 each side, the side columns computed by four
-// lanes of warp 0), and after one barrier per group every lane reads the
+// columns: the CTA's 512 and 8 each side, the side columns computed one per
+// lane by 16 lanes of warp 0), and after one barrier per group every lane reads the
 // 4 + 2h columns its outputs need and runs the separable passes: a
 // horizontal dot product per rank, then a vertical one accumulated in
 // registers (KS rolling output rows, so each m row is read once).  The
@@ -80,8 +80,7 @@ struct StreamSmem {
     static constexpr size_t rowc = ring + ring_bytes;
     static constexpr size_t rowj = rowc + sizeof(float4) * ROWS;
     static constexpr size_t thr = (rowj + sizeof(int2) * ROWS + 15) & ~(size_t)15;     // k sigma of a group's output rows
-    static constexpr size_t hcoef = thr + sizeof(float) * G * ST_COLS;                   // side columns' spline values
-    static constexpr size_t bar = (hcoef + sizeof(float4) * 16 + 127) & ~(size_t)127;
+    static constexpr size_t bar = (thr + sizeof(float) * G * ST_COLS + 127) & ~(size_t)127;
     static constexpr size_t stage = bar + 128;
     __host__ __device__ static constexpr size_t box_bytes(int esz) { return ((size_t)ST_BOXW * G * esz + 127) & ~(size_t)127; }
     __host__ __device__ static constexpr size_t total(int esz) { return stage + (size_t)ST_STAGES * 3 * box_bytes(esz); }
@@ -253,6 +252,47 @@ __device__ __forceinline__ float2 col4_eval2(const Col4& c, const float4& rc, in
     return ffma2(splat2(rc.z), c.w1[p], ffma2(splat2(rc.y), c.w0[p], ffma2(splat2(rc.x), c.d[p], c.u[p])));
 }
 
+// one raw pixel of a stage buffer (ring column c) as a float
+template <bool F32>
+__device__ __forceinline__ float stage1(const unsigned char* st, size_t boxb, int s, int c)
+{
+    constexpr int ESZ = F32 ? 4 : 2;
+    const int box = c / ST_BOXW, cc = c - box * ST_BOXW;
+    const unsigned char* p = st + box * boxb + ((size_t)s * ST_BOXW + cc) * ESZ;
+    if constexpr (F32) return *reinterpret_cast<const float*>(p);
+    else return (float)*reinterpret_cast<const uint16_t*>(p);
+}
+
+// one raw pixel into a stage buffer
+template <bool F32>
+__device__ __forceinline__ void stage_put1(unsigned char* st, size_t boxb, int s, int c, float v)
+{
+    constexpr int ESZ = F32 ? 4 : 2;
+    const int box = c / ST_BOXW, cc = c - box * ST_BOXW;
+    unsigned char* p = st + box * boxb + ((size_t)s * ST_BOXW + cc) * ESZ;
+    if constexpr (F32) *reinterpret_cast<float*>(p) = v;
+    else *reinterpret_cast<uint16_t*>(p) = (uint16_t)v;
+}
+
+// one pixel of frame row gy at column x (mirrored) as a float (DIRECT)
+template <bool F32>
+__device__ __forceinline__ float load1(const Image& im, int gy, int x)
+{
+    const int64_t i = (int64_t)gy * im.pitch + mirror_idx(x, im.W);
+    if constexpr (F32) return __ldg(reinterpret_cast<const float*>(im.data) + i);
+    else return (float)__ldg(reinterpret_cast<const uint16_t*>(im.data) + i);
+}
+
+// the spline values of one map at one column x for node rows (j0, j1):
+// (u, d, w0, w1) as in Col4
+__device__ __forceinline__ float4 col1_load(const SplineTab& s, int j0, int j1, int x, int W)
+{
+    const AxCoef cx = axis_coef(s.ax, (float)mirror_idx(x, W));
+    const float2 a = row_eval(s, j0, cx);
+    const float2 b = row_eval(s, j1, cx);
+    return make_float4(a.x, b.x - a.x, a.y, b.y);
+}
+
 // 4 raw pixels into a stage buffer (the TMA box layout)
 template <bool F32>
 __device__ __forceinline__ void stage_put4(unsigned char* st, size_t boxb, int s, int c, const Raw4<F32>& r)
@@ -310,7 +350,6 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
     float* ring = reinterpret_cast<float*>(smem + SM::ring);
     float4* rowc = reinterpret_cast<float4*>(smem + SM::rowc);
     int2* rowj = reinterpret_cast<int2*>(smem + SM::rowj);
-    float4* hcoef = reinterpret_cast<float4*>(smem + SM::hcoef);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::bar);
     unsigned char* stg = smem + SM::stage;
     constexpr size_t boxb = SM::box_bytes(ESZ);
@@ -328,10 +367,10 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
     const int ng = (nin + G - 1) / G;                     // rows past nin are computed (valid addresses) and unused
     const int xs = X0 + ST_STRIP * warp + ST_CPL * lane;  // the lane's first column
     const int slot0 = ST_HALO + ST_STRIP * warp + ST_CPL * lane;
-    // lanes 0..3 of warp 0 also compute the ring's side columns
-    const bool hl = warp == 0 && lane < 4;
-    const int hx = lane < 2 ? X0 - ST_HALO + 4 * lane : X0 + ST_COLS + 4 * (lane - 2);
-    const int hslot = lane < 2 ? 4 * lane : ST_HALO + ST_COLS + 4 * (lane - 2);
+    // lanes 0..15 of warp 0 also compute the ring's side columns, one each
+    const bool hl = warp == 0 && lane < 2 * ST_HALO;
+    const int hx = lane < ST_HALO ? X0 - ST_HALO + lane : X0 + ST_COLS + (lane - ST_HALO);
+    const int hslot = lane < ST_HALO ? lane : ST_COLS + lane;
 
     // ---- row table: spline coefficients of every input row (mirrored)
     for (int k = tid; k < ng * G; k += ST_NT) {
@@ -351,13 +390,14 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
     // flight during group g's filter pass and land in its stage after it
     const bool vec = !TMA && X0 - ST_HALO >= 0 && X0 + ST_COLS + ST_HALO <= W && (im.pitch % ST_CPL) == 0 &&
                      ((((uintptr_t)im.data) & (F32 ? 15 : 7)) == 0);
-    Raw4<F32> raw[G], hraw[G];
+    Raw4<F32> raw[G];
+    float hraw[G];
     auto fetch = [&](int g) {
 #pragma unroll
         for (int s = 0; s < G; ++s) {
             const int gy = mirror_idx(Y0 - H + g * G + s, Hf);
             raw[s] = load4<F32>(im, gy, xs, vec);
-            if (hl) hraw[s] = load4<F32>(im, gy, hx, vec);
+            if (hl) hraw[s] = load1<F32>(im, gy, hx);
         }
     };
     auto put = [&](int g) {
@@ -365,7 +405,7 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
 #pragma unroll
         for (int s = 0; s < G; ++s) {
             stage_put4<F32>(sp, boxb, s, slot0, raw[s]);
-            if (hl) stage_put4<F32>(sp, boxb, s, hslot, hraw[s]);
+            if (hl) stage_put1<F32>(sp, boxb, s, hslot, hraw[s]);
         }
     };
     if (!TMA) {
@@ -386,6 +426,7 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
     // (cb; the side columns' in hcoef), k sigma at the output rows' (cs);
     // the k sigma of a group's output rows wait in thrb for the filter pass
     Col4 cb, cs;
+    float4 hcb = make_float4(0.f, 0.f, 0.f, 0.f);      // side column's background spline values
     float* thrb = reinterpret_cast<float*>(smem + SM::thr);
     int jb = -1, js = -1, jh = -1;
     uint64_t badh = 0;
@@ -453,27 +494,15 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
                 *reinterpret_cast<float4*>(thrb + s * ST_COLS + slot0 - ST_HALO) = make_float4(t01.x, t01.y, t23.x, t23.y);
             }
             if (hl) {
-                float4* hc = hcoef + 4 * lane;
                 if (j.x != jh) {
-                    const Col4 c = col4_load(A.sb, j.x, j.y, hx, W, 1.f);
-                    hc[0] = make_float4(c.u[0].x, c.u[0].y, c.u[1].x, c.u[1].y);
-                    hc[1] = make_float4(c.d[0].x, c.d[0].y, c.d[1].x, c.d[1].y);
-                    hc[2] = make_float4(c.w0[0].x, c.w0[0].y, c.w0[1].x, c.w0[1].y);
-                    hc[3] = make_float4(c.w1[0].x, c.w1[0].y, c.w1[1].x, c.w1[1].y);
+                    hcb = col1_load(A.sb, j.x, j.y, hx, W);
                     jh = j.x;
                 }
-                const float4 hu = hc[0], hd = hc[1], h0 = hc[2], h1 = hc[3];
-                const float au[4] = {hu.x, hu.y, hu.z, hu.w}, ad[4] = {hd.x, hd.y, hd.z, hd.w};
-                const float a0[4] = {h0.x, h0.y, h0.z, h0.w}, a1[4] = {h1.x, h1.y, h1.z, h1.w};
-                stage4<F32>(sg, boxb, s, hslot).to_float(v);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    bool b = F32 && !isfinite(v[e]);
-                    if (!FAST && !TMA && im.mask)
-                        b = b || im.mask[(int64_t)mirror_idx(Y0 - H + k, Hf) * W + mirror_idx(hx + e, W)] != 0;
-                    m[e] = b ? 0.f : v[e] - fmaf(rc.z, a1[e], fmaf(rc.y, a0[e], fmaf(rc.x, ad[e], au[e])));
-                }
-                *reinterpret_cast<float4*>(rg + s * ST_RW + hslot) = make_float4(m[0], m[1], m[2], m[3]);
+                const float hv = stage1<F32>(sg, boxb, s, hslot);
+                bool b = F32 && !isfinite(hv);
+                if (!FAST && !TMA && im.mask)
+                    b = b || im.mask[(int64_t)mirror_idx(Y0 - H + k, Hf) * W + mirror_idx(hx, W)] != 0;
+                rg[s * ST_RW + hslot] = b ? 0.f : hv - fmaf(rc.z, hcb.w, fmaf(rc.y, hcb.z, fmaf(rc.x, hcb.y, hcb.x)));
             }
         }
         if (__syncthreads_or(timed_out)) {
