@@ -51,26 +51,59 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------ oracle leg ---
-def oracle_sample(img, cfg, budget_s=12.0, max_crops=6, crop=2048):
-    """The CPU oracle (single thread) on crops of the frame until about
-    `budget_s` of CPU work; returns (Mpix/s, seconds, description)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and its core count."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return name or platform.machine(), os.cpu_count() or 1
+
+
+def oracle_sample(img, cfg, budget_s=12.0, max_crops=6, crop=2048, threads=1, repeats=1):
+    """The CPU oracle on crops of the frame until about `budget_s` of CPU
+    work, on `threads` host threads (0: every core), best of `repeats` per
+    crop; returns (Mpix/s, seconds, description, threads used)."""
     import oracle
+    used = oracle.set_threads(threads)
     H, W = img.shape
     offs = [(0, 0), (H // 2, W // 2), (H - crop, W - crop), (0, W - crop), (H - crop, 0), (H // 4, W // 3)]
     tot_px, tot_t, n = 0, 0.0, 0
-    for (y0, x0) in offs[:max_crops]:
-        sub = img[y0:y0 + crop, x0:x0 + crop]
-        t0 = time.perf_counter()
-        oracle.extract(sub, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii, cfg.gain,
-                       saturation=cfg.saturation)
-        tot_t += time.perf_counter() - t0
-        tot_px += sub.size
-        n += 1
-        if tot_t >= budget_s:
-            break
+    try:
+        for (y0, x0) in offs[:max_crops]:
+            sub = img[y0:y0 + crop, x0:x0 + crop]
+            best = None
+            for _ in range(repeats):
+                t0 = time.perf_counter()
+                oracle.extract(sub, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii, cfg.gain,
+                               saturation=cfg.saturation)
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            tot_t += best
+            tot_px += sub.size
+            n += 1
+            if tot_t >= budget_s:
+                break
+    finally:
+        oracle.set_threads(1)
     desc = (f"{n} crop(s) of {crop}x{crop} px ({tot_px / 1e6:.1f} Mpix) of the {cfg.name} frame, full oracle "
-            f"path (background, filter, threshold, labelling, moments, apertures), 1 thread")
-    return tot_px / 1e6 / tot_t, tot_t, desc
+            f"path (background, filter, threshold, labelling, moments, apertures), {used} thread(s)"
+            + (f", best of {repeats} per crop" if repeats > 1 else ""))
+    return tot_px / 1e6 / tot_t, tot_t, desc, used
 
 
 # ---------------------------------------------------------- clock sampler ---
@@ -174,8 +207,9 @@ def run_reference(args):
     times = []
     desc = ""
     mpix = 0.0
+    used = 1
     for i in range(args.warmup + args.steps):
-        v, t, desc = oracle_sample(img, cfg, budget_s=0.0, max_crops=1, crop=args.ref_crop)
+        v, t, desc, used = oracle_sample(img, cfg, budget_s=0.0, max_crops=1, crop=args.ref_crop, threads=0)
         if i >= args.warmup:
             times.append(t)
             mpix = args.ref_crop * args.ref_crop / 1e6
@@ -185,7 +219,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / len(times), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)", "config": workload_config(cfg),
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+                             "cpu": cpu_model()[0], "nproc": cpu_model()[1],
                              "sample": desc + "; each step one crop"},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -512,9 +547,15 @@ def run_gpu(args):
             line["serving"]["learned"] = serving_section(h_frame, cfg, net, gp)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, t, desc = oracle_sample(img, cfg)
-        line["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                                "seconds": round(t, 2)}
+        # the oracle on the host's cores: every core (its parallel loops; the
+        # labelling stays sequential), and the plain single-threaded definition
+        model, nproc = cpu_model()
+        va, ta, da, used = oracle_sample(img, cfg, budget_s=6.0, threads=0, repeats=3)
+        v1, t1, d1, _ = oracle_sample(img, cfg, budget_s=3.0, max_crops=2, threads=1, repeats=3)
+        line["cpu_baseline"] = {"value": round(va, 4), "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": da, "seconds": round(ta, 2), "cpu": model, "nproc": nproc,
+                                "single_thread": {"value": round(v1, 4), "unit": UNIT, "cores": 1, "sample": d1,
+                                                  "seconds": round(t1, 2)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     replicas.finish(dist)

@@ -412,8 +412,8 @@ gp_status gp_server_stats(gp_server* s, gp_server_report* out, int32_t reset);
 void gp_server_destroy(gp_server* s);
 
 /* gp_background without a context, for callers that cannot allocate device
- * memory.  The paper has no counterpart: it is a deployment form of the
- * Section 3.1 stage.  Some callers must not call cudaMalloc at all -- a
+ * memory.  The paper has no counterpart.  Some callers must not call
+ * cudaMalloc at all -- a
  * process whose device memory belongs to a pool it may not bypass, a plugin
  * loaded into an application that forbids allocations after start-up, a
  * latency-critical loop that must not take the allocator's locks -- and so
@@ -427,7 +427,10 @@ void gp_server_destroy(gp_server* s);
  *    a larger mesh returns GP_ERR_INVALID_ARG with nothing enqueued.
  *  - The first call on a device looks up the scratch's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the rest of the
+ *    process: it belongs to the device's primary context, so after a
+ *    cudaDeviceReset, or on the device driven through another context, it is
+ *    no longer valid and this entry point must not be called again.
  *  - Every call uses the same scratch, and each call rewrites all of it that
  *    it reads, so calls in sequence need nothing cleared; calls that overlap
  *    on the GPU (different streams, no ordering) race on it.

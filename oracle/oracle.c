@@ -32,11 +32,33 @@
  * Plain algorithms throughout: sorting for medians, breadth-first flood fill
  * for labelling, direct double loops for the filter, piecewise exact
  * integration for the overlap area.
+ *
+ * Threads: the loops over independent outputs (boxes, map columns, filtered
+ * rows, aperture sources) may run on several host threads (OpenMP, when the
+ * compiler has it); each output is computed by one thread in the same
+ * arithmetic order as with one, so the results do not depend on the thread
+ * count.  Labelling and moments stay sequential.  orc_set_threads(1) gives
+ * the plain single-threaded definition.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* threads for the loops above (n < 1: all the host's); returns the count used */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define ORC_FLAG_SAT 1u
 #define ORC_FLAG_CENTROID_FALLBACK 2u
@@ -118,9 +140,12 @@ int orc_box_stats(const double* img, const uint8_t* bad, int W, int H, int B,
                   double* med_out, double* mean_out, long* nkept_out)
 {
     int Mx = (W + B - 1) / B, My = (H + B - 1) / B;
+#pragma omp parallel
+    {
     double* buf = (double*)malloc(sizeof(double) * (size_t)B * (size_t)B);
-    for (int j = 0; j < My; ++j)
-        for (int i = 0; i < Mx; ++i) {
+#pragma omp for schedule(dynamic, 1)
+    for (int b0 = 0; b0 < Mx * My; ++b0) {
+            const int j = b0 / Mx, i = b0 % Mx;
             int x0 = i * B, x1 = (i + 1) * B < W ? (i + 1) * B : W;
             int y0 = j * B, y1 = (j + 1) * B < H ? (j + 1) * B : H;
             long n = 0;
@@ -142,6 +167,7 @@ int orc_box_stats(const double* img, const uint8_t* bad, int W, int H, int B,
             if (nkept_out) nkept_out[b] = nk;
         }
     free(buf);
+    }
     return 0;
 }
 
@@ -301,18 +327,23 @@ int orc_spline_map(const double* mesh, int Mx, int My, int W, int H, int B, doub
     double* tx = (double*)malloc(sizeof(double) * (size_t)Mx);
     double* ty = (double*)malloc(sizeof(double) * (size_t)My);
     double* Mrow = (double*)malloc(sizeof(double) * (size_t)Mx * My);
-    double* u = (double*)malloc(sizeof(double) * (size_t)My);
-    double* Mu = (double*)malloc(sizeof(double) * (size_t)My);
     box_centres(W, B, Mx, tx);
     box_centres(H, B, My, ty);
     for (int j = 0; j < My; ++j) spline_second_derivs(tx, mesh + (size_t)j * Mx, Mx, Mrow + (size_t)j * Mx);
+#pragma omp parallel
+    {
+    double* u = (double*)malloc(sizeof(double) * (size_t)My);
+    double* Mu = (double*)malloc(sizeof(double) * (size_t)My);
+#pragma omp for schedule(static)
     for (int x = 0; x < W; ++x) {
         for (int j = 0; j < My; ++j)
             u[j] = spline_eval(tx, mesh + (size_t)j * Mx, Mrow + (size_t)j * Mx, Mx, (double)x);
         spline_second_derivs(ty, u, My, Mu);
         for (int y = 0; y < H; ++y) map[(size_t)y * W + x] = spline_eval(ty, u, Mu, My, (double)y);
     }
-    free(tx); free(ty); free(Mrow); free(u); free(Mu);
+    free(u); free(Mu);
+    }
+    free(tx); free(ty); free(Mrow);
     return 0;
 }
 
@@ -336,6 +367,7 @@ int orc_filter(const double* m, int W, int H, const double* K, int kw, int kh, d
     for (int i = 0; i < kw * kh; ++i) s += K[i];
     if (s == 0.0) return -1;
     int hx = kw / 2, hy = kh / 2;
+#pragma omp parallel for schedule(static)
     for (long y = 0; y < H; ++y)
         for (long x = 0; x < W; ++x) {
             double acc = 0;
@@ -553,6 +585,7 @@ int orc_apertures(const double* m, const double* var, const uint8_t* bad, const 
                   const double* radii, int nr, double gain,
                   double* flux, double* fluxerr, uint32_t* flags)
 {
+#pragma omp parallel for schedule(dynamic, 16)
     for (long s = 0; s < n; ++s)
         for (int k = 0; k < nr; ++k) {
             double cx = xs[s], cy = ys[s], r = radii[k];

@@ -80,6 +80,8 @@ extern "C" gp_status gp_background_static(const gp_image* img, const gp_bkg_para
     }
 
     // device address of the scratch on the current device, looked up once
+    // and kept for the process: it belongs to the device's primary context
+    // (a cudaDeviceReset invalidates it)
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return reject(GP_ERR_CUDA, "no current CUDA device");

@@ -153,12 +153,10 @@ def test_adamw_step_is_the_published_update():
     assert np.allclose(p.cpu().numpy(), expect, atol=1e-6)
 
 
-def test_training_reduces_loss_and_matches_plain_estimator():
-    """Train briefly on GPU-drawn frames; the network must learn the plain
-    estimator's meshes, and on held-out frames its error against the true
-    sky is compared with the plain estimator's.  The gain is the background
-    stage's time (one histogram pass + network instead of iterative
-    clipping and median filtering) at that accuracy."""
+def test_training_reduces_loss_and_learns_the_plain_estimator():
+    """Train briefly on GPU-drawn frames with the library's own forward and
+    backward kernels: the loss falls and the network learns the plain
+    estimator's meshes on held-out frames."""
     ctx = gp.Context(0, workspace_bytes=512 << 20)
     try:
         train = learned.build_dataset(ctx, 96, seed0=1_000_000, size=2048, mesh=64)
@@ -170,10 +168,29 @@ def test_training_reduces_loss_and_matches_plain_estimator():
         ev = learned.evaluate(net, held)
         print(ev)
         assert ev["bkg_rmse_learned_vs_plain"] < 0.5
-        assert ev["bkg_rmse_learned_vs_truth"] < 1.5 * ev["bkg_rmse_plain_vs_truth"] + 0.2
-        frame = learned.training_frame(7, 4096)
+    finally:
+        ctx.close()
+
+
+def test_trained_network_gains_over_the_plain_estimator():
+    """The committed network (trained on the GPU on 2,000 frames, mesh 64)
+    on frames it never saw: its background is closer to the true sky than
+    the plain clipped estimator's, by a margin, and its background stage
+    (one histogram pass and the network, in place of iterative clipping and
+    the median filter) is faster, by a margin."""
+    import os
+    path = os.path.join(os.path.dirname(learned.__file__), "weights", "learned_bkg.npz")
+    net = learned.load(path)
+    ctx = gp.Context(0, workspace_bytes=1 << 30)
+    try:
+        held = learned.build_dataset(ctx, 32, seed0=3_000_000, size=4096, mesh=64)
+        ev = learned.evaluate(net, held)
+        print(ev)
+        assert ev["bkg_rmse_learned_vs_truth"] < 0.95 * ev["bkg_rmse_plain_vs_truth"]
+        assert ev["rms_relerr_learned_vs_truth"] < 0.05
+        frame = learned.training_frame(3_100_000, 4096)
         t = learned.time_background(ctx, frame.image, 64, net)
         print(t)
-        assert t["learned_ms"] > 0 and t["plain_ms"] > 0
+        assert t["learned_ms"] < 0.8 * t["plain_ms"]
     finally:
         ctx.close()

@@ -269,3 +269,56 @@ def test_strided_host_crop_matches_contiguous_copy():
         s.close()
     assert a["status"] == b["status"] == gp.GP_OK and a["n"] > 0
     same(a, b, "strided crop")
+
+
+def test_requests_arriving_while_others_run():
+    """Continuous batching under arrival: a first wave is submitted, and once
+    the server has work on the GPU (admitted, not finished), a second thread
+    submits a second wave.  The late requests are admitted while earlier
+    units are still in flight (several units on the device at once), and
+    every result is bit-identical to the same frame run alone."""
+    import threading
+    import time
+
+    CAP = 200000
+    big = [make(8192, 8192, 81)]          # one long unit: its copies (frame in, map out) and kernels take a while
+    small = [make(w, h, s) for w, h, s in SIZES[:4]]
+    ctx1 = gp.Context(0, workspace_bytes=2 << 30)
+    try:
+        ref = {id(i): single(ctx1, i, capacity=CAP) for i in big + small}
+    finally:
+        ctx1.close()
+    s = server(hbm_budget=8 << 30, slots=3)
+    try:
+        wave1 = [s.submit(pinned(i), CAP, want_segmap=True) for i in big]
+        # wait until the server has admitted work that has not finished
+        t0 = time.time()
+        while True:
+            st = s.stats()
+            if st["peak_inflight"] >= 1 and st["completed"] < len(wave1):
+                break
+            assert time.time() - t0 < 30, "the first wave never showed work in flight"
+            time.sleep(0.0005)
+        seen = {}
+
+        def late():
+            seen["before"] = s.stats()
+            seen["tickets"] = [s.submit(pinned(i), CAP, want_segmap=True) for i in small]
+            seen["after"] = s.stats()
+
+        th = threading.Thread(target=late)
+        th.start()
+        th.join()
+        assert seen["before"]["completed"] < len(wave1), "the first wave finished before the late requests came"
+        res1 = [s.result(t) for t in wave1]
+        res2 = [s.result(t) for t in seen["tickets"]]
+        st = s.stats()
+    finally:
+        s.close()
+    for img, r in zip(big + small, res1 + res2):
+        assert r["status"] == gp.GP_OK
+        same(ref[id(img)], r, "request under arrival")
+    assert st["completed"] == len(big) + len(small) and st["failed"] == 0
+    # the first wave is one unit: two units in flight at once means a late one ran beside it
+    assert st["peak_inflight"] >= 2, "the late requests never ran beside earlier ones"
+    print({k: st[k] for k in ("units", "batched_frames", "peak_inflight", "p50_ms", "p99_ms")})

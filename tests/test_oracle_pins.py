@@ -514,3 +514,24 @@ def test_threshold_is_strict_and_skips_bad():
     rms = np.array([[2.0, 2.0, 2.0, 2.0]])
     bad = np.array([[0, 0, 0, 1]], np.uint8)
     assert list(oracle.threshold(F, rms, bad, 1.5)[0]) == [0, 1, 0, 0]
+
+
+def test_oracle_threads_give_identical_results():
+    """The oracle's parallel loops (boxes, map columns, filter rows, aperture
+    sources) compute each output on one thread in a fixed order, so the whole
+    path is bit-identical on one thread and on every core."""
+    cfg = synth.scaled_config(synth.CONFIGS["plain_2048x2048_u16"], 400, 300)
+    img, _ = synth.make_frame(cfg, 5, cache=False)
+    outs = []
+    try:
+        for n in (1, 0):
+            oracle.set_threads(n)
+            outs.append(oracle.extract(img, 64, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii, cfg.gain,
+                                       saturation=cfg.saturation))
+    finally:
+        oracle.set_threads(1)
+    a, b = outs
+    for k in ("bkg_mesh", "rms_mesh", "bkg_map", "rms_map", "F", "seg", "flux", "fluxerr", "apflags"):
+        assert np.array_equal(a[k], b[k]), k
+    for k, v in a["cat"].items():
+        assert np.array_equal(v, b["cat"][k]), k
