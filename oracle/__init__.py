@@ -78,6 +78,7 @@ def lib():
             L.orc_overlap_area.argtypes = [d, d, d, d, d]
             L.orc_overlap_area.restype = d
             L.orc_apertures.argtypes = [vp, vp, vp, vp, i, i, vp, vp, l, vp, i, d, vp, vp, vp]
+            L.orc_growth.argtypes = [vp, vp, vp, vp, i, i, vp, vp, l, vp, i, d, vp, vp, vp]
             L.orc_set_threads.argtypes = [i]
             L.orc_set_threads.restype = i
             _lib = L
@@ -273,6 +274,27 @@ def apertures(m, var, bad, sat, xs, ys, radii, gain):
     flags = np.zeros((n, nr), np.uint32)
     lib().orc_apertures(_p(m), _p(var), _p(bad), _p(sat), W, H, _p(xs), _p(ys), n, _p(radii), nr,
                         float(gain), _p(flux), _p(err), _p(flags))
+    return flux, err, flags
+
+
+def growth_radii(fwhm):
+    """[R20] the paper's integer radii, ceil(0.75 FWHM) .. ceil(5 FWHM)."""
+    return np.arange(int(np.ceil(0.75 * fwhm)), int(np.ceil(5.0 * fwhm)) + 1, dtype=np.int32)
+
+
+def growth(m, var, bad, sat, xs, ys, radii, gain):
+    """[R20][R21] top-hat growth curves (flux, fluxerr, flags), each n x nr."""
+    m, var, bad = _f64(m), _f64(var), _u8(bad)
+    sat = _u8(sat) if sat is not None else None
+    H, W = m.shape
+    xs, ys = _f64(xs), _f64(ys)
+    radii = np.ascontiguousarray(radii, dtype=np.int32)
+    n, nr = xs.size, radii.size
+    flux = np.zeros((n, nr))
+    err = np.zeros((n, nr))
+    flags = np.zeros((n, nr), np.uint32)
+    lib().orc_growth(_p(m), _p(var), _p(bad), _p(sat), W, H, _p(xs), _p(ys), n, _p(radii), nr, float(gain),
+                     _p(flux), _p(err), _p(flags))
     return flux, err, flags
 
 

@@ -535,3 +535,90 @@ def test_oracle_threads_give_identical_results():
         assert np.array_equal(a[k], b[k]), k
     for k, v in a["cat"].items():
         assert np.array_equal(v, b["cat"][k]), k
+
+
+# ------------------------------------------------ top-hat growth curves ---
+def _tophat(r):
+    u = np.arange(-r, r + 1)
+    return (u[:, None] ** 2 + u[None, :] ** 2 <= r * r).astype(np.float64)
+
+
+def test_growth_radii_are_the_papers_range():
+    """Section 3.4: integer radii from ceil(0.75 FWHM) to ceil(5 FWHM)."""
+    assert oracle.growth_radii(3.0).tolist() == list(range(3, 16))
+    assert oracle.growth_radii(2.0).tolist() == list(range(2, 11))
+    assert oracle.growth_radii(4.1).tolist() == list(range(4, 22))
+
+
+def test_growth_counts_lattice_points_on_a_constant_image():
+    """A unit image: each sum is the number of pixels of the top-hat, the
+    Gauss circle count N(r)."""
+    g = golden()
+    radii = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 15]
+    m = np.ones((64, 70))
+    f, e, fl = oracle.growth(m, np.zeros_like(m), np.zeros(m.shape, np.uint8), None, [35.3], [31.6], radii, 0.0)
+    assert f[0].tolist() == [g[f"gauss_circle_r{r}"] for r in radii]
+    assert np.all(fl == 0)
+
+
+def test_growth_is_the_tophat_correlation_sampled_at_the_source_pixel():
+    """The paper's formulation: the frame (bad pixels zeroed) correlated with
+    a top-hat kernel, read at the pixel nearest the position; the variance
+    map through the same kernel; Poisson term F / gain; flags from the
+    pixels under the kernel."""
+    rng = np.random.default_rng(3)
+    H, W = 90, 120
+    m = rng.normal(0, 20, (H, W))
+    var = rng.uniform(10, 50, (H, W))
+    bad = (rng.random((H, W)) < 0.01).astype(np.uint8)
+    sat = (rng.random((H, W)) < 0.01).astype(np.uint8)
+    xs = np.concatenate([rng.uniform(10, W - 10, 20), [0.2, W - 0.7, 3.49, 3.51]])
+    ys = np.concatenate([rng.uniform(10, H - 10, 20), [45.0, 2.0, H - 1.2, 0.3]])
+    radii = np.array([1, 3, 6, 9], np.int32)
+    f, e, fl = oracle.growth(m, var, bad, sat, xs, ys, radii, 2.0)
+    mz = np.where(bad != 0, 0.0, m)
+    vz = np.where(bad != 0, 0.0, var)
+    for k, r in enumerate(radii):
+        T = _tophat(r)
+        cf = ndimage.correlate(mz, T, mode="constant", cval=0.0)
+        cv = ndimage.correlate(vz, T, mode="constant", cval=0.0)
+        cb = ndimage.correlate(bad.astype(np.float64), T, mode="constant", cval=0.0)
+        cs = ndimage.correlate((sat & (bad == 0)).astype(np.float64), T, mode="constant", cval=0.0)
+        inside = ndimage.correlate(np.ones((H, W)), T, mode="constant", cval=0.0)
+        for s in range(xs.size):
+            xc, yc = int(np.floor(xs[s] + 0.5)), int(np.floor(ys[s] + 0.5))
+            assert abs(f[s, k] - cf[yc, xc]) <= 1e-9 * (1 + abs(cf[yc, xc]))
+            vv = cv[yc, xc] + (max(cf[yc, xc], 0.0) / 2.0)
+            assert abs(e[s, k] - np.sqrt(vv)) <= 1e-9 * np.sqrt(vv)
+            want = (oracle.FLAG_TRUNCATED if inside[yc, xc] < T.sum() else 0) | \
+                   (oracle.FLAG_BAD if cb[yc, xc] > 0 else 0) | (oracle.FLAG_SAT if cs[yc, xc] > 0 else 0)
+            assert fl[s, k] == want, (s, r)
+
+
+def test_growth_of_a_delta_and_against_exact_overlap_sums():
+    """A single bright pixel at the source pixel: every radius holds exactly
+    its value.  A smooth star: the top-hat and the exact disc overlap of the
+    same radius differ only through the pixels the circle crosses, so their
+    difference is bounded by the boundary pixels' values."""
+    m = np.zeros((41, 41))
+    m[20, 20] = 1234.5
+    z = np.zeros(m.shape, np.uint8)
+    f, _, _ = oracle.growth(m, np.zeros_like(m), z, None, [20.3], [19.8], [0, 1, 5, 12], 0.0)
+    assert np.all(f == 1234.5)
+    # a Moffat star (FWHM 3, beta 2.5) of unit flux drawn 6x finer
+    H = W = 61
+    s = 6
+    yy, xx = (np.mgrid[0:H * s, 0:W * s] + 0.5) / s - 0.5
+    alpha = 3.0 / (2 * np.sqrt(2 ** (1 / 2.5) - 1))
+    prof = (1.5 / (np.pi * alpha ** 2)) * (1 + ((xx - 30.0) ** 2 + (yy - 30.0) ** 2) / alpha ** 2) ** -2.5
+    img = prof.reshape(H, s, W, s).mean(axis=(1, 3))
+    zz = np.zeros(img.shape, np.uint8)
+    radii = np.arange(3, 16, dtype=np.int32)
+    ft, _, _ = oracle.growth(img, np.zeros_like(img), zz, None, [30.0], [30.0], radii, 0.0)
+    fx, _, _ = oracle.apertures(img, np.zeros_like(img), zz, None, [30.0], [30.0], radii.astype(np.float64), 0.0)
+    for k, r in enumerate(radii):
+        T = _tophat(r)
+        ring = ndimage.binary_dilation(T > 0) & ~ndimage.binary_erosion(np.pad(T > 0, 1))[1:-1, 1:-1]
+        border = img[30 - r:30 + r + 1, 30 - r:30 + r + 1][ring].sum()
+        assert abs(ft[0, k] - fx[0, k]) <= border
+    assert np.all(np.diff(ft[0]) > 0)               # a non-negative image: the curve grows
