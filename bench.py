@@ -171,8 +171,9 @@ def kernel_traffic(kernel, workload):
         return None
 
 
-STAGE_KERNEL = {"box_stats": "k_boxstats_win", "detect_tiles": "k_detect_tile", "measure": "k_measure",
-                "tile_merge": "k_finalize", "label_rank": "k_rank_scan", "mesh_spline": "k_mesh_all"}
+STAGE_KERNEL = {"box_stats": "k_boxstats_win", "mesh_spline": "k_mesh_all", "threshold": "k_stream",
+                "label_tiles": "k_label_tiles", "tile_merge": "k_merge", "label_rank": "k_rank_scan",
+                "measure": "k_measure"}
 
 
 def algorithmic_bytes(stage, cfg, cat):
@@ -182,8 +183,12 @@ def algorithmic_bytes(stage, cfg, cat):
     npix = cfg.width * cfg.height
     if stage == "box_stats":
         return npix * bpp
-    if stage == "detect_tiles":
-        return npix * (bpp + 4)
+    if stage == "threshold":
+        # frame read once; uint32 map (zero, or the pixel's m at foreground) and packed mask written
+        return npix * (bpp + 4) + npix // 8
+    if stage == "label_tiles" and cat is not None:
+        # at least: the labels of the kept segments' pixels written, their m read back
+        return int(cat["npix"].astype(np.int64).sum()) * 8
     if stage == "measure" and cat is not None:
         bw = (cat["xmax"] - cat["xmin"] + 1).astype(np.int64)
         bh = (cat["ymax"] - cat["ymin"] + 1).astype(np.int64)
@@ -225,6 +230,45 @@ def run_reference(args):
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------- growth curves ---
+def growth_section(ctx, ex, t_img, cfg, nsrc, stream, dev, steps, peak):
+    """gp_growth at every catalog centroid with the paper's integer radii,
+    ceil(0.75 FWHM) .. ceil(5 FWHM) (Section 3.4), FWHM the frame's PSF
+    width.  Kernel time from the context's stage events; bytes are the
+    pixels under the largest top-hat, once per source."""
+    import numpy as np
+    import torch
+    fwhm = float(np.mean(cfg.fwhm))
+    radii = np.arange(int(np.ceil(0.75 * fwhm)), int(np.ceil(5.0 * fwhm)) + 1, dtype=np.int32)
+    n = min(nsrc, CAPACITY)
+    xs = ex.out["catalog"]["x"][:n]
+    ys = ex.out["catalog"]["y"][:n]
+    bkg = {"bkg_mesh": ex.out["bkg_mesh"], "rms_mesh": ex.out["rms_mesh"], "mesh": cfg.mesh}
+    for _ in range(3):
+        ctx.gp_growth(t_img, bkg, xs, ys, radii, gain=cfg.gain, saturation=cfg.saturation)
+    ctx.sync()
+    ctx.set_timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ctx.gp_growth(t_img, bkg, xs, ys, radii, gain=cfg.gain, saturation=cfg.saturation)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.sync()
+    st = ctx.stats()
+    ctx.set_timing(False)
+    kms = st["ms"]["measure"] / max(st["calls"], 1)
+    rmax = int(radii[-1])
+    pix = sum(1 for u in range(-rmax, rmax + 1) for v in range(-rmax, rmax + 1) if u * u + v * v <= rmax * rmax)
+    nbytes = n * pix * (2 if cfg.dtype == "u16" else 4) + n * len(radii) * 20
+    return {"sources": n, "radii": [int(radii[0]), rmax], "nr": int(len(radii)), "fwhm": fwhm,
+            "kernel": "k_growth", "kernel_ms": round(kms, 4), "call_ms": round(a.elapsed_time(b) / steps, 4),
+            "pixels_per_source": pix, "algorithmic_bytes": nbytes,
+            "achieved_GBs": round(nbytes / (kms / 1e3) / 1e9, 1),
+            "frac_of_hbm": round(nbytes / (kms / 1e3) / 1e9 / peak, 4),
+            "sources_per_s": round(n / (kms / 1e3), 1)}
 
 
 # --------------------------------------------------------------- serving ---
@@ -540,6 +584,10 @@ def run_gpu(args):
     if line_learned:
         line["learned"] = line_learned
 
+    # ---- growth curves (top-hat apertures, Section 3.4) at the catalog's centroids
+    if not args.no_growth:
+        line["growth"] = growth_section(ctx, ex, t_img, cfg, nsrc, stream, dev, args.steps, peak)
+
     # ---- the request server on a mixed stream (plain, and learned when trained weights exist)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_section(h_frame, cfg, None, gp)
@@ -575,6 +623,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-background form")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server stream")
+    ap.add_argument("--no-growth", action="store_true", help="skip the growth-curve measurement")
     ap.add_argument("--size", default=None,
                     help="WxH: run the workload's recipe on a frame of this size (profiling cases)")
     args = ap.parse_args()

@@ -79,13 +79,13 @@ gp_status gp_ctx_sync(gp_ctx* ctx, gp_stream stream);
 
 /* Stage timing.  When enabled, every call records CUDA events on its stream
  * at the boundaries of its stages (box statistics; mesh filter and spline
- * tables; detection tiles; tile merge; label ranking; moments and
- * apertures) into a ring of 256 call slots.  gp_ctx_stats() waits for the
+ * tables; threshold pass; tile labelling; tile merge; label ranking;
+ * moments and apertures) into a ring of 256 call slots.  gp_ctx_stats() waits for the
  * recorded events, returns the device time of each stage summed over the
  * calls recorded since the previous gp_ctx_stats() (at most the last 256),
  * and starts a new accumulation.  Disabled by default; the events add a few
  * microseconds per call. */
-#define GP_NSTAGES 6
+#define GP_NSTAGES 7
 typedef struct {
     int32_t calls;                 /* calls summed */
     int32_t launches;              /* kernels launched by the most recent call */
@@ -201,6 +201,27 @@ gp_status gp_detect(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const g
 gp_status gp_aperture(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
                       const double* x, const double* y, int32_t n, const gp_ap_params* p,
                       double* flux, double* fluxerr, uint32_t* flags, gp_stream stream);
+
+/* Section 3.4, growth curves: for each source i and each integer radius
+ * radii[k] (HOST array, nr of them, strictly increasing, 0 <= radius <=
+ * GP_GROWTH_MAX_R, 1 <= nr <= GP_GROWTH_MAX_NR), the sum of m over the
+ * top-hat {(u, v) : u^2 + v^2 <= radius^2} centred on the pixel nearest the
+ * source, (floor(x[i] + 1/2), floor(y[i] + 1/2)): the value at that pixel of
+ * the frame's cross-correlation with the top-hat, which the paper forms for
+ * the whole frame by FFT.  Pixels outside the frame or bad (masked, NaN)
+ * are left out and flagged GP_FLAG_TRUNCATED / GP_FLAG_BAD; GP_FLAG_SAT
+ * marks a saturated pixel under the top-hat.  fluxerr^2 = sum of sigma(p)^2
+ * over the same pixels + max(flux, 0) / gain (gain <= 0: no Poisson term).
+ * x, y: device, n sources; flux, fluxerr, flags: device, n*nr
+ * (source-major), caller-owned.  Sums are reproducible bit for bit.
+ * GP_ERR_INVALID_ARG on a null array with n > 0, n < 0 or a radius list
+ * outside the rules above; nothing is launched then. */
+#define GP_GROWTH_MAX_NR 32
+#define GP_GROWTH_MAX_R 255
+gp_status gp_growth(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
+                    const double* x, const double* y, int32_t n, const int32_t* radii,
+                    int32_t nr, float gain, double* flux, double* fluxerr, uint32_t* flags,
+                    gp_stream stream);
 
 /* The three stages in one call; apertures at each segment's centroid, rows
  * aligned with the catalog (capacity*nr). */

@@ -26,13 +26,14 @@ GP_OK, GP_ERR_INVALID_ARG, GP_ERR_OOM, GP_ERR_CAPACITY, GP_ERR_CUDA, GP_ERR_TIME
     GP_ERR_NOT_IMPLEMENTED, GP_ERR_INTERNAL = range(8)
 GP_U16, GP_F32 = 0, 1
 GP_FLAG_SAT, GP_FLAG_CENTROID_FALLBACK, GP_FLAG_TRUNCATED, GP_FLAG_BAD = 1, 2, 4, 8
+GP_GROWTH_MAX_NR, GP_GROWTH_MAX_R = 32, 255
 
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CAPACITY", 4: "GP_ERR_CUDA",
                 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NOT_IMPLEMENTED", 7: "GP_ERR_INTERNAL"}
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_ctx_set_walk_limit", "gp_workspace_bytes",
-           "gp_background", "gp_detect", "gp_aperture", "gp_extract", "gp_label_mask", "gp_background_static",
+           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_extract", "gp_label_mask", "gp_background_static",
            "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
            "gp_cnn_denorm", "gp_extract_batch", "gp_server_create", "gp_server_submit", "gp_server_wait",
@@ -74,8 +75,8 @@ class GpCatalog(C.Structure):
                 ("ypeak", C.c_void_p), ("flags", C.c_void_p)]
 
 
-GP_NSTAGES = 6
-STAGE_NAMES = ("box_stats", "mesh_spline", "detect_tiles", "tile_merge", "label_rank", "measure")
+GP_NSTAGES = 7
+STAGE_NAMES = ("box_stats", "mesh_spline", "threshold", "label_tiles", "tile_merge", "label_rank", "measure")
 
 
 class GpStats(C.Structure):
@@ -172,6 +173,9 @@ def load_library():
         L.gp_aperture.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), vp, vp, i32, C.POINTER(GpApParams),
                                   vp, vp, vp, vp]
         L.gp_aperture.restype = st
+        L.gp_growth.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), vp, vp, i32, C.POINTER(C.c_int32), i32,
+                                C.c_float, vp, vp, vp, vp]
+        L.gp_growth.restype = st
         L.gp_extract.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
                                  C.POINTER(GpApParams), C.POINTER(GpBkg), vp, C.POINTER(GpCatalog), vp, vp, vp, vp]
         L.gp_extract.restype = st
@@ -381,6 +385,23 @@ class Context:
         _check(load_library().gp_aperture(self._h, C.byref(gi), C.byref(b), x.data_ptr(), y.data_ptr(), n,
                                           C.byref(ap), flux.data_ptr(), ferr.data_ptr(), fl.data_ptr(),
                                           _stream_handle(stream)))
+        return flux[:n], ferr[:n], fl[:n]
+
+    def gp_growth(self, img, bkg, x, y, radii, gain=0.0, mask=None, saturation=0.0, stream=None):
+        """Top-hat growth curves at integer radii (strictly increasing)."""
+        import torch
+        gi = make_image(img, mask, saturation)
+        r = np.ascontiguousarray(np.asarray(radii, dtype=np.int32).reshape(-1))
+        n = int(x.numel())
+        x = x.to(device=img.device, dtype=torch.float64).contiguous()
+        y = y.to(device=img.device, dtype=torch.float64).contiguous()
+        flux = torch.empty((max(n, 1), max(r.size, 1)), dtype=torch.float64, device=img.device)
+        ferr = torch.empty_like(flux)
+        fl = torch.empty((max(n, 1), max(r.size, 1)), dtype=torch.int32, device=img.device)
+        b = self._bkg_struct(bkg)
+        _check(load_library().gp_growth(self._h, C.byref(gi), C.byref(b), x.data_ptr(), y.data_ptr(), n,
+                                        r.ctypes.data_as(C.POINTER(C.c_int32)), r.size, float(gain),
+                                        flux.data_ptr(), ferr.data_ptr(), fl.data_ptr(), _stream_handle(stream)))
         return flux[:n], ferr[:n], fl[:n]
 
     def gp_extract(self, img, mesh, kernel, thresh, minarea, radii, gain, capacity, mask=None, saturation=0.0,

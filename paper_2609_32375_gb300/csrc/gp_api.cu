@@ -226,15 +226,18 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     Image im = to_image(img);
     GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
     if (p->nnear) GP_CUDA(cudaMemsetAsync(p->nnear, 0, sizeof(int), st));
-    GP_CUDA(launch_detect_tiles(im, sb, sr, taps, p->kw, p->kh, p->thresh, p->minarea, segmap, p->mask_out, p->nnear,
-                                nullptr, w.D, w.T, w.P, w.C, ctx->dstatus, st));
+    const DetectArgs A = detect_args(im, sb, sr, taps, p->kw, p->kh, p->thresh, p->minarea, segmap, p->mask_out,
+                                     p->nnear, nullptr, w.D, w.T, w.P, w.C, ctx->dstatus);
+    GP_CUDA(launch_stream_any(A, nullptr, 1, detect_grid(W, H, false), st));
     mark(ctx, 3, st);
-    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, W, H, p->minarea, ctx->walk_limit, ctx->dstatus, st));
+    GP_CUDA(launch_label_any(A, nullptr, 1, st));
     mark(ctx, 4, st);
-    GP_CUDA(launch_rank(w.C, cat->n, cat->capacity, true, ctx->dstatus, st));
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, W, H, p->minarea, ctx->walk_limit, ctx->dstatus, st));
     mark(ctx, 5, st);
-    GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
+    GP_CUDA(launch_rank(w.C, cat->n, cat->capacity, true, ctx->dstatus, st));
     mark(ctx, 6, st);
+    GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
+    mark(ctx, 7, st);
     ctx->launches += 3 + 4 + 4 + 1 + (nr > 0 ? 1 : 0);
     return GP_OK;
 }
@@ -528,12 +531,46 @@ gp_status gp_aperture(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const
     s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, &ctx->launches, st);
     if (s == GP_ERR_OOM) return oom(cv);
     if (s != GP_OK) return s;
-    mark_to(ctx, 2, 5, st);
+    mark_to(ctx, 2, GP_NSTAGES - 1, st);
     if (n > 0) {
         GP_CUDA(launch_aperture(to_image(img), sb, sr, x, y, n, p->radii, p->nr, p->gain, flux, fluxerr, flags, st));
         ctx->launches += 2;
     }
-    mark(ctx, 6, st);
+    mark(ctx, GP_NSTAGES, st);
+    return GP_OK;
+}
+
+gp_status gp_growth(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const double* x, const double* y, int32_t n,
+                    const int32_t* radii, int32_t nr, float gain, double* flux, double* fluxerr, uint32_t* flags,
+                    gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg(img, bkg, true)) != GP_OK) return s;
+    if (!radii || nr < 1 || nr > GP_GROWTH_MAX_NR)
+        return fail(GP_ERR_INVALID_ARG, "growth radii: need 1..%d of them", GP_GROWTH_MAX_NR);
+    for (int k = 0; k < nr; ++k) {
+        if (radii[k] < 0 || radii[k] > GP_GROWTH_MAX_R)
+            return fail(GP_ERR_INVALID_ARG, "growth radius %d outside 0..%d", radii[k], GP_GROWTH_MAX_R);
+        if (k > 0 && radii[k] <= radii[k - 1]) return fail(GP_ERR_INVALID_ARG, "growth radii not increasing");
+    }
+    if (n < 0) return fail(GP_ERR_INVALID_ARG, "negative source count");
+    if (n > 0 && (!x || !y || !flux || !fluxerr || !flags)) return fail(GP_ERR_INVALID_ARG, "null growth array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    mark(ctx, 1, st);
+    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, &ctx->launches, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    mark_to(ctx, 2, GP_NSTAGES - 1, st);
+    if (n > 0) {
+        GP_CUDA(launch_growth(to_image(img), sb, sr, x, y, n, radii, nr, gain, flux, fluxerr, flags, st));
+        ctx->launches += 1;
+    }
+    mark(ctx, GP_NSTAGES, st);
     return GP_OK;
 }
 
@@ -565,13 +602,16 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
     begin_call(ctx, st);
     mark_to(ctx, 1, 2, st);
     GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
-    GP_CUDA(launch_detect_tiles(im, none, none, nullptr, 1, 1, 1.f, minarea, segmap, nullptr, nullptr, mask, w.D, w.T,
-                                w.P, w.C, ctx->dstatus, st));
+    const DetectArgs A = detect_args(im, none, none, nullptr, 1, 1, 1.f, minarea, segmap, nullptr, nullptr, mask, w.D,
+                                     w.T, w.P, w.C, ctx->dstatus);
+    GP_CUDA(launch_stream_any(A, nullptr, 1, detect_grid(width, height, true), st));
     mark(ctx, 3, st);
-    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, width, height, minarea, ctx->walk_limit, ctx->dstatus, st));
+    GP_CUDA(launch_label_any(A, nullptr, 1, st));
     mark(ctx, 4, st);
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, width, height, minarea, ctx->walk_limit, ctx->dstatus, st));
+    mark(ctx, 5, st);
     GP_CUDA(launch_rank(w.C, n_out, -1, false, ctx->dstatus, st));
-    mark_to(ctx, 5, 6, st);
+    mark_to(ctx, 6, 7, st);
     ctx->launches += 3 + 4 + 2;
     return GP_OK;
 }
@@ -598,7 +638,7 @@ gp_status gp_box_quantiles(gp_ctx* ctx, const gp_image* img, int32_t mesh, float
     begin_call(ctx, st);
     GP_CUDA(launch_boxstats(to_image(img), mesh, 3.0, 0, w.bkg_raw, w.rms_raw, w.valid, quant, st));
     ctx->launches += 1;
-    mark_to(ctx, 1, 6, st);
+    mark_to(ctx, 1, GP_NSTAGES, st);
     return GP_OK;
 }
 

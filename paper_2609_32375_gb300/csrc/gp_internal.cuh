@@ -332,6 +332,23 @@ struct Image {
     int is_f32;
 };
 
+// one pixel's value and whether it is bad (masked, or NaN / Inf in an FP32
+// frame); (x, y) must lie inside the frame
+template <bool F32>
+__device__ __forceinline__ float load_px(const Image& im, int x, int y, bool& bad)
+{
+    float v;
+    if (F32) {
+        v = __ldg(reinterpret_cast<const float*>(im.data) + (int64_t)y * im.pitch + x);
+        bad = !isfinite(v);
+    } else {
+        v = (float)__ldg(reinterpret_cast<const uint16_t*>(im.data) + (int64_t)y * im.pitch + x);
+        bad = false;
+    }
+    if (im.mask && im.mask[(int64_t)y * im.W + x]) bad = true;
+    return v;
+}
+
 // ------------------------------------------------ per-frame arguments ---
 // Every kernel of the pipeline runs either one frame, its arguments passed
 // by value (`one`, a __grid_constant__ parameter, so taking its address

@@ -31,10 +31,6 @@ int stream_ks(int kw, int kh);
 int detect_grid(int W, int H, bool given_mask);
 cudaError_t launch_stream_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxgrid,
                               cudaStream_t st);
-cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
-                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
-                                int* nnear, const uint8_t* in_mask, const DetMask& dm, const Tiles& T,
-                                const Pieces& P, const Comps& C, int* status, cudaStream_t st);
 cudaError_t launch_resolve(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
                            int H, int minarea, int walk_limit, int* status, cudaStream_t st);
 cudaError_t launch_rank(const Comps& C, int* n_out, int capacity, bool place, int* status, cudaStream_t st);
@@ -46,6 +42,11 @@ cudaError_t launch_measure(const Image& im, const SplineTab& sb, const SplineTab
 cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,
                             const double* ys, int n, const float* radii, int nr, float gain, double* flux,
                             double* ferr, uint32_t* fl, cudaStream_t st);
+
+// growth curves (k_growth.cu); radii strictly increasing, nr <= GP_GROWTH_MAX_NR
+cudaError_t launch_growth(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,
+                          const double* ys, int n, const int* radii, int nr, float gain, double* flux,
+                          double* ferr, uint32_t* flags, cudaStream_t st);
 
 // Batch-capable forms.  Each takes one frame's argument record (`one`, used
 // alone when batch == nullptr) or a device array of nframes records, one per
@@ -63,8 +64,9 @@ DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr
                        float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
                        const uint8_t* in_mask, const DetMask& dm, const Tiles& T, const Pieces& P, const Comps& C,
                        int* status);
-cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxgrid,
-                              cudaStream_t st);
+// the detection stage is two launches: the streaming threshold pass (or the
+// packing of a given mask), then the labelling of the listed tiles
+cudaError_t launch_label_any(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st);
 ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
                          int H, int minarea, int walk_limit, int* status);
 cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch, int nframes, int maxtiles,

@@ -398,21 +398,23 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     }
     ex.at(2);
     if (!detect) {
-        ex.at_range(3, 6);
+        ex.at_range(3, GP_NSTAGES);
         return GP_OK;
     }
 
     // ---- detection, segment resolution, catalog order, measurement
     for (int f = 0; f < n; ++f)
         if (F[f].nnear) PL_CUDA(cudaMemsetAsync(F[f].nnear, 0, sizeof(int), ex.st));
-    PL_CUDA(launch_detect_any(det[0], d_det, n, maxgrid, ex.st));
+    PL_CUDA(launch_stream_any(det[0], d_det, n, maxgrid, ex.st));
     ex.at(3);
-    PL_CUDA(launch_resolve_any(res[0], d_res, n, maxtiles, ex.st));
+    PL_CUDA(launch_label_any(det[0], d_det, n, ex.st));
     ex.at(4);
-    PL_CUDA(launch_rank_any(rank[0], d_rank, n, ex.st));
+    PL_CUDA(launch_resolve_any(res[0], d_res, n, maxtiles, ex.st));
     ex.at(5);
-    PL_CUDA(launch_measure_any(meas[0], d_meas, n, ex.st));
+    PL_CUDA(launch_rank_any(rank[0], d_rank, n, ex.st));
     ex.at(6);
+    PL_CUDA(launch_measure_any(meas[0], d_meas, n, ex.st));
+    ex.at(7);
     ex.launches += 3 + 4 + 4 + 1 + (P.nr > 0 ? 1 : 0);
     return GP_OK;
 }

@@ -1165,11 +1165,8 @@ static void launch_label_both(const DetectArgs& one, const DetectArgs* batch, in
 // every frame of a batch shares `one`'s dtype, kernel size and mode
 // (labelling a given mask or detecting); maxgrid = detect_grid() of the
 // largest frame
-cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, int nframes, int maxgrid,
-                              cudaStream_t st)
+cudaError_t launch_label_any(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st)
 {
-    cudaError_t e = launch_stream_any(one, batch, nframes, maxgrid, st);
-    if (e != cudaSuccess) return e;
     if (one.in_mask) {
         if (batch) launch_label_both<true, true>(one, batch, nframes, st);
         else launch_label_both<true, false>(one, batch, nframes, st);
@@ -1178,16 +1175,6 @@ cudaError_t launch_detect_any(const DetectArgs& one, const DetectArgs* batch, in
         else launch_label_both<false, false>(one, batch, nframes, st);
     }
     return cudaGetLastError();
-}
-
-cudaError_t launch_detect_tiles(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps,
-                                int kw, int kh, float thresh, int minarea, uint32_t* seg, uint8_t* mask_out,
-                                int* nnear, const uint8_t* in_mask, const DetMask& dm, const Tiles& T,
-                                const Pieces& P, const Comps& C, int* status, cudaStream_t st)
-{
-    const DetectArgs A = detect_args(im, sb, sr, taps, kw, kh, thresh, minarea, seg, mask_out, nnear, in_mask, dm, T,
-                                     P, C, status);
-    return launch_detect_any(A, nullptr, 1, detect_grid(im.W, im.H, in_mask != nullptr), st);
 }
 
 ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,

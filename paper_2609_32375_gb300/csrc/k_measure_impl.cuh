@@ -25,83 +25,54 @@ __device__ __forceinline__ float chord_int(float a, float b, float r2)
     return 0.5f * fmaf(r2, theta, fmaf(d, hb, -a * q));
 }
 
-// exact area of disc(0, r) n [x0,x1] x [y0,y1]: integrate the length of
-// [y0,y1] n [-h(x), h(x)] over x, split where h(x) = |y0|, |y1|.  On each
-// piece the top is y1 or the arc and the bottom y0 or the arc; rectangle parts
-// add directly and only arc-bounded pieces need the arc integral.  Those are
-// collected first: in a pixel that a circle of radius >= 1 crosses there are
-// one or two, so the warp runs the integral once or twice per pixel instead of
-// once per piece.  The roles come from squared comparisons (h^2 = r^2 - x^2).
-// Every product and sum is an explicit operation (fmaf, __fmul_rn,
-// __fadd_rn), so no instance of the kernels contracts it differently and a
-// frame gives the same bits in a batched launch as alone.
-static __device__ float disc_rect_area(float x0, float x1, float y0, float y1, float r)
+// exact area of disc(0, r) n [x0,x1] x [y0,y1] for a rectangle in the first
+// quadrant (0 <= x0 < x1, 0 <= y0 < y1).  There the arc y = h(x) =
+// sqrt(r^2 - x^2) falls monotonically: columns left of xa (h(xa) = y1) are
+// covered to the full height, columns right of xb (h(xb) = y0) not at all,
+// and in between to the height h(x) - y0.  So the area is one rectangle and
+// one arc integral.  Every product and sum is an explicit operation (fmaf,
+// __fmul_rn, __fadd_rn), so no instance of the kernels contracts it
+// differently and a frame gives the same bits in a batched launch as alone.
+__device__ __forceinline__ float quadrant_area(float x0, float x1, float y0, float y1, float r2)
 {
-    const float r2 = r * r;
-    const float a = fmaxf(x0, -r), b = fminf(x1, r);
-    if (!(a < b)) return 0.f;
-    float p[6];
-    p[0] = a;
-    p[5] = b;
-    const float c0 = fabsf(y0) < r ? sqrtf(fmaxf(fmaf(-y0, y0, r2), 0.f)) : 0.f;
-    const float c1 = fabsf(y1) < r ? sqrtf(fmaxf(fmaf(-y1, y1, r2), 0.f)) : 0.f;
-    p[1] = fminf(fmaxf(-c0, a), b);
-    p[2] = fminf(fmaxf(c0, a), b);
-    p[3] = fminf(fmaxf(-c1, a), b);
-    p[4] = fminf(fmaxf(c1, a), b);
-    // sort p[1..4]
-#define GP_CSWAP(i, j) { float lo_ = fminf(p[i], p[j]); float hi_ = fmaxf(p[i], p[j]); p[i] = lo_; p[j] = hi_; }
-    GP_CSWAP(1, 2); GP_CSWAP(3, 4); GP_CSWAP(1, 3); GP_CSWAP(2, 4); GP_CSWAP(2, 3);
-#undef GP_CSWAP
-    const float y02 = y0 * y0, y12 = y1 * y1;
-    float area = 0.f;
-    float l0 = 0.f, h0 = 0.f, k0 = 0.f, l1 = 0.f, h1 = 0.f, k1 = 0.f;   // the first two arc pieces
-    int n = 0;
-    // the pieces without branches: an empty piece (w = 0) adds an exact zero
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const float lo = p[k], hi = p[k + 1];
-        const float w = hi - lo;                                   // >= 0: the points are sorted
-        const float mid = 0.5f * (lo + hi);
-        const float hm2 = fmaxf(fmaf(-mid, mid, r2), 0.f);      // h(mid)^2
-        const bool top_h = y1 >= 0.f && hm2 <= y12;                // the arc is below the top edge
-        const bool bot_h = y0 <= 0.f && hm2 <= y02;                // the arc is above the bottom edge
-        const bool plain = !top_h && !bot_h;
-        // an arc piece is empty when its top is at or below its bottom
-        const bool empty = (top_h && bot_h) ? !(hm2 > 0.f) : top_h ? !(y0 < 0.f || hm2 > y02)
-                                                                   : !(y1 > 0.f || hm2 > y12);
-        const bool arc = w > 0.f && !plain && !empty;
-        // rectangle parts: the full height of a plain piece; on an arc piece
-        // the edges that the arc does not replace
-        const float rect = plain ? __fmul_rn(y1 - y0, w)
-                         : arc   ? __fsub_rn(top_h ? 0.f : __fmul_rn(y1, w), bot_h ? 0.f : __fmul_rn(y0, w))
-                                 : 0.f;
-        area = __fadd_rn(area, rect);
-        const float kg = (top_h && bot_h) ? 2.f : 1.f;
-        const bool s0 = arc && n == 0, s1 = arc && n == 1;
-        l0 = s0 ? lo : l0; h0 = s0 ? hi : h0; k0 = s0 ? kg : k0;
-        l1 = s1 ? lo : l1; h1 = s1 ? hi : h1; k1 = s1 ? kg : k1;
-        if (arc && n >= 2) area = fmaf(kg, chord_int(lo, hi, r2), area);   // radii below 1 only
-        n += arc ? 1 : 0;
-    }
-    if (n > 0) area = fmaf(k0, chord_int(l0, h0, r2), area);
-    if (n > 1) area = fmaf(k1, chord_int(l1, h1, r2), area);
-    return area;
+    if (!(fmaf(x0, x0, __fmul_rn(y0, y0)) < r2)) return 0.f;   // the nearest corner is outside
+    const float xa = sqrtf(fmaxf(fmaf(-y1, y1, r2), 0.f));
+    const float xb = sqrtf(fmaxf(fmaf(-y0, y0, r2), 0.f));
+    const float lo = fminf(fmaxf(xa, x0), x1);
+    const float d = fmaxf(__fsub_rn(fminf(x1, xb), lo), 0.f);
+    const float rect = __fmul_rn(__fsub_rn(y1, y0), __fsub_rn(lo, x0));
+    return __fadd_rn(rect, fmaf(-y0, d, chord_int(lo, __fadd_rn(lo, d), r2)));
 }
 
-template <bool F32>
-__device__ __forceinline__ float load_px(const Image& im, int x, int y, bool& bad)
+// One side of a pixel [a, a + 1] folded onto t >= 0: the piece [p0, p1],
+// and for a pixel that straddles 0 the second piece [0, q1].
+struct Fold {
+    float p0, p1, q1;
+    bool two;
+};
+
+__device__ __forceinline__ Fold fold_side(float a)
 {
-    float v;
-    if (F32) {
-        v = __ldg(reinterpret_cast<const float*>(im.data) + (int64_t)y * im.pitch + x);
-        bad = !isfinite(v);
-    } else {
-        v = (float)__ldg(reinterpret_cast<const uint16_t*>(im.data) + (int64_t)y * im.pitch + x);
-        bad = false;
-    }
-    if (im.mask && im.mask[(int64_t)y * im.W + x]) bad = true;
-    return v;
+    const float b = __fadd_rn(a, 1.f);
+    Fold f;
+    f.two = a < 0.f && b > 0.f;
+    f.p0 = a >= 0.f ? a : (b <= 0.f ? -b : 0.f);
+    f.p1 = a >= 0.f ? b : (b <= 0.f ? -a : b);
+    f.q1 = -a;
+    return f;
+}
+
+// exact area of disc(0, r) n [dx0, dx0 + 1] x [dy0, dy0 + 1]: the pixel folded
+// into the first quadrant by symmetry, a pixel on an axis split in two
+__device__ __forceinline__ float pixel_area(float dx0, float dy0, float r)
+{
+    const float r2 = __fmul_rn(r, r);
+    const Fold fx = fold_side(dx0), fy = fold_side(dy0);
+    float A = quadrant_area(fx.p0, fx.p1, fy.p0, fy.p1, r2);
+    if (fx.two) A = __fadd_rn(A, quadrant_area(0.f, fx.q1, fy.p0, fy.p1, r2));
+    if (fy.two) A = __fadd_rn(A, quadrant_area(fx.p0, fx.p1, 0.f, fy.q1, r2));
+    if (fx.two && fy.two) A = __fadd_rn(A, quadrant_area(0.f, fx.q1, 0.f, fy.q1, r2));
+    return A;
 }
 
 // Pixels crossed by a circle wait in a per-warp queue so that the exact
@@ -114,8 +85,10 @@ struct BEntry {
 constexpr int QCAP = 64;      // at most 31 waiting + 32 added by one row
 constexpr int MEAS_NT = 256;
 
+// the flag bits a lane collects: bit k a bad pixel under disc k, bit 8 + k a
+// saturated one
 template <int NR>
-__device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn, DF* f, DF* v, uint32_t* fl)
+__device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn, DF* f, DF* v, uint32_t& pk)
 {
     __syncwarp();
     const int lane = threadIdx.x & 31;
@@ -125,13 +98,13 @@ __device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn
         while (rm) {
             const int k = __ffs(rm) - 1;
             rm &= rm - 1u;
-            const float A = disc_rect_area(e.dx0, e.dx0 + 1.f, e.dy0, e.dy0 + 1.f, ap.r[k]);
+            const float A = pixel_area(e.dx0, e.dy0, ap.r[k]);
             if (!(A > 0.f)) continue;
+            if (e.kf & 0x100) { pk |= 1u << k; continue; }
+            if (e.kf & 0x200) pk |= 0x100u << k;
 #pragma unroll
             for (int kk = 0; kk < NR; ++kk) {
                 if (kk != k) continue;
-                if (e.kf & 0x100) { fl[kk] |= GP_FLAG_BAD; continue; }
-                if (e.kf & 0x200) fl[kk] |= GP_FLAG_SAT;
                 df_add_prod(f[kk], A, e.m);
                 df_add_prod(v[kk], A, e.var);
             }
@@ -140,14 +113,64 @@ __device__ __forceinline__ void flush_queue(const ApSpec& ap, BEntry* wq, int qn
     __syncwarp();
 }
 
+// Sums NV float-float values (a power of two) over the warp, one value per
+// lane group at the end: in each of the first log2(NV) butterfly steps the
+// partners split the values between them (each keeps one half and receives
+// the other lane's copy of it), then the remaining steps sum the one value
+// left.  Value i ends in the lanes whose bits (16, 8, ...) spell i.  The
+// order of every combination is fixed, so the sums are reproducible.
+template <int C, int O>
+__device__ __forceinline__ void df_scatter_step(DF* v, int lane)
+{
+    if constexpr (O > 0) {
+        const bool upper = (lane & O) != 0;
+        if constexpr (C > 1) {
+            constexpr int h = C / 2;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const DF send = upper ? v[i] : v[i + h];
+                const DF keep = upper ? v[i + h] : v[i];
+                DF recv;
+                recv.hi = __shfl_xor_sync(0xffffffffu, send.hi, O);
+                recv.lo = __shfl_xor_sync(0xffffffffu, send.lo, O);
+                v[i] = upper ? df_merge(recv, keep) : df_merge(keep, recv);
+            }
+            df_scatter_step<h, O / 2>(v, lane);
+        } else {
+            DF w;
+            w.hi = __shfl_xor_sync(0xffffffffu, v[0].hi, O);
+            w.lo = __shfl_xor_sync(0xffffffffu, v[0].lo, O);
+            v[0] = upper ? df_merge(w, v[0]) : df_merge(v[0], w);
+            df_scatter_step<1, O / 2>(v, lane);
+        }
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ DF df_reduce_scatter(DF* v)
+{
+    df_scatter_step<NV, 16>(v, threadIdx.x & 31);
+    return v[0];
+}
+
+// the value index df_reduce_scatter<NV> leaves in this lane: the top
+// log2(NV) of the lane's five bits
+template <int NV>
+__device__ __forceinline__ int scatter_index(int lane)
+{
+    return lane / (32 / NV);
+}
+
 // Apertures around (cx, cy) for all radii; executed by one full warp.
 // One lane per pixel column: the column's x-spline coefficients and the
 // node-row values u_j, w_j of both maps are evaluated once per column and
-// reused down the column, so each pixel costs a few FMAs for B(p) and
-// sigma(p).  Pixels wholly inside a disc add directly; pixels the circle
-// crosses go through the queue.  The queue order and the lane assignment are
-// fixed, and lane results are combined in a fixed order, so the sums are
-// reproducible.  Lane 0 writes.
+// reused down the column; the y-spline coefficients of up to 32 rows are
+// evaluated one row per lane and fetched by shuffle, so each pixel costs a
+// few FMAs for B(p) and sigma(p).  Pixels wholly inside disc k add to a lane's
+// float32 column sums (at most 32 terms, then folded into float-float sums);
+// pixels the circle crosses go through the queue.  The queue order and the
+// lane assignment are fixed, and lane results are combined in a fixed order,
+// so the sums are reproducible.
 template <bool F32, int NR>
 __device__ void aperture_warp(const Image& im, const SplineTab& sb, const SplineTab& sr, const ApSpec& ap,
                               double cx, double cy, double* flux, double* ferr, uint32_t* aflags, BEntry* wq)
@@ -171,106 +194,113 @@ __device__ void aperture_warp(const Image& im, const SplineTab& sb, const Spline
     const int xa = max(xi - rc - 1, 0), ya = max(yi - rc - 1, 0);
     int xb = min(xi + rc + 2, W - 1), yb = min(yi + rc + 2, H - 1);
     if (!near) { xb = -1; yb = -1; }
-    DF f[NR > 0 ? NR : 1], v[NR > 0 ? NR : 1];
-    uint32_t fl[NR > 0 ? NR : 1];
+    constexpr int NRA = NR > 0 ? NR : 1;
+    constexpr int NV = 2 * NRA <= 2 ? 2 : 2 * NRA <= 4 ? 4 : 2 * NRA <= 8 ? 8 : 16;
+    DF acc[NV];                                      // flux sums of radii 0..NR-1, then variance sums
 #pragma unroll
-    for (int k = 0; k < NR; ++k) { f[k] = df_zero(); v[k] = df_zero(); fl[k] = 0u; }
+    for (int i = 0; i < NV; ++i) acc[i] = df_zero();
+    DF* f = acc;
+    DF* v = acc + NRA;
+    uint32_t pk = 0u;                                // bad (bit k) / saturated (bit 8 + k) under disc k
     const float rmax2 = ap.rmax * ap.rmax;
+    const int nyn = sb.ay.n;
     int qn = 0;                                      // warp-uniform queue length
     for (int xbase = xa; xbase <= xb; xbase += 32) {
         const int x = xbase + lane;
         const bool colok = x <= xb;
+        const int xl = colok ? x : xb;
         const float dx0 = (float)(x - xi) - xf - 0.5f, dx1 = dx0 + 1.f;
         const float nx = fmaxf(0.f, fmaxf(dx0, -dx1));
         const float fx = fmaxf(dx0 * dx0, dx1 * dx1);
-        const AxCoef ccx = axis_coef(sb.ax, (float)(colok ? x : xb));
+        const AxCoef ccx = axis_coef(sb.ax, (float)xl);
         int jc = -1;                       // node row pair cached for this column
         float ub0 = 0, ub1 = 0, wb0 = 0, wb1 = 0, ur0 = 0, ur1 = 0, wr0 = 0, wr1 = 0;
-        for (int y = ya; y <= yb; ++y) {
-            const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
-            const float ny = fmaxf(0.f, fmaxf(dy0, -dy1));
-            if (!(ny * ny < rmax2)) continue;        // a row beyond the largest disc (the whole warp)
-            const float dmin2 = fmaf(nx, nx, ny * ny);
-            const float dmax2 = fx + fmaxf(dy0 * dy0, dy1 * dy1);
-            const bool live = colok && dmin2 < rmax2;
-            bool bad = true, sat = false;
-            float m = 0.f, var = 0.f;
-            if (live) {
-                const float val = load_px<F32>(im, x, y, bad);
-                if (!bad) {
-                    const AxCoef ccy = axis_coef(sb.ay, (float)y);
-                    if (ccy.i != jc) {
-                        const float2 b0 = row_eval(sb, ccy.i, ccx), b1 = row_eval(sb, ccy.i1, ccx);
-                        const float2 r0 = row_eval(sr, ccy.i, ccx), r1 = row_eval(sr, ccy.i1, ccx);
-                        ub0 = b0.x; wb0 = b0.y; ub1 = b1.x; wb1 = b1.y;
-                        ur0 = r0.x; wr0 = r0.y; ur1 = r1.x; wr1 = r1.y;
-                        jc = ccy.i;
-                    }
-                    m = val - axis_combine(ccy, ub0, ub1, wb0, wb1);
-                    const float sg = axis_combine(ccy, ur0, ur1, wr0, wr1);
-                    var = sg * sg;
-                    sat = im.sat > 0.f && val >= im.sat;
+        for (int ybase = ya; ybase <= yb; ybase += 32) {
+            const AxCoef cyl = axis_coef(sb.ay, (float)min(ybase + lane, yb));   // row ybase + lane
+            const int yend = min(yb, ybase + 31);
+            float fs[NRA], vs[NRA];
+#pragma unroll
+            for (int k = 0; k < NRA; ++k) { fs[k] = 0.f; vs[k] = 0.f; }
+            for (int y = ybase; y <= yend; ++y) {
+                const float dy0 = (float)(y - yi) - yf - 0.5f, dy1 = dy0 + 1.f;
+                const float ny = fmaxf(0.f, fmaxf(dy0, -dy1));
+                if (!(ny * ny < rmax2)) continue;        // a row beyond the largest disc (the whole warp)
+                const int j = y - ybase;
+                AxCoef ccy;
+                ccy.i = __shfl_sync(0xffffffffu, cyl.i, j);
+                ccy.b = __shfl_sync(0xffffffffu, cyl.b, j);
+                ccy.c0 = __shfl_sync(0xffffffffu, cyl.c0, j);
+                ccy.c1 = __shfl_sync(0xffffffffu, cyl.c1, j);
+                ccy.i1 = min(ccy.i + 1, nyn - 1);
+                if (ccy.i != jc) {
+                    const float2 b0 = row_eval(sb, ccy.i, ccx), b1 = row_eval(sb, ccy.i1, ccx);
+                    const float2 r0 = row_eval(sr, ccy.i, ccx), r1 = row_eval(sr, ccy.i1, ccx);
+                    ub0 = b0.x; wb0 = b0.y; ub1 = b1.x; wb1 = b1.y;
+                    ur0 = r0.x; wr0 = r0.y; ur1 = r1.x; wr1 = r1.y;
+                    jc = ccy.i;
+                }
+                const float dmin2 = fmaf(nx, nx, ny * ny);
+                const float dmax2 = fx + fmaxf(dy0 * dy0, dy1 * dy1);
+                const bool live = colok && dmin2 < rmax2;
+                bool bad;
+                const float val = load_px<F32>(im, xl, y, bad);
+                const float sg = axis_combine(ccy, ur0, ur1, wr0, wr1);
+                const float m = bad ? 0.f : __fsub_rn(val, axis_combine(ccy, ub0, ub1, wb0, wb1));
+                const float var = bad ? 0.f : __fmul_rn(sg, sg);
+                const bool sat = !bad && im.sat > 0.f && val >= im.sat;
+                unsigned fm = 0u, bm = 0u;           // radii holding the pixel whole / crossing it
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const float r2 = ap.r[k] * ap.r[k];
+                    const bool full = live && dmax2 <= r2;
+                    const bool in = live && dmin2 < r2;
+                    fs[k] = __fadd_rn(fs[k], full ? m : 0.f);
+                    vs[k] = __fadd_rn(vs[k], full ? var : 0.f);
+                    fm |= full ? 1u << k : 0u;
+                    bm |= (in && !full) ? 1u << k : 0u;
+                }
+                pk |= bad ? fm : (sat ? fm << 8 : 0u);
+                // one queue entry per crossed pixel, for all its radii
+                const bool bnd = bm != 0u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bnd);
+                if (bnd) {
+                    BEntry e;
+                    e.dx0 = dx0; e.dy0 = dy0; e.m = m; e.var = var;
+                    e.kf = (int)bm | (bad ? 0x100 : 0) | (sat ? 0x200 : 0);
+                    wq[qn + __popc(bal & lt)] = e;
+                }
+                qn += __popc(bal);
+                if (qn >= 32) {
+                    // one full round of 32 entries; the rest (< 32) moves to the front
+                    flush_queue<NR>(ap, wq, 32, f, v, pk);
+                    if (lane < qn - 32) wq[lane] = wq[lane + 32];
+                    __syncwarp();
+                    qn -= 32;
                 }
             }
-            unsigned bm = 0u;                        // radii whose circle crosses this pixel
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                const float r = ap.r[k], r2 = r * r;
-                // rows that disc k does not reach skip it: ny depends on the row only, so the
-                // branch is the same for the whole warp
-                if (!(ny * ny < r2)) continue;
-                const bool in = live && dmin2 < r2;
-                const bool full = in && dmax2 <= r2;
-                if (full) {
-                    if (bad) fl[k] |= GP_FLAG_BAD;
-                    else {
-                        if (sat) fl[k] |= GP_FLAG_SAT;
-                        df_add(f[k], m);
-                        df_add(v[k], var);
-                    }
-                }
-                if (in && !full) bm |= 1u << k;
-            }
-            // one queue entry per crossed pixel, for all its radii
-            const bool bnd = bm != 0u;
-            const unsigned bal = __ballot_sync(0xffffffffu, bnd);
-            if (bnd) {
-                BEntry e;
-                e.dx0 = dx0; e.dy0 = dy0; e.m = m; e.var = var;
-                e.kf = (int)bm | (bad ? 0x100 : 0) | (sat ? 0x200 : 0);
-                wq[qn + __popc(bal & lt)] = e;
-            }
-            qn += __popc(bal);
-            if (qn >= 32) {
-                // one full round of 32 entries; the rest (< 32) moves to the front
-                flush_queue<NR>(ap, wq, 32, f, v, fl);
-                if (lane < qn - 32) wq[lane] = wq[lane + 32];
-                __syncwarp();
-                qn -= 32;
+                df_add(f[k], fs[k]);
+                df_add(v[k], vs[k]);
             }
         }
     }
-    flush_queue<NR>(ap, wq, qn, f, v, fl);
-    // Warp sums of every radius (all lanes hold them after the butterflies);
-    // lane k stores radius k's raw float-float sums, and k_ap_finish turns
-    // them into the flux, its error and the edge flag one (source, radius)
-    // per thread, so the float64 steps issue once for 32 results.
-    DF my_f = df_zero(), my_v = df_zero();
-    uint32_t my_fl = 0u;
+    flush_queue<NR>(ap, wq, qn, f, v, pk);
+    // Warp sums of every radius, one value per lane group; the lane holding
+    // radius k's flux sum (and the one holding its variance sum) stores the
+    // raw float-float pair, and k_ap_finish turns them into the flux, its
+    // error and the edge flag one (source, radius) per thread, so the
+    // float64 steps issue once for 32 results.
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        const DF fs = df_warp_sum(f[k]);
-        const DF vs = df_warp_sum(v[k]);
-        uint32_t ff = fl[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ff |= __shfl_xor_sync(0xffffffffu, ff, o);
-        if (lane == k) { my_f = fs; my_v = vs; my_fl = ff; }
+    for (int o = 16; o > 0; o >>= 1) pk |= __shfl_xor_sync(0xffffffffu, pk, o);
+    const DF s = df_reduce_scatter<NV>(acc);
+    const int idx = scatter_index<NV>(lane);
+    const bool first = (lane & ((32 / NV) - 1)) == 0;     // one writer per value
+    if (first && idx < NR) {
+        reinterpret_cast<float2*>(flux)[idx] = make_float2(s.hi, s.lo);
+        aflags[idx] = ((pk >> idx) & 1u ? GP_FLAG_BAD : 0u) | ((pk >> (8 + idx)) & 1u ? GP_FLAG_SAT : 0u);
     }
-    if (lane < NR) {
-        reinterpret_cast<float2*>(flux)[lane] = make_float2(my_f.hi, my_f.lo);
-        reinterpret_cast<float2*>(ferr)[lane] = make_float2(my_v.hi, my_v.lo);
-        aflags[lane] = my_fl;
-    }
+    if (first && idx >= NRA && idx < NRA + NR) reinterpret_cast<float2*>(ferr)[idx - NRA] = make_float2(s.hi, s.lo);
 }
 
 // Radius k's results at (cx, cy) from the raw sums in *flux and *ferr: the
@@ -352,7 +382,8 @@ __global__ void __launch_bounds__(MEAS_NT, 3) k_measure(const MeasureArgs* __res
 }
 
 template <bool F32, int NR>
-__global__ void __launch_bounds__(MEAS_NT, 3) k_aperture(Image im, SplineTab sb, SplineTab sr, ApSpec ap,
+__global__ void __launch_bounds__(MEAS_NT, 3) k_aperture(Image im, SplineTab sb, SplineTab sr,
+                                                      const __grid_constant__ ApSpec ap,
                                                       const double* xs, const double* ys, int n, double* flux,
                                                       double* ferr, uint32_t* fl)
 {
