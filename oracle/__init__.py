@@ -298,6 +298,102 @@ def growth(m, var, bad, sat, xs, ys, radii, gain):
     return flux, err, flags
 
 
+# ------------------------------------------- optimal radius (Section 3.4) ---
+# The paper searches the radius of largest S/N only for high-S/N isolated
+# calibrators, fits log10 r_opt = a log10 nu + b to them (nu the detection
+# significance) and gives every other source the radius of the fit.  The
+# selection thresholds and the rounding onto the radius grid are readings
+# [R22]-[R27].
+def significance(F, rms_map, xp, yp):
+    """[R24] nu = F / sigma at each source's peak pixel (0 where sigma <= 0)."""
+    F, rms_map = _f64(F), _f64(rms_map)
+    xp = np.asarray(xp, np.int64)
+    yp = np.asarray(yp, np.int64)
+    s = rms_map[yp, xp]
+    return np.where(s > 0, F[yp, xp] / np.where(s > 0, s, 1.0), 0.0)
+
+
+def snr_argmax(flux, fluxerr):
+    """[R22][R23] S/N = flux / fluxerr per source and radius (0 where
+    fluxerr <= 0) and the index of its largest value (the first on ties)."""
+    flux, fluxerr = _f64(flux), _f64(fluxerr)
+    snr = np.where(fluxerr > 0, flux / np.where(fluxerr > 0, fluxerr, 1.0), 0.0)
+    return np.argmax(snr, axis=1).astype(np.int32), snr
+
+
+def isolated(xs, ys, dmin):
+    """[R25] True where no other source lies closer than dmin (all pairs)."""
+    xs, ys = _f64(xs), _f64(ys)
+    n = xs.size
+    iso = np.ones(n, bool)
+    for i0 in range(0, n, 512):
+        i1 = min(n, i0 + 512)
+        d2 = (xs[i0:i1, None] - xs[None, :]) ** 2 + (ys[i0:i1, None] - ys[None, :]) ** 2
+        close = d2 < dmin * dmin
+        close[np.arange(i1 - i0), np.arange(i0, i1)] = False
+        iso[i0:i1] = ~close.any(axis=1)
+    return iso
+
+
+def calibrators(cat_flags, growth_flags, snr, kopt, iso, nu, snr_min):
+    """[R25] unflagged (catalog and every growth radius), isolated, nu > 0 and
+    S/N >= snr_min at the best radius."""
+    n = len(kopt)
+    best = snr[np.arange(n), kopt]
+    return ((np.asarray(cat_flags) == 0) & np.all(np.asarray(growth_flags) == 0, axis=1) & iso & (nu > 0)
+            & (best >= snr_min))
+
+
+def power_law_fit(nu, r, sel):
+    """[R26] ordinary least squares of log10 r on log10 nu over the selected
+    sources, from the centred sums: a = sum (x - mx)(y - my) / sum (x - mx)^2,
+    b = my - a mx.  Returns (a, b, n); a and b are NaN below 3 sources or
+    when every x is the same."""
+    x = np.log10(_f64(nu)[sel])
+    y = np.log10(_f64(r)[sel])
+    n = x.size
+    if n < 3 or x.max() == x.min():
+        return float("nan"), float("nan"), n
+    mx, my = x.sum() / n, y.sum() / n
+    dx = x - mx
+    a = (dx * (y - my)).sum() / (dx * dx).sum()
+    return a, my - a * mx, n
+
+
+def assign_radius(nu, a, b, radii):
+    """[R27] index of the grid radius nearest to r_fit = 10^(a log10 nu + b)
+    (ties to the larger radius; beyond the grid, its end); the smallest
+    radius where nu <= 0 or the fit failed."""
+    nu = _f64(nu)
+    radii = _f64(radii)
+    k = np.zeros(nu.size, np.int32)
+    if not (np.isfinite(a) and np.isfinite(b)):
+        return k
+    ok = nu > 0
+    rf = 10.0 ** (a * np.log10(np.where(ok, nu, 1.0)) + b)
+    d = np.abs(radii[None, :] - rf[:, None])
+    last = radii.size - 1 - np.argmin(d[:, ::-1], axis=1)    # the larger radius on ties
+    return np.where(ok, last, 0).astype(np.int32)
+
+
+def optimal_radius(m, var, bad, sat, F, rms_map, cat, radii, gain, snr_min, d_iso):
+    """The optimal-radius step: growth curves at the centroids, nu at the
+    peak pixels, the best radius of every source, the calibrators, the fit,
+    and each source's radius (a calibrator keeps its own best radius)."""
+    radii = np.ascontiguousarray(radii, dtype=np.int32)
+    flux, err, gfl = growth(m, var, bad, sat, cat["x"], cat["y"], radii, gain)
+    nu = significance(F, rms_map, cat["xpeak"], cat["ypeak"])
+    kopt, snr = snr_argmax(flux, err)
+    iso = isolated(cat["x"], cat["y"], d_iso)
+    cal = calibrators(cat["flags"], gfl, snr, kopt, iso, nu, snr_min)
+    a, b, ncal = power_law_fit(nu, radii[kopt], cal)
+    kas = assign_radius(nu, a, b, radii)
+    kfin = np.where(cal, kopt, kas).astype(np.int32)
+    i = np.arange(len(kfin))
+    return dict(flux=flux, fluxerr=err, flags=gfl, nu=nu, snr=snr, kopt=kopt, iso=iso, calib=cal, a=a, b=b,
+                ncal=ncal, kassign=kas, kfinal=kfin, flux_opt=flux[i, kfin], fluxerr_opt=err[i, kfin])
+
+
 # ------------------------------------------------------------ whole path ---
 def extract(image, mesh, kernel, thresh, minarea, radii, gain, mask=None, saturation=0.0,
             fsize=3, clip_k=3.0, clip_maxiter=10):

@@ -622,3 +622,104 @@ def test_growth_of_a_delta_and_against_exact_overlap_sums():
         border = img[30 - r:30 + r + 1, 30 - r:30 + r + 1][ring].sum()
         assert abs(ft[0, k] - fx[0, k]) <= border
     assert np.all(np.diff(ft[0]) > 0)               # a non-negative image: the curve grows
+
+
+# ------------------------------------------- optimal radius (Section 3.4) ---
+def test_snr_argmax_finds_the_background_limited_gaussian_optimum():
+    """For a Gaussian star of width s on flat noise, S/N(r) is proportional
+    to (1 - exp(-r^2 / 2 s^2)) / r, whose maximum sits where e^x = 1 + 2x with
+    x = r^2 / 2 s^2 (the derivative set to zero).  The root is found here by
+    bracketing, independently of the oracle."""
+    from scipy.optimize import brentq
+    x = brentq(lambda t: np.exp(t) - 1.0 - 2.0 * t, 0.5, 5.0)
+    for s in (1.3, 2.0, 3.4):
+        r = np.arange(0.5, 12.0, 0.001)
+        flux = 1e4 * (1.0 - np.exp(-r * r / (2 * s * s)))
+        err = 7.0 * np.sqrt(np.pi) * r
+        k, snr = oracle.snr_argmax(flux[None, :], err[None, :])
+        assert abs(r[k[0]] - s * np.sqrt(2 * x)) <= 0.0011
+        assert snr.shape == (1, r.size)
+
+
+def test_snr_argmax_takes_the_first_of_equal_values_and_zero_error_as_no_signal():
+    flux = np.array([[1.0, 2.0, 2.0, 1.0], [5.0, 5.0, 5.0, 5.0], [3.0, 1.0, 2.0, 4.0]])
+    err = np.array([[1.0, 1.0, 1.0, 1.0], [0.0, 1.0, 0.5, 0.5], [1.0, 1.0, 1.0, 0.0]])
+    k, snr = oracle.snr_argmax(flux, err)
+    assert k.tolist() == [1, 2, 0]
+    assert snr[1, 0] == 0.0 and snr[2, 3] == 0.0
+
+
+def test_isolated_excludes_pairs_closer_than_the_distance():
+    xs = np.array([0.0, 3.0, 20.0, 40.0, 50.0])
+    ys = np.array([0.0, 4.0, 0.0, 0.0, 0.0])          # (0,0)-(3,4) at 5; (40,0)-(50,0) at 10 exactly
+    assert oracle.isolated(xs, ys, 5.0).tolist() == [True, True, True, True, True]
+    assert oracle.isolated(xs, ys, 5.0001).tolist() == [False, False, True, True, True]
+    assert oracle.isolated(xs, ys, 10.5).tolist() == [False, False, True, False, False]
+
+
+def test_power_law_fit_recovers_exact_laws_and_matches_polyfit():
+    rng = np.random.default_rng(3)
+    nu = 10 ** rng.uniform(0.5, 3.0, 200)
+    a0, b0 = 0.21, 0.47
+    r = 10 ** (a0 * np.log10(nu) + b0)
+    sel = np.ones(nu.size, bool)
+    a, b, n = oracle.power_law_fit(nu, r, sel)
+    assert n == 200 and abs(a - a0) < 1e-12 and abs(b - b0) < 1e-12
+    rn = r * 10 ** rng.normal(0, 0.05, nu.size)
+    sel[::3] = False
+    a, b, n = oracle.power_law_fit(nu, rn, sel)
+    pa, pb = np.polyfit(np.log10(nu[sel]), np.log10(rn[sel]), 1)
+    assert n == sel.sum() and abs(a - pa) < 1e-10 and abs(b - pb) < 1e-10
+    a, b, n = oracle.power_law_fit(nu, rn, np.arange(nu.size) < 2)
+    assert n == 2 and np.isnan(a) and np.isnan(b)
+    a, b, n = oracle.power_law_fit(np.full(5, 7.0), np.arange(1.0, 6.0), np.ones(5, bool))
+    assert np.isnan(a)                                  # no spread in nu
+
+
+def test_assign_radius_rounds_onto_the_grid():
+    radii = np.arange(3, 16, dtype=np.int32)
+    # b alone sets r_fit when a = 0: r_fit = 10^b
+    cases = [(4.2, 1), (4.5, 2), (4.49, 1), (100.0, 12), (0.5, 0), (15.0, 12), (2.9, 0)]
+    for rfit, k in cases:
+        got = oracle.assign_radius(np.array([10.0]), 0.0, np.log10(rfit), radii)
+        assert got[0] == k, (rfit, got)
+    assert oracle.assign_radius(np.array([0.0, -3.0]), 0.5, 0.1, radii).tolist() == [0, 0]
+    assert oracle.assign_radius(np.array([10.0]), float("nan"), 0.1, radii).tolist() == [0]
+    # a non-uniform grid: the nearest radius
+    g = np.array([2, 5, 11], np.int32)
+    for rfit, k in ((3.6, 1), (3.4, 0), (8.2, 2), (7.8, 1)):
+        assert oracle.assign_radius(np.array([10.0]), 0.0, np.log10(rfit), g).tolist() == [k]
+    # an exact tie (10^1 = 10 between 5 and 15) goes to the larger radius
+    assert oracle.assign_radius(np.array([10.0]), 0.0, 1.0, np.array([5, 15], np.int32)).tolist() == [1]
+
+
+def test_calibrators_need_every_condition():
+    n = 6
+    snr = np.array([[10, 60, 40]] * n, float)
+    kopt = np.full(n, 1, np.int32)
+    cat_flags = np.zeros(n, np.uint32)
+    gfl = np.zeros((n, 3), np.uint32)
+    iso = np.ones(n, bool)
+    nu = np.full(n, 30.0)
+    cat_flags[1] = 1
+    gfl[2, 2] = 4
+    iso[3] = False
+    nu[4] = -1.0
+    snr[5, 1] = 49.0
+    cal = oracle.calibrators(cat_flags, gfl, snr, kopt, iso, nu, 50.0)
+    assert cal.tolist() == [True, False, False, False, False, False]
+
+
+def test_significance_is_the_filtered_value_over_sigma_at_the_peak():
+    m = np.zeros((40, 50))
+    m[20, 30] = 500.0
+    m[5, 7] = -80.0
+    K = np.outer([1, 2, 3, 2, 1], [1, 4, 6, 4, 1]).astype(float)
+    K /= K.sum()
+    F = oracle.matched_filter(m, K)
+    rms = np.full(m.shape, 4.0)
+    rms[5, 7] = 0.0
+    nu = oracle.significance(F, rms, [30, 7, 31], [20, 5, 20])
+    assert nu[0] == pytest.approx(500.0 * K[2, 2] / 4.0, rel=1e-15)
+    assert nu[1] == 0.0                                      # sigma 0 gives no significance
+    assert nu[2] == pytest.approx(500.0 * K[2, 1] / 4.0, rel=1e-15)   # F(p) takes m(p + u) with tap u
