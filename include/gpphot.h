@@ -223,6 +223,54 @@ gp_status gp_growth(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
                     int32_t nr, float gain, double* flux, double* fluxerr, uint32_t* flags,
                     gp_stream stream);
 
+/* Section 3.4, optimal aperture radius.  The paper searches the radius of
+ * largest S/N only on high-S/N isolated calibrators, fits
+ * log10 r_opt = a log10 nu + b to them, with nu the detection significance,
+ * and gives every other source the radius of the fit.  Here, for the
+ * catalog rows min(*cat->n, cat->capacity) (device columns x, y, xpeak,
+ * ypeak and flags as gp_extract leaves them):
+ *  - the growth curves at the centroids, as gp_growth;
+ *  - nu = F / sigma at the peak pixel, F the matched filter of gp_detect
+ *    (dp's kernel; dp->thresh and dp->minarea are not used);
+ *  - kopt, the radius index of largest S/N = flux / fluxerr (the first of
+ *    equal values; S/N 0 where fluxerr <= 0);
+ *  - calibrators: catalog flags 0, no growth flag at any radius, nu > 0,
+ *    S/N at kopt >= snr_min, and no other row's centroid closer than d_iso;
+ *  - the least-squares fit of log10 r[kopt] on log10 nu over the
+ *    calibrators (fit = a, b, their number, status: 0 fitted, 1 fewer than
+ *    three or all nu equal);
+ *  - kfinal: a calibrator's kopt; for the others the grid radius nearest to
+ *    10^(a log10 nu + b) (ties to the larger), or index 0 when nu <= 0 or
+ *    the fit failed; flux_opt and fluxerr_opt are the growth curve there.
+ * Every output is device memory, capacity rows (capacity*nr for the curves,
+ * source-major; 4 doubles for fit), caller-owned.  GP_ERR_INVALID_ARG on a
+ * null pointer, radii outside gp_growth's rules, snr_min not finite or
+ * d_iso < 0; nothing is launched then. */
+typedef struct {
+    const int32_t* radii;  /* HOST pointer: the growth-curve radii */
+    int32_t nr;
+    float gain;            /* Poisson term of the errors (<= 0: none) */
+    float snr_min;         /* calibrators: least S/N at their best radius */
+    float d_iso;           /* calibrators: no other centroid closer (px) */
+} gp_ropt_params;
+
+typedef struct {
+    double* flux;          /* capacity*nr growth curves */
+    double* fluxerr;
+    uint32_t* flags;
+    float* nu;             /* capacity */
+    int32_t* kopt;         /* capacity */
+    uint8_t* calib;        /* capacity: 1 for a calibrator */
+    int32_t* kfinal;       /* capacity */
+    double* flux_opt;      /* capacity */
+    double* fluxerr_opt;   /* capacity */
+    double* fit;           /* 4 */
+} gp_ropt_out;
+
+gp_status gp_optimal_radius(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
+                            const gp_det_params* dp, const gp_catalog* cat,
+                            const gp_ropt_params* p, gp_ropt_out* out, gp_stream stream);
+
 /* The three stages in one call; apertures at each segment's centroid, rows
  * aligned with the catalog (capacity*nr). */
 gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp,

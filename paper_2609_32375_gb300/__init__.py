@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_ctx_set_walk_limit", "gp_workspace_bytes",
-           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_extract", "gp_label_mask", "gp_background_static",
+           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_optimal_radius", "gp_extract", "gp_label_mask", "gp_background_static",
            "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
            "gp_cnn_denorm", "gp_extract_batch", "gp_server_create", "gp_server_submit", "gp_server_wait",
@@ -89,6 +89,16 @@ class GpCnnWeights(C.Structure):
 
 class GpApParams(C.Structure):
     _fields_ = [("radii", C.POINTER(C.c_float)), ("nr", C.c_int32), ("gain", C.c_float)]
+
+
+class GpRoptParams(C.Structure):
+    _fields_ = [("radii", C.POINTER(C.c_int32)), ("nr", C.c_int32), ("gain", C.c_float), ("snr_min", C.c_float),
+                ("d_iso", C.c_float)]
+
+
+class GpRoptOut(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("flux", "fluxerr", "flags", "nu", "kopt", "calib", "kfinal", "flux_opt",
+                                          "fluxerr_opt", "fit")]
 
 
 GP_MAX_BATCH = 64
@@ -176,6 +186,9 @@ def load_library():
         L.gp_growth.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), vp, vp, i32, C.POINTER(C.c_int32), i32,
                                 C.c_float, vp, vp, vp, vp]
         L.gp_growth.restype = st
+        L.gp_optimal_radius.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), C.POINTER(GpDetParams),
+                                        C.POINTER(GpCatalog), C.POINTER(GpRoptParams), C.POINTER(GpRoptOut), vp]
+        L.gp_optimal_radius.restype = st
         L.gp_extract.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
                                  C.POINTER(GpApParams), C.POINTER(GpBkg), vp, C.POINTER(GpCatalog), vp, vp, vp, vp]
         L.gp_extract.restype = st
@@ -403,6 +416,36 @@ class Context:
                                         r.ctypes.data_as(C.POINTER(C.c_int32)), r.size, float(gain),
                                         flux.data_ptr(), ferr.data_ptr(), fl.data_ptr(), _stream_handle(stream)))
         return flux[:n], ferr[:n], fl[:n]
+
+    def gp_optimal_radius(self, img, bkg, kernel, catalog, radii, gain=0.0, snr_min=50.0, d_iso=30.0, mask=None,
+                          saturation=0.0, stream=None):
+        """The optimal-radius step over a catalog's rows (device columns as
+        gp_extract leaves them, with its count "n")."""
+        import torch
+        gi = make_image(img, mask, saturation)
+        k, kp = _taps(kernel)
+        dp = GpDetParams(kp, k.shape[1], k.shape[0], 1.0, 1, None, None)
+        cap = int(catalog["x"].numel())
+        cat = GpCatalog(cap, catalog["n"].data_ptr(), *[catalog[n].data_ptr() for n, _ in CATALOG_COLUMNS])
+        r = np.ascontiguousarray(np.asarray(radii, dtype=np.int32).reshape(-1))
+        dev = img.device
+        nr = max(r.size, 1)
+        out = {"flux": torch.empty((max(cap, 1), nr), dtype=torch.float64, device=dev),
+               "fluxerr": torch.empty((max(cap, 1), nr), dtype=torch.float64, device=dev),
+               "flags": torch.empty((max(cap, 1), nr), dtype=torch.int32, device=dev),
+               "nu": torch.empty(max(cap, 1), dtype=torch.float32, device=dev),
+               "kopt": torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+               "calib": torch.empty(max(cap, 1), dtype=torch.uint8, device=dev),
+               "kfinal": torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+               "flux_opt": torch.empty(max(cap, 1), dtype=torch.float64, device=dev),
+               "fluxerr_opt": torch.empty(max(cap, 1), dtype=torch.float64, device=dev),
+               "fit": torch.empty(4, dtype=torch.float64, device=dev)}
+        o = GpRoptOut(*[out[n].data_ptr() for n, _ in GpRoptOut._fields_])
+        p = GpRoptParams(r.ctypes.data_as(C.POINTER(C.c_int32)), r.size, float(gain), float(snr_min), float(d_iso))
+        b = self._bkg_struct(bkg)
+        _check(load_library().gp_optimal_radius(self._h, C.byref(gi), C.byref(b), C.byref(dp), C.byref(cat),
+                                                C.byref(p), C.byref(o), _stream_handle(stream)))
+        return out
 
     def gp_extract(self, img, mesh, kernel, thresh, minarea, radii, gain, capacity, mask=None, saturation=0.0,
                    filter_size=3, clip_k=3.0, clip_maxiter=10, maps=False, mask_out=False, count_near=False,

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -33,6 +34,8 @@ struct gp_ctx {
     int launches;          // kernels launched by the current / last call
     int walk_limit;        // union-find walk bound of the tile merge (0: the library default)
     ArgStage stage;        // pinned staging of batched calls' argument records
+    SideStream side;       // the crowded tiles' labelling beside the common form
+    int side_made;
 };
 
 namespace {
@@ -230,7 +233,7 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
                                      p->nnear, nullptr, w.D, w.T, w.P, w.C, ctx->dstatus);
     GP_CUDA(launch_stream_any(A, nullptr, 1, detect_grid(W, H, false), st));
     mark(ctx, 3, st);
-    GP_CUDA(launch_label_any(A, nullptr, 1, st));
+    GP_CUDA(launch_label_any(A, nullptr, 1, st, ctx->side_made ? &ctx->side : nullptr));
     mark(ctx, 4, st);
     GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, W, H, p->minarea, ctx->walk_limit, ctx->dstatus, st));
     mark(ctx, 5, st);
@@ -238,7 +241,7 @@ gp_status run_detect(gp_ctx* ctx, Carver& cv, const gp_image* img, const SplineT
     mark(ctx, 6, st);
     GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, radii, nr, gain, flux, fluxerr, apflags, st));
     mark(ctx, 7, st);
-    ctx->launches += 3 + 4 + 4 + 1 + (nr > 0 ? 1 : 0);
+    ctx->launches += 1 + label_launches(false) + 4 + 4 + 1 + (nr > 0 ? 1 : 0);
     return GP_OK;
 }
 
@@ -250,6 +253,7 @@ Exec ctx_exec(gp_ctx* ctx, cudaStream_t st)
     ex.cv = Carver{ctx->base, ctx->arena_bytes - STATUS_BYTES};
     ex.st = st;
     ex.stage = &ctx->stage;
+    ex.side = ctx->side_made ? &ctx->side : nullptr;
     ex.mark = ctx_mark;
     ex.mark_ud = ctx;
     return ex;
@@ -374,6 +378,7 @@ gp_status gp_ctx_create(int device, size_t workspace_bytes, gp_ctx** out)
     c->slot = 0;
     c->launches = 0;
     c->walk_limit = 0;
+    c->side_made = 0;
     c->arena_bytes = workspace_bytes + STATUS_BYTES;
     cudaError_t e = cudaMalloc(&c->arena, c->arena_bytes);
     if (e != cudaSuccess) {
@@ -389,6 +394,15 @@ gp_status gp_ctx_create(int device, size_t workspace_bytes, gp_ctx** out)
         delete c;
         return cuda_fail(e, "context initialisation");
     }
+    // the side stream; without it the labelling forms run one after the other
+    if (cudaStreamCreateWithFlags(&c->side.st, cudaStreamNonBlocking) == cudaSuccess) {
+        if (cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming) == cudaSuccess) {
+            if (cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming) == cudaSuccess) c->side_made = 1;
+            else cudaEventDestroy(c->side.fork);
+        }
+        if (!c->side_made) cudaStreamDestroy(c->side.st);
+    }
+    cudaGetLastError();
     *out = c;
     return GP_OK;
 }
@@ -401,6 +415,12 @@ void gp_ctx_destroy(gp_ctx* ctx)
         for (int i = 0; i < RING; ++i)
             for (int k = 0; k < NMARK; ++k) cudaEventDestroy(ctx->ev[i][k]);
     ctx->stage.release();
+    if (ctx->side_made) {
+        cudaStreamSynchronize(ctx->side.st);
+        cudaEventDestroy(ctx->side.fork);
+        cudaEventDestroy(ctx->side.join);
+        cudaStreamDestroy(ctx->side.st);
+    }
     cudaFree(ctx->arena);
     delete ctx;
 }
@@ -567,8 +587,66 @@ gp_status gp_growth(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const d
     if (s != GP_OK) return s;
     mark_to(ctx, 2, GP_NSTAGES - 1, st);
     if (n > 0) {
-        GP_CUDA(launch_growth(to_image(img), sb, sr, x, y, n, radii, nr, gain, flux, fluxerr, flags, st));
+        GP_CUDA(launch_growth(to_image(img), sb, sr, x, y, n, nullptr, radii, nr, gain, flux, fluxerr, flags, st));
         ctx->launches += 1;
+    }
+    mark(ctx, GP_NSTAGES, st);
+    return GP_OK;
+}
+
+gp_status gp_optimal_radius(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* dp,
+                            const gp_catalog* cat, const gp_ropt_params* p, gp_ropt_out* out, gp_stream stream)
+{
+    gp_status s;
+    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg(img, bkg, true)) != GP_OK) return s;
+    if ((s = check_det(dp, taps)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if (!p || !out) return fail(GP_ERR_INVALID_ARG, "null parameters or outputs");
+    if (!p->radii || p->nr < 1 || p->nr > GP_GROWTH_MAX_NR)
+        return fail(GP_ERR_INVALID_ARG, "growth radii: need 1..%d of them", GP_GROWTH_MAX_NR);
+    for (int k = 0; k < p->nr; ++k) {
+        if (p->radii[k] < 0 || p->radii[k] > GP_GROWTH_MAX_R)
+            return fail(GP_ERR_INVALID_ARG, "growth radius %d outside 0..%d", p->radii[k], GP_GROWTH_MAX_R);
+        if (k > 0 && p->radii[k] <= p->radii[k - 1]) return fail(GP_ERR_INVALID_ARG, "growth radii not increasing");
+    }
+    if (!std::isfinite(p->snr_min) || !std::isfinite(p->d_iso) || p->d_iso < 0.f)
+        return fail(GP_ERR_INVALID_ARG, "snr_min must be finite and d_iso >= 0");
+    if (!out->fit || (cat->capacity > 0 && (!out->flux || !out->fluxerr || !out->flags || !out->nu || !out->kopt ||
+                                             !out->calib || !out->kfinal || !out->flux_opt || !out->fluxerr_opt)))
+        return fail(GP_ERR_INVALID_ARG, "null optimal-radius output");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    mark(ctx, 1, st);
+    s = run_spline(cv, bkg, img->width, img->height, &sb, &sr, &ctx->launches, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    double cs;
+    int ncx, ncy;
+    iso_grid(img->width, img->height, p->d_iso, &cs, &ncx, &ncy);
+    RoptWork w;
+    w.count = cv.take<int>((size_t)ncx * ncy);
+    w.start = cv.take<int>((size_t)ncx * ncy);
+    w.fill = cv.take<int>((size_t)ncx * ncy);
+    w.items = cv.take<int>(cat->capacity > 0 ? cat->capacity : 1);
+    if (!cv.ok()) return oom(cv);
+    mark_to(ctx, 2, GP_NSTAGES - 1, st);
+    if (cat->capacity > 0) {
+        const Image im = to_image(img);
+        GP_CUDA(launch_growth(im, sb, sr, cat->x, cat->y, cat->capacity, cat->n, p->radii, p->nr, p->gain, out->flux,
+                              out->fluxerr, out->flags, st));
+        GP_CUDA(launch_ropt(im, sb, sr, taps, dp->kw, dp->kh, *cat, out->flux, out->fluxerr, out->flags, p->radii,
+                            p->nr, p->snr_min, p->d_iso, w, out->nu, out->kopt, out->calib, out->kfinal, out->flux_opt,
+                            out->fluxerr_opt, out->fit, st));
+        ctx->launches += 1 + 7;
+    } else {
+        const double none[4] = {NAN, NAN, 0.0, 1.0};
+        GP_CUDA(cudaMemcpyAsync(out->fit, none, sizeof none, cudaMemcpyHostToDevice, st));
+        GP_CUDA(cudaStreamSynchronize(st));
     }
     mark(ctx, GP_NSTAGES, st);
     return GP_OK;
@@ -606,7 +684,7 @@ gp_status gp_label_mask(gp_ctx* ctx, const uint8_t* mask, int32_t width, int32_t
                                      w.T, w.P, w.C, ctx->dstatus);
     GP_CUDA(launch_stream_any(A, nullptr, 1, detect_grid(width, height, true), st));
     mark(ctx, 3, st);
-    GP_CUDA(launch_label_any(A, nullptr, 1, st));
+    GP_CUDA(launch_label_any(A, nullptr, 1, st, nullptr));
     mark(ctx, 4, st);
     GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, width, height, minarea, ctx->walk_limit, ctx->dstatus, st));
     mark(ctx, 5, st);

@@ -53,6 +53,10 @@ constexpr int MAX_NR = 8;        // most aperture radii per call
 // side over ST_RC rows; the packed foreground mask holds, per frame row and
 // strip, four 32-bit words, word c bit l = column 4 l + c of the strip
 constexpr int ST_CPL = 4;
+// most foreground pixels of a tile that the labelling kernel's common form
+// takes; a census of the listed tiles sends the ones above it to the
+// crowded form
+constexpr int LT_FG = 512;
 constexpr int ST_STRIP = 32 * ST_CPL;
 
 // default bound on the steps of a global union-find walk (a cycle would be a
@@ -319,8 +323,10 @@ struct DetMask {
     uint4* bits;          // [H][ceil(W / ST_STRIP)]
     int* tl_list;         // [ntiles] appended tile indices
     int* tl_count;        // scalar, cleared per call
-    int* dl_list;         // [ntiles] tiles too crowded for the labelling kernel's common form
+    int* dl_list;         // [ntiles] tiles with more than LT_FG foreground pixels (the tile census lists them)
     int* dl_count;        // scalar, cleared per call
+    int* rl_list;         // [ntiles] tiles the labelling kernel's common form defers (more than its runs)
+    int* rl_count;        // scalar, cleared per call
 };
 
 struct Image {
@@ -414,8 +420,10 @@ struct DetectArgs {
     int nstrip;               // ceil(W / ST_STRIP)
     int* tl_list;             // detection tiles holding foreground (appended)
     int* tl_count;
-    int* dl_list;             // of those, the ones deferred to the big labelling form
+    int* dl_list;             // of those, the ones with more than LT_FG foreground pixels (crowded form)
     int* dl_count;
+    int* rl_list;             // of the others, the ones the common form defers (crowded form, after it)
+    int* rl_count;
     Tiles T;
     Pieces P;
     Comps C;

@@ -43,10 +43,23 @@ cudaError_t launch_aperture(const Image& im, const SplineTab& sb, const SplineTa
                             const double* ys, int n, const float* radii, int nr, float gain, double* flux,
                             double* ferr, uint32_t* fl, cudaStream_t st);
 
-// growth curves (k_growth.cu); radii strictly increasing, nr <= GP_GROWTH_MAX_NR
+// growth curves (k_growth.cu); radii strictly increasing, nr <= GP_GROWTH_MAX_NR;
+// n sources, or min(n, *n_dev) when n_dev (a device count) is given
 cudaError_t launch_growth(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,
-                          const double* ys, int n, const int* radii, int nr, float gain, double* flux,
-                          double* ferr, uint32_t* flags, cudaStream_t st);
+                          const double* ys, int n, const int* n_dev, const int* radii, int nr, float gain,
+                          double* flux, double* ferr, uint32_t* flags, cudaStream_t st);
+
+// optimal aperture radius (k_ropt.cu): the growth curves of the catalog rows
+// are given; scratch of the isolation grid from iso_grid()
+struct RoptWork {
+    int *count, *start, *fill, *items;
+};
+void iso_grid(int W, int H, float d_iso, double* cs, int* ncx, int* ncy);
+cudaError_t launch_ropt(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw, int kh,
+                        const gp_catalog& cat, const double* flux, const double* ferr, const uint32_t* gflags,
+                        const int* radii, int nr, float snr_min, float d_iso, const RoptWork& w, float* nu,
+                        int* kopt, uint8_t* calib, int* kfinal, double* flux_opt, double* ferr_opt, double* fit,
+                        cudaStream_t st);
 
 // Batch-capable forms.  Each takes one frame's argument record (`one`, used
 // alone when batch == nullptr) or a device array of nframes records, one per
@@ -64,9 +77,19 @@ DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr
                        float thresh, int minarea, uint32_t* seg, uint8_t* mask_out, int* nnear,
                        const uint8_t* in_mask, const DetMask& dm, const Tiles& T, const Pieces& P, const Comps& C,
                        int* status);
-// the detection stage is two launches: the streaming threshold pass (or the
-// packing of a given mask), then the labelling of the listed tiles
-cudaError_t launch_label_any(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st);
+// A second stream for work that runs beside the main stream within one
+// call, with the events that fork it from and join it back to the main one.
+struct SideStream {
+    cudaStream_t st;
+    cudaEvent_t fork, join;
+};
+
+// the detection stage: the streaming threshold pass (or the packing of a
+// given mask), then the labelling of the listed tiles: the crowded tiles on
+// `side` (null: on `st`) beside the common form, then the deferred ones
+cudaError_t launch_label_any(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st,
+                             const SideStream* side);
+int label_launches(bool given_mask);
 ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,
                          int H, int minarea, int walk_limit, int* status);
 cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch, int nframes, int maxtiles,

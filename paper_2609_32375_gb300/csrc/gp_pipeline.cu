@@ -79,6 +79,8 @@ void carve_det(Carver& cv, int W, int H, int capacity, DetWork& w, int** zero)
     w.D.tl_count = w.zero + 16;
     w.D.dl_list = cv.take<int>(ntiles);
     w.D.dl_count = w.zero + 17;
+    w.D.rl_list = cv.take<int>(ntiles);
+    w.D.rl_count = w.zero + 18;
     w.P.count = w.zero + 0;
     w.P.cap = piece_cap_for(npix);
     w.P.root = cv.take<uint32_t>(w.P.cap);
@@ -407,7 +409,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
         if (F[f].nnear) PL_CUDA(cudaMemsetAsync(F[f].nnear, 0, sizeof(int), ex.st));
     PL_CUDA(launch_stream_any(det[0], d_det, n, maxgrid, ex.st));
     ex.at(3);
-    PL_CUDA(launch_label_any(det[0], d_det, n, ex.st));
+    PL_CUDA(launch_label_any(det[0], d_det, n, ex.st, ex.side));
     ex.at(4);
     PL_CUDA(launch_resolve_any(res[0], d_res, n, maxtiles, ex.st));
     ex.at(5);
@@ -415,7 +417,7 @@ gp_status run_frames(Exec& ex, int n, FrameIO* F, const Params& P, bool detect)
     ex.at(6);
     PL_CUDA(launch_measure_any(meas[0], d_meas, n, ex.st));
     ex.at(7);
-    ex.launches += 3 + 4 + 4 + 1 + (P.nr > 0 ? 1 : 0);
+    ex.launches += 1 + label_launches(false) + 4 + 4 + 1 + (P.nr > 0 ? 1 : 0);
     return GP_OK;
 }
 

@@ -75,6 +75,7 @@ struct Exec {
     Carver cv;
     cudaStream_t st;
     ArgStage* stage;                 // required when a call has more than one frame
+    const SideStream* side = nullptr;   // for work beside `st` within the call (null: all on `st`)
     int launches = 0;                // kernels launched by the call
     // stage boundary k (0..GP_NSTAGES) reached on the stream
     void (*mark)(void* ud, int k, cudaStream_t st) = nullptr;

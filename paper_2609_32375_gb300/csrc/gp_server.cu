@@ -172,6 +172,7 @@ struct Unit {
 
 struct Slot {
     cudaStream_t st = nullptr;
+    SideStream side{nullptr, nullptr, nullptr};   // the crowded tiles' labelling beside st
     ArgStage stage;
     Unit* unit = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // unit start, inputs in, pipeline done, results out
@@ -391,6 +392,7 @@ gp_status gp_server::launch(Unit* u)
     Exec ex;
     ex.cv = Carver{dws, ws_bytes};
     ex.st = st;
+    ex.side = &sl.side;
     ex.stage = &sl.stage;
     gp_status s = run_extract(ex, n, F.data(), P);
     if (s == GP_ERR_OOM)
@@ -596,6 +598,9 @@ gp_status gp_server_create(const gp_server_config* cfg, gp_server** out)
             sl.stage.release();
             for (cudaEvent_t& x : sl.ev)
                 if (x) cudaEventDestroy(x);
+            if (sl.side.fork) cudaEventDestroy(sl.side.fork);
+            if (sl.side.join) cudaEventDestroy(sl.side.join);
+            if (sl.side.st) cudaStreamDestroy(sl.side.st);
             if (sl.st) cudaStreamDestroy(sl.st);
         }
         if (sv->dpool) cudaFree(sv->dpool);
@@ -613,6 +618,9 @@ gp_status gp_server_create(const gp_server_config* cfg, gp_server** out)
     for (Slot& sl : sv->slots) {
         e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&sl.ev[k]);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.side.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.side.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.side.join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = sl.stage.init((size_t)512 << 10);
         if (e != cudaSuccess) return undo(GP_ERR_CUDA, "slot streams", e);
     }
@@ -798,9 +806,13 @@ void gp_server_destroy(gp_server* s)
     for (Unit* u : units) delete u;
     for (Slot& sl : s->slots) {
         if (sl.st) cudaStreamSynchronize(sl.st);
+        if (sl.side.st) cudaStreamSynchronize(sl.side.st);
         sl.stage.release();
         for (cudaEvent_t& x : sl.ev)
             if (x) cudaEventDestroy(x);
+        if (sl.side.fork) cudaEventDestroy(sl.side.fork);
+        if (sl.side.join) cudaEventDestroy(sl.side.join);
+        if (sl.side.st) cudaStreamDestroy(sl.side.st);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
     cudaFree(s->dpool);

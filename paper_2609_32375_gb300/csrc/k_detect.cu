@@ -258,7 +258,7 @@ template <bool BIG>
 struct LabelCfg {
     static constexpr int NW = BIG ? 2 : 4;
     static constexpr int RUNS = BIG ? MAXRUN : 256;
-    static constexpr int FG = BIG ? TX * TY : 512;
+    static constexpr int FG = BIG ? TX * TY : LT_FG;
 };
 
 // a kept segment of at most this many pixels is summed by one lane (32 such
@@ -379,7 +379,8 @@ __device__ __forceinline__ bool pix_sat(const DetectArgs& A, bool async, uint32_
 
 template <bool LABEL_ONLY, bool BATCH, bool BIG>
 __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 5) k_label_tiles(const DetectArgs* __restrict__ batch,
-                                                                        const __grid_constant__ DetectArgs one)
+                                                                        const __grid_constant__ DetectArgs one,
+                                                                        int late)
 {
     using Cfg = LabelCfg<BIG>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -387,8 +388,10 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 5) k_label_t
     LabelSmem<BIG>& S = reinterpret_cast<LabelSmem<BIG>*>(smem_raw)[warp];
     const DetectArgs& A = det_frame<BATCH>(batch, one);
     const int W = A.im.W, H = A.im.H, ntx = A.T.ntx;
-    const int* list = BIG ? A.dl_list : A.tl_list;
-    const int ntl = *(BIG ? A.dl_count : A.tl_count);
+    // the crowded form takes the tiles the threshold pass listed, or (late)
+    // the ones the common form deferred
+    const int* list = BIG ? (late ? A.rl_list : A.dl_list) : A.tl_list;
+    const int ntl = *(BIG ? (late ? A.rl_count : A.dl_count) : A.tl_count);
     const int nwarps = gridDim.x * Cfg::NW;
     const uint32_t FULL = 0xffffffffu;
     const bool sat_on = A.im.sat > 0.f;
@@ -432,7 +435,9 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 5) k_label_t
         const int tot = __shfl_sync(FULL, incl, 31);
         const int NR = tot & 0xffff, NF = tot >> 16;
         if (!BIG && (NR > Cfg::RUNS || (!LABEL_ONLY && NF > Cfg::FG))) {
-            if (lane == 0) A.dl_list[atomicAdd(A.dl_count, 1)] = tile;   // crowded: the big form takes it
+            // crowded: the threshold pass listed it for the crowded form when
+            // it has too many foreground pixels; too many runs alone defers it
+            if (lane == 0 && (LABEL_ONLY || NF <= Cfg::FG)) A.rl_list[atomicAdd(A.rl_count, 1)] = tile;
             wcur = mask_row(tile_n);
             tile = tile_n;
             continue;
@@ -1127,6 +1132,7 @@ DetectArgs detect_args(const Image& im, const SplineTab& sb, const SplineTab& sr
     A.bits = dm.bits; A.nstrip = (im.W + ST_STRIP - 1) / ST_STRIP;
     A.tl_list = dm.tl_list; A.tl_count = dm.tl_count;
     A.dl_list = dm.dl_list; A.dl_count = dm.dl_count;
+    A.rl_list = dm.rl_list; A.rl_count = dm.rl_count;
     A.T = T; A.P = P; A.C = C; A.status = status;
     return A;
 }
@@ -1142,39 +1148,84 @@ static int stride_grid(int per_frame, int nframes)
 // four warps per SM, the big form (crowded tiles) at four CTAs of two warps
 constexpr int LT_CTAS = 152 * 5;
 constexpr int LT_BIG_CTAS = 152 * 4;
+constexpr int LT_LATE_CTAS = 152;         // the deferred tiles: few or none
 
 int detect_grid(int W, int H, bool given_mask) { return given_mask ? pack_warps(W, H) : stream_ctas(W, H); }
 
+// The crowded tiles: one warp per listed tile counts its foreground pixels
+// from the packed mask (lane = tile row) and lists the tile for the crowded
+// form when the common form cannot hold them.
+template <bool BATCH>
+__global__ void __launch_bounds__(256) k_tile_census(const DetectArgs* __restrict__ batch,
+                                                     const __grid_constant__ DetectArgs one)
+{
+    const DetectArgs& A = det_frame<BATCH>(batch, one);
+    const int lane = threadIdx.x & 31;
+    const int ntl = *A.tl_count;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < ntl; it += nw) {
+        const int tile = A.tl_list[it];
+        const int ty = tile / A.T.ntx, tx = tile - ty * A.T.ntx;
+        const int y = ty * TY + lane;
+        int c = 0;
+        if (y < A.im.H) {
+            const uint4 w = A.bits[(int64_t)y * A.nstrip + (tx >> 1)];
+            const uint32_t m = (tx & 1) ? 0xffff0000u : 0x0000ffffu;
+            c = __popc(w.x & m) + __popc(w.y & m) + __popc(w.z & m) + __popc(w.w & m);
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c > LT_FG) A.dl_list[atomicAdd(A.dl_count, 1)] = tile;
+    }
+}
+
 template <bool LO, bool BATCH, bool BIG>
-static void launch_label(const DetectArgs& one, const DetectArgs* batch, dim3 g, cudaStream_t st)
+static void launch_label(const DetectArgs& one, const DetectArgs* batch, dim3 g, int late, cudaStream_t st)
 {
     const size_t smem = sizeof(LabelSmem<BIG>) * LabelCfg<BIG>::NW;
     auto* fn = k_label_tiles<LO, BATCH, BIG>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fn<<<g, 32 * LabelCfg<BIG>::NW, smem, st>>>(batch, one);
+    fn<<<g, 32 * LabelCfg<BIG>::NW, smem, st>>>(batch, one, late);
 }
 
+// The census of the listed tiles, then the common form on `st` and the
+// crowded tiles on the side stream when there is one (they touch other
+// tiles' records only, so the two forms run side by side), else before it
+// on `st`; then the tiles the common form deferred, on `st` once both are
+// done.
 template <bool LO, bool BATCH>
-static void launch_label_both(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st)
+static cudaError_t launch_label_forms(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st,
+                                      const SideStream* side)
 {
-    launch_label<LO, BATCH, false>(one, batch, dim3(BATCH ? stride_grid(LT_CTAS, nframes) : LT_CTAS, nframes), st);
-    launch_label<LO, BATCH, true>(one, batch, dim3(BATCH ? stride_grid(LT_BIG_CTAS, nframes) : LT_BIG_CTAS, nframes),
-                                  st);
+    const dim3 gc(BATCH ? stride_grid(LT_CTAS, nframes) : LT_CTAS, nframes);
+    const dim3 gb(BATCH ? stride_grid(LT_BIG_CTAS, nframes) : LT_BIG_CTAS, nframes);
+    const dim3 gl(BATCH ? stride_grid(LT_LATE_CTAS, nframes) : LT_LATE_CTAS, nframes);
+    cudaError_t e = cudaSuccess;
+    if (!LO) {
+        k_tile_census<BATCH><<<gc, 256, 0, st>>>(batch, one);
+        if (side) {
+            if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(side->st, side->fork, 0)) != cudaSuccess) return e;
+            launch_label<LO, BATCH, true>(one, batch, gb, 0, side->st);
+            if ((e = cudaEventRecord(side->join, side->st)) != cudaSuccess) return e;
+        } else {
+            launch_label<LO, BATCH, true>(one, batch, gb, 0, st);
+        }
+    }
+    launch_label<LO, BATCH, false>(one, batch, gc, 0, st);
+    if (!LO && side && (e = cudaStreamWaitEvent(st, side->join, 0)) != cudaSuccess) return e;
+    launch_label<LO, BATCH, true>(one, batch, gl, 1, st);
+    return cudaGetLastError();
 }
 
-// every frame of a batch shares `one`'s dtype, kernel size and mode
-// (labelling a given mask or detecting); maxgrid = detect_grid() of the
-// largest frame
-cudaError_t launch_label_any(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st)
+int label_launches(bool given_mask) { return given_mask ? 2 : 4; }
+
+cudaError_t launch_label_any(const DetectArgs& one, const DetectArgs* batch, int nframes, cudaStream_t st,
+                             const SideStream* side)
 {
-    if (one.in_mask) {
-        if (batch) launch_label_both<true, true>(one, batch, nframes, st);
-        else launch_label_both<true, false>(one, batch, nframes, st);
-    } else {
-        if (batch) launch_label_both<false, true>(one, batch, nframes, st);
-        else launch_label_both<false, false>(one, batch, nframes, st);
-    }
-    return cudaGetLastError();
+    if (one.in_mask) return batch ? launch_label_forms<true, true>(one, batch, nframes, st, side)
+                                  : launch_label_forms<true, false>(one, batch, nframes, st, side);
+    return batch ? launch_label_forms<false, true>(one, batch, nframes, st, side)
+                 : launch_label_forms<false, false>(one, batch, nframes, st, side);
 }
 
 ResolveArgs resolve_args(const Tiles& T, const Pieces& P, const Comps& C, const DetMask& dm, uint32_t* seg, int W,

@@ -41,8 +41,8 @@ struct GrowthSpec {
 template <bool F32>
 __global__ void __launch_bounds__(GR_NT) k_growth(Image im, SplineTab sb, SplineTab sr,
                                                   const __grid_constant__ GrowthSpec gs, const double* __restrict__ xs,
-                                                  const double* __restrict__ ys, int n, double* flux, double* ferr,
-                                                  uint32_t* flags)
+                                                  const double* __restrict__ ys, int n, const int* __restrict__ n_dev,
+                                                  double* flux, double* ferr, uint32_t* flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nr = gs.nr, rmax = gs.rmax, r2max = rmax * rmax;
@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(GR_NT) k_growth(Image im, SplineTab sb, Spline
     __syncthreads();
     const int W = im.W, H = im.H;
     const int wid = blockIdx.x * GR_W + warp, nw = gridDim.x * GR_W;
+    if (n_dev) n = min(n, *n_dev);           // a device count (catalog rows), at most n
     for (int s = wid; s < n; s += nw) {
         const double cxd = floor(xs[s] + 0.5), cyd = floor(ys[s] + 0.5);
         // positions far outside the frame (or NaN) give empty sums, flagged
@@ -181,8 +182,8 @@ size_t growth_smem_bytes(int nr, int rmax)
 }
 
 cudaError_t launch_growth(const Image& im, const SplineTab& sb, const SplineTab& sr, const double* xs,
-                          const double* ys, int n, const int* radii, int nr, float gain, double* flux,
-                          double* ferr, uint32_t* flags, cudaStream_t st)
+                          const double* ys, int n, const int* n_dev, const int* radii, int nr, float gain,
+                          double* flux, double* ferr, uint32_t* flags, cudaStream_t st)
 {
     GrowthSpec gs;
     memset(&gs, 0, sizeof gs);
@@ -195,10 +196,10 @@ cudaError_t launch_growth(const Image& im, const SplineTab& sb, const SplineTab&
     const int grid = 152 * 4;
     if (im.is_f32) {
         cudaFuncSetAttribute(k_growth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_growth<true><<<grid, GR_NT, smem, st>>>(im, sb, sr, gs, xs, ys, n, flux, ferr, flags);
+        k_growth<true><<<grid, GR_NT, smem, st>>>(im, sb, sr, gs, xs, ys, n, n_dev, flux, ferr, flags);
     } else {
         cudaFuncSetAttribute(k_growth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_growth<false><<<grid, GR_NT, smem, st>>>(im, sb, sr, gs, xs, ys, n, flux, ferr, flags);
+        k_growth<false><<<grid, GR_NT, smem, st>>>(im, sb, sr, gs, xs, ys, n, n_dev, flux, ferr, flags);
     }
     return cudaGetLastError();
 }

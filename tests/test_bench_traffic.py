@@ -20,7 +20,7 @@ def load_bench(root):
 def test_committed_traffic_is_well_formed():
     b = load_bench(ROOT)
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    assert "k_detect_tile" in d                      # the dominant kernel
+    assert "k_stream" in d                           # the dominant kernel
     for kernel, e in d.items():
         assert e["read"] + e["write"] == e["dram_bytes_per_launch"]
         assert os.path.exists(os.path.join(ROOT, e["summary"]))
