@@ -394,6 +394,63 @@ def optimal_radius(m, var, bad, sat, F, rms_map, cat, radii, gain, snr_min, d_is
                 ncal=ncal, kassign=kas, kfinal=kfin, flux_opt=flux[i, kfin], fluxerr_opt=err[i, kfin])
 
 
+# --------------------------- spatially varying matched filter (Section 3.2) ---
+# The second detection pass correlates m with the local PSF, a reference P0
+# plus K eigenmodes e_k whose coefficients c_k vary over the frame:
+# S = P0 (x) m + sum_k c_k (e_k (x) m), each term a plain correlation with a
+# mirror border, weighted by its coefficient map [R28]; the maps are the
+# natural cubic spline through per-tile coefficients [R29]; foreground is
+# S > k sigma [R30].
+def correlate(m, kernel):
+    """[R28] sum over taps (u, v) of K[v, u] m(x + u - kw/2, y + v - kh/2),
+    mirror border without edge repeat, the kernel used as given."""
+    m, K = _f64(m), _f64(kernel)
+    kh, kw = K.shape
+    hy, hx = kh // 2, kw // 2
+    H, W = m.shape
+    pad = np.pad(m, ((hy, hy), (hx, hx)), mode="reflect")
+    out = np.zeros_like(m)
+    for v in range(kh):
+        for u in range(kw):
+            out += K[v, u] * pad[v:v + H, u:u + W]
+    return out
+
+
+def coefficient_maps(coef, W, H, tile):
+    """[R29] per-pixel coefficient maps from K meshes of per-tile values."""
+    coef = _f64(coef)
+    return [spline_map(coef[k], W, H, tile) for k in range(coef.shape[0])]
+
+
+def psf_filter(m, p0, modes, coef, tile):
+    """[R28][R29] S = P0 (x) m + sum_k c_k * (e_k (x) m)."""
+    H, W = m.shape
+    S = correlate(m, p0)
+    for c, e in zip(coefficient_maps(coef, W, H, tile), np.asarray(modes, np.float64)):
+        S = S + c * correlate(m, e)
+    return S
+
+
+def detect_psf(image, mesh, p0, modes, coef, tile, thresh, minarea, mask=None, saturation=0.0,
+               fsize=3, clip_k=3.0, clip_maxiter=10):
+    """The second detection pass in the stage order of extract(): background
+    and noise map, the spatially varying filter, threshold [R30], labelling
+    and moments."""
+    img, bad = pixel_values(image, mask)
+    H, W = img.shape
+    bkg_mesh, rms_mesh, _ = background_meshes(img, bad, mesh, fsize, clip_k, clip_maxiter)
+    bkg_map = spline_map(bkg_mesh, W, H, mesh)
+    rms_map = spline_map(rms_mesh, W, H, mesh)
+    m = np.where(bad != 0, 0.0, img - bkg_map)
+    S = psf_filter(m, p0, modes, coef, tile)
+    fg = threshold(S, rms_map, bad, thresh)
+    seg, n = label(fg, minarea)
+    sat = saturated(image, saturation)
+    cat = moments(seg, m, sat)
+    return dict(bkg_mesh=bkg_mesh, rms_mesh=rms_mesh, bkg_map=bkg_map, rms_map=rms_map, m=m, bad=bad, S=S, fg=fg,
+                seg=seg, cat=cat, near=near_threshold(S, rms_map, thresh))
+
+
 # ------------------------------------------------------------ whole path ---
 def extract(image, mesh, kernel, thresh, minarea, radii, gain, mask=None, saturation=0.0,
             fsize=3, clip_k=3.0, clip_maxiter=10):

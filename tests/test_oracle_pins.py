@@ -723,3 +723,73 @@ def test_significance_is_the_filtered_value_over_sigma_at_the_peak():
     assert nu[0] == pytest.approx(500.0 * K[2, 2] / 4.0, rel=1e-15)
     assert nu[1] == 0.0                                      # sigma 0 gives no significance
     assert nu[2] == pytest.approx(500.0 * K[2, 1] / 4.0, rel=1e-15)   # F(p) takes m(p + u) with tap u
+
+
+# --------------------------- spatially varying matched filter (Section 3.2) ---
+def _psf_inputs(seed=5, K=3, kw=7, kh=5, W=90, H=70, tile=32):
+    rng = np.random.default_rng(seed)
+    m = rng.normal(0, 10, (H, W))
+    p0 = rng.random((kh, kw))
+    p0 /= p0.sum()
+    modes = rng.normal(0, 0.05, (K, kh, kw))
+    coef = rng.normal(0, 1, (K, -(-H // tile), -(-W // tile)))
+    return m, p0, modes, coef, tile
+
+
+def test_correlate_is_scipy_mirror_correlation_with_the_kernel_as_given():
+    from scipy import ndimage
+    m, p0, modes, _, _ = _psf_inputs()
+    for K in (p0, modes[0], modes[1] - modes[1].mean()):        # unit sum, arbitrary, zero sum
+        ref = ndimage.correlate(m, K, mode="mirror")
+        assert np.allclose(oracle.correlate(m, K), ref, rtol=0, atol=1e-12)
+
+
+def test_psf_filter_without_modes_is_the_plain_matched_filter():
+    m, p0, modes, coef, tile = _psf_inputs()
+    S = oracle.psf_filter(m, p0, modes[:0], coef[:0], tile)
+    assert np.allclose(S, oracle.matched_filter(m, p0), rtol=0, atol=1e-12)
+
+
+def test_psf_filter_with_constant_coefficients_is_one_kernel():
+    """With every tile holding the same coefficients the filter is the
+    correlation with the single kernel P0 + sum_k c_k e_k (linearity)."""
+    from scipy import ndimage
+    m, p0, modes, coef, tile = _psf_inputs()
+    c = np.array([0.7, -1.3, 2.1])
+    const = np.broadcast_to(c[:, None, None], coef.shape).copy()
+    S = oracle.psf_filter(m, p0, modes, const, tile)
+    ref = ndimage.correlate(m, p0 + np.tensordot(c, modes, axes=1), mode="mirror")
+    assert np.allclose(S, ref, rtol=0, atol=1e-10)
+
+
+def test_psf_filter_of_a_delta_reads_the_local_kernel():
+    """m = delta at q: S(p) = P0[q - p + h] + sum_k c_k(p) e_k[q - p + h],
+    the tap orientation of a correlation, with each pixel's own coefficients."""
+    m, p0, modes, coef, tile = _psf_inputs()
+    H, W = m.shape
+    d = np.zeros_like(m)
+    qy, qx = 33, 41
+    d[qy, qx] = 1.0
+    S = oracle.psf_filter(d, p0, modes, coef, tile)
+    cm = oracle.coefficient_maps(coef, W, H, tile)
+    kh, kw = p0.shape
+    for py in range(qy - kh // 2, qy + kh // 2 + 1):
+        for px in range(qx - kw // 2, qx + kw // 2 + 1):
+            v, u = qy - py + kh // 2, qx - px + kw // 2
+            want = p0[v, u] + sum(cm[k][py, px] * modes[k][v, u] for k in range(len(modes)))
+            assert S[py, px] == pytest.approx(want, abs=1e-14)
+    assert S[qy + kh // 2 + 1, qx] == 0.0
+
+
+def test_coefficient_maps_are_linear_for_linear_tiles():
+    W, H, tile = 200, 150, 40
+    My, Mx = -(-H // tile), -(-W // tile)
+    ax = oracle.spline_map(np.zeros((My, Mx)), W, H, tile)       # shape check
+    assert ax.shape == (H, W)
+    # tile centres (first pixel + (w - 1)/2); a mesh linear in them gives the same plane everywhere
+    cx = np.array([min(i * tile + (min(tile, W - i * tile) - 1) / 2, W) for i in range(Mx)])
+    cy = np.array([min(j * tile + (min(tile, H - j * tile) - 1) / 2, H) for j in range(My)])
+    mesh = 0.25 + 0.01 * cx[None, :] - 0.02 * cy[:, None]
+    c = oracle.coefficient_maps(mesh[None], W, H, tile)[0]
+    yy, xx = np.mgrid[0:H, 0:W]
+    assert np.allclose(c, 0.25 + 0.01 * xx - 0.02 * yy, rtol=0, atol=1e-10)
