@@ -275,6 +275,77 @@ def growth_section(ctx, ex, t_img, cfg, nsrc, stream, dev, steps, peak):
             "sources_per_s": round(n / (kms / 1e3), 1)}
 
 
+def timed_calls(ctx, fn, steps, stream, dev):
+    """Mean call time (CUDA events) and per-stage device times of `steps` calls."""
+    import torch
+    for _ in range(3):
+        fn()
+    ctx.sync()
+    ctx.set_timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        r = fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.sync()
+    st = ctx.stats()
+    ctx.set_timing(False)
+    return a.elapsed_time(b) / steps, {k: v / max(st["calls"], 1) for k, v in st["ms"].items()}, r
+
+
+def ropt_section(ctx, ex, t_img, cfg, stream, dev, steps):
+    """gp_optimal_radius over the catalog: growth curves at the paper's radii,
+    nu, calibrators (S/N >= 20, no centroid within 2 r_max), the fit, every
+    row's radius (Section 3.4)."""
+    import numpy as np
+    fwhm = float(np.mean(cfg.fwhm))
+    radii = np.arange(int(np.ceil(0.75 * fwhm)), int(np.ceil(5.0 * fwhm)) + 1, dtype=np.int32)
+    bkg = {"bkg_mesh": ex.out["bkg_mesh"], "rms_mesh": ex.out["rms_mesh"], "mesh": cfg.mesh}
+    cat = ex.out["catalog"]
+    ms, stg, out = timed_calls(ctx, lambda: ctx.gp_optimal_radius(t_img, bkg, cfg.kernel, cat, radii, gain=cfg.gain,
+                                                                  snr_min=20.0, d_iso=2.0 * float(radii[-1]),
+                                                                  saturation=cfg.saturation), steps, stream, dev)
+    fit = out["fit"].cpu().numpy()
+    return {"rows": int(cat["n"].item()), "radii": [int(radii[0]), int(radii[-1])], "call_ms": round(ms, 4),
+            "kernels_ms": round(stg["measure"], 4), "calibrators": int(fit[2]), "a": float(fit[0]),
+            "b": float(fit[1]), "snr_min": 20.0, "d_iso": 2.0 * float(radii[-1])}
+
+
+def psf_section(ctx, ex, t_img, cfg, stream, dev, steps, peak):
+    """gp_detect_psf, the second detection pass with a spatially varying PSF
+    (Section 3.2), on the same frame: a 13 x 13 Gaussian reference (the
+    paper's smallest stamp, half-side 6) and 5 modes, coefficients on
+    2048-pixel tiles.  The model is synthetic (the Eigen-PSF stage is out of
+    scope), seeded."""
+    import numpy as np
+    import torch
+    H, W = t_img.shape
+    size, K, tile = 13, 5, 2048
+    h = size // 2
+    yy, xx = np.mgrid[-h:h + 1, -h:h + 1].astype(np.float64)
+    s = float(np.mean(cfg.fwhm)) / 2.3548
+    g = np.exp(-(xx * xx + yy * yy) / (2 * s * s))
+    p0 = (g / g.sum()).astype(np.float32)
+    r2 = xx * xx + yy * yy
+    modes = np.array([xx * p0, yy * p0, (r2 - 2 * s * s) * p0, (xx * xx - yy * yy) * p0, xx * yy * p0], np.float32)
+    rng = np.random.default_rng(7)
+    coef = torch.from_numpy(rng.uniform(-0.3, 0.3, (K, -(-H // tile), -(-W // tile))).astype(np.float32)).to(dev)
+    bkg = {"bkg_mesh": ex.out["bkg_mesh"], "rms_mesh": ex.out["rms_mesh"], "mesh": cfg.mesh}
+    ms, stg, out = timed_calls(ctx, lambda: ctx.gp_detect_psf(t_img, bkg, p0, modes, coef, tile, cfg.thresh,
+                                                              cfg.minarea, CAPACITY, saturation=cfg.saturation),
+                               steps, stream, dev)
+    kms = stg["threshold"]
+    bpp = 2 if cfg.dtype == "u16" else 4
+    nbytes = W * H * (bpp + 4) + W * H // 8
+    flops = 2.0 * W * H * (K + 1) * size * size
+    return {"model": f"P0 {size}x{size} + {K} modes, tile {tile}", "segments": int(out["catalog"]["n"].item()),
+            "call_ms": round(ms, 4), "stages_ms": {k: round(v, 4) for k, v in stg.items()},
+            "kernel": "k_psf", "kernel_ms": round(kms, 4), "algorithmic_bytes": nbytes,
+            "achieved_GBs": round(nbytes / (kms / 1e3) / 1e9, 1), "frac_of_hbm": round(nbytes / (kms / 1e3) / 1e9 / peak, 4),
+            "fp32_tflops": round(flops / (kms / 1e3) / 1e12, 2)}
+
+
 # --------------------------------------------------------------- serving ---
 # Frame classes of the request stream: the paper's 4.2 to 151.2 MP range as
 # crops of the dense frame (its source density, so 3,700 to 134,000 sources).
@@ -591,6 +662,8 @@ def run_gpu(args):
     # ---- growth curves (top-hat apertures, Section 3.4) at the catalog's centroids
     if not args.no_growth:
         line["growth"] = growth_section(ctx, ex, t_img, cfg, nsrc, stream, dev, args.steps, peak)
+        line["optimal_radius"] = ropt_section(ctx, ex, t_img, cfg, stream, dev, args.steps)
+        line["psf_detect"] = psf_section(ctx, ex, t_img, cfg, stream, dev, args.steps, peak)
 
     # ---- the request server on a mixed stream (plain, and learned when trained weights exist)
     if rank == 0 and world == 1 and not args.no_serving:

@@ -271,6 +271,33 @@ gp_status gp_optimal_radius(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
                             const gp_det_params* dp, const gp_catalog* cat,
                             const gp_ropt_params* p, gp_ropt_out* out, gp_stream stream);
 
+/* Section 3.2, the second detection pass with a spatially varying PSF: the
+ * local PSF is a reference P0 plus K eigenmodes e_k weighted by coefficient
+ * maps c_k, and the matched filter is the sum of K + 1 correlations,
+ *   S(p) = (P0 (x) m)(p) + sum_k c_k(p) (e_k (x) m)(p),
+ * with m = I - B (bad pixels 0) and a mirror border.  The kernels are used
+ * as given (no normalisation).  c_k is the natural cubic spline through the
+ * centres of square tiles of side `tile` holding the per-tile coefficients
+ * (the background mesh's interpolation).  Foreground is S > thresh * sigma(p);
+ * labelling, minarea, segmap and catalog are those of gp_detect. */
+#define GP_PSF_MAX_MODES 8
+typedef struct {
+    const float* p0;       /* HOST: kh rows of kw taps */
+    const float* modes;    /* HOST: K kernels of kh*kw taps, mode-major */
+    int32_t K, kw, kh;     /* 0 <= K <= GP_PSF_MAX_MODES; kw, kh odd <= 15 */
+    const float* coef;     /* DEVICE: K meshes of ceil(H/tile) rows of ceil(W/tile), mode-major */
+    int32_t tile;          /* >= 1 */
+    float thresh;          /* > 0 */
+    int32_t minarea;       /* >= 1 */
+} gp_psf_params;
+
+/* segmap: device width*height, caller-owned; cat as in gp_detect.
+ * GP_ERR_INVALID_ARG on a null pointer or a parameter outside the ranges
+ * above; nothing is launched then. */
+gp_status gp_detect_psf(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
+                        const gp_psf_params* p, uint32_t* segmap, gp_catalog* cat,
+                        gp_stream stream);
+
 /* The three stages in one call; apertures at each segment's centroid, rows
  * aligned with the catalog (capacity*nr). */
 gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp,

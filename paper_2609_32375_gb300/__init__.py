@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_ctx_set_walk_limit", "gp_workspace_bytes",
-           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_optimal_radius", "gp_extract", "gp_label_mask", "gp_background_static",
+           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_optimal_radius", "gp_detect_psf", "gp_extract", "gp_label_mask", "gp_background_static",
            "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
            "gp_cnn_denorm", "gp_extract_batch", "gp_server_create", "gp_server_submit", "gp_server_wait",
@@ -89,6 +89,12 @@ class GpCnnWeights(C.Structure):
 
 class GpApParams(C.Structure):
     _fields_ = [("radii", C.POINTER(C.c_float)), ("nr", C.c_int32), ("gain", C.c_float)]
+
+
+class GpPsfParams(C.Structure):
+    _fields_ = [("p0", C.POINTER(C.c_float)), ("modes", C.POINTER(C.c_float)), ("K", C.c_int32), ("kw", C.c_int32),
+                ("kh", C.c_int32), ("coef", C.c_void_p), ("tile", C.c_int32), ("thresh", C.c_float),
+                ("minarea", C.c_int32)]
 
 
 class GpRoptParams(C.Structure):
@@ -189,6 +195,9 @@ def load_library():
         L.gp_optimal_radius.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), C.POINTER(GpDetParams),
                                         C.POINTER(GpCatalog), C.POINTER(GpRoptParams), C.POINTER(GpRoptOut), vp]
         L.gp_optimal_radius.restype = st
+        L.gp_detect_psf.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), C.POINTER(GpPsfParams), vp,
+                                    C.POINTER(GpCatalog), vp]
+        L.gp_detect_psf.restype = st
         L.gp_extract.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
                                  C.POINTER(GpApParams), C.POINTER(GpBkg), vp, C.POINTER(GpCatalog), vp, vp, vp, vp]
         L.gp_extract.restype = st
@@ -416,6 +425,29 @@ class Context:
                                         r.ctypes.data_as(C.POINTER(C.c_int32)), r.size, float(gain),
                                         flux.data_ptr(), ferr.data_ptr(), fl.data_ptr(), _stream_handle(stream)))
         return flux[:n], ferr[:n], fl[:n]
+
+    def gp_detect_psf(self, img, bkg, p0, modes, coef, tile, thresh, minarea, capacity, mask=None, saturation=0.0,
+                      stream=None):
+        """The second detection pass with the spatially varying PSF
+        P0 + sum_k c_k e_k; coef: device tensor [K, ceil(H/tile), ceil(W/tile)]."""
+        import torch
+        gi = make_image(img, mask, saturation)
+        p0 = np.ascontiguousarray(np.asarray(p0, dtype=np.float32))
+        kh, kw = p0.shape
+        modes = np.ascontiguousarray(np.asarray(modes, dtype=np.float32).reshape(-1, kh, kw))
+        K = modes.shape[0]
+        if K:
+            coef = coef.to(device=img.device, dtype=torch.float32).contiguous()
+        H, W = img.shape
+        out = {"segmap": torch.empty((H, W), dtype=torch.int32, device=img.device)}
+        cols, cat = allocate_catalog(capacity, img.device)
+        p = GpPsfParams(p0.ctypes.data_as(C.POINTER(C.c_float)), modes.ctypes.data_as(C.POINTER(C.c_float)), K, kw,
+                        kh, coef.data_ptr() if K else None, int(tile), float(thresh), int(minarea))
+        b = self._bkg_struct(bkg)
+        _check(load_library().gp_detect_psf(self._h, C.byref(gi), C.byref(b), C.byref(p), out["segmap"].data_ptr(),
+                                            C.byref(cat), _stream_handle(stream)))
+        out["catalog"] = cols
+        return out
 
     def gp_optimal_radius(self, img, bkg, kernel, catalog, radii, gain=0.0, snr_min=50.0, d_iso=30.0, mask=None,
                           saturation=0.0, stream=None):

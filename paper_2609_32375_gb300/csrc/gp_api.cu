@@ -594,6 +594,70 @@ gp_status gp_growth(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const d
     return GP_OK;
 }
 
+gp_status gp_detect_psf(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_psf_params* p, uint32_t* segmap,
+                        gp_catalog* cat, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg(img, bkg, true)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if (!p || !segmap) return fail(GP_ERR_INVALID_ARG, "null PSF parameters or segmap");
+    if (!p->p0 || p->K < 0 || p->K > GP_PSF_MAX_MODES || (p->K > 0 && (!p->modes || !p->coef)))
+        return fail(GP_ERR_INVALID_ARG, "PSF model: need P0, and 0..%d modes with their coefficients", GP_PSF_MAX_MODES);
+    if (p->kw < 1 || p->kh < 1 || !(p->kw & 1) || !(p->kh & 1) || p->kw > 2 * HMAX + 1 || p->kh > 2 * HMAX + 1)
+        return fail(GP_ERR_INVALID_ARG, "PSF kernels %dx%d must have odd sides <= %d", p->kw, p->kh, 2 * HMAX + 1);
+    if (p->tile < 1) return fail(GP_ERR_INVALID_ARG, "coefficient tile side must be >= 1");
+    if (!(p->thresh > 0.f) || !std::isfinite(p->thresh)) return fail(GP_ERR_INVALID_ARG, "thresh must be > 0");
+    if (p->minarea < 1) return fail(GP_ERR_INVALID_ARG, "minarea must be >= 1");
+    for (int i = 0; i < p->kw * p->kh * (1 + p->K); ++i) {
+        const float v = i < p->kw * p->kh ? p->p0[i] : p->modes[i - p->kw * p->kh];
+        if (!std::isfinite(v)) return fail(GP_ERR_INVALID_ARG, "a PSF tap is not finite");
+    }
+    const int W = img->width, H = img->height;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    mark(ctx, 1, st);
+    s = run_spline(cv, bkg, W, H, &sb, &sr, &ctx->launches, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    // the coefficient maps' spline tables
+    const int cmx = (W + p->tile - 1) / p->tile, cmy = (H + p->tile - 1) / p->tile;
+    SplineTab ct[GP_PSF_MAX_MODES];
+    double* scratch = cv.take<double>(spline_scratch_doubles(cmx, cmy));
+    float4* tabs = cv.take<float4>((size_t)cmx * cmy * (p->K > 0 ? p->K : 1));
+    DetWork w;
+    carve_det(cv, W, H, cat->capacity, w);
+    if (!cv.ok()) return oom(cv);
+    const Axis cax = make_axis(W, p->tile), cay = make_axis(H, p->tile);
+    for (int k = 0; k < p->K; ++k) {
+        float4* tab = tabs + (size_t)k * cmx * cmy;
+        GP_CUDA(launch_spline_tables(p->coef + (size_t)k * cmx * cmy, cax, cay, scratch, tab, st));
+        ct[k] = make_tab(tab, W, H, p->tile);
+        ctx->launches += 2;
+    }
+    mark(ctx, 2, st);
+    const Image im = to_image(img);
+    GP_CUDA(cudaMemsetAsync(w.zero, 0, (size_t)w.nzero * sizeof(int), st));
+    const float one = 1.f;
+    const DetectArgs A = detect_args(im, sb, sr, &one, 1, 1, p->thresh, p->minarea, segmap, nullptr, nullptr, nullptr,
+                                     w.D, w.T, w.P, w.C, ctx->dstatus);
+    GP_CUDA(launch_psf(A, p->p0, p->modes, p->K, p->kw, p->kh, ct, st));
+    mark(ctx, 3, st);
+    GP_CUDA(launch_label_any(A, nullptr, 1, st, ctx->side_made ? &ctx->side : nullptr));
+    mark(ctx, 4, st);
+    GP_CUDA(launch_resolve(w.T, w.P, w.C, w.D, segmap, W, H, p->minarea, ctx->walk_limit, ctx->dstatus, st));
+    mark(ctx, 5, st);
+    GP_CUDA(launch_rank(w.C, cat->n, cat->capacity, true, ctx->dstatus, st));
+    mark(ctx, 6, st);
+    GP_CUDA(launch_measure(im, sb, sr, w.C, segmap, *cat, nullptr, 0, 0.f, nullptr, nullptr, nullptr, st));
+    mark(ctx, 7, st);
+    ctx->launches += 1 + label_launches(false) + 4 + 4 + 1;
+    return GP_OK;
+}
+
 gp_status gp_optimal_radius(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* dp,
                             const gp_catalog* cat, const gp_ropt_params* p, gp_ropt_out* out, gp_stream stream)
 {

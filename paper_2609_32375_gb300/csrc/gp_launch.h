@@ -49,6 +49,12 @@ cudaError_t launch_growth(const Image& im, const SplineTab& sb, const SplineTab&
                           const double* ys, int n, const int* n_dev, const int* radii, int nr, float gain,
                           double* flux, double* ferr, uint32_t* flags, cudaStream_t st);
 
+// the spatially varying matched filter's threshold pass (k_psf.cu): the
+// outputs of launch_stream_any for the pixel arguments of D; taps of P0 and
+// the nk modes (kh*kw each), coefficient spline tables of the modes
+cudaError_t launch_psf(const DetectArgs& D, const float* p0, const float* modes, int nk, int kw, int kh,
+                       const SplineTab* coef_tabs, cudaStream_t st);
+
 // optimal aperture radius (k_ropt.cu): the growth curves of the catalog rows
 // are given; scratch of the isolation grid from iso_grid()
 struct RoptWork {
