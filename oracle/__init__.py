@@ -451,6 +451,88 @@ def detect_psf(image, mesh, p0, modes, coef, tile, thresh, minarea, mask=None, s
                 seg=seg, cat=cat, near=near_threshold(S, rms_map, thresh))
 
 
+# ----------------------------------------- cosmetic filters (Section 3.1) ---
+# Two optional corrections before the background: a salt-and-pepper filter
+# for random telegraph noise that replaces isolated outliers of a
+# median-filtered residual [R31], and a cosmic-ray filter in the manner of
+# L.A.Cosmic that flags sharp edges through a Laplacian and fills the flagged
+# pixels from their neighbours [R32].  Windows have a mirror border; bad
+# pixels (masked or non-finite) are left out of every window and are never
+# flagged or changed.
+def window_median(a, size):
+    """Median of each size x size window (mirror border) over its finite
+    values (the mean of the two middle ones for an even count); NaN where a
+    window holds none."""
+    a = _f64(a)
+    h = size // 2
+    pad = np.pad(a, h, mode="reflect")
+    win = np.lib.stride_tricks.sliding_window_view(pad, (size, size))
+    flat = win.reshape(a.shape + (size * size,))
+    with np.errstate(all="ignore"):
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", RuntimeWarning)
+            return np.nanmedian(flat, axis=-1)
+
+
+def _shift(a, dy, dx):
+    """a(y + dy, x + dx) with a mirror border."""
+    H, W = a.shape
+    ys = np.array([_mirror(y + dy, H) for y in range(H)])
+    xs = np.array([_mirror(x + dx, W) for x in range(W)])
+    return a[np.ix_(ys, xs)]
+
+
+def _mirror(i, n):
+    if n == 1:
+        return 0
+    p = 2 * (n - 1)
+    i = abs(i) % p
+    return p - i if i >= n else i
+
+
+def rtn_filter(image, t, mask=None):
+    """[R31] r = I - med3(I); a good pixel with |r| > t whose 8 neighbours
+    hold no such pixel takes med3.  Returns (corrected frame, replaced)."""
+    img, bad = pixel_values(image, mask)
+    a = np.where(bad != 0, np.nan, img)
+    med = window_median(a, 3)
+    with np.errstate(invalid="ignore"):
+        out = (bad == 0) & (np.abs(a - med) > t)
+    others = np.zeros(a.shape, np.int32)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy or dx:
+                others += _shift(out.astype(np.int32), dy, dx)
+    rep = out & (others == 0)
+    return np.where(rep, med, np.where(bad != 0, np.asarray(image, np.float64), img)), rep
+
+
+def cr_filter(image, gain, read_noise, sigclip=4.5, objlim=5.0, mask=None):
+    """[R32] One pass: L = 4 I - (the 4 nearest neighbours), L+ = max(L, 0);
+    the noise N = sqrt(max(med5(I), 0) gain + rn^2) / gain (ADU); S =
+    L+ / (sqrt(20) N) (L's standard deviation for independent pixel noise N:
+    4^2 + 4 x 1^2 = 20) less its 5x5 median; the fine structure F = med3(I) - med7(med3(I)),
+    floored at 0.01; flagged where S > sigclip and L+ / F > objlim; a flagged
+    pixel takes the median of the good unflagged pixels of its 5x5 window
+    (unchanged when there are none).  Returns (corrected frame, flagged)."""
+    img, bad = pixel_values(image, mask)
+    a = np.where(bad != 0, np.nan, img)
+    L = 4 * a - _shift(a, 0, -1) - _shift(a, 0, 1) - _shift(a, -1, 0) - _shift(a, 1, 0)
+    Lp = np.maximum(L, 0.0)                        # NaN stays NaN
+    noise = np.sqrt(np.maximum(window_median(a, 5), 0.0) * gain + read_noise * read_noise) / gain
+    S = Lp / (np.sqrt(20.0) * noise)
+    Sp = S - window_median(S, 5)
+    m3 = window_median(a, 3)
+    F = np.maximum(m3 - window_median(m3, 7), 0.01)
+    with np.errstate(invalid="ignore"):
+        flag = (bad == 0) & (Sp > sigclip) & (Lp / F > objlim)
+    clean = np.where(flag, np.nan, a)
+    fill = window_median(clean, 5)
+    rep = flag & np.isfinite(fill)
+    return np.where(rep, fill, np.where(bad != 0, np.asarray(image, np.float64), img)), flag
+
+
 # ------------------------------------------------------------ whole path ---
 def extract(image, mesh, kernel, thresh, minarea, radii, gain, mask=None, saturation=0.0,
             fsize=3, clip_k=3.0, clip_maxiter=10):

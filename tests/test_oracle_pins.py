@@ -793,3 +793,62 @@ def test_coefficient_maps_are_linear_for_linear_tiles():
     c = oracle.coefficient_maps(mesh[None], W, H, tile)[0]
     yy, xx = np.mgrid[0:H, 0:W]
     assert np.allclose(c, 0.25 + 0.01 * xx - 0.02 * yy, rtol=0, atol=1e-10)
+
+
+# ----------------------------------------- cosmetic filters (Section 3.1) ---
+def test_window_median_is_scipy_median_filter_and_skips_bad_values():
+    from scipy import ndimage
+    rng = np.random.default_rng(8)
+    a = rng.normal(0, 5, (37, 41))
+    for size in (3, 5, 7):
+        assert np.array_equal(oracle.window_median(a, size), ndimage.median_filter(a, size=size, mode="mirror"))
+    b = np.arange(9.0).reshape(3, 3)
+    b[0, 0] = np.nan                                   # 8 values 1..8 around the centre: median 4.5
+    assert oracle.window_median(b, 3)[1, 1] == 4.5
+    assert np.isnan(oracle.window_median(np.full((4, 4), np.nan), 3)).all()
+
+
+def test_rtn_replaces_isolated_outliers_only():
+    rng = np.random.default_rng(9)
+    img = (1000 + 3 * rng.standard_normal((40, 50))).round()
+    img[10, 10] += 300                    # isolated: replaced by its 3x3 median
+    img[20, 20] += 300                    # a pair of neighbours: kept
+    img[20, 21] += 300
+    img[30, 5] -= 40                      # below the threshold: kept
+    mask = np.zeros(img.shape, np.uint8)
+    img[5, 40] += 500
+    mask[5, 40] = 1                       # bad: never changed
+    out, rep = oracle.rtn_filter(img, 100.0, mask=mask)
+    assert rep.sum() == 1 and rep[10, 10]
+    from scipy import ndimage
+    assert out[10, 10] == ndimage.median_filter(img, size=3, mode="mirror")[10, 10]
+    keep = ~rep
+    assert np.array_equal(out[keep], img[keep])
+
+
+def test_cr_filter_noise_ramp_star_and_hits():
+    rng = np.random.default_rng(10)
+    H, W = 200, 210
+    sigma = np.sqrt(1000.0 + 25.0)
+    noise = 1000 + sigma * rng.standard_normal((H, W))
+    # the Laplacian of independent pixel noise has standard deviation sqrt(20) sigma
+    L = 4 * noise[1:-1, 1:-1] - noise[:-2, 1:-1] - noise[2:, 1:-1] - noise[1:-1, :-2] - noise[1:-1, 2:]
+    assert L.std() == pytest.approx(np.sqrt(20.0) * sigma, rel=0.02)
+    _, fl = oracle.cr_filter(noise, 1.0, 5.0)
+    assert fl.sum() <= 2
+    yy, xx = np.mgrid[0:H, 0:W]
+    _, fl = oracle.cr_filter(1000 + 0.5 * xx + 0.25 * yy, 1.0, 5.0)   # a noiseless ramp: L = 0
+    assert not fl.any()
+    img = noise + 5000 * np.exp(-((xx - 150) ** 2 + (yy - 40) ** 2) / (2 * 1.274 ** 2))   # FWHM 3 star
+    img[50, 60] += 800
+    img[120, 100] += 2000
+    img[120, 101] += 1500
+    out, fl = oracle.cr_filter(img, 1.0, 5.0)
+    assert set(map(tuple, np.argwhere(fl))) == {(50, 60), (120, 100), (120, 101)}
+    # a flagged pixel takes the median of the good unflagged pixels of its 5x5 window
+    w = img[48:53, 58:63].copy().ravel()
+    assert out[50, 60] == np.median(np.delete(w, 12))
+    w = img[118:123, 98:103].ravel()
+    keep = [i for i in range(25) if i not in (12, 13)]
+    assert out[120, 100] == np.median(w[keep])
+    assert np.array_equal(out[~fl], img[~fl])
