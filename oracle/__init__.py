@@ -508,14 +508,15 @@ def rtn_filter(image, t, mask=None):
     return np.where(rep, med, np.where(bad != 0, np.asarray(image, np.float64), img)), rep
 
 
-def cr_filter(image, gain, read_noise, sigclip=4.5, objlim=5.0, mask=None):
+def cr_filter(image, gain, read_noise, sigclip=4.5, objlim=5.0, mask=None, details=False):
     """[R32] One pass: L = 4 I - (the 4 nearest neighbours), L+ = max(L, 0);
     the noise N = sqrt(max(med5(I), 0) gain + rn^2) / gain (ADU); S =
     L+ / (sqrt(20) N) (L's standard deviation for independent pixel noise N:
     4^2 + 4 x 1^2 = 20) less its 5x5 median; the fine structure F = med3(I) - med7(med3(I)),
     floored at 0.01; flagged where S > sigclip and L+ / F > objlim; a flagged
     pixel takes the median of the good unflagged pixels of its 5x5 window
-    (unchanged when there are none).  Returns (corrected frame, flagged)."""
+    (unchanged when there are none).  Returns (corrected frame, flagged), and
+    with details the two decision values (S less its median, L+ / F)."""
     img, bad = pixel_values(image, mask)
     a = np.where(bad != 0, np.nan, img)
     L = 4 * a - _shift(a, 0, -1) - _shift(a, 0, 1) - _shift(a, -1, 0) - _shift(a, 1, 0)
@@ -530,7 +531,121 @@ def cr_filter(image, gain, read_noise, sigclip=4.5, objlim=5.0, mask=None):
     clean = np.where(flag, np.nan, a)
     fill = window_median(clean, 5)
     rep = flag & np.isfinite(fill)
-    return np.where(rep, fill, np.where(bad != 0, np.asarray(image, np.float64), img)), flag
+    out = np.where(rep, fill, np.where(bad != 0, np.asarray(image, np.float64), img))
+    if details:
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return out, flag, dict(sp=Sp, ratio=Lp / F)
+    return out, flag
+
+
+# ------------------------------------------- multi-threshold deblending ---
+# The paper's detection takes local maxima and does not deblend; the
+# segments of the SExtractor reading are split by multi-thresholding
+# [R33]-[R37]: levels of the significance nu = F / sigma between the
+# threshold and the segment's peak; the branches (components) of each level
+# set form a tree by containment; a branch is significant when its sum of m
+# exceeds mincont times the segment's and it has minarea pixels; a branch
+# with two or more significant children splits, each significant child
+# being examined in turn; the other pixels go to the seeds by growth within
+# the level sets, from the highest level down.
+def _components(mask):
+    """8-connected components of a small boolean mask: ids 1..n in raster
+    order of their first pixel (0 outside)."""
+    lab, _ = label(mask.astype(np.uint8), 1)
+    u = np.unique(lab[lab > 0])
+    ids = np.zeros(lab.shape, np.int64)
+    for k, L in enumerate(u, 1):
+        ids[lab == L] = k
+    return ids, len(u)
+
+
+def deblend_segment(nu, m, inseg, thresh, minarea, nthresh=32, mincont=0.005):
+    """One segment (the boolean map `inseg` over its bounding box, nu and m
+    there): the object id of each of its pixels (0 outside; ids 1.. in the
+    order of the seeds' first pixels), and the number of objects."""
+    npix = int(inseg.sum())
+    total = float(m[inseg].sum())
+    one = np.where(inseg, 1, 0)
+    if npix < 2 * minarea or not total > 0:
+        return one, 1
+    numax = float(nu[inseg].max())
+    if not numax > thresh:
+        return one, 1
+    levels = [thresh * (numax / thresh) ** (i / nthresh) for i in range(nthresh)]
+    comp = []
+    for i, t in enumerate(levels):                       # [R33][R34]
+        q = inseg if i == 0 else (inseg & (nu > t))
+        comp.append(_components(q)[0])
+
+    def significant(i, c):                               # [R35]
+        px = comp[i] == c
+        return px.sum() >= minarea and float(m[px].sum()) > mincont * total
+
+    def children(i, c):
+        if i + 1 >= nthresh:
+            return []
+        ids = np.unique(comp[i + 1][(comp[i] == c) & (comp[i + 1] > 0)])
+        return [int(k) for k in ids]
+
+    def objects(i, c):                                   # [R36]
+        sig = [k for k in children(i, c) if significant(i + 1, k)]
+        if len(sig) >= 2:
+            out = []
+            for k in sig:
+                out += objects(i + 1, k)
+            return out
+        if len(sig) == 1:
+            return objects(i + 1, sig[0])
+        return [(i, c)]
+
+    seeds = objects(0, 1)
+    if len(seeds) < 2:
+        return one, 1
+    H, W = inseg.shape
+    first = [int(np.flatnonzero((comp[i] == c).ravel())[0]) for i, c in seeds]
+    order = np.argsort(first, kind="stable")
+    own = np.zeros((H, W), np.int64)
+    for k, j in enumerate(order, 1):
+        i, c = seeds[j]
+        own[comp[i] == c] = k
+    for i in range(nthresh - 1, -1, -1):                 # [R37]
+        q = inseg if i == 0 else (inseg & (nu > levels[i]))
+        while True:
+            big = np.iinfo(np.int64).max
+            pad = np.pad(np.where(own > 0, own, big), 1, constant_values=big)
+            best = np.full((H, W), big, np.int64)
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dy or dx:
+                        best = np.minimum(best, pad[1 + dy:1 + dy + H, 1 + dx:1 + dx + W])
+            grow = q & (own == 0) & (best < big)
+            if not grow.any():
+                break
+            own = np.where(grow, best, own)
+    return own, len(seeds)
+
+
+def deblend(seg, nu, m, thresh, minarea, nthresh=32, mincont=0.005):
+    """The deblended segmentation map: every segment split into its objects,
+    each labelled 1 + the minimum linear index of its pixels [R37]."""
+    seg = np.asarray(seg)
+    H, W = seg.shape
+    out = seg.astype(np.uint32).copy()
+    nsplit = 0
+    for L in np.unique(seg[seg > 0]):
+        ys, xs = np.nonzero(seg == L)
+        y0, y1, x0, x1 = ys.min(), ys.max() + 1, xs.min(), xs.max() + 1
+        inseg = seg[y0:y1, x0:x1] == L
+        own, n = deblend_segment(nu[y0:y1, x0:x1], m[y0:y1, x0:x1], inseg, thresh, minarea, nthresh, mincont)
+        if n < 2:
+            continue
+        nsplit += 1
+        sub = out[y0:y1, x0:x1]
+        for k in range(1, n + 1):
+            py, px = np.nonzero(own == k)
+            lab = 1 + min((y0 + py) * W + (x0 + px))
+            sub[py, px] = lab
+    return out, nsplit
 
 
 # ------------------------------------------------------------ whole path ---

@@ -852,3 +852,89 @@ def test_cr_filter_noise_ramp_star_and_hits():
     keep = [i for i in range(25) if i not in (12, 13)]
     assert out[120, 100] == np.median(w[keep])
     assert np.array_equal(out[~fl], img[~fl])
+
+
+# ------------------------------------------- multi-threshold deblending ---
+def _blend(peaks, H=48, W=72, s=2.5):
+    yy, xx = np.mgrid[0:H, 0:W]
+    m = np.zeros((H, W))
+    for x0, y0, a in peaks:
+        m += a * np.exp(-((xx - x0) ** 2 + (yy - y0) ** 2) / (2 * s * s))
+    return m
+
+
+def _deblend_map(m, thresh=1.5, minarea=5, **kw):
+    nu = m.copy()                                    # sigma 1 and an identity filter: nu = m
+    seg, n = oracle.label((nu > thresh).astype(np.uint8), minarea)
+    out, nsplit = oracle.deblend(seg, nu, m, thresh, minarea, **kw)
+    return seg, out, nsplit
+
+
+def _objects_are_connected_partitions(seg, out):
+    for L in np.unique(seg[seg > 0]):
+        inseg = seg == L
+        labs = np.unique(out[inseg])
+        assert 0 not in labs and np.all(out[~(seg > 0)] == 0)
+        for k in labs:
+            obj = out == k
+            assert np.all(inseg[obj])
+            assert oracle.label(obj.astype(np.uint8), 1)[1] == 1          # 8-connected
+            assert k == 1 + np.flatnonzero(obj.ravel())[0]                # canonical label
+
+
+def test_deblend_keeps_a_single_star():
+    m = _blend([(30, 20, 200.0)])
+    seg, out, nsplit = _deblend_map(m)
+    assert nsplit == 0 and np.array_equal(out, seg)
+
+
+def test_deblend_splits_a_touching_pair_at_their_peaks():
+    m = _blend([(26, 24, 150.0), (40, 25, 110.0)])
+    seg, out, nsplit = _deblend_map(m)
+    assert len(np.unique(seg[seg > 0])) == 1 and nsplit == 1
+    labs = np.unique(out[out > 0])
+    assert len(labs) == 2
+    assert out[24, 26] != out[25, 40]                  # each peak in its own object
+    _objects_are_connected_partitions(seg, out)
+    # a pixel on the line between the peaks goes to the nearer, brighter side
+    assert out[24, 29] == out[24, 26] and out[25, 37] == out[25, 40]
+
+
+def test_deblend_contrast_decides_a_faint_companion():
+    """A sharp companion 10 px from a bright star, joined to it above the
+    threshold (the saddle stays above 1.5): with 0.4 % of the segment's flux
+    it stays part of the star, with 1.6 % it is split off (minarea 1, so the
+    contrast alone decides)."""
+    for amp, split in ((5.0, False), (20.0, True)):
+        m = _blend([(30, 24, 200.0)], s=2.5) + _blend([(40, 24, amp)], s=1.0)
+        seg, out, nsplit = _deblend_map(m, minarea=1)
+        assert len(np.unique(seg[seg > 0])) == 1
+        frac = amp * 2 * np.pi / m[seg > 0].sum()
+        assert (frac > 0.005) == split
+        assert (nsplit == 1) == split, (amp, nsplit)
+        if split:
+            assert out[24, 30] != out[24, 40]
+            _objects_are_connected_partitions(seg, out)
+
+
+def test_deblend_three_peaks_and_nested_levels():
+    m = _blend([(20, 20, 180.0), (33, 21, 140.0), (27, 33, 120.0)])
+    seg, out, nsplit = _deblend_map(m)
+    assert nsplit == 1
+    assert len({out[20, 20], out[21, 33], out[33, 27]}) == 3
+    assert len(np.unique(out[seg > 0])) == 3
+    _objects_are_connected_partitions(seg, out)
+    # fewer levels cannot resolve more than they separate; one level never splits
+    _, out1, ns1 = _deblend_map(m, nthresh=1)
+    assert ns1 == 0
+    # mincont 1: no branch carries the whole flux, nothing splits
+    _, _, nsx = _deblend_map(m, mincont=1.0)
+    assert nsx == 0
+
+
+def test_deblend_leaves_isolated_segments_alone():
+    m = _blend([(15, 15, 100.0)]) + _blend([(55, 30, 120.0), (62, 31, 90.0)])
+    seg, out, nsplit = _deblend_map(m)
+    L = seg[15, 15]
+    assert np.array_equal(out[seg == L], seg[seg == L])
+    assert nsplit == 1
