@@ -298,6 +298,65 @@ gp_status gp_detect_psf(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
                         const gp_psf_params* p, uint32_t* segmap, gp_catalog* cat,
                         gp_stream stream);
 
+/* Section 3.1, the optional cosmetic corrections that precede the
+ * background, each enabled by its parameters:
+ *  - cosmic rays (cr_gain > 0), in the manner of L.A.Cosmic at the native
+ *    scale: L = 4 I - (the four nearest neighbours), L+ = max(L, 0); the
+ *    noise N = sqrt(max(med5(I), 0) cr_gain + cr_read_noise^2) / cr_gain
+ *    (ADU; gain in e-/ADU, read noise in e-); S = L+ / (sqrt(20) N) less its
+ *    5 x 5 median; the fine structure F = med3(I) - med7(med3(I)), at least
+ *    0.01; a pixel is flagged where S > cr_sigclip and L+ / F > cr_objlim and
+ *    takes the median of the good unflagged pixels of its 5 x 5 window;
+ *  - then salt-and-pepper noise (rtn_t > 0): a pixel whose residual from its
+ *    3 x 3 median exceeds rtn_t (ADU) in magnitude, with no such pixel among
+ *    its 8 neighbours, takes the median.
+ * Windows have a mirror border; bad pixels (the image's mask, non-finite
+ * values) are left out of every window and are never flagged or changed.
+ * out: device width*height float32, the corrected frame (bad pixels keep
+ * their values).  flags (device width*height, nullable): bit 1 replaced by
+ * the salt-and-pepper filter, bit 2 flagged as a cosmic ray.  counts
+ * (device, 2 ints, nullable, cleared by the call): replaced, flagged.
+ * GP_ERR_INVALID_ARG on a null out, both filters off, or cr_read_noise <= 0
+ * with cr_gain > 0; GP_ERR_OOM when both are on and the workspace cannot hold
+ * the intermediate frame (width*height floats). */
+typedef struct {
+    float rtn_t;
+    float cr_gain, cr_read_noise, cr_sigclip, cr_objlim;
+} gp_cosmetic_params;
+
+gp_status gp_cosmetic(gp_ctx* ctx, const gp_image* img, const gp_cosmetic_params* p, float* out,
+                      uint8_t* flags, int32_t* counts, gp_stream stream);
+
+/* Multi-threshold deblending of the segments of `segmap` (the rows of `cat`,
+ * as gp_detect or gp_extract leave them, with dp their detection kernel,
+ * threshold and minarea).  The paper's detection takes local maxima and
+ * does not deblend; this is the SExtractor reading.  For a segment of at
+ * least 2 minarea pixels, nu = F / sigma: levels
+ * t_i = thresh (nu_max / thresh)^(i / nthresh), i = 0..nthresh-1; the
+ * branches of a level are the 8-connected components of {nu > t_i} in the
+ * segment; a branch is significant with minarea pixels and a sum of m above
+ * mincont times the segment's (which must be > 0); from the whole segment
+ * upwards a branch hands on to its significant children, and one without is
+ * a seed.  With two or more seeds the other pixels go to the seeds by growth
+ * within the level sets from the highest level down (a pixel takes the
+ * smallest rank, by first pixel, of its attributed 8-neighbours), and each
+ * object is labelled 1 + its minimum linear index in `segmap` (in place).
+ * `objects` receives a catalog row per object of the split segments, in
+ * label order (the columns of gp_catalog; n = their number).  counts
+ * (device, 2 ints, nullable): segments split, objects made.  The scratch is
+ * the context's workspace; a segment that does not fit is left whole and
+ * the call's status is GP_ERR_CAPACITY (as is more than 1024 objects in a
+ * segment, or more objects than objects->capacity).  GP_ERR_INVALID_ARG on
+ * null pointers, nthresh outside 1..64 or mincont outside [0, 1]. */
+typedef struct {
+    int32_t nthresh;       /* number of levels (SExtractor: 32) */
+    float mincont;         /* minimum contrast (SExtractor: 0.005) */
+} gp_deblend_params;
+
+gp_status gp_deblend(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* dp,
+                     const gp_deblend_params* p, uint32_t* segmap, const gp_catalog* cat,
+                     gp_catalog* objects, int32_t* counts, gp_stream stream);
+
 /* The three stages in one call; apertures at each segment's centroid, rows
  * aligned with the catalog (capacity*nr). */
 gp_status gp_extract(gp_ctx* ctx, const gp_image* img, const gp_bkg_params* bp,

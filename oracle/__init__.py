@@ -559,19 +559,29 @@ def _components(mask):
     return ids, len(u)
 
 
-def deblend_segment(nu, m, inseg, thresh, minarea, nthresh=32, mincont=0.005):
+def deblend_segment(nu, m, inseg, thresh, minarea, nthresh=32, mincont=0.005, margins=None):
     """One segment (the boolean map `inseg` over its bounding box, nu and m
     there): the object id of each of its pixels (0 outside; ids 1.. in the
-    order of the seeds' first pixels), and the number of objects."""
+    order of the seeds' first pixels), and the number of objects.  With a
+    `margins` dict, it also records how close the decisions came to their
+    bounds: the least relative distance of a pixel's nu to a level above
+    the first ("nu"), and of a branch's sum of m to the contrast bound,
+    relative to the segment's sum of |m| ("flux")."""
     npix = int(inseg.sum())
     total = float(m[inseg].sum())
     one = np.where(inseg, 1, 0)
+    if margins is not None:
+        margins.update(nu=np.inf, flux=np.inf)
     if npix < 2 * minarea or not total > 0:
         return one, 1
     numax = float(nu[inseg].max())
     if not numax > thresh:
         return one, 1
     levels = [thresh * (numax / thresh) ** (i / nthresh) for i in range(nthresh)]
+    if margins is not None:
+        v = nu[inseg]
+        margins["nu"] = min(float(np.min(np.abs(v - t) / t)) for t in levels[1:]) if nthresh > 1 else np.inf
+        sabs = float(np.abs(m[inseg]).sum())
     comp = []
     for i, t in enumerate(levels):                       # [R33][R34]
         q = inseg if i == 0 else (inseg & (nu > t))
@@ -579,7 +589,10 @@ def deblend_segment(nu, m, inseg, thresh, minarea, nthresh=32, mincont=0.005):
 
     def significant(i, c):                               # [R35]
         px = comp[i] == c
-        return px.sum() >= minarea and float(m[px].sum()) > mincont * total
+        f = float(m[px].sum())
+        if margins is not None and px.sum() >= minarea:
+            margins["flux"] = min(margins["flux"], abs(f - mincont * total) / sabs)
+        return px.sum() >= minarea and f > mincont * total
 
     def children(i, c):
         if i + 1 >= nthresh:
@@ -625,9 +638,10 @@ def deblend_segment(nu, m, inseg, thresh, minarea, nthresh=32, mincont=0.005):
     return own, len(seeds)
 
 
-def deblend(seg, nu, m, thresh, minarea, nthresh=32, mincont=0.005):
+def deblend(seg, nu, m, thresh, minarea, nthresh=32, mincont=0.005, margins=None):
     """The deblended segmentation map: every segment split into its objects,
-    each labelled 1 + the minimum linear index of its pixels [R37]."""
+    each labelled 1 + the minimum linear index of its pixels [R37].  With a
+    `margins` dict: per segment label, its decision margins."""
     seg = np.asarray(seg)
     H, W = seg.shape
     out = seg.astype(np.uint32).copy()
@@ -636,7 +650,10 @@ def deblend(seg, nu, m, thresh, minarea, nthresh=32, mincont=0.005):
         ys, xs = np.nonzero(seg == L)
         y0, y1, x0, x1 = ys.min(), ys.max() + 1, xs.min(), xs.max() + 1
         inseg = seg[y0:y1, x0:x1] == L
-        own, n = deblend_segment(nu[y0:y1, x0:x1], m[y0:y1, x0:x1], inseg, thresh, minarea, nthresh, mincont)
+        mg = {} if margins is not None else None
+        own, n = deblend_segment(nu[y0:y1, x0:x1], m[y0:y1, x0:x1], inseg, thresh, minarea, nthresh, mincont, mg)
+        if margins is not None:
+            margins[int(L)] = mg
         if n < 2:
             continue
         nsplit += 1

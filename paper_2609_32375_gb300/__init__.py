@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR
 
 EXPORTS = ("gp_ctx_create", "gp_ctx_destroy", "gp_last_error", "gp_ctx_sync", "gp_ctx_set_timing", "gp_ctx_stats",
            "gp_ctx_set_walk_limit", "gp_workspace_bytes",
-           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_optimal_radius", "gp_detect_psf", "gp_extract", "gp_label_mask", "gp_background_static",
+           "gp_background", "gp_detect", "gp_aperture", "gp_growth", "gp_optimal_radius", "gp_detect_psf", "gp_cosmetic", "gp_deblend", "gp_extract", "gp_label_mask", "gp_background_static",
            "gp_background_learned", "gp_extract_learned", "gp_box_quantiles", "gp_cnn_conv3x3", "gp_cnn_conv3x3_wgrad",
            "gp_cnn_relu_backward", "gp_cnn_mse", "gp_cnn_pack", "gp_cnn_adamw", "gp_cnn_features", "gp_cnn_targets",
            "gp_cnn_denorm", "gp_extract_batch", "gp_server_create", "gp_server_submit", "gp_server_wait",
@@ -89,6 +89,15 @@ class GpCnnWeights(C.Structure):
 
 class GpApParams(C.Structure):
     _fields_ = [("radii", C.POINTER(C.c_float)), ("nr", C.c_int32), ("gain", C.c_float)]
+
+
+class GpDeblendParams(C.Structure):
+    _fields_ = [("nthresh", C.c_int32), ("mincont", C.c_float)]
+
+
+class GpCosmeticParams(C.Structure):
+    _fields_ = [("rtn_t", C.c_float), ("cr_gain", C.c_float), ("cr_read_noise", C.c_float),
+                ("cr_sigclip", C.c_float), ("cr_objlim", C.c_float)]
 
 
 class GpPsfParams(C.Structure):
@@ -198,6 +207,11 @@ def load_library():
         L.gp_detect_psf.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), C.POINTER(GpPsfParams), vp,
                                     C.POINTER(GpCatalog), vp]
         L.gp_detect_psf.restype = st
+        L.gp_cosmetic.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpCosmeticParams), vp, vp, vp, vp]
+        L.gp_cosmetic.restype = st
+        L.gp_deblend.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkg), C.POINTER(GpDetParams),
+                                 C.POINTER(GpDeblendParams), vp, C.POINTER(GpCatalog), C.POINTER(GpCatalog), vp, vp]
+        L.gp_deblend.restype = st
         L.gp_extract.argtypes = [vp, C.POINTER(GpImage), C.POINTER(GpBkgParams), C.POINTER(GpDetParams),
                                  C.POINTER(GpApParams), C.POINTER(GpBkg), vp, C.POINTER(GpCatalog), vp, vp, vp, vp]
         L.gp_extract.restype = st
@@ -425,6 +439,40 @@ class Context:
                                         r.ctypes.data_as(C.POINTER(C.c_int32)), r.size, float(gain),
                                         flux.data_ptr(), ferr.data_ptr(), fl.data_ptr(), _stream_handle(stream)))
         return flux[:n], ferr[:n], fl[:n]
+
+    def gp_deblend(self, img, bkg, kernel, thresh, minarea, segmap, catalog, nthresh=32, mincont=0.005,
+                   obj_capacity=100000, mask=None, saturation=0.0, stream=None):
+        """Multi-threshold deblending of `segmap` (modified in place) with its
+        catalog `catalog` (device columns and count "n"); returns the objects'
+        catalog and the counts (segments split, objects)."""
+        import torch
+        gi = make_image(img, mask, saturation)
+        k, kp = _taps(kernel)
+        dp = GpDetParams(kp, k.shape[1], k.shape[0], float(thresh), int(minarea), None, None)
+        cap = int(catalog["x"].numel())
+        cat = GpCatalog(cap, catalog["n"].data_ptr(), *[catalog[n].data_ptr() for n, _ in CATALOG_COLUMNS])
+        cols, ocat = allocate_catalog(obj_capacity, img.device)
+        counts = torch.zeros(2, dtype=torch.int32, device=img.device)
+        p = GpDeblendParams(int(nthresh), float(mincont))
+        b = self._bkg_struct(bkg)
+        _check(load_library().gp_deblend(self._h, C.byref(gi), C.byref(b), C.byref(dp), C.byref(p), segmap.data_ptr(),
+                                         C.byref(cat), C.byref(ocat), counts.data_ptr(), _stream_handle(stream)))
+        return {"objects": cols, "counts": counts}
+
+    def gp_cosmetic(self, img, rtn_t=0.0, cr_gain=0.0, cr_read_noise=0.0, cr_sigclip=4.5, cr_objlim=5.0, mask=None,
+                    stream=None):
+        """The cosmetic corrections (cosmic rays, then salt-and-pepper noise):
+        the corrected float32 frame, per-pixel flags and the two counts."""
+        import torch
+        gi = make_image(img, mask, 0.0)
+        H, W = img.shape
+        out = {"image": torch.empty((H, W), dtype=torch.float32, device=img.device),
+               "flags": torch.empty((H, W), dtype=torch.uint8, device=img.device),
+               "counts": torch.zeros(2, dtype=torch.int32, device=img.device)}
+        p = GpCosmeticParams(float(rtn_t), float(cr_gain), float(cr_read_noise), float(cr_sigclip), float(cr_objlim))
+        _check(load_library().gp_cosmetic(self._h, C.byref(gi), C.byref(p), out["image"].data_ptr(),
+                                          out["flags"].data_ptr(), out["counts"].data_ptr(), _stream_handle(stream)))
+        return out
 
     def gp_detect_psf(self, img, bkg, p0, modes, coef, tile, thresh, minarea, capacity, mask=None, saturation=0.0,
                       stream=None):

@@ -594,6 +594,89 @@ gp_status gp_growth(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const d
     return GP_OK;
 }
 
+gp_status gp_deblend(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_det_params* dp,
+                     const gp_deblend_params* p, uint32_t* segmap, const gp_catalog* cat, gp_catalog* objects,
+                     int32_t* counts, gp_stream stream)
+{
+    gp_status s;
+    float taps[(2 * HMAX + 1) * (2 * HMAX + 1)];
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if ((s = check_bkg(img, bkg, true)) != GP_OK) return s;
+    if ((s = check_det(dp, taps)) != GP_OK) return s;
+    if ((s = check_cat(cat)) != GP_OK) return s;
+    if ((s = check_cat(objects)) != GP_OK) return s;
+    if (!p || !segmap || !counts) return fail(GP_ERR_INVALID_ARG, "null deblending parameters, segmap or counts");
+    if (p->nthresh < 1 || p->nthresh > 64) return fail(GP_ERR_INVALID_ARG, "nthresh must be 1..64");
+    if (!(p->mincont >= 0.f && p->mincont <= 1.f)) return fail(GP_ERR_INVALID_ARG, "mincont must be in [0, 1]");
+    const int W = img->width, H = img->height;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    SplineTab sb, sr;
+    begin_call(ctx, st);
+    mark(ctx, 1, st);
+    s = run_spline(cv, bkg, W, H, &sb, &sr, &ctx->launches, st);
+    if (s == GP_ERR_OOM) return oom(cv);
+    if (s != GP_OK) return s;
+    const int rows = cat->capacity > 0 ? cat->capacity : 1;
+    DeblendWork w;
+    w.cand = cv.take<int>(rows);
+    w.cand_count = cv.take<int>(2);
+    w.obj_count = w.cand_count + 1;
+    w.off = cv.take<int64_t>(rows);
+    w.obj_cap = objects->capacity > 0 ? objects->capacity : 1;
+    w.obj = cv.take<DbObj>(w.obj_cap);
+    w.scratch = cv.take<char>(0);                     // 256-byte aligned; the rest of the arena
+    if (!cv.ok()) return oom(cv);
+    w.scratch_bytes = (int64_t)(cv.cap - cv.off);
+    mark_to(ctx, 2, GP_NSTAGES - 1, st);
+    GP_CUDA(launch_deblend(to_image(img), sb, sr, taps, dp->kw, dp->kh, dp->thresh, dp->minarea, p->nthresh,
+                           p->mincont, segmap, *cat, w, *objects, counts, ctx->dstatus, st));
+    ctx->launches += 4;
+    mark(ctx, GP_NSTAGES, st);
+    return GP_OK;
+}
+
+gp_status gp_cosmetic(gp_ctx* ctx, const gp_image* img, const gp_cosmetic_params* p, float* out, uint8_t* flags,
+                      int32_t* counts, gp_stream stream)
+{
+    gp_status s;
+    if ((s = check_ctx(ctx)) != GP_OK) return s;
+    if ((s = check_image(img)) != GP_OK) return s;
+    if (!p || !out) return fail(GP_ERR_INVALID_ARG, "null parameters or output");
+    const bool cr = p->cr_gain > 0.f, rtn = p->rtn_t > 0.f;
+    if (!cr && !rtn) return fail(GP_ERR_INVALID_ARG, "both cosmetic filters are off");
+    if (cr && (!(p->cr_read_noise > 0.f) || !std::isfinite(p->cr_gain) || !std::isfinite(p->cr_read_noise) ||
+               !std::isfinite(p->cr_sigclip) || !std::isfinite(p->cr_objlim)))
+        return fail(GP_ERR_INVALID_ARG, "cosmic-ray filter: finite parameters and read noise > 0 needed");
+    if (rtn && !std::isfinite(p->rtn_t)) return fail(GP_ERR_INVALID_ARG, "salt-and-pepper threshold not finite");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Carver cv{ctx->base, ctx->arena_bytes - STATUS_BYTES};
+    const int W = img->width, H = img->height;
+    float* mid = (cr && rtn) ? cv.take<float>((size_t)W * H) : nullptr;
+    if (!cv.ok()) return oom(cv);
+    begin_call(ctx, st);
+    if (counts) GP_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), st));
+    const Image im = to_image(img);
+    if (cr) {
+        GP_CUDA(launch_cr(im, p->cr_gain, p->cr_read_noise, p->cr_sigclip, p->cr_objlim, rtn ? mid : out, flags,
+                          counts ? counts + 1 : nullptr, st));
+        ctx->launches += 1;
+    }
+    if (rtn) {
+        Image ir = im;
+        if (cr) {
+            ir.data = mid;
+            ir.pitch = W;
+            ir.is_f32 = 1;
+        }
+        GP_CUDA(launch_rtn(ir, p->rtn_t, out, flags, cr, counts, st));
+        ctx->launches += 1;
+    }
+    mark_to(ctx, 1, GP_NSTAGES, st);
+    return GP_OK;
+}
+
 gp_status gp_detect_psf(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg, const gp_psf_params* p, uint32_t* segmap,
                         gp_catalog* cat, gp_stream stream)
 {
@@ -697,6 +780,7 @@ gp_status gp_optimal_radius(gp_ctx* ctx, const gp_image* img, const gp_bkg* bkg,
     w.start = cv.take<int>((size_t)ncx * ncy);
     w.fill = cv.take<int>((size_t)ncx * ncy);
     w.items = cv.take<int>(cat->capacity > 0 ? cat->capacity : 1);
+    w.xy = cv.take<double2>(cat->capacity > 0 ? cat->capacity : 1);
     if (!cv.ok()) return oom(cv);
     mark_to(ctx, 2, GP_NSTAGES - 1, st);
     if (cat->capacity > 0) {

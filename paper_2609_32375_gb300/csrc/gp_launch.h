@@ -55,10 +55,42 @@ cudaError_t launch_growth(const Image& im, const SplineTab& sb, const SplineTab&
 cudaError_t launch_psf(const DetectArgs& D, const float* p0, const float* modes, int nk, int kw, int kh,
                        const SplineTab* coef_tabs, cudaStream_t st);
 
+// cosmetic corrections (k_cosmetic.cu)
+cudaError_t launch_cr(const Image& im, float gain, float rn, float sigclip, float objlim, float* out, uint8_t* flags,
+                      int* count, cudaStream_t st);
+cudaError_t launch_rtn(const Image& im, float thr, float* out, uint8_t* flags, bool keep, int* count, cudaStream_t st);
+
+// multi-threshold deblending (k_deblend.cu): an object's catalog row before
+// the rows are put in label order, and the call's scratch
+struct DbObj {
+    uint32_t label, parent;
+    int npix;
+    double flux, x, y, x2, y2, xy;
+    int xmin, xmax, ymin, ymax;
+    float peak;
+    int xpeak, ypeak;
+    uint32_t flags;
+};
+struct DeblendWork {
+    int* cand;             // [rows] candidate rows
+    int* cand_count;       // [2] candidates, then the staged objects
+    int* obj_count;        // cand_count + 1
+    int64_t* off;          // [rows] bytes per candidate, then scratch offsets
+    DbObj* obj;            // [obj_cap] staged object rows
+    int obj_cap;
+    char* scratch;
+    int64_t scratch_bytes;
+};
+cudaError_t launch_deblend(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw,
+                           int kh, float thresh, int minarea, int nthresh, float mincont, uint32_t* seg,
+                           const gp_catalog& cat, const DeblendWork& w, const gp_catalog& objects, int* counts,
+                           int* status, cudaStream_t st);
+
 // optimal aperture radius (k_ropt.cu): the growth curves of the catalog rows
 // are given; scratch of the isolation grid from iso_grid()
 struct RoptWork {
     int *count, *start, *fill, *items;
+    double2* xy;          // [rows] (log10 nu, log10 r) of the calibrators
 };
 void iso_grid(int W, int H, float d_iso, double* cs, int* ncx, int* ncy);
 cudaError_t launch_ropt(const Image& im, const SplineTab& sb, const SplineTab& sr, const float* taps, int kw, int kh,

@@ -505,7 +505,16 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 5) k_label_t
             }
         }
         __syncwarp();
-        for (int q = rb; q < rb + nr; ++q) S.par[q] = lfind(S.par, q);
+        // flatten in two phases: the roots (found with path halving) go to
+        // cnt first, then into par once every lane's walks are over -- a
+        // halving store from a stale read can then never land on a root
+        // that another lane has already written
+        for (int q = rb; q < rb + nr; ++q) S.cnt[q] = lfind(S.par, q);
+        __syncwarp();
+        for (int q = rb; q < rb + nr; ++q) {
+            S.par[q] = S.cnt[q];
+            S.cnt[q] = 0;
+        }
         __syncwarp();
         // ---- pixels and shared-edge contact per root, one atomic per run
         {

@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(256) k_iso_calib(const double* __restrict__ xs
                                                    const uint32_t* __restrict__ cflags,
                                                    const uint32_t* __restrict__ gflags, const double* __restrict__ flux,
                                                    const double* __restrict__ ferr, const float* __restrict__ nu,
-                                                   const int* __restrict__ kopt, int nr, double snr_min, uint8_t* calib)
+                                                   const int* __restrict__ kopt, int nr, double snr_min,
+                                                   const __grid_constant__ RoptRadii rad, uint8_t* calib, double2* xy)
 {
     const int n = min(*n_dev, cap);
     const double d2 = d_iso * d_iso;
@@ -180,6 +181,9 @@ __global__ void __launch_bounds__(256) k_iso_calib(const double* __restrict__ xs
             ok = (e > 0.0 ? flux[(int64_t)i * nr + k] / e : 0.0) >= snr_min;
         }
         calib[i] = ok ? 1 : 0;
+        // the fit's coordinates of a calibrator, here where every row has a
+        // thread (float64 logarithms are slow; the fit is one CTA)
+        if (ok) xy[i] = make_double2(log10((double)nu[i]), log10((double)rad.r[kopt[i]]));
     }
 }
 
@@ -199,9 +203,8 @@ __device__ double block_sum(double v, double* red)
 }
 
 __global__ void __launch_bounds__(FIT_NT) k_ropt_fit(const int* __restrict__ n_dev, int cap,
-                                                    const uint8_t* __restrict__ calib, const float* __restrict__ nu,
-                                                    const int* __restrict__ kopt,
-                                                    const __grid_constant__ RoptRadii rad, double* fit)
+                                                    const uint8_t* __restrict__ calib,
+                                                    const double2* __restrict__ xy, double* fit)
 {
     __shared__ double red[FIT_NT];
     const int n = min(*n_dev, cap);
@@ -209,7 +212,8 @@ __global__ void __launch_bounds__(FIT_NT) k_ropt_fit(const int* __restrict__ n_d
     double c = 0.0, sx = 0.0, sy = 0.0, xmin = INFINITY, xmax = -INFINITY;
     for (int i = t; i < n; i += FIT_NT) {
         if (!calib[i]) continue;
-        const double x = log10((double)nu[i]), y = log10((double)rad.r[kopt[i]]);
+        const double2 q = xy[i];
+        const double x = q.x, y = q.y;
         c += 1.0; sx += x; sy += y;
         xmin = fmin(xmin, x); xmax = fmax(xmax, x);
     }
@@ -240,7 +244,8 @@ __global__ void __launch_bounds__(FIT_NT) k_ropt_fit(const int* __restrict__ n_d
     double sxx = 0.0, sxy = 0.0;
     for (int i = t; i < n; i += FIT_NT) {
         if (!calib[i]) continue;
-        const double dx = log10((double)nu[i]) - mx, dy = log10((double)rad.r[kopt[i]]) - my;
+        const double2 q = xy[i];
+        const double dx = q.x - mx, dy = q.y - my;
         sxx = fma(dx, dx, sxx);
         sxy = fma(dx, dy, sxy);
     }
@@ -323,8 +328,8 @@ cudaError_t launch_ropt(const Image& im, const SplineTab& sb, const SplineTab& s
     k_iso_scan<<<1, 1024, 0, st>>>(w.count, ncell, w.start, w.fill);
     k_iso_fill<<<grid, 256, 0, st>>>(cat.x, cat.y, cat.n, cap, cs, ncx, ncy, w.start, w.fill, w.items);
     k_iso_calib<<<grid, 256, 0, st>>>(cat.x, cat.y, cat.n, cap, cs, ncx, ncy, (double)d_iso, w.start, w.count, w.items,
-                                      cat.flags, gflags, flux, ferr, nu, kopt, nr, (double)snr_min, calib);
-    k_ropt_fit<<<1, FIT_NT, 0, st>>>(cat.n, cap, calib, nu, kopt, R, fit);
+                                      cat.flags, gflags, flux, ferr, nu, kopt, nr, (double)snr_min, R, calib, w.xy);
+    k_ropt_fit<<<1, FIT_NT, 0, st>>>(cat.n, cap, calib, w.xy, fit);
     k_ropt_assign<<<grid, 256, 0, st>>>(cat.n, cap, calib, nu, kopt, R, fit, flux, ferr, kfinal, flux_opt, ferr_opt);
     return cudaGetLastError();
 }
