@@ -256,7 +256,7 @@ __device__ __forceinline__ void comp_store_raw(const Comps& C, int id, DF s, DF 
 // every tile fits (1024 runs, 2048 pixels).
 template <bool BIG>
 struct LabelCfg {
-    static constexpr int NW = BIG ? 2 : 4;
+    static constexpr int NW = 2;
     static constexpr int RUNS = BIG ? MAXRUN : 256;
     static constexpr int FG = BIG ? TX * TY : LT_FG;
 };
@@ -378,7 +378,7 @@ __device__ __forceinline__ bool pix_sat(const DetectArgs& A, bool async, uint32_
 }
 
 template <bool LABEL_ONLY, bool BATCH, bool BIG>
-__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 5) k_label_tiles(const DetectArgs* __restrict__ batch,
+__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_tiles(const DetectArgs* __restrict__ batch,
                                                                         const __grid_constant__ DetectArgs one,
                                                                         int late)
 {
@@ -1153,9 +1153,10 @@ static int stride_grid(int per_frame, int nframes)
     return g < 16 ? 16 : g;
 }
 
-// the labelling kernel's persistent grids: the common form at five CTAs of
-// four warps per SM, the big form (crowded tiles) at four CTAs of two warps
-constexpr int LT_CTAS = 152 * 5;
+// the labelling kernel's persistent grids: the common form at ten CTAs of two
+// warps per SM (two warps per CTA let ten CTAs' shared memory fit, against
+// four of four warps), the big form (crowded tiles) at four CTAs of two warps
+constexpr int LT_CTAS = 152 * 10;
 constexpr int LT_BIG_CTAS = 152 * 4;
 constexpr int LT_LATE_CTAS = 152;         // the deferred tiles: few or none
 
