@@ -226,6 +226,30 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
         const double nu_max = red[0];
         __syncthreads();
         if (!(total > 0) || !(nu_max > (double)A.thresh)) continue;
+        // a branch always holds a local maximum of nu (its largest value), so a
+        // segment with fewer than two (plateaus counted per pixel) cannot split
+        int nmax = 0;
+        for (int q = t; q < Ar; q += DB_NT) {
+            const float v = s.nu[q];
+            if (v == -INFINITY) continue;
+            const int qy = q / w, qx = q - qy * w;
+            bool mx = true;
+            for (int dy = -1; dy <= 1 && mx; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int yy = qy + dy, xx = qx + dx;
+                    if ((dy || dx) && yy >= 0 && yy < h && xx >= 0 && xx < w && s.nu[yy * w + xx] > v) { mx = false; break; }
+                }
+            nmax += mx ? 1 : 0;
+        }
+        redl[t] = nmax;
+        __syncthreads();
+        for (int o = DB_NT / 2; o > 0; o >>= 1) {
+            if (t < o) redl[t] += redl[t + o];
+            __syncthreads();
+        }
+        const long long nmaxima = redl[0];
+        __syncthreads();
+        if (nmaxima < 2) continue;
         const double cthr = A.mincont * (double)total;
         const double lr = log(nu_max / (double)A.thresh);
         // ---- the branch tree, one level at a time
