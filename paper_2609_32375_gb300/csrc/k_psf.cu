@@ -12,10 +12,11 @@
 // A CTA takes one 128-column strip and one 32-row tile band.  m over the band
 // and a halo of KS/2 is formed in shared memory (B from per-row and
 // per-column spline coefficients); a thread takes one column and 8 rows and
-// correlates them with each kernel in turn: per tap column it loads the
-// 8 + KS - 1 values of its column once and applies the KS taps of that column
-// to its 8 rows from registers.  The taps (zero-padded to KS x KS, centred)
-// are kernel parameters.
+// correlates them with two kernels at a time: per tap column it loads the
+// 8 + KS - 1 values of its column once and applies the KS tap pairs of that
+// column to its 8 rows with paired FMAs (each half rounds as one fmaf, so the
+// results do not depend on the pairing).  The taps (zero-padded to KS x KS,
+// centred) are kernel parameters.
 #include <math.h>
 #include <string.h>
 
@@ -29,6 +30,21 @@ constexpr int PS_COLS = ST_STRIP;           // columns: one mask strip (two tile
 constexpr int PS_RPT = 8;                   // rows per thread
 constexpr int PS_NT = PS_COLS * (PS_ROWS / PS_RPT);   // 512 threads
 
+// two FMAs with one rounding each, in one instruction (Blackwell's paired
+// FP32 path): the lanes of a pair are independent, so the results are those
+// of two fmaf
+__device__ __forceinline__ float2 psf_ffma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return *reinterpret_cast<float2*>(&d);
+}
+
+constexpr int PS_NPAIR = (GP_PSF_MAX_MODES + 2) / 2;   // kernel pairs (P0 and the modes, a zero kernel last if odd)
+
 struct PsfArgs {
     Image im;
     SplineTab sb, sr;
@@ -41,7 +57,7 @@ struct PsfArgs {
     int* tl_list;
     int* tl_count;
     Tiles T;
-    float taps[GP_PSF_MAX_MODES + 1][KMAX];  // P0, then the modes, each KS x KS
+    float2 taps[PS_NPAIR][KMAX];             // kernels 2p and 2p + 1 of P0, then the modes, each KS x KS
 };
 
 template <bool F32, int KS>
@@ -100,40 +116,53 @@ __global__ void __launch_bounds__(PS_NT) k_psf(const __grid_constant__ PsfArgs A
     float S[PS_RPT];
 #pragma unroll
     for (int r = 0; r < PS_RPT; ++r) S[r] = 0.f;
-    for (int k = 0; k <= A.nk; ++k) {
-        float F[PS_RPT];
+    const int npair = (A.nk + 2) / 2;
+    for (int pr = 0; pr < npair; ++pr) {
+        // kernels 2 pr and 2 pr + 1 together: one paired FMA per tap and row
+        float2 F2[PS_RPT];
 #pragma unroll
-        for (int r = 0; r < PS_RPT; ++r) F[r] = 0.f;
+        for (int r = 0; r < PS_RPT; ++r) F2[r] = make_float2(0.f, 0.f);
 #pragma unroll UNROLL_U
         for (int u = 0; u < KS; ++u) {
-            float w[PS_RPT + KS - 1];
+            float2 w[PS_RPT + KS - 1];
 #pragma unroll
-            for (int q = 0; q < PS_RPT + KS - 1; ++q) w[q] = ms[r0 + q][col + u];
+            for (int q = 0; q < PS_RPT + KS - 1; ++q) {
+                const float a = ms[r0 + q][col + u];
+                w[q] = make_float2(a, a);
+            }
 #pragma unroll
             for (int v = 0; v < KS; ++v) {
-                const float tap = A.taps[k][v * KS + u];
+                const float2 tap = A.taps[pr][v * KS + u];
 #pragma unroll
-                for (int r = 0; r < PS_RPT; ++r) F[r] = fmaf(tap, w[r + v], F[r]);
+                for (int r = 0; r < PS_RPT; ++r) F2[r] = psf_ffma2(tap, w[r + v], F2[r]);
             }
         }
-        if (k == 0) {
 #pragma unroll
-            for (int r = 0; r < PS_RPT; ++r) S[r] = F[r];
-        } else {
-            const SplineTab& ct = A.ct[k - 1];
-            const AxCoef cx = axis_coef(ct.ax, (float)xq);
-            int jc = -1;
-            float u0 = 0.f, u1 = 0.f, w0 = 0.f, w1 = 0.f;
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * pr + h;
+            if (k > A.nk) break;
+            float F[PS_RPT];
 #pragma unroll
-            for (int r = 0; r < PS_RPT; ++r) {
-                const int y = min(Y0 + r0 + r, Hf - 1);
-                const AxCoef cy = axis_coef(ct.ay, (float)y);
-                if (cy.i != jc) {
-                    const float2 a0 = row_eval(ct, cy.i, cx), a1 = row_eval(ct, cy.i1, cx);
-                    u0 = a0.x; w0 = a0.y; u1 = a1.x; w1 = a1.y;
-                    jc = cy.i;
+            for (int r = 0; r < PS_RPT; ++r) F[r] = h ? F2[r].y : F2[r].x;
+            if (k == 0) {
+#pragma unroll
+                for (int r = 0; r < PS_RPT; ++r) S[r] = F[r];
+            } else {
+                const SplineTab& ct = A.ct[k - 1];
+                const AxCoef cx = axis_coef(ct.ax, (float)xq);
+                int jc = -1;
+                float u0 = 0.f, u1 = 0.f, w0 = 0.f, w1 = 0.f;
+#pragma unroll
+                for (int r = 0; r < PS_RPT; ++r) {
+                    const int y = min(Y0 + r0 + r, Hf - 1);
+                    const AxCoef cy = axis_coef(ct.ay, (float)y);
+                    if (cy.i != jc) {
+                        const float2 a0 = row_eval(ct, cy.i, cx), a1 = row_eval(ct, cy.i1, cx);
+                        u0 = a0.x; w0 = a0.y; u1 = a1.x; w1 = a1.y;
+                        jc = cy.i;
+                    }
+                    S[r] = fmaf(axis_combine(cy, u0, u1, w0, w1), F[r], S[r]);
                 }
-                S[r] = fmaf(axis_combine(cy, u0, u1, w0, w1), F[r], S[r]);
             }
         }
     }
@@ -199,7 +228,11 @@ cudaError_t launch_psf(const DetectArgs& D, const float* p0, const float* modes,
     for (int k = 0; k <= nk; ++k) {
         const float* src = k == 0 ? p0 : modes + (size_t)(k - 1) * kw * kh;
         for (int v = 0; v < kh; ++v)
-            for (int u = 0; u < kw; ++u) A.taps[k][(v + oy) * ks + (u + ox)] = src[v * kw + u];
+            for (int u = 0; u < kw; ++u) {
+                float2& t = A.taps[k / 2][(v + oy) * ks + (u + ox)];
+                if (k & 1) t.y = src[v * kw + u];
+                else t.x = src[v * kw + u];
+            }
     }
     const dim3 g((D.im.W + PS_COLS - 1) / PS_COLS, (D.im.H + PS_ROWS - 1) / PS_ROWS);
     const bool f32 = D.im.is_f32;
