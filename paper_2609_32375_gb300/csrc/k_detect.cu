@@ -726,6 +726,29 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_
 }
 
 // ------------------------------------------------------------ tile merge ---
+// The contacts across one tile edge: a[i] is this tile's edge pixel i and b[k]
+// the neighbour's facing pixel k (local piece indices, -1 off the foreground),
+// 8-connected (k = i - 1, i, i + 1).  A pixel's contact is skipped where the
+// same pair of pieces is united by its straight contact or by the straight
+// contact of the pixel before (i - 1) or after (i + 1): a run of pixels along
+// the edge then unites each pair of pieces once instead of up to three times
+// per pixel.  (Every skipped pair is united by a straight contact that is
+// itself kept or skipped only for an identical pair at a lower index.)
+__device__ __forceinline__ void unite_edge(const int16_t* a, const int16_t* b, int n, int base, int nbase, int lane,
+                                           int* parent, int lim, int* status)
+{
+    for (int i = lane; i < n; i += 32) {
+        const int ai = a[i];
+        if (ai < 0) continue;
+        const int bi = b[i];
+        const int ap = i > 0 ? a[i - 1] : -1, bp = i > 0 ? b[i - 1] : -1;
+        const int an = i + 1 < n ? a[i + 1] : -1, bn = i + 1 < n ? b[i + 1] : -1;
+        if (bi >= 0 && !(ap == ai && bp == bi)) gunite(parent, base + ai, nbase + bi, lim, status);
+        if (bp >= 0 && bp != bi && ap != ai) gunite(parent, base + ai, nbase + bp, lim, status);
+        if (bn >= 0 && bn != bi && an != ai) gunite(parent, base + ai, nbase + bn, lim, status);
+    }
+}
+
 // One warp per listed tile with pieces: its right and bottom edges and its
 // two lower diagonal corners against the neighbouring tiles' edge records
 // (a tile without pieces records none).
@@ -747,34 +770,12 @@ __global__ void k_merge(const ResolveArgs* __restrict__ batch, const __grid_cons
         const int tw = min(TX, W - tx * TX), th = min(TY, H - ty * TY);
         const int base = T.piece_base[tile];
         const int16_t* e = T.edges + (int64_t)tile * EDGE_PER_TILE;
-        if (tx + 1 < ntx && T.piece_cnt[tile + 1] > 0) {
-            const int nbase = T.piece_base[tile + 1];
-            const int16_t* en = T.edges + (int64_t)(tile + 1) * EDGE_PER_TILE;
-            for (int i = lane; i < th; i += 32) {
-                const int a = e[TY + i];
-                if (a < 0) continue;
-                for (int d = -1; d <= 1; ++d) {
-                    const int k = i + d;
-                    if (k < 0 || k >= th) continue;
-                    const int b = en[k];
-                    if (b >= 0) gunite(P.parent, base + a, nbase + b, lim, status);
-                }
-            }
-        }
-        if (ty + 1 < nty && T.piece_cnt[tile + ntx] > 0) {
-            const int nbase = T.piece_base[tile + ntx];
-            const int16_t* en = T.edges + (int64_t)(tile + ntx) * EDGE_PER_TILE;
-            for (int j = lane; j < tw; j += 32) {
-                const int a = e[2 * TY + TX + j];
-                if (a < 0) continue;
-                for (int d = -1; d <= 1; ++d) {
-                    const int k = j + d;
-                    if (k < 0 || k >= tw) continue;
-                    const int b = en[2 * TY + k];
-                    if (b >= 0) gunite(P.parent, base + a, nbase + b, lim, status);
-                }
-            }
-        }
+        if (tx + 1 < ntx && T.piece_cnt[tile + 1] > 0)      // right column against the left one of the tile right
+            unite_edge(e + TY, T.edges + (int64_t)(tile + 1) * EDGE_PER_TILE, th, base, T.piece_base[tile + 1],
+                       lane, P.parent, lim, status);
+        if (ty + 1 < nty && T.piece_cnt[tile + ntx] > 0)    // bottom row against the top one of the tile below
+            unite_edge(e + 2 * TY + TX, T.edges + (int64_t)(tile + ntx) * EDGE_PER_TILE + 2 * TY, tw, base,
+                       T.piece_base[tile + ntx], lane, P.parent, lim, status);
         if (lane == 0 && ty + 1 < nty) {
             // bottom-right pixel of this tile and top-left pixel of the tile below-right
             if (tx + 1 < ntx && T.piece_cnt[tile + ntx + 1] > 0) {
@@ -804,6 +805,9 @@ __global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_
         P.proot[p] = r;
         if (r < 0) { set_status(status, GP_ERR_TIMEOUT); continue; }
         if (r == p) continue;
+        // the unions are done: pointing p at its root shortens the other
+        // threads' walks through p (they read the old parent or the root)
+        P.parent[p] = r;
         atomicMin(P.agg_min + r, P.root[p]);
         atomicAdd(P.agg_npix + r, P.npix[p]);
         const int4 b = P.bbox[p];
@@ -942,12 +946,25 @@ __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_c
         }
         const uint32_t prov = P.root[p] + 1u;
         if (fin == prov) continue;
+        // the piece's box, 8 pixels per lane at a time: all loads first, then
+        // the stores (a pixel of another label is never this piece's, and
+        // this piece's pixels are rewritten by this warp only)
         const int4 b = P.bbox[p];
-        const int bw = b.y - b.x + 1, bh = b.w - b.z + 1;
-        for (int q = lane; q < bw * bh; q += 32) {
-            const int y = b.z + q / bw, x = b.x + q % bw;
-            uint32_t* sp = seg + (int64_t)y * W + x;
-            if (*sp == prov) *sp = fin;
+        const int bw = b.y - b.x + 1, npx = bw * (b.w - b.z + 1);
+        constexpr int RW = 8;
+        for (int q0 = lane; q0 < npx; q0 += 32 * RW) {
+            uint32_t v[RW];
+            int64_t off[RW];
+#pragma unroll
+            for (int j = 0; j < RW; ++j) {
+                const int q = q0 + 32 * j;
+                const int y = b.z + q / bw, x = b.x + q % bw;
+                off[j] = (int64_t)y * W + x;
+                v[j] = q < npx ? seg[off[j]] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < RW; ++j)
+                if (v[j] == prov) seg[off[j]] = fin;
         }
     }
 }
