@@ -566,28 +566,55 @@ __global__ void __launch_bounds__(WB_NT, 8) k_boxstats_win(const BoxArgs* __rest
     };
     const int nchunks = cpr * bh;
     if (vec) {
+        // 16-byte chunks (8 values); a thread's (row, chunk) advance by the
+        // fixed step of one pass of the CTA, without a division per chunk.
+        // Both values of a 32-bit word inside the window (the common case)
+        // cost a subtraction and a shared atomic each; the rest go through
+        // count().  The range of the window's values comes from the
+        // histogram afterwards, so only values outside it update vmin/vmax.
         constexpr int U = 4;
-        for (int c0 = tid; c0 < nchunks; c0 += U * WB_NT) {
+        const int dr = WB_NT / cpr, dc = WB_NT - dr * cpr;
+        int ry = tid / cpr, rc = tid - ry * cpr;
+        while (ry < bh) {
             uint4 q[U];
+            int nq = 0;
 #pragma unroll
             for (int kk = 0; kk < U; ++kk) {
-                const int c = c0 + kk * WB_NT;
-                if (c < nchunks) {
-                    const int ry = c / cpr, rc = c - ry * cpr;
+                if (ry < bh) {
                     q[kk] = __ldg(reinterpret_cast<const uint4*>(img + (int64_t)(y0 + ry) * pitch + x0 + rc * 8));
+                    ++nq;
                 }
+                rc += dc;
+                ry += dr;
+                if (rc >= cpr) { rc -= cpr; ++ry; }
             }
 #pragma unroll
             for (int kk = 0; kk < U; ++kk) {
-                if (c0 + kk * WB_NT >= nchunks) break;
+                if (kk >= nq) break;
                 const uint32_t w4[4] = {q[kk].x, q[kk].y, q[kk].z, q[kk].w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    count(w4[e] & 0xffffu);
-                    count(w4[e] >> 16);
+                    const uint32_t u0 = w4[e] & 0xffffu, u1 = w4[e] >> 16;
+                    const uint32_t d0 = u0 - w0, d1 = u1 - w0;
+                    if ((d0 | d1) < (uint32_t)NWIN) {          // NWIN is a power of two
+                        atomicAdd(&win[d0], 1u);
+                        atomicAdd(&win[d1], 1u);
+                    } else {
+                        count(u0);
+                        count(u1);
+                        ngood -= 2u;                           // counted per chunk below
+                    }
                 }
+                ngood += 8u;
             }
         }
+        __syncthreads();
+        // the smallest and largest value held in the window
+        for (int w = tid; w < NWIN; w += WB_NT)
+            if (win[w]) {
+                vmin = min(vmin, w0 + (uint32_t)w);
+                vmax = max(vmax, w0 + (uint32_t)w);
+            }
     } else {
         for (int c = tid; c < nchunks; c += WB_NT) {
             const int ry = c / cpr, rc = c - ry * cpr;
