@@ -79,8 +79,7 @@ struct StreamSmem {
     static constexpr size_t ring_bytes = sizeof(float) * 2 * G * ST_RW;
     static constexpr size_t rowc = ring + ring_bytes;
     static constexpr size_t rowj = rowc + sizeof(float4) * ROWS;
-    static constexpr size_t thr = (rowj + sizeof(int2) * ROWS + 15) & ~(size_t)15;     // k sigma of a group's output rows
-    static constexpr size_t bar = (thr + sizeof(float) * G * ST_COLS + 127) & ~(size_t)127;
+    static constexpr size_t bar = (rowj + sizeof(int2) * ROWS + 127) & ~(size_t)127;
     static constexpr size_t stage = bar + 128;
     __host__ __device__ static constexpr size_t box_bytes(int esz) { return ((size_t)ST_BOXW * G * esz + 127) & ~(size_t)127; }
     __host__ __device__ static constexpr size_t total(int esz) { return stage + (size_t)ST_STAGES * 3 * box_bytes(esz); }
@@ -423,11 +422,10 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
     }
 
     // per-lane spline state: background at the input rows' node interval
-    // (cb; the side columns' in hcoef), k sigma at the output rows' (cs);
-    // the k sigma of a group's output rows wait in thrb for the filter pass
+    // (cb; the side columns' in hcoef), k sigma at the output rows' (cs),
+    // evaluated where each output row is thresholded
     Col4 cb, cs;
     float4 hcb = make_float4(0.f, 0.f, 0.f, 0.f);      // side column's background spline values
-    float* thrb = reinterpret_cast<float*>(smem + SM::thr);
     int jb = -1, js = -1, jh = -1;
     uint64_t badh = 0;
     const int nstrip = A.nstrip;
@@ -453,8 +451,7 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
         bool timed_out = false;
         if (TMA) timed_out = !mbar_wait(bar + g % ST_STAGES, (uint32_t)((g / ST_STAGES) & 1));
 
-        // ---- m = I - B for the group's rows (a bad pixel contributes 0), and
-        // k sigma of the output rows this group completes (row k - 2h)
+        // ---- m = I - B for the group's rows (a bad pixel contributes 0)
 #pragma unroll 1
         for (int s = 0; s < G; ++s) {
             const int k = g * G + s;
@@ -482,17 +479,6 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
                 if (HIST) badh = (badh << 4) | nib;
             }
             *reinterpret_cast<float4*>(rg + s * ST_RW + slot0) = make_float4(m[0], m[1], m[2], m[3]);
-            const int y = k - 2 * H;
-            if (y >= 0 && y < nout) {
-                const int2 jy = rowj[y + H];
-                const float4 ry = rowc[y + H];
-                if (jy.x != js) {
-                    cs = col4_load(A.sr, jy.x, jy.y, xs, W, A.thresh);
-                    js = jy.x;
-                }
-                const float2 t01 = col4_eval2(cs, ry, 0), t23 = col4_eval2(cs, ry, 1);
-                *reinterpret_cast<float4*>(thrb + s * ST_COLS + slot0 - ST_HALO) = make_float4(t01.x, t01.y, t23.x, t23.y);
-            }
             if (hl) {
                 if (j.x != jh) {
                     hcb = col1_load(A.sb, j.x, j.y, hx, W);
@@ -599,8 +585,15 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
             const int Y = Y0 + y;
             const float F[4] = {acc[(s + 1) % KS][0].x, acc[(s + 1) % KS][0].y, acc[(s + 1) % KS][1].x,
                                 acc[(s + 1) % KS][1].y};
-            const float4 tq = *reinterpret_cast<const float4*>(thrb + s * ST_COLS + slot0 - ST_HALO);
-            const float tv4[4] = {tq.x, tq.y, tq.z, tq.w};
+            // k sigma of the output row
+            const int2 jy = rowj[y + H];
+            const float4 ry = rowc[y + H];
+            if (jy.x != js) {
+                cs = col4_load(A.sr, jy.x, jy.y, xs, W, A.thresh);
+                js = jy.x;
+            }
+            const float2 t01 = col4_eval2(cs, ry, 0), t23 = col4_eval2(cs, ry, 1);
+            const float tv4[4] = {t01.x, t01.y, t23.x, t23.y};
             bool fg[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
