@@ -8,6 +8,33 @@
 
 namespace gp {
 
+// ------------------------------------------- programmatic dependent launch ---
+// A kernel launched by launch_dep may be scheduled while the kernel before it
+// in the stream is finishing.  pdl_wait() blocks until that kernel has
+// completed and its memory is visible; every such kernel calls it before its
+// first access to global memory.  pdl_release() lets the next kernel start
+// being scheduled (it still waits in its own pdl_wait()).  Both are no-ops in
+// a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KP, typename... A>
+static inline cudaError_t launch_dep(void (*k)(KP...), dim3 g, dim3 b, size_t smem, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t c = {};
+    c.gridDim = g;
+    c.blockDim = b;
+    c.dynamicSmemBytes = smem;
+    c.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    return cudaLaunchKernelEx(&c, k, static_cast<A&&>(args)...);
+}
+
+
 // --------------------------------------------------- float64 reciprocals ---
 // Float64 runs at a small fraction of the float32 rate on this GPU, and a
 // float64 division or square root is a long instruction sequence.  These

@@ -185,6 +185,8 @@ __device__ void boxstats_u16_box(const BoxArgs& A, int box, uint32_t* hist);
 // listed there): the full 65,536-bin histogram in shared memory.
 __global__ void __launch_bounds__(U16_NT, 1) k_boxstats_u16(const BoxArgs* __restrict__ batch, const __grid_constant__ BoxArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const BoxArgs& A = frame_args(batch, one);
     extern __shared__ uint32_t hist[];                    // U16_WORDS
     const bool listed = A.fb_list != nullptr;
@@ -464,6 +466,8 @@ struct WinHist {
 __global__ void __launch_bounds__(WB_NT, 8) k_boxstats_win(const BoxArgs* __restrict__ batch,
                                                         const __grid_constant__ BoxArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const BoxArgs& A = frame_args(batch, one);
     const int box = blockIdx.x;
     if (box >= A.nbox) return;
@@ -1098,6 +1102,8 @@ __device__ void solve_line(const AxisLU& L, int n, const float* v, int vs, float
 __global__ void __launch_bounds__(MA_NT) k_mesh_all(const MeshArgs* __restrict__ batch,
                                                     const __grid_constant__ MeshArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const MeshArgs& MA = frame_args(batch, one);
     const double* __restrict__ bkg_raw = MA.bkg_raw;
     const double* __restrict__ rms_raw = MA.rms_raw;
@@ -1299,7 +1305,7 @@ MeshArgs mesh_args(const double* bkg_raw, const double* rms_raw, const int* vali
 cudaError_t launch_mesh_all_any(const MeshArgs& one, const MeshArgs* batch, int nframes, size_t smem, cudaStream_t st)
 {
     cudaFuncSetAttribute(k_mesh_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mesh_all<<<dim3(1, nframes), MA_NT, smem, st>>>(batch, one);
+    launch_dep(k_mesh_all, dim3(1, nframes), dim3(MA_NT), smem, st, batch, one);
     return cudaGetLastError();
 }
 
@@ -1337,10 +1343,10 @@ cudaError_t launch_boxstats_any(const BoxArgs& one, const BoxArgs* batch, int nf
     if (!is_f32 && one.fb_list) {
         // windowed histograms, then the full histogram for the boxes they
         // could not finish (a persistent grid over the fallback lists)
-        k_boxstats_win<<<grid, WB_NT, 0, st>>>(batch, one);
+        launch_dep(k_boxstats_win, grid, dim3(WB_NT), 0, st, batch, one);
         const size_t smem = U16_WORDS * sizeof(uint32_t);
         cudaFuncSetAttribute(k_boxstats_u16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_boxstats_u16<<<dim3(maxbox < 152 ? maxbox : 152, nframes), U16_NT, smem, st>>>(batch, one);
+        launch_dep(k_boxstats_u16, dim3(maxbox < 152 ? maxbox : 152, nframes), dim3(U16_NT), smem, st, batch, one);
         return cudaGetLastError();
     }
     if (!is_f32) {

@@ -382,6 +382,8 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_
                                                                         const __grid_constant__ DetectArgs one,
                                                                         int late)
 {
+    pdl_wait();
+    pdl_release();
     using Cfg = LabelCfg<BIG>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -754,6 +756,8 @@ __device__ __forceinline__ void unite_edge(const int16_t* a, const int16_t* b, i
 // (a tile without pieces records none).
 __global__ void k_merge(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const ResolveArgs& R = frame_args(batch, one);
     const Tiles& T = R.T;
     const Pieces& P = R.P;
@@ -796,6 +800,8 @@ __global__ void k_merge(const ResolveArgs* __restrict__ batch, const __grid_cons
 // --------------------------------------------------------- piece resolve ---
 __global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const ResolveArgs& R = frame_args(batch, one);
     const Pieces& P = R.P;
     int* status = R.status;
@@ -825,6 +831,8 @@ __global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_
 // from its provisional one rewrites its pixels in the map.
 __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const ResolveArgs& R = frame_args(batch, one);
     const Tiles& T = R.T;
     const Pieces& P = R.P;
@@ -974,6 +982,8 @@ __global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_c
 // found and carry GP_FLAG_CENTROID_FALLBACK.
 __global__ void k_mom_finish(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const ResolveArgs& R = frame_args(batch, one);
     const Comps& C = R.C;
     const int n = min(*C.count, C.cap);
@@ -998,6 +1008,8 @@ __global__ void k_mom_finish(const ResolveArgs* __restrict__ batch, const __grid
 // ------------------------------------------------------------------ rank ---
 __global__ void k_rank_count(const RankArgs* __restrict__ batch, const __grid_constant__ RankArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const Comps& C = frame_args(batch, one).C;
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
@@ -1013,6 +1025,8 @@ constexpr int SCAN_NT = 1024;
 __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restrict__ batch,
                                                        const __grid_constant__ RankArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const RankArgs& R = frame_args(batch, one);
     const Comps& C = R.C;
     int* n_out = R.n_out;
@@ -1082,6 +1096,8 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restric
 
 __global__ void k_rank_scatter(const RankArgs* __restrict__ batch, const __grid_constant__ RankArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const Comps& C = frame_args(batch, one).C;
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
@@ -1093,6 +1109,8 @@ __global__ void k_rank_scatter(const RankArgs* __restrict__ batch, const __grid_
 
 __global__ void k_rank_place(const RankArgs* __restrict__ batch, const __grid_constant__ RankArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const Comps& C = frame_args(batch, one).C;
     const int n = min(*C.count, C.cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
@@ -1186,6 +1204,8 @@ template <bool BATCH>
 __global__ void __launch_bounds__(256) k_tile_census(const DetectArgs* __restrict__ batch,
                                                      const __grid_constant__ DetectArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const DetectArgs& A = det_frame<BATCH>(batch, one);
     const int lane = threadIdx.x & 31;
     const int ntl = *A.tl_count;
@@ -1211,7 +1231,7 @@ static void launch_label(const DetectArgs& one, const DetectArgs* batch, dim3 g,
     const size_t smem = sizeof(LabelSmem<BIG>) * LabelCfg<BIG>::NW;
     auto* fn = k_label_tiles<LO, BATCH, BIG>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fn<<<g, 32 * LabelCfg<BIG>::NW, smem, st>>>(batch, one, late);
+    launch_dep(fn, g, dim3(32 * LabelCfg<BIG>::NW), smem, st, batch, one, late);
 }
 
 // The census of the listed tiles, then the common form on `st` and the
@@ -1228,7 +1248,7 @@ static cudaError_t launch_label_forms(const DetectArgs& one, const DetectArgs* b
     const dim3 gl(BATCH ? stride_grid(LT_LATE_CTAS, nframes) : LT_LATE_CTAS, nframes);
     cudaError_t e = cudaSuccess;
     if (!LO) {
-        k_tile_census<BATCH><<<gc, 256, 0, st>>>(batch, one);
+        launch_dep(k_tile_census<BATCH>, gc, dim3(256), 0, st, batch, one);
         if (side) {
             if ((e = cudaEventRecord(side->fork, st)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(side->st, side->fork, 0)) != cudaSuccess) return e;
@@ -1271,10 +1291,10 @@ cudaError_t launch_resolve_any(const ResolveArgs& one, const ResolveArgs* batch,
     const dim3 g(stride_grid(152 * 8, nframes), nframes);
     // the merge: one warp per listed tile (latency-bound chains), up to 152 x 32 CTAs of 4 warps
     const int mcta = std::min((maxtiles + 3) / 4, 152 * 32);
-    k_merge<<<dim3(std::max(1, mcta / (nframes > 1 ? 2 : 1)), nframes), 128, 0, st>>>(batch, one);
-    k_aggregate<<<g, 256, 0, st>>>(batch, one);
-    k_finalize<<<g, 256, 0, st>>>(batch, one);
-    k_mom_finish<<<g, 256, 0, st>>>(batch, one);
+    launch_dep(k_merge, dim3(std::max(1, mcta / (nframes > 1 ? 2 : 1)), nframes), dim3(128), 0, st, batch, one);
+    launch_dep(k_aggregate, g, dim3(256), 0, st, batch, one);
+    launch_dep(k_finalize, g, dim3(256), 0, st, batch, one);
+    launch_dep(k_mom_finish, g, dim3(256), 0, st, batch, one);
     return cudaGetLastError();
 }
 
@@ -1296,11 +1316,11 @@ RankArgs rank_args(const Comps& C, int* n_out, int capacity, bool place, int* st
 cudaError_t launch_rank_any(const RankArgs& one, const RankArgs* batch, int nframes, cudaStream_t st)
 {
     const dim3 g(stride_grid(152 * 4, nframes), nframes);
-    k_rank_count<<<g, 256, 0, st>>>(batch, one);
-    k_rank_scan<<<dim3(1, nframes), SCAN_NT, 0, st>>>(batch, one);
+    launch_dep(k_rank_count, g, dim3(256), 0, st, batch, one);
+    launch_dep(k_rank_scan, dim3(1, nframes), dim3(SCAN_NT), 0, st, batch, one);
     if (one.place) {
-        k_rank_scatter<<<g, 256, 0, st>>>(batch, one);
-        k_rank_place<<<g, 256, 0, st>>>(batch, one);
+        launch_dep(k_rank_scatter, g, dim3(256), 0, st, batch, one);
+        launch_dep(k_rank_place, g, dim3(256), 0, st, batch, one);
     }
     return cudaGetLastError();
 }

@@ -57,7 +57,7 @@ cudaError_t launch_measure_any(const MeasureArgs& one, const MeasureArgs* batch,
     const cudaError_t e = one.im.is_f32 ? dispatch_nr<MeasureLaunch, true>(one.ap.nr, one, grid, st)
                                         : dispatch_nr<MeasureLaunch, false>(one.ap.nr, one, grid, st);
     if (e != cudaSuccess || one.ap.nr == 0) return e;
-    k_ap_finish_rows<false><<<grid, 256, 0, st>>>(nullptr, one);
+    launch_dep(k_ap_finish_rows<false>, grid, dim3(256), 0, st, (const MeasureArgs*)nullptr, one);
     return cudaGetLastError();
 }
 

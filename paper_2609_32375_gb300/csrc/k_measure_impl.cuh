@@ -349,6 +349,8 @@ template <bool F32, int NR, bool BATCH>
 __global__ void __launch_bounds__(MEAS_NT, 3) k_measure(const MeasureArgs* __restrict__ batch,
                                                      const __grid_constant__ MeasureArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const MeasureArgs& A = measure_frame<BATCH>(batch, one);
     __shared__ BEntry queue[MEAS_NT / 32][QCAP];
     BEntry* wq = queue[threadIdx.x >> 5];
@@ -401,6 +403,8 @@ template <bool BATCH>
 __global__ void __launch_bounds__(256) k_ap_finish_rows(const MeasureArgs* __restrict__ batch,
                                                         const __grid_constant__ MeasureArgs one)
 {
+    pdl_wait();
+    pdl_release();
     const MeasureArgs& A = measure_frame<BATCH>(batch, one);
     const int nr = A.ap.nr;
     const int nrow = min(min(*A.C.count, A.C.cap), A.capacity);
@@ -444,7 +448,7 @@ template <bool F32, int NR>
 struct MeasureLaunch {
     static cudaError_t run(const MeasureArgs& one, dim3 g, cudaStream_t st)
     {
-        k_measure<F32, NR, false><<<g, 256, 0, st>>>(nullptr, one);
+        launch_dep(k_measure<F32, NR, false>, g, dim3(256), 0, st, (const MeasureArgs*)nullptr, one);
         return cudaGetLastError();
     }
 };
@@ -453,7 +457,7 @@ template <bool F32, int NR>
 struct MeasureBatchLaunch {
     static cudaError_t run(const MeasureArgs& one, const MeasureArgs* batch, dim3 g, cudaStream_t st)
     {
-        k_measure<F32, NR, true><<<g, 256, 0, st>>>(batch, one);
+        launch_dep(k_measure<F32, NR, true>, g, dim3(256), 0, st, batch, one);
         return cudaGetLastError();
     }
 };

@@ -334,6 +334,8 @@ __global__ void __launch_bounds__(ST_NT) k_stream(const DetectArgs* __restrict__
                                                   const __grid_constant__ DetectArgs one,
                                                   const __grid_constant__ CUtensorMap tmap)
 {
+    pdl_wait();
+    pdl_release();
     using Cfg = StreamCfg<KS>;
     using SM = StreamSmem<KS>;
     constexpr int H = Cfg::H, G = Cfg::G, NV = Cfg::NV, WOFF = Cfg::WOFF;
@@ -668,7 +670,7 @@ cudaError_t launch_stream_inst(const DetectArgs& one, const DetectArgs* batch, i
     const size_t smem = StreamSmem<KS>::total(F32 ? 4 : 2);
     auto* fn = k_stream<F32, KS, MODE, FAST>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fn<<<dim3(maxcta, nframes), ST_NT, smem, st>>>(batch, one, map);
+    launch_dep(fn, dim3(maxcta, nframes), dim3(ST_NT), smem, st, batch, one, map);
     return cudaGetLastError();
 }
 
