@@ -54,9 +54,11 @@ cudaError_t launch_measure_any(const MeasureArgs& one, const MeasureArgs* batch,
     if (g < 16) g = 16;
     const dim3 grid(g, nframes);
     if (batch) return launch_measure_batched(one, batch, grid, st);
-    const cudaError_t e = one.im.is_f32 ? dispatch_nr<MeasureLaunch, true>(one.ap.nr, one, grid, st)
-                                        : dispatch_nr<MeasureLaunch, false>(one.ap.nr, one, grid, st);
-    if (e != cudaSuccess || one.ap.nr == 0) return e;
+    if (one.ap.nr > 0) {
+        const cudaError_t e = one.im.is_f32 ? dispatch_nr<MeasureLaunch, true>(one.ap.nr, one, grid, st)
+                                            : dispatch_nr<MeasureLaunch, false>(one.ap.nr, one, grid, st);
+        if (e != cudaSuccess) return e;
+    }
     launch_dep(k_ap_finish_rows<false>, grid, dim3(256), 0, st, (const MeasureArgs*)nullptr, one);
     return cudaGetLastError();
 }

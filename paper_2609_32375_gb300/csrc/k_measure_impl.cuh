@@ -332,8 +332,8 @@ __device__ __forceinline__ void ap_finish(double cx, double cy, const ApSpec& ap
     *fl = f;
 }
 
-// One warp per catalog row (segments in label order): copy the segment's
-// finished moments into the row, then the apertures at its centroid.
+// One warp per catalog row (segments in label order): the apertures at its
+// centroid (the row's other columns are written by k_ap_finish_rows).
 // the frame's arguments: the kernel parameter itself for a single frame (a
 // compile-time choice: hot-loop fields stay constant-bank operands), else the
 // batch record of frame blockIdx.y
@@ -354,29 +354,12 @@ __global__ void __launch_bounds__(MEAS_NT, 3) k_measure(const MeasureArgs* __res
     const MeasureArgs& A = measure_frame<BATCH>(batch, one);
     __shared__ BEntry queue[MEAS_NT / 32][QCAP];
     BEntry* wq = queue[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ncomp = min(*A.C.count, A.C.cap);
     const int nrow = min(ncomp, A.capacity);
-    const int W = A.im.W;
     for (int r = wid; r < nrow; r += nw) {
-        const int c = A.C.perm[r];
-        const double2 xy = A.C.xy[c];
-        if (lane == 0) {
-            const int4 bb = A.C.bbox[c];
-            const Mom2 m2 = A.C.mom2[c];
-            const uint32_t pL = A.C.peakL[c];
-            A.label[r] = A.C.label[c];
-            A.npix[r] = A.C.npix[c];
-            A.flux_iso[r] = A.C.flux[c];
-            A.x[r] = xy.x; A.y[r] = xy.y;
-            A.x2[r] = m2.x2; A.y2[r] = m2.y2; A.xy[r] = m2.xy;
-            A.xmin[r] = bb.x; A.xmax[r] = bb.y; A.ymin[r] = bb.z; A.ymax[r] = bb.w;
-            A.peak[r] = A.C.peak[c];
-            A.xpeak[r] = (int)(pL % (uint32_t)W); A.ypeak[r] = (int)(pL / (uint32_t)W);
-            A.flags[r] = A.C.flags[c];
-        }
+        const double2 xy = A.C.xy[A.C.perm[r]];
         if constexpr (NR > 0)
             aperture_warp<F32, NR>(A.im, A.sb, A.sr, A.ap, xy.x, xy.y, A.apflux + (int64_t)r * NR,
                                    A.apferr + (int64_t)r * NR, A.apflags + (int64_t)r * NR, wq);
@@ -398,7 +381,9 @@ __global__ void __launch_bounds__(MEAS_NT, 3) k_aperture(Image im, SplineTab sb,
                                fl + (int64_t)i * NR, wq);
 }
 
-// the aperture results of the catalog rows (one (row, radius) per thread)
+// The catalog rows in label order: thread (row, 0) copies the segment's
+// finished moments into the row, and thread (row, k) finishes the aperture
+// results of radius k (one (row, radius) per thread).
 template <bool BATCH>
 __global__ void __launch_bounds__(256) k_ap_finish_rows(const MeasureArgs* __restrict__ batch,
                                                         const __grid_constant__ MeasureArgs one)
@@ -406,12 +391,32 @@ __global__ void __launch_bounds__(256) k_ap_finish_rows(const MeasureArgs* __res
     pdl_wait();
     pdl_release();
     const MeasureArgs& A = measure_frame<BATCH>(batch, one);
-    const int nr = A.ap.nr;
+    const int nr = A.ap.nr, nk = nr > 0 ? nr : 1;
+    const int W = A.im.W;
     const int nrow = min(min(*A.C.count, A.C.cap), A.capacity);
-    const int64_t n = (int64_t)nrow * nr;
+    const int64_t n = (int64_t)nrow * nk;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / nr), k = (int)(i - (int64_t)r * nr);
-        ap_finish(A.x[r], A.y[r], A.ap, k, A.im.W, A.im.H, A.apflux + i, A.apferr + i, A.apflags + i);
+        const int r = (int)(i / nk), k = (int)(i - (int64_t)r * nk);
+        const int c = A.C.perm[r];
+        const double2 xy = A.C.xy[c];
+        if (k == 0) {
+            const int4 bb = A.C.bbox[c];
+            const Mom2 m2 = A.C.mom2[c];
+            const uint32_t pL = A.C.peakL[c];
+            A.label[r] = A.C.label[c];
+            A.npix[r] = A.C.npix[c];
+            A.flux_iso[r] = A.C.flux[c];
+            A.x[r] = xy.x; A.y[r] = xy.y;
+            A.x2[r] = m2.x2; A.y2[r] = m2.y2; A.xy[r] = m2.xy;
+            A.xmin[r] = bb.x; A.xmax[r] = bb.y; A.ymin[r] = bb.z; A.ymax[r] = bb.w;
+            A.peak[r] = A.C.peak[c];
+            A.xpeak[r] = (int)(pL % (uint32_t)W); A.ypeak[r] = (int)(pL / (uint32_t)W);
+            A.flags[r] = A.C.flags[c];
+        }
+        if (nr > 0) {
+            const int64_t j = (int64_t)r * nr + k;
+            ap_finish(xy.x, xy.y, A.ap, k, A.im.W, A.im.H, A.apflux + j, A.apferr + j, A.apflags + j);
+        }
     }
 }
 
