@@ -2,9 +2,10 @@
 // overlap areas (paper Section 3.4).
 //
 // One warp per source.  The segment moments were finished after detection
-// (k_mom_finish); here each row is written in label order and the apertures
-// scan the pixels around the centroid once for all radii, leaving raw sums
-// that k_ap_finish_rows / k_ap_finish_list finish one result per thread.  Every sum is a float-float
+// (k_mom_finish); here the apertures scan the pixels around the centroid once
+// for all radii, leaving raw sums that k_ap_finish_rows / k_ap_finish_list
+// finish one result per thread (k_ap_finish_rows also writes each catalog
+// row, in label order).  Every sum is a float-float
 // (compensated) accumulation of FP32 products, reduced across the warp in a
 // fixed butterfly order, so results are reproducible run to run and carry
 // about 48 bits -- the float64-class accumulation the paper asks of aperture
