@@ -9,19 +9,55 @@
 #include "gp_launch.h"
 
 namespace gp {
-// integral of sqrt(r^2 - t^2) over [a, b], -r <= a <= b <= r, written with
-// differences formed algebraically (no cancellation between large terms)
+// square root by the hardware approximation (sqrt.approx.f32, about one ulp)
+__device__ __forceinline__ float sqrt_ap(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// The angle atan(y / x) in [0, pi/2] for x, y >= 0, not both 0.  With
+// u = min / max in [0, 1], atan(u) = u P(u^2), P the degree-8 polynomial
+// that fits atan(u) / u on [0, 1] in least squares (weights iterated toward
+// equal relative error; relative error below 2e-8 in exact arithmetic), and
+// atan(y / x) = pi/2 - atan(x / y) above the diagonal.
+__device__ __forceinline__ float atan_q1(float y, float x)
+{
+    const bool sw = y > x;
+    const float u = __fdividef(sw ? x : y, sw ? y : x);
+    const float s = u * u;
+    float p = 0.002903404f;
+    p = fmaf(p, s, -0.01628242f);
+    p = fmaf(p, s, 0.043038424f);
+    p = fmaf(p, s, -0.07533597f);
+    p = fmaf(p, s, 0.10654641f);
+    p = fmaf(p, s, -0.14207125f);
+    p = fmaf(p, s, 0.19993053f);
+    p = fmaf(p, s, -0.33333093f);
+    p = fmaf(p, s, 1.0f);
+    const float a = u * p;
+    return sw ? 1.57079637f - a : a;
+}
+
+// integral of sqrt(r^2 - t^2) over [a, b], 0 <= a <= b <= r, written with
+// differences formed algebraically (no cancellation between large terms):
+// r^2 theta / 2 + (b hb - a ha) / 2 with theta = asin(b/r) - asin(a/r) from
+// its sine and cosine.  The square roots, the one division and the angle use
+// the fast forms above; on the host, this arithmetic against the oracle's
+// float64 areas over radii 0.3-100 gives a worst absolute error of 1.5e-6
+// at r = 10 and 1.5e-5 at r = 100.
 __device__ __forceinline__ float chord_int(float a, float b, float r2)
 {
     float d = b - a;
     if (!(d > 0.f)) return 0.f;
-    float ha = sqrtf(fmaxf(fmaf(-a, a, r2), 0.f));
-    float hb = sqrtf(fmaxf(fmaf(-b, b, r2), 0.f));
+    float ha = sqrt_ap(fmaxf(fmaf(-a, a, r2), 0.f));
+    float hb = sqrt_ap(fmaxf(fmaf(-b, b, r2), 0.f));
     float s = ha + hb;
-    float q = s > 0.f ? d * (a + b) / s : 0.f;      // ha - hb
+    float q = s > 0.f ? __fdividef(d * (a + b), s) : 0.f;      // ha - hb
     float sin_t = fmaf(d, ha, a * q);               // (b ha - a hb), r^2 sin(theta)
     float cos_t = fmaf(ha, hb, a * b);              // (ha hb + a b), r^2 cos(theta)
-    float theta = atan2f(sin_t, cos_t);             // asin(b/r) - asin(a/r)
+    float theta = atan_q1(sin_t, cos_t);            // asin(b/r) - asin(a/r), in [0, pi/2]
     return 0.5f * fmaf(r2, theta, fmaf(d, hb, -a * q));
 }
 
@@ -36,8 +72,8 @@ __device__ __forceinline__ float chord_int(float a, float b, float r2)
 __device__ __forceinline__ float quadrant_area(float x0, float x1, float y0, float y1, float r2)
 {
     if (!(fmaf(x0, x0, __fmul_rn(y0, y0)) < r2)) return 0.f;   // the nearest corner is outside
-    const float xa = sqrtf(fmaxf(fmaf(-y1, y1, r2), 0.f));
-    const float xb = sqrtf(fmaxf(fmaf(-y0, y0, r2), 0.f));
+    const float xa = sqrt_ap(fmaxf(fmaf(-y1, y1, r2), 0.f));
+    const float xb = sqrt_ap(fmaxf(fmaf(-y0, y0, r2), 0.f));
     const float lo = fminf(fmaxf(xa, x0), x1);
     const float d = fmaxf(__fsub_rn(fminf(x1, xb), lo), 0.f);
     const float rect = __fmul_rn(__fsub_rn(y1, y0), __fsub_rn(lo, x0));
