@@ -25,10 +25,13 @@ int comp_cap_for(int64_t npix, int capacity)
     return (int)std::min<int64_t>(c, 1ll << 30);
 }
 
+// Buckets of 2^shift labels for the rank; at most 16,384 of them, so the
+// one-CTA scan reads 16 counts per thread (the place step sorts within a
+// bucket, about three segments at the densest workloads' 151 MP).
 static void bucket_geometry(int64_t npix, int* shift, int* nb)
 {
     int s = 0;
-    while (((npix - 1) >> s) + 1 > 65536) ++s;
+    while (((npix - 1) >> s) + 1 > 16384) ++s;
     *shift = s;
     *nb = (int)(((npix - 1) >> s) + 1);
 }

@@ -829,7 +829,7 @@ __global__ void k_aggregate(const ResolveArgs* __restrict__ batch, const __grid_
 // reproducible) and emit the segment; a segment of a single piece is emitted
 // from that piece's sums directly (the merge would add zeros to them).  Every piece whose final label differs
 // from its provisional one rewrites its pixels in the map.
-__global__ void k_finalize(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
+__global__ void __launch_bounds__(256, 4) k_finalize(const ResolveArgs* __restrict__ batch, const __grid_constant__ ResolveArgs one)
 {
     pdl_wait();
     pdl_release();
@@ -1034,7 +1034,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_rank_scan(const RankArgs* __restric
     int* status = R.status;
     __shared__ int wsum[SCAN_NT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nb = C.nb;                                     // <= 65,536
+    const int nb = C.nb;                                     // <= 16,384
     const int per = ((nb + SCAN_NT - 1) / SCAN_NT + 3) & ~3; // a multiple of 4 buckets per thread
     const int b0 = min(tid * per, nb), b1 = min(b0 + per, nb);
     const bool vec = (((uintptr_t)C.bcnt | (uintptr_t)C.boff) & 15) == 0;
