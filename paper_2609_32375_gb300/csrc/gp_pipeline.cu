@@ -27,7 +27,7 @@ int comp_cap_for(int64_t npix, int capacity)
 
 // Buckets of 2^shift labels for the rank; at most 16,384 of them, so the
 // one-CTA scan reads 16 counts per thread (the place step sorts within a
-// bucket, about three segments at the densest workloads' 151 MP).
+// bucket, about four segments on the dense 151 MP frame).
 static void bucket_geometry(int64_t npix, int* shift, int* nb)
 {
     int s = 0;
