@@ -271,8 +271,8 @@ struct LabelSmem {
     int par[R];                   // union-find; after flattening, the component's root run
     int cnt[R];                   // at roots: pixels + (runs on a shared tile edge << 16)
     int val[R];                   // at roots: the map value (1 + minimum linear index), 0 when dropped
-    int16_t pidx[R];              // at piece roots: local piece index, else -1
-    int16_t cidx[R];              // at kept final-segment roots: local index
+    int16_t kidx[R];              // at kept roots: the local piece index (>= 0), or -2 - the local
+                                  // final-segment index; else -1
     int16_t pos[R];               // the run's row * TX + first column
     int16_t fidx[R];              // compact index of the run's first pixel
     int16_t klist[R];             // kept roots in label order
@@ -326,8 +326,8 @@ __device__ __forceinline__ void emit_root(const DetectArgs& A, const LabelSmem<B
 {
     const uint32_t L = (uint32_t)S.val[r] - 1u;
     const int npix = S.cnt[r] & 0xffff;
-    if (S.pidx[r] >= 0) {
-        const int id = pbase + S.pidx[r];
+    if (S.kidx[r] >= 0) {
+        const int id = pbase + S.kidx[r];
         if (id < A.P.cap) {
             A.P.root[id] = L; A.P.npix[id] = npix; A.P.bbox[id] = bb; A.P.parent[id] = id;
             A.P.agg_min[id] = L; A.P.agg_npix[id] = npix; A.P.agg_bbox[id] = bb;
@@ -344,7 +344,7 @@ __device__ __forceinline__ void emit_root(const DetectArgs& A, const LabelSmem<B
         }
         return;
     }
-    const int id = cbase + S.cidx[r];
+    const int id = cbase + (-2 - S.kidx[r]);
     if (id >= A.C.cap) {
         set_status(A.status, GP_ERR_INTERNAL);
         return;
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_
                 const int x = __ffsll((long long)hb) - 1;
                 hb &= hb - 1;
                 const int xe = run_end(M, x);
-                S.par[q] = q; S.cnt[q] = 0; S.val[q] = 0; S.pidx[q] = -1; S.cidx[q] = -1;
+                S.par[q] = q; S.cnt[q] = 0; S.val[q] = 0; S.kidx[q] = -1;
                 S.pos[q] = (int16_t)(y * TX + x);
                 S.fidx[q] = (int16_t)f;
                 S.len[q] = (uint8_t)(xe - x);
@@ -550,8 +550,7 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_
                 const int p = S.pos[k];
                 S.val[k] = (int)((uint32_t)(y0 + p / TX) * (uint32_t)W + (uint32_t)(x0 + p % TX) + 1u);
                 S.klist[nk + __popc((bp | bc) & lt)] = (int16_t)k;
-                if (piece) S.pidx[k] = (int16_t)(np + __popc(bp & lt));
-                else S.cidx[k] = (int16_t)(nc + __popc(bc & lt));
+                S.kidx[k] = piece ? (int16_t)(np + __popc(bp & lt)) : (int16_t)(-2 - (nc + __popc(bc & lt)));
             }
             np += __popc(bp);
             nc += __popc(bc);
@@ -589,7 +588,8 @@ __global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_
             const int rbB = __shfl_sync(FULL, rb, th - 1);
             auto piece_at = [&](uint64_t Mr, uint64_t Hr, int rbase, int x) -> int16_t {
                 if (!((Mr >> x) & 1ull)) return (int16_t)-1;
-                return S.pidx[S.par[rbase + __popcll((long long)(Hr & upto(x))) - 1]];
+                const int16_t k = S.kidx[S.par[rbase + __popcll((long long)(Hr & upto(x))) - 1]];
+                return k >= 0 ? k : (int16_t)-1;
             };
             ed[y] = y < th ? piece_at(M, heads, rb, 0) : (int16_t)-1;                 // colL
             ed[TY + y] = y < th ? piece_at(M, heads, rb, tw - 1) : (int16_t)-1;       // colR
@@ -1231,6 +1231,9 @@ static void launch_label(const DetectArgs& one, const DetectArgs* batch, dim3 g,
     const size_t smem = sizeof(LabelSmem<BIG>) * LabelCfg<BIG>::NW;
     auto* fn = k_label_tiles<LO, BATCH, BIG>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // all of the unified L1 / shared memory as shared memory: ten CTAs of the
+    // common form (22 KB each) per SM
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     launch_dep(fn, g, dim3(32 * LabelCfg<BIG>::NW), smem, st, batch, one, late);
 }
 
