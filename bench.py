@@ -667,10 +667,11 @@ def run_gpu(args):
                                "path": "one stream: H2D, gp_extract, D2H of the filled rows, CUDA events"},
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clk}
-    # ---- the learned-background form on the same frame (when trained weights exist)
-    wpath = os.path.join(ROOT, "paper_2609_32375_gb300", "weights", "learned_bkg.npz")
-    if os.path.exists(wpath) and not args.no_learned:
-        from paper_2609_32375_gb300 import learned as L
+    # ---- the learned-background form on the same frame (when weights trained
+    # at this mesh size are committed)
+    from paper_2609_32375_gb300 import learned as L
+    wpath = L.weights_for_mesh(cfg.mesh)
+    if wpath and not args.no_learned:
         net = L.load(wpath, device=dev)
         exl = gp.Extractor(ctx, (H, W), t_img.dtype, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii,
                            cfg.gain, CAPACITY, saturation=cfg.saturation, device=dev, net=net)

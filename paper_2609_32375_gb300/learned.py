@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 import time
 from dataclasses import dataclass
 
@@ -233,11 +234,11 @@ class TrainFrame:
     var: object             # float32 [H, W] noise variance of the sky
 
 
-def training_frame(seed: int, size: int = 4096, device="cuda", read_noise=5.0):
+def training_frame(seed: int, size: int = 4096, device="cuda", read_noise=5.0, stars=(500, 20000)):
     """One seeded training frame drawn on the GPU: sky with a gradient,
-    vignetting, a moonlight ramp and random-field nebulosity, 500-20,000
-    Moffat stars (beta 2.5, FWHM 2-5 px, F^-1.5 fluxes on [1e2, 1e5]),
-    Poisson and read noise."""
+    vignetting, a moonlight ramp and random-field nebulosity, a number of
+    Moffat stars drawn log-uniformly from `stars` (beta 2.5, FWHM 2-5 px,
+    F^-1.5 fluxes on [1e2, 1e5]), Poisson and read noise."""
     import torch
     import torch.nn.functional as Fn
     g = torch.Generator(device=device).manual_seed(int(seed))
@@ -264,7 +265,8 @@ def training_frame(seed: int, size: int = 4096, device="cuda", read_noise=5.0):
     field = Fn.interpolate(field[None, None], size=(H, W), mode="bilinear", align_corners=False)[0, 0]
     sky = (sky0 + grad + ramp + field) * vig
     # stars
-    nstar = int(round(math.exp(math.log(500) + (math.log(20000) - math.log(500)) * float(u(1)))))
+    lo, hi = float(stars[0]), float(stars[1])
+    nstar = int(round(math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * float(u(1)))))
     xs = u(nstar) * W
     ys = u(nstar) * H
     fl = (1e2 ** -0.5 + u(nstar) * (1e5 ** -0.5 - 1e2 ** -0.5)) ** -2.0
@@ -294,14 +296,24 @@ def truth_meshes(frame: TrainFrame, mesh: int):
     return b, r
 
 
-def build_dataset(ctx, n, seed0, size=4096, mesh=64, stream=None):
-    """Features, normalised plain targets, norms and truth meshes of n frames."""
+def as_u16(img):
+    """A float frame rounded and clamped to the uint16 range, as a uint16 tensor
+    (the integer detour keeps to casts every torch build has)."""
+    import torch
+    v = img.round().clamp_(0, 65535).to(torch.int32)
+    return torch.where(v > 32767, v - 65536, v).to(torch.int16).view(torch.uint16)
+
+
+def build_dataset(ctx, n, seed0, size=4096, mesh=64, stream=None, stars=(500, 20000), u16=False):
+    """Features, normalised plain targets, norms and truth meshes of n frames
+    (as uint16 frames when `u16`)."""
     import torch
     quants, pb, pr, tb, tr = [], [], [], [], []
     for i in range(n):
-        fr = training_frame(seed0 + i, size)
-        quants.append(box_quantiles(ctx, fr.image, mesh, stream))
-        plain = ctx.gp_background(fr.image, mesh, stream=stream)
+        fr = training_frame(seed0 + i, size, stars=stars)
+        img = as_u16(fr.image) if u16 else fr.image
+        quants.append(box_quantiles(ctx, img, mesh, stream))
+        plain = ctx.gp_background(img, mesh, stream=stream)
         pb.append(plain["bkg_mesh"])
         pr.append(plain["rms_mesh"])
         b, r = truth_meshes(fr, mesh)
@@ -384,6 +396,22 @@ def save(net: Network, path: str, meta=None):
     np.savez(path, **arrays)
 
 
+def meta(path: str) -> dict:
+    """The training record saved with a weights file (empty if none)."""
+    import ast
+    z = np.load(path)
+    return ast.literal_eval(bytes(z["meta"]).decode()) if "meta" in z else {}
+
+
+def weights_for_mesh(mesh: int):
+    """The committed weights trained at this mesh size (None if there are none)."""
+    import glob
+    for p in sorted(glob.glob(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "*.npz"))):
+        if meta(p).get("mesh") == mesh:
+            return p
+    return None
+
+
 def load(path: str, device="cuda") -> Network:
     import torch
     z = np.load(path)
@@ -410,12 +438,18 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--stars-per-mp", type=float, nargs=2, default=None, metavar=("LO", "HI"),
+                    help="stars per megapixel, drawn log-uniformly (default: 500-20,000 per frame)")
+    ap.add_argument("--u16", action="store_true",
+                    help="round the frames to uint16 (always for meshes above 128, which the float path does not take)")
     ap.add_argument("--out", default=None, help="write the trained weights (.npz)")
     a = ap.parse_args(argv)
+    u16 = a.u16 or a.mesh > 128
+    stars = (500, 20000) if a.stars_per_mp is None else tuple(v * a.size * a.size / 1e6 for v in a.stars_per_mp)
     ctx = Context(0, workspace_bytes=1 << 30)
     t0 = time.time()
-    train_set = build_dataset(ctx, a.frames, seed0=1_000_000, size=a.size, mesh=a.mesh)
-    held = build_dataset(ctx, a.held, seed0=1_000_000 + a.frames, size=a.size, mesh=a.mesh)
+    train_set = build_dataset(ctx, a.frames, seed0=1_000_000, size=a.size, mesh=a.mesh, stars=stars, u16=u16)
+    held = build_dataset(ctx, a.held, seed0=1_000_000 + a.frames, size=a.size, mesh=a.mesh, stars=stars, u16=u16)
     t_data = time.time() - t0
     net = Network(seed=0)
     t0 = time.time()
@@ -423,9 +457,10 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_train = time.time() - t0
     ev = evaluate(net, held)
-    frame = training_frame(1_000_000 + a.frames + a.held, a.size)
-    tm = time_background(ctx, frame.image, a.mesh, net)
+    frame = training_frame(1_000_000 + a.frames + a.held, a.size, stars=stars)
+    tm = time_background(ctx, as_u16(frame.image) if u16 else frame.image, a.mesh, net)
     res = {"frames": a.frames, "held_out": a.held, "size": a.size, "mesh": a.mesh, "epochs": a.epochs,
+           "stars": [round(v, 1) for v in stars], "u16": u16,
            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "data_s": round(t_data, 1),
            "train_s": round(t_train, 1), **{k: round(v, 5) for k, v in ev.items()},
            **{k: round(v, 4) for k, v in tm.items()}}

@@ -194,3 +194,30 @@ def test_trained_network_gains_over_the_plain_estimator():
         assert t["learned_ms"] < 0.8 * t["plain_ms"]
     finally:
         ctx.close()
+
+
+def test_mesh256_network_on_the_dense_recipe():
+    """The committed mesh-256 network (trained on uint16 8192^2 frames up to
+    1,500 stars per megapixel) on a 4096^2 crop of the dense 151 MP recipe:
+    its meshes stay within the accuracy measured for it at full size
+    (background 0.20 sigma RMS from the clipped mesh, noise 6.5 %), with a
+    margin; a regression guard, not the clipped estimator's accuracy."""
+    import synth
+    path = learned.weights_for_mesh(256)
+    assert path is not None, "no committed weights trained at mesh 256"
+    net = learned.load(path)
+    cfg = synth.scaled_config(synth.CONFIGS["dense_12288x12304_u16"], 4096, 4096)
+    img, _ = synth.make_frame(cfg, 0)
+    ctx = gp.Context(0, workspace_bytes=1 << 30)
+    try:
+        t = torch.from_numpy(img).cuda()
+        plain = ctx.gp_background(t, 256)
+        lrn = learned.background_learned(ctx, t, 256, net)
+        ctx.sync()
+        pr = plain["rms_mesh"].clamp_min(1e-6)
+        dbk = float(((lrn["bkg_mesh"] - plain["bkg_mesh"]) / pr).pow(2).mean().sqrt())
+        drm = float(((lrn["rms_mesh"] - plain["rms_mesh"]) / pr).pow(2).mean().sqrt())
+        print(f"background {dbk:.3f} sigma, noise {drm:.3f} relative")
+        assert dbk < 0.35 and drm < 0.12
+    finally:
+        ctx.close()
