@@ -670,7 +670,8 @@ gp_status gp_cosmetic(gp_ctx* ctx, const gp_image* img, const gp_cosmetic_params
             ir.pitch = W;
             ir.is_f32 = 1;
         }
-        GP_CUDA(launch_rtn(ir, p->rtn_t, out, flags, cr, counts, st));
+        const bool clean = !im.is_f32 && !im.mask;      // the cosmic-ray output of such a frame holds no NaN
+        GP_CUDA(launch_rtn(ir, p->rtn_t, out, flags, cr, counts, clean, st));
         ctx->launches += 1;
     }
     mark_to(ctx, 1, GP_NSTAGES, st);

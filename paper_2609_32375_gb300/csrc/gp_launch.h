@@ -58,7 +58,10 @@ cudaError_t launch_psf(const DetectArgs& D, const float* p0, const float* modes,
 // cosmetic corrections (k_cosmetic.cu)
 cudaError_t launch_cr(const Image& im, float gain, float rn, float sigclip, float objlim, float* out, uint8_t* flags,
                       int* count, cudaStream_t st);
-cudaError_t launch_rtn(const Image& im, float thr, float* out, uint8_t* flags, bool keep, int* count, cudaStream_t st);
+// clean: the input holds no bad pixel (a uint16 frame without a mask, or the
+// cosmic-ray filter's float output of one)
+cudaError_t launch_rtn(const Image& im, float thr, float* out, uint8_t* flags, bool keep, int* count, bool clean,
+                       cudaStream_t st);
 
 // multi-threshold deblending (k_deblend.cu): an object's catalog row before
 // the rows are put in label order, and the call's scratch
