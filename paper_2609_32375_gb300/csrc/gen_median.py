@@ -82,8 +82,8 @@ def check(n, ops, trials=20000):
         assert w[(n - 1) // 2] == sorted(v)[(n - 1) // 2]
 
 
-def main():
-    here = os.path.dirname(os.path.abspath(__file__))
+def render():
+    """The text of median_sel.cuh."""
     lines = ["// median_sel.cuh -- written by gen_median.py (do not edit): median-selection",
              "// networks pruned from Batcher's odd-even merge sort (see gen_median.py).",
              "// med_sel<N>(v) returns the middle value of v[0 .. N-1] (N odd, no NaN);",
@@ -105,7 +105,12 @@ def main():
                 lines.append(f"    v[{j}] = fmaxf(v[{i}], v[{j}]);")
         lines += [f"    return v[{(n - 1) // 2}];", "}", ""]
     lines += ["}  // namespace gp", ""]
-    open(os.path.join(here, "median_sel.cuh"), "w").write("\n".join(lines))
+    return "\n".join(lines)
+
+
+def main():
+    here = os.path.dirname(os.path.abspath(__file__))
+    open(os.path.join(here, "median_sel.cuh"), "w").write(render())
 
 
 if __name__ == "__main__":
