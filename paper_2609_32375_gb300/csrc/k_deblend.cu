@@ -35,6 +35,7 @@ namespace gp {
 
 constexpr int DB_NT = 512;
 constexpr int DB_MAX_SEEDS = 1024;
+constexpr int DB_MAX_LEVELS = 64;            // nthresh at most (checked by the API)
 constexpr double DB_FIX = 1048576.0;         // 2^20
 
 struct DeblendArgs {
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
     __shared__ int seeds[DB_MAX_SEEDS];        // first pixel of each seed, then sorted
     __shared__ int seedid[DB_MAX_SEEDS];
     __shared__ unsigned olab[DB_MAX_SEEDS];    // minimum frame index of each object
+    __shared__ float tlev[DB_MAX_LEVELS + 1];  // the level thresholds, rounded down to float
     const int t = threadIdx.x;
     const Image& im = A.im;
     const int W = im.W, H = im.H;
@@ -252,11 +254,17 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
         if (nmaxima < 2) continue;
         const double cthr = A.mincont * (double)total;
         const double lr = log(nu_max / (double)A.thresh);
+        // t_i = thresh (nu_max / thresh)^(i / nthresh), once per level, in
+        // float64, rounded down to float: for a float nu, nu > t_i exactly
+        // when nu > rd(t_i), so every comparison below is one of floats
+        for (int i = t; i <= A.nthresh; i += DB_NT)
+            tlev[i] = __double2float_rd((double)A.thresh * exp(lr * (double)i / (double)A.nthresh));
+        __syncthreads();
         // ---- the branch tree, one level at a time
         for (int i = 0; i + 1 < A.nthresh; ++i) {
-            const double tl = (double)A.thresh * exp(lr * (double)(i + 1) / (double)A.nthresh);
+            const float tl = tlev[i + 1];
             for (int q = t; q <= Ar; q += DB_NT) {
-                if (q < Ar) s.lab[q] = (s.act[q] >= 0 && (double)s.nu[q] > tl) ? q : -1;
+                if (q < Ar) s.lab[q] = (s.act[q] >= 0 && s.nu[q] > tl) ? q : -1;
                 s.fs[q] = 0; s.cnt[q] = 0; s.sig[q] = 0;
             }
             __syncthreads();
@@ -348,12 +356,12 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
         int* cur = s.own;
         int* nxt = s.own2;
         for (int i = A.nthresh - 1; i >= 0; --i) {
-            const double tl = (double)A.thresh * exp(lr * (double)i / (double)A.nthresh);
+            const float tl = tlev[i];
             for (;;) {
                 int ch = 0;
                 for (int q = t; q < Ar; q += DB_NT) {
                     int v = cur[q];
-                    if (v == 0 && s.nu[q] > -INFINITY && (i == 0 || (double)s.nu[q] > tl)) {
+                    if (v == 0 && s.nu[q] > -INFINITY && (i == 0 || s.nu[q] > tl)) {
                         const int qy = q / w, qx = q - qy * w;
                         int best = INT_MAX;
                         for (int dy = -1; dy <= 1; ++dy)
