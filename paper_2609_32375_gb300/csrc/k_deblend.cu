@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
     __shared__ int seedid[DB_MAX_SEEDS];
     __shared__ unsigned olab[DB_MAX_SEEDS];    // minimum frame index of each object
     __shared__ float tlev[DB_MAX_LEVELS + 1];  // the level thresholds, rounded down to float
+    __shared__ int fr_n[2];                    // growth: candidates of this round, of the next
     const int t = threadIdx.x;
     const Image& im = A.im;
     const int W = im.W, H = im.H;
@@ -260,15 +261,34 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
         for (int i = t; i <= A.nthresh; i += DB_NT)
             tlev[i] = __double2float_rd((double)A.thresh * exp(lr * (double)i / (double)A.nthresh));
         __syncthreads();
-        // ---- the branch tree, one level at a time
+        // ---- the branch tree, one level at a time, over the list of the
+        // pixels still active (own: this level's list, first: the next
+        // level's).  A pixel leaves the list when it leaves the tree, and its
+        // lab is then -1 for good; the nodes the listed pixels point to are
+        // listed pixels themselves (a significant branch's root stays in it)
+        // or node Ar.  Roots are the components' smallest pixels and the
+        // sums are exact, so the list order does not matter.
+        int* lst = s.own;
+        int* lnx = s.first;
+        if (t == 0) { fr_n[0] = 0; fr_n[1] = 0; }
+        __syncthreads();
+        for (int q = t; q < Ar; q += DB_NT) {
+            s.lab[q] = -1;
+            if (s.act[q] >= 0) lst[atomicAdd(&fr_n[0], 1)] = q;
+        }
+        __syncthreads();
         for (int i = 0; i + 1 < A.nthresh; ++i) {
             const float tl = tlev[i + 1];
-            for (int q = t; q <= Ar; q += DB_NT) {
-                if (q < Ar) s.lab[q] = (s.act[q] >= 0 && s.nu[q] > tl) ? q : -1;
+            const int nl = fr_n[0];
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
+                s.lab[q] = s.nu[q] > tl ? q : -1;
                 s.fs[q] = 0; s.cnt[q] = 0; s.sig[q] = 0;
             }
+            if (t == 0) { s.fs[Ar] = 0; s.cnt[Ar] = 0; s.sig[Ar] = 0; fr_n[1] = 0; }
             __syncthreads();
-            for (int q = t; q < Ar; q += DB_NT) {
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
                 if (s.lab[q] < 0) continue;
                 const int qy = q / w, qx = q - qy * w;
                 // the neighbours before q in raster order: W, NW, N, NE
@@ -283,9 +303,13 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
             __syncthreads();
             // roots into a second array (own2 is free until the growth)
             int* root = s.own2;
-            for (int q = t; q < Ar; q += DB_NT) root[q] = s.lab[q] >= 0 ? db_root(s.lab, q) : -1;
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
+                root[q] = s.lab[q] >= 0 ? db_root(s.lab, q) : -1;
+            }
             __syncthreads();
-            for (int q = t; q < Ar; q += DB_NT) {
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
                 const int rt = root[q];
                 if (rt < 0) continue;
                 atomicAdd(reinterpret_cast<unsigned long long*>(s.fs + rt), (unsigned long long)s.mf[q]);
@@ -293,7 +317,8 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
             }
             __syncthreads();
             // a significant branch marks its parent node (the active node of its pixels)
-            for (int q = t; q < Ar; q += DB_NT) {
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
                 if (root[q] != q) continue;
                 if (s.cnt[q] >= A.minarea && (double)s.fs[q] > cthr) {
                     atomicOr(s.sig + q, 1);
@@ -301,24 +326,35 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
                 }
             }
             __syncthreads();
-            int any = 0;
-            for (int q = t; q < Ar; q += DB_NT) {
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
                 const int node = s.act[q];
-                if (node < 0) continue;
                 if (!(s.sig[node] & 2)) {           // no significant child: the node is a seed
                     s.seed[q] = node + 1;
                     s.act[q] = -1;
+                    s.lab[q] = -1;
                 } else if (root[q] >= 0 && (s.sig[root[q]] & 1)) {
                     s.act[q] = root[q];
-                    any = 1;
+                    lnx[atomicAdd(&fr_n[1], 1)] = q;
                 } else {
                     s.act[q] = -1;
+                    s.lab[q] = -1;
                 }
             }
-            if (!__syncthreads_or(any)) break;
+            __syncthreads();
+            int* tmp = lst; lst = lnx; lnx = tmp;
+            if (t == 0) fr_n[0] = fr_n[1];
+            __syncthreads();
+            if (fr_n[0] == 0) break;
         }
-        for (int q = t; q < Ar; q += DB_NT)
-            if (s.act[q] >= 0) s.seed[q] = s.act[q] + 1;
+        {
+            const int nl = fr_n[0];
+            for (int k = t; k < nl; k += DB_NT) {
+                const int q = lst[k];
+                s.seed[q] = s.act[q] + 1;
+            }
+        }
+        __syncthreads();
         // ---- the seeds, in the order of their first pixels
         for (int q = t; q <= Ar; q += DB_NT) s.first[q] = INT_MAX;
         if (t == 0) nseed_s = 0;
@@ -346,39 +382,96 @@ __global__ void __launch_bounds__(DB_NT) k_deblend(const __grid_constant__ Deble
             s.cnt[seedid[k]] = rk + 1;
         }
         __syncthreads();
+        // own: the object rank of each pixel (0 none); own2: the round in which
+        // the pixel was assigned (seeds 0; -1 unassigned, -2 a candidate of
+        // the coming round)
         for (int q = t; q < Ar; q += DB_NT) {
             const int v = s.seed[q] ? s.cnt[s.seed[q] - 1] : 0;
             s.own[q] = v;
-            s.own2[q] = v;
+            s.own2[q] = v > 0 ? 0 : -1;
         }
         __syncthreads();
-        // ---- growth within the level sets, from the highest level down
+        // ---- growth within the level sets, from the highest level down, in
+        // synchronous rounds: in a round every unassigned pixel of the level
+        // set with an assigned 8-neighbour takes the smallest object rank
+        // among the neighbours assigned before the round.  A level's first
+        // round finds its candidates by a scan of the box; after that a
+        // pixel can become a candidate only through a neighbour assigned in
+        // the round before (one assigned earlier would have made it one
+        // already), so each later round visits the neighbours of the last
+        // round's pixels only.  Lists: lab (this round's candidates), act
+        // (the next round's), first (their new ranks).
         int* cur = s.own;
-        int* nxt = s.own2;
+        int* stamp = s.own2;
+        int* lc = s.lab;
+        int* ln = s.act;
+        int* nr = s.first;
+        int round = 0;
         for (int i = A.nthresh - 1; i >= 0; --i) {
             const float tl = tlev[i];
-            for (;;) {
-                int ch = 0;
-                for (int q = t; q < Ar; q += DB_NT) {
-                    int v = cur[q];
-                    if (v == 0 && s.nu[q] > -INFINITY && (i == 0 || s.nu[q] > tl)) {
-                        const int qy = q / w, qx = q - qy * w;
-                        int best = INT_MAX;
-                        for (int dy = -1; dy <= 1; ++dy)
-                            for (int dx = -1; dx <= 1; ++dx) {
-                                if (!dy && !dx) continue;
-                                const int yy = qy + dy, xx = qx + dx;
-                                if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
-                                const int o = cur[yy * w + xx];
-                                if (o > 0 && o < best) best = o;
-                            }
-                        if (best != INT_MAX) { v = best; ch = 1; }
+            auto eligible = [&](int q) { return s.nu[q] > -INFINITY && (i == 0 || s.nu[q] > tl); };
+            if (t == 0) { fr_n[0] = 0; fr_n[1] = 0; }
+            __syncthreads();
+            for (int q = t; q < Ar; q += DB_NT) {
+                if (cur[q] != 0 || !eligible(q)) continue;
+                const int qy = q / w, qx = q - qy * w;
+                bool adj = false;
+                for (int dy = -1; dy <= 1 && !adj; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int yy = qy + dy, xx = qx + dx;
+                        if ((dy || dx) && yy >= 0 && yy < h && xx >= 0 && xx < w && cur[yy * w + xx] > 0) { adj = true; break; }
                     }
-                    nxt[q] = v;
+                if (adj) {
+                    stamp[q] = -2;
+                    lc[atomicAdd(&fr_n[0], 1)] = q;
                 }
-                const int any = __syncthreads_or(ch);
-                int* tmp = cur; cur = nxt; nxt = tmp;
-                if (!any) break;
+            }
+            __syncthreads();
+            for (;;) {
+                const int nc = fr_n[0];
+                if (nc == 0) break;
+                ++round;
+                // the new ranks, from the state before the round
+                for (int k = t; k < nc; k += DB_NT) {
+                    const int q = lc[k];
+                    const int qy = q / w, qx = q - qy * w;
+                    int best = INT_MAX;
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dy && !dx) continue;
+                            const int yy = qy + dy, xx = qx + dx;
+                            if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                            const int o = yy * w + xx;
+                            if (stamp[o] >= 0 && stamp[o] < round && cur[o] < best) best = cur[o];
+                        }
+                    nr[k] = best;
+                }
+                __syncthreads();
+                for (int k = t; k < nc; k += DB_NT) {
+                    const int q = lc[k];
+                    cur[q] = nr[k];
+                    stamp[q] = round;
+                }
+                if (t == 0) fr_n[1] = 0;
+                __syncthreads();
+                // the next round's candidates: unassigned neighbours in the level set
+                for (int k = t; k < nc; k += DB_NT) {
+                    const int q = lc[k];
+                    const int qy = q / w, qx = q - qy * w;
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dy && !dx) continue;
+                            const int yy = qy + dy, xx = qx + dx;
+                            if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                            const int o = yy * w + xx;
+                            if (stamp[o] == -1 && eligible(o) && atomicCAS(stamp + o, -1, -2) == -1)
+                                ln[atomicAdd(&fr_n[1], 1)] = o;
+                        }
+                }
+                __syncthreads();
+                int* tmp = lc; lc = ln; ln = tmp;
+                if (t == 0) fr_n[0] = fr_n[1];
+                __syncthreads();
             }
         }
         // ---- labels: 1 + the minimum linear index of each object
