@@ -83,7 +83,7 @@ constexpr int ST_CPL = 4;
 // most foreground pixels of a tile that the labelling kernel's common form
 // takes; a census of the listed tiles sends the ones above it to the
 // crowded form
-constexpr int LT_FG = 512;
+constexpr int LT_FG = 384;
 constexpr int ST_STRIP = 32 * ST_CPL;
 
 // default bound on the steps of a global union-find walk (a cycle would be a

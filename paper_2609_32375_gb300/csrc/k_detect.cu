@@ -378,7 +378,7 @@ __device__ __forceinline__ bool pix_sat(const DetectArgs& A, bool async, uint32_
 }
 
 template <bool LABEL_ONLY, bool BATCH, bool BIG>
-__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 10) k_label_tiles(const DetectArgs* __restrict__ batch,
+__global__ void __launch_bounds__(32 * LabelCfg<BIG>::NW, BIG ? 4 : 11) k_label_tiles(const DetectArgs* __restrict__ batch,
                                                                         const __grid_constant__ DetectArgs one,
                                                                         int late)
 {
@@ -1189,10 +1189,10 @@ static int stride_grid(int per_frame, int nframes)
     return g < 16 ? 16 : g;
 }
 
-// the labelling kernel's persistent grids: the common form at ten CTAs of two
-// warps per SM (two warps per CTA let ten CTAs' shared memory fit, against
-// four of four warps), the big form (crowded tiles) at four CTAs of two warps
-constexpr int LT_CTAS = 152 * 10;
+// the labelling kernel's persistent grids: the common form at eleven CTAs of
+// two warps per SM (21 KB of shared memory and at most 88 registers each),
+// the big form (crowded tiles) at four CTAs of two warps
+constexpr int LT_CTAS = 152 * 11;
 constexpr int LT_BIG_CTAS = 152 * 4;
 constexpr int LT_LATE_CTAS = 152;         // the deferred tiles: few or none
 
@@ -1232,8 +1232,8 @@ static void launch_label(const DetectArgs& one, const DetectArgs* batch, dim3 g,
     const size_t smem = sizeof(LabelSmem<BIG>) * LabelCfg<BIG>::NW;
     auto* fn = k_label_tiles<LO, BATCH, BIG>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // all of the unified L1 / shared memory as shared memory: ten CTAs of the
-    // common form (22 KB each) per SM
+    // all of the unified L1 / shared memory as shared memory: eleven CTAs of
+    // the common form (21 KB each) per SM
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     launch_dep(fn, g, dim3(32 * LabelCfg<BIG>::NW), smem, st, batch, one, late);
 }
