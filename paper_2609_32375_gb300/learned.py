@@ -28,6 +28,7 @@ ARCH = (5, 32, 48, 48, 32, 32, 2)
 CIP = (16, 32, 48, 48, 32, 32)      # padded input channels per layer
 COP = (32, 48, 48, 32, 32, 16)      # padded output channels per layer
 NSLOT = 64                          # weight-gradient partial slots
+_STATE_LISTS = ("W", "b", "mW", "vW", "mb", "vb")   # per-layer tensors of the training state
 
 
 def _s(stream=None):
@@ -75,12 +76,18 @@ class Network:
         return w
 
     def state_dict(self):
-        return {"W": [w.cpu() for w in self.W], "b": [b.cpu() for b in self.b], "step": self.step}
+        """Master weights, biases, AdamW moments and the step count (CPU copies)."""
+        d = {k: [t.cpu() for t in getattr(self, k)] for k in _STATE_LISTS}
+        d["step"] = self.step
+        return d
 
     def load_state_dict(self, d):
-        for l in range(6):
-            self.W[l].copy_(d["W"][l])
-            self.b[l].copy_(d["b"][l])
+        """Restores what state_dict() gave; a dict with weights only (a
+        trained-weights file) leaves the AdamW moments at zero."""
+        for k in _STATE_LISTS:
+            if k in d:
+                for dst, src in zip(getattr(self, k), d[k]):
+                    dst.copy_(src)
         self.step = d.get("step", 0)
         self.pack()
 
@@ -328,13 +335,29 @@ def build_dataset(ctx, n, seed0, size=4096, mesh=64, stream=None, stars=(500, 20
             "true_bkg": torch.stack(tb), "true_rms": torch.stack(tr)}
 
 
-def train(net: Network, data, epochs=60, batch=32, lr=2e-3, seed=0, log=None):
-    """Minibatch AdamW on the dataset; returns the per-epoch mean losses."""
+def train(net: Network, data, epochs=60, batch=32, lr=2e-3, seed=0, log=None, checkpoint=None):
+    """Minibatch AdamW on the dataset; returns the per-epoch mean losses.
+
+    With `checkpoint` (a file path), the whole training state -- weights,
+    AdamW moments, step count, finished epochs and their losses -- is written
+    there after every epoch, and a run that finds the file resumes after its
+    last finished epoch: the permutations of the finished epochs are drawn
+    again and discarded, and the learning-rate schedule is a function of the
+    epoch, so the resumed run continues exactly as the uninterrupted one."""
     import torch
     n = data["feat"].shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
-    for ep in range(epochs):
+    start = 0
+    if checkpoint and os.path.exists(checkpoint):
+        rec = load_checkpoint(net, checkpoint)
+        if (rec["epochs"], rec["batch"], rec["seed"], rec["n"]) != (epochs, batch, seed, n):
+            raise ValueError(f"checkpoint {checkpoint} is for another schedule: {rec}")
+        hist = list(rec["losses"])
+        start = len(hist)
+        for _ in range(start):
+            torch.randperm(n, generator=g)
+    for ep in range(start, epochs):
         perm = torch.randperm(n, generator=g).to(data["feat"].device)
         losses = []
         lr_e = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))
@@ -345,7 +368,34 @@ def train(net: Network, data, epochs=60, batch=32, lr=2e-3, seed=0, log=None):
         hist.append(float(torch.stack(losses).mean()))
         if log:
             log(f"epoch {ep} loss {hist[-1]:.5f}")
+        if checkpoint:
+            save_checkpoint(net, checkpoint, {"epochs": epochs, "batch": batch, "seed": seed, "n": n,
+                                              "losses": hist})
     return hist
+
+
+def save_checkpoint(net, path: str, rec: dict):
+    """The training state of `net` and the schedule record `rec` (epochs,
+    batch, seed, n, losses so far) in one .npz, replaced atomically."""
+    arrays = {f"{k}{l}": t.cpu().numpy() for k in _STATE_LISTS for l, t in enumerate(getattr(net, k))}
+    arrays["step"] = np.array(net.step, dtype=np.int64)
+    arrays["record"] = np.frombuffer(repr(rec).encode(), dtype=np.uint8)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, **arrays)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(net, path: str) -> dict:
+    """Restores a save_checkpoint() file into `net`; returns its record."""
+    import ast
+
+    import torch
+    z = np.load(path)
+    nl = len(net.W)
+    d = {k: [torch.from_numpy(z[f"{k}{l}"]) for l in range(nl)] for k in _STATE_LISTS}
+    d["step"] = int(z["step"])
+    net.load_state_dict(d)
+    return ast.literal_eval(bytes(z["record"]).decode())
 
 
 def evaluate(net: Network, data):
@@ -443,6 +493,8 @@ def main(argv=None):
     ap.add_argument("--u16", action="store_true",
                     help="round the frames to uint16 (always for meshes above 128, which the float path does not take)")
     ap.add_argument("--out", default=None, help="write the trained weights (.npz)")
+    ap.add_argument("--checkpoint", default=None,
+                    help="training-state file, written after every epoch; an existing one is resumed")
     a = ap.parse_args(argv)
     u16 = a.u16 or a.mesh > 128
     stars = (500, 20000) if a.stars_per_mp is None else tuple(v * a.size * a.size / 1e6 for v in a.stars_per_mp)
@@ -453,7 +505,7 @@ def main(argv=None):
     t_data = time.time() - t0
     net = Network(seed=0)
     t0 = time.time()
-    hist = train(net, train_set, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    hist = train(net, train_set, epochs=a.epochs, batch=a.batch, lr=a.lr, checkpoint=a.checkpoint)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     ev = evaluate(net, held)
