@@ -236,6 +236,57 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------- smaller frames ---
+def sizes_section(ctx, t_img, cfg, gp, stream, dev, steps, warmup, peak):
+    """The same step, device-resident, on crops of the frame at the paper's
+    smaller sizes (2048^2 = 4.2 MP, 4096^2 = 16.8 MP, 8192^2 = 67.1 MP, the
+    serving classes): Mpix/s and the path's fraction of the copy bandwidth.
+    These frames fit (or nearly fit) in L2, so a 256 MB write flushes it
+    between steps, and each step is timed by its own event pair."""
+    import torch
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    bpp = t_img.element_size()
+    out = {}
+    for sz in SERVE_SIZES:
+        if sz is None:
+            continue
+        w, h = sz
+        crop = t_img[:h, :w].contiguous()
+        ccfg = synth_scaled(cfg, w, h)
+        cap = max(8192, (w * h) // 512)
+        ex = gp.Extractor(ctx, (h, w), crop.dtype, cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii,
+                          cfg.gain, cap, saturation=cfg.saturation, device=dev)
+        for _ in range(max(3, warmup)):
+            ex.run(crop)
+        ctx.sync()
+        n, cat = ex.catalog_host()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            ex.run(crop)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        mean_ms = sum(ms) / len(ms)
+        pb = w * h * (2 * bpp + 4) + (algorithmic_bytes("measure", ccfg, cat) or 0)
+        out[f"{w * h / 1e6:.1f}MP"] = {
+            "width": w, "height": h, "segments": n, "value": round(w * h / 1e6 / (mean_ms / 1e3), 2), "unit": UNIT,
+            "ms_per_step": round(mean_ms, 4), "p50_ms": round(ms[len(ms) // 2], 4),
+            "path_algorithmic_bytes": pb, "path_frac": round(pb / (mean_ms / 1e3) / 1e9 / peak, 4)}
+        del ex
+    out["note"] = ("crops of the dense frame, L2 flushed by a 256 MB write before every step, "
+                   "per-step CUDA events; path bytes = 2 frame reads + uint32 map + aperture footprints")
+    return out
+
+
+def synth_scaled(cfg, w, h):
+    import synth
+    return synth.scaled_config(cfg, w, h)
+
+
 # ---------------------------------------------------------- growth curves ---
 def growth_section(ctx, ex, t_img, cfg, nsrc, stream, dev, steps, peak):
     """gp_growth at every catalog centroid with the paper's integer radii,
@@ -667,6 +718,9 @@ def run_gpu(args):
                                "path": "one stream: H2D, gp_extract, D2H of the filled rows, CUDA events"},
             "gpu_launches": stats["launches"] * args.steps,
             "clocks": clk}
+    # ---- the same step on the smaller frame sizes of the paper's range
+    if not args.no_sizes:
+        line["sizes"] = sizes_section(ctx, t_img, cfg, gp, stream, dev, args.steps, args.warmup, peak)
     # ---- the learned-background form on the same frame (when weights trained
     # at this mesh size are committed)
     from paper_2609_32375_gb300 import learned as L
@@ -749,6 +803,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-background form")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server stream")
     ap.add_argument("--no-growth", action="store_true", help="skip the growth-curve measurement")
+    ap.add_argument("--no-sizes", action="store_true", help="skip the 4.2-67.1 MP frame sizes")
     ap.add_argument("--size", default=None,
                     help="WxH: run the workload's recipe on a frame of this size (profiling cases)")
     args = ap.parse_args()
