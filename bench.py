@@ -282,6 +282,56 @@ def sizes_section(ctx, t_img, cfg, gp, stream, dev, steps, warmup, peak):
     return out
 
 
+def batching_section(ctx, t_img, cfg, gp, stream, dev, steps, warmup, nb=8, side=2048):
+    """nb frames of side^2 px (crops of the frame at distinct offsets) extracted
+    one call per frame, and in one gp_extract_batch call (every stage one
+    launch over all frames, grid y = frame): the fixed per-frame cost that
+    batching removes.  L2 flushed by a 256 MB write before every step."""
+    import torch
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    H, W = t_img.shape
+    offs = [((i * 3 * side) % (W - side), ((i * 5 * side) // 2) % (H - side)) for i in range(nb)]
+    crops = [t_img[y:y + side, x:x + side].contiguous() for x, y in offs]
+    cap = max(8192, side * side // 512)
+    args = (cfg.mesh, cfg.kernel, cfg.thresh, cfg.minarea, cfg.radii, cfg.gain, cap)
+    one = gp.Extractor(ctx, (side, side), t_img.dtype, *args, saturation=cfg.saturation, device=dev)
+    bat = gp.BatchExtractor(ctx, [(side, side)] * nb, t_img.dtype, *args, saturation=cfg.saturation, device=dev)
+
+    def single(counts=None):
+        for c in crops:
+            one.run(c)
+            if counts is not None:
+                counts.append(int(one.out["catalog"]["n"].item()))
+
+    def batched(counts=None):
+        outs = bat.run(crops)
+        if counts is not None:
+            counts.extend(int(o["catalog"]["n"].item()) for o in outs)
+
+    res = {}
+    for name, fn in (("single_calls", single), ("one_batched_call", batched)):
+        for _ in range(max(3, warmup)):
+            fn()
+        ctx.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        counts = []
+        fn(counts)
+        res[name] = {"ms_per_step": round(ms, 4), "ms_per_frame": round(ms / nb, 4),
+                     "value": round(nb * side * side / 1e6 / (ms / 1e3), 2), "unit": UNIT, "segments": counts}
+    res["same_segment_counts"] = res["single_calls"]["segments"] == res["one_batched_call"]["segments"]
+    res["frames"] = f"{nb} crops of {side}x{side} px at distinct offsets"
+    return res
+
+
 def synth_scaled(cfg, w, h):
     import synth
     return synth.scaled_config(cfg, w, h)
@@ -721,6 +771,7 @@ def run_gpu(args):
     # ---- the same step on the smaller frame sizes of the paper's range
     if not args.no_sizes:
         line["sizes"] = sizes_section(ctx, t_img, cfg, gp, stream, dev, args.steps, args.warmup, peak)
+        line["batching"] = batching_section(ctx, t_img, cfg, gp, stream, dev, args.steps, args.warmup)
     # ---- the learned-background form on the same frame (when weights trained
     # at this mesh size are committed)
     from paper_2609_32375_gb300 import learned as L
@@ -803,7 +854,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-background form")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server stream")
     ap.add_argument("--no-growth", action="store_true", help="skip the growth-curve measurement")
-    ap.add_argument("--no-sizes", action="store_true", help="skip the 4.2-67.1 MP frame sizes")
+    ap.add_argument("--no-sizes", action="store_true", help="skip the 4.2-67.1 MP frame sizes and the batched small frames")
     ap.add_argument("--size", default=None,
                     help="WxH: run the workload's recipe on a frame of this size (profiling cases)")
     args = ap.parse_args()
