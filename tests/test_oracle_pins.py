@@ -938,3 +938,64 @@ def test_deblend_leaves_isolated_segments_alone():
     L = seg[15, 15]
     assert np.array_equal(out[seg == L], seg[seg == L])
     assert nsplit == 1
+
+
+def _moffat(H, W, stars, fwhm=3.0, beta=2.5):
+    """Moffat stars (x0, y0, total flux) sampled at pixel centres."""
+    alpha = fwhm / (2.0 * np.sqrt(2.0 ** (1.0 / beta) - 1.0))
+    yy, xx = np.mgrid[0:H, 0:W]
+    m = np.zeros((H, W))
+    for x0, y0, f in stars:
+        r2 = (xx - x0) ** 2 + (yy - y0) ** 2
+        m += f * (beta - 1.0) / (np.pi * alpha * alpha) * (1.0 + r2 / (alpha * alpha)) ** (-beta)
+    return m
+
+
+def _bridged_pair(H=48, W=72):
+    """Two well-separated Moffat stars (32 px apart, far below threshold
+    between them) joined by a faint one-pixel bridge of 3 (threshold 1.5)."""
+    m = _moffat(H, W, [(20, 24, 5000.0), (52, 24, 4000.0)])
+    m[24, 20:53] = np.maximum(m[24, 20:53], 3.0)
+    return m
+
+
+def test_deblend_splits_moffats_joined_by_a_faint_bridge():
+    m = _bridged_pair()
+    seg, out, nsplit = _deblend_map(m)
+    assert len(np.unique(seg[seg > 0])) == 1            # one segment through the bridge
+    assert nsplit == 1
+    assert len(np.unique(out[out > 0])) == 2
+    assert out[24, 20] != out[24, 52]
+    _objects_are_connected_partitions(seg, out)
+    # the bridge goes to the nearer star on either side of the midpoint
+    assert out[24, 30] == out[24, 20] and out[24, 44] == out[24, 52]
+
+
+def test_deblend_keeps_a_single_moffat_with_a_faint_tail():
+    m = _moffat(48, 72, [(20, 24, 5000.0)])
+    m[24, 20:53] = np.maximum(m[24, 20:53], 3.0)         # the same bridge, no star at its far end
+    seg, out, nsplit = _deblend_map(m)
+    assert nsplit == 0 and np.array_equal(out, seg)
+
+
+def test_deblend_is_invariant_to_flux_scaling():
+    """Scaling m, nu and the threshold by one factor leaves every level set
+    (t_i / thresh depends on nu_max / thresh only) and every contrast ratio
+    unchanged.  By a power of two the arithmetic is exact, so the maps must be
+    identical.  The frames sweep a companion's distance and brightness, so
+    that for some of them whether a level falls between the saddle and the
+    companion's peak decides the split: a ladder that is not anchored at the
+    threshold (t_i = thresh * nu_max^(i/N), say) moves with the scale there
+    and changes 13 of the sweep's 44 scaled maps."""
+    m = _bridged_pair() + _moffat(48, 72, [(36, 8, 800.0)])
+    frames = [m] + [_blend([(26, 24, 150.0), (26 + d, 24.5, a2)])
+                    for d in np.arange(4.0, 9.01, 0.5) for a2 in (60.0, 120.0)]
+    nsplit = 0
+    for f in frames:
+        _, ref, nref = _deblend_map(f, thresh=1.5)
+        nsplit += nref
+        for c in (4.0, 0.25):
+            _, out, n = _deblend_map(c * f, thresh=1.5 * c)
+            assert n == nref
+            assert np.array_equal(out, ref), c
+    assert 0 < nsplit < len(frames)         # the sweep crosses the split boundary
