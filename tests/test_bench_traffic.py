@@ -43,3 +43,25 @@ def test_traffic_turns_null_when_a_source_changes(tmp_path):
     assert b.kernel_traffic("k_y", "w") is None
     src.write_text("__global__ void k_x() { /* changed */ }\n")
     assert b.kernel_traffic("k_x", "w") is None
+
+
+def test_algorithmic_bytes_follow_the_stated_units():
+    """The roofline numerators: the streaming pass reads the frame once and
+    writes the uint32 map and the 1-bit mask; the box statistics read the
+    frame once; the measurement reads each segment's box (pixel and map) and
+    each source's aperture window of side 2 r_max + 3."""
+    import numpy as np
+    import synth
+    b = load_bench(ROOT)
+    cfg = synth.CONFIGS["dense_12288x12304_u16"]
+    npix = 12288 * 12304
+    assert b.algorithmic_bytes("threshold", cfg, None) == npix * 6 + npix // 8 == 926_048_256
+    assert b.algorithmic_bytes("box_stats", cfg, None) == npix * 2
+    cat = {"xmin": np.array([10, 0]), "xmax": np.array([12, 4]), "ymin": np.array([5, 7]), "ymax": np.array([8, 7]),
+           "npix": np.array([9, 5])}
+    side = int(2 * max(cfg.radii) + 3)
+    assert b.algorithmic_bytes("measure", cfg, cat) == (3 * 4 + 5 * 1) * (4 + 2) + 2 * side * side * 2
+    assert b.algorithmic_bytes("label_tiles", cfg, cat) == (9 + 5) * 8
+    f32 = synth.CONFIGS["plain_1024x1024_f32"]
+    assert b.algorithmic_bytes("threshold", f32, None) == 1024 * 1024 * 8 + 1024 * 1024 // 8
+    assert b.algorithmic_bytes("mesh_spline", cfg, None) is None
