@@ -6,6 +6,12 @@ tests/, the smoke check and bench.py's CPU-baseline leg import this package;
 the CUDA library never does, and the two share no code.  The loops live in
 oracle.c (compiled with gcc, no fast-math, no FMA contraction); the
 element-wise glue between steps is plain numpy.
+
+Parity unpinned (readings of the paper that no printed value fixes; their
+arithmetic is pinned, the choice is not): the box mode rule [R4, oracle.c],
+the significance nu of a source as F / sigma at its catalog peak [R24], and
+the attribution of a split segment's pixels outside the seeds by growth
+within the level sets [R37].
 """
 from __future__ import annotations
 

@@ -15,7 +15,9 @@
  *   [R3]  iterative k-sigma clip about the median, population std, stop when
  *         the kept set is unchanged or after maxiter passes
  *   [R4]  box background = median if sigma==0 or |mean-median|/sigma > 0.3,
- *         else 2.5 median - 1.5 mean; box rms = sigma
+ *         else 2.5 median - 1.5 mean; box rms = sigma.  Parity unpinned: the
+ *         mode rule is a reading (the SExtractor estimate); its branch choice
+ *         and the symmetric case are pinned, its skewed-branch value is not
  *   [R5]  boxes with < 50 % good pixels are filled from valid neighbours
  *   [R6]  fsize x fsize median filter of each mesh, window clipped to mesh
  *   [R7]  tensor-product natural cubic spline through the box centres,
