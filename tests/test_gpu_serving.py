@@ -290,6 +290,9 @@ def test_requests_arriving_while_others_run():
         ctx1.close()
     s = server(hbm_budget=8 << 30, slots=3)
     try:
+        # the late frames are page-locked beforehand, so their submits take
+        # microseconds and land while the first wave is on the GPU
+        small_host = [pinned(i) for i in small]
         wave1 = [s.submit(pinned(i), CAP, want_segmap=True) for i in big]
         # wait until the server has admitted work that has not finished
         t0 = time.time()
@@ -303,7 +306,7 @@ def test_requests_arriving_while_others_run():
 
         def late():
             seen["before"] = s.stats()
-            seen["tickets"] = [s.submit(pinned(i), CAP, want_segmap=True) for i in small]
+            seen["tickets"] = [s.submit(h, CAP, want_segmap=True) for h in small_host]
             seen["after"] = s.stats()
 
         th = threading.Thread(target=late)
